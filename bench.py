@@ -1,0 +1,361 @@
+#!/usr/bin/env python3
+"""NEP benchmark on one GB300 (or N replicas under torchrun).
+
+Workload: the 900,000-atom MD run -- 50^3 rock-salt cells (a = 6 A, box
+300 A), Te on anions, cations 40% Ge / 40% Sb / 20% vacant, jitter 0.1 A;
+NEP n_R=8, n_A=6, K=8/8, l_max=4 + 4-body (D=38), MLP 38-30-1 with random
+weights; velocity Verlet, dt = 2 fs, 900 K Maxwell-Boltzmann start, cell-list
+rebuild every 10 steps with a 1 A skin.  One bench step = one MD step
+(kick, drift, [rebuild], energy+forces+virial, kick), all in libnep kernels.
+
+value: atom-steps/s over all ranks (device-timed, inputs resident in HBM).
+e2e:   the same metric through the C ABI from pinned host buffers: positions
+       copied in, E/F/V copied out every step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "NEP atom-steps/s (E+F+virial), train configs/s vs plain FP32 at stated force err"
+WORKLOAD = ("md900k: 900,000-atom rock-salt Ge-Sb-Te (50^3 cells, a=6 A, 20% cation vacancies), "
+            "NEP n_R=8 n_A=6 K=8/8 l_max=4 +4-body (D=38), MLP 38-30-1 tanh, FP32, velocity Verlet "
+            "dt=2 fs, 900 K, cell-list rebuild every 10 steps, skin 1 A")
+CAP, CAP_ANG, SKIN, DT, REBUILD = 112, 48, 1.0, 2.0, 10
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=100)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        reasons = set()
+        for r in rows:
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"), r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        loaded = sorted(sm)[len(sm) // 4:] if sm else []
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "power_w_max": max(pw) if pw else None,
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------- flop counting
+def algorithmic_flops(h, nbar_rad: float, nbar_ang: float) -> dict:
+    """FP32 flops per atom of each kernel (FMA = 2, other FP op = 1, SFU = 1),
+    for neighbours inside the cutoffs; the operation counts of the kernels'
+    formulation (species-resolved radial sums, S_nlm, owner pair forces)."""
+    NR, NA, KR, KA, H, T = h.n_rad, h.n_ang, h.k_rad, h.k_ang, h.n_hidden, h.n_types
+    D = NR + NA * 4 + (NA if h.has_4body else 0)
+    basis = lambda K: 8 + 5 * (K - 1)             # cos, x, Chebyshev recursion, (T+1) fc/2
+    basis_d = lambda K: 20 + 13 * (K - 2)          # with derivatives
+    rad_desc = 21 + basis(KR) + 2 * T * KR
+    ang_desc = 10 + basis(KA) + 2 * NA * KA + 45 + 2 * NA * 24
+    atom_desc = 2 * NR * T * KR + 3 * NA * 24 + 40 * NA + H * (4 * D + 6) + 2 * T * KR * NR
+    rad_force = 22 + basis_d(KR) + 4 * KR + 34
+    ang_force = 10 + basis_d(KA) + 4 * NA * KA + 45 + 4 * NA * 24 + 4 * 24 + 150 + 30
+    atom_force = 3 * NA * 24 + 60 * NA
+    return {"desc": nbar_rad * rad_desc + nbar_ang * ang_desc + atom_desc,
+            "force": nbar_rad * rad_force + nbar_ang * ang_force + atom_force}
+
+
+def launches_per_step(rebuild: bool) -> int:
+    # kick, [pack, wrap, cell plan, plan scan, bin, 3 scan, fill, sort, build, rev],
+    # pack, chunk plan, descriptor, force, gather, final reduce, kick
+    return 8 + (12 if rebuild else 0)
+
+
+# --------------------------------------------------------------- cpu legs
+CPU_SNIPPET = r"""
+import json, sys, time, os
+sys.path.insert(0, {root!r})
+import numpy as np
+from paper_2607_06969_gb300 import inputs as I
+from oracle import nep_oracle as O
+ncell, nsteps = {ncell}, {nsteps}
+s = I.rocksalt(ncell, vacancy=0.2, tag=1)
+h = I.HYPER_SMALL
+th = I.init_params(h).astype(np.float32).astype(np.float64)
+p = s.pos32()
+t0 = time.perf_counter()
+pairs = None
+for k in range(nsteps):
+    if k % {rebuild} == 0:
+        pairs = O.neighbor_pairs(p, s.box, s.atom_off, h.rc_rad + {skin})
+    O.energy_forces_virial(h, th, p.astype(np.float64), s.types, s.box, s.atom_off, pairs)
+dt = time.perf_counter() - t0
+print(json.dumps(dict(atoms=s.n_atoms, steps=nsteps, seconds=dt)))
+"""
+
+
+def run_oracle_sample(ncell: int, nsteps: int) -> dict:
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = CPU_SNIPPET.format(root=ROOT, ncell=ncell, nsteps=nsteps, rebuild=REBUILD, skin=SKIN)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline() -> dict:
+    d = run_oracle_sample(5, 10)
+    v = d["atoms"] * d["steps"] / d["seconds"]
+    return {"value": v, "unit": "atom-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"FP64 numpy oracle, one thread: 10 MD-step force evaluations (list rebuilt "
+                      f"once) of a {d['atoms']}-atom 5^3-cell periodic sample of the same rock-salt "
+                      f"structure and model, {d['seconds']:.1f} s"}
+
+
+def reference_arm(args, rank: int) -> None:
+    if rank != 0:
+        return
+    # each step: one E+F+V of a 3^3-cell (194-atom) periodic sample, list every 10 steps
+    run_oracle_sample(3, max(3, args.warmup))
+    d = run_oracle_sample(3, args.steps)
+    v = d["atoms"] * d["steps"] / d["seconds"]
+    line = {"metric": METRIC, "value": v, "unit": "atom-steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * d["seconds"] / d["steps"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample": "3^3-cell periodic sample per step"},
+            "cpu_baseline": {"value": v, "unit": "atom-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{d['atoms']}-atom 3^3-cell periodic sample, one E+F+V per step"},
+            "e2e": {"value": v, "unit": "atom-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank)
+        return
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    from paper_2607_06969_gb300 import binding as nb
+    from paper_2607_06969_gb300 import inputs as I
+
+    s, h = I.workload_md900k()
+    N = s.n_atoms
+    theta = I.init_params(h).astype(np.float32)
+    vel0 = I.maxwell_boltzmann(s.types, 900.0).astype(np.float32)
+    masses = I.MASSES.astype(np.float32)
+
+    model = nb.Model(h, theta)
+    dsys = nb.DeviceSystem.from_inputs(s)
+    pos_host0 = np.ascontiguousarray(s.pos32().T)
+    cap, cap_ang = CAP, CAP_ANG
+    for _ in range(3):   # grow the list if the build reports an overflow
+        nl = nb.NeighborList(N, cap, cap_ang, shifts=False)
+        ws = nb.Workspace(model, N, 1, cap, cap_ang)
+        nb.neighbors(model, dsys, nl, SKIN, ws)
+        st = nb.check_list(nl)
+        if st == nb.NEP_OK:
+            break
+        if st != nb.NEP_ERR_CAPACITY:
+            raise RuntimeError(nb.last_error())
+        need = nl.status.cpu().numpy()
+        cap, cap_ang = int(need[1]) + 16, int(need[2]) + 8
+        cap = max(cap, cap_ang)
+    else:
+        raise RuntimeError("neighbour list did not fit")
+    e_atom, force, e_tot, vir = nb.energy_forces_virial(model, dsys, nl, ws)
+    torch.cuda.synchronize()
+
+    # neighbour statistics inside the cutoffs (for the flop count), from the list
+    with torch.no_grad():
+        cnt = nl.cnt.long()
+        nbr = nl.nbr.view(cap, N).long()
+        valid = torch.arange(cap, device="cuda")[:, None] < cnt[None, :]
+        L = float(s.box[0, 0])
+        nrad = nang = 0.0
+        for a in range(0, N, 100000):
+            sl = slice(a, min(N, a + 100000))
+            d2 = torch.zeros_like(nbr[:, sl], dtype=torch.float32)
+            for c in range(3):
+                d = dsys.pos[c][nbr[:, sl]] - dsys.pos[c][sl][None, :]
+                d = d - L * torch.round(d / L)
+                d2 += d * d
+            v = valid[:, sl]
+            nrad += float(((d2 < h.rc_rad ** 2) & v).sum())
+            nang += float(((d2 < h.rc_ang ** 2) & v).sum())
+        nbar_rad, nbar_ang = nrad / N, nang / N
+        del nbr, valid
+
+    vel = torch.from_numpy(np.ascontiguousarray(vel0.T)).cuda()
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+
+    def md(k, s_):
+        nb.md_step(model, dsys, nl, vel, force, e_tot, vir, masses, DT, SKIN, k % REBUILD == 0, ws, stream=s_)
+
+    # warm-up steps (eager)
+    with torch.cuda.stream(stream):
+        for k in range(args.warmup):
+            md(k, stream)
+    stream.synchronize()
+    if nb.check_list(nl, stream) != nb.NEP_OK:
+        raise RuntimeError("list overflow during warm-up: " + nb.last_error())
+
+    # capture the K timed steps, with events around the two pair kernels of every step
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        for k in range(K):
+            nb.set_timing_events(model, evs[k])
+            md(k, stream)
+    # first replay uploads the graph (untimed), second is timed
+    g.replay()
+    torch.cuda.synchronize()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    with torch.cuda.stream(stream):
+        start.record(stream)
+        g.replay()
+        stop.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = start.elapsed_time(stop)
+    if nb.check_list(nl, stream) != nb.NEP_OK:
+        raise RuntimeError("list overflow during the timed steps: " + nb.last_error())
+    t_desc = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    t_force = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+    ms_max = ms
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = world * N * K / (ms_max * 1e-3)
+
+    # roofline of the dominant kernel (FP32 CUDA-core bound)
+    fl = algorithmic_flops(h, nbar_rad, nbar_ang)
+    props = torch.cuda.get_device_properties(local)
+    sm_count = props.multi_processor_count
+    peak = sm_count * 128 * 2 * 2070e6 / 1e12
+    dom = "force" if t_force >= t_desc else "desc"
+    t_dom = t_force if dom == "force" else t_desc
+    achieved = fl[dom] * N / (t_dom * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                "flops_per_atom": fl[dom], "nbar_rad": nbar_rad, "nbar_ang": nbar_ang,
+                "kernel_ms": {"desc": t_desc, "force": t_force}}
+
+    # end to end through the C ABI from pinned host buffers
+    KE = max(1, min(args.e2e_steps, K))
+    pos_host = torch.from_numpy(pos_host0).pin_memory()
+    f_host = torch.empty(3, N, dtype=torch.float32).pin_memory()
+    e_host = torch.empty(1, dtype=torch.float64).pin_memory()
+    v_host = torch.empty(1, 9, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for k in range(KE):
+            dsys.pos.copy_(pos_host, non_blocking=True)
+            if k % REBUILD == 0:
+                nb.neighbors(model, dsys, nl, SKIN, ws, stream=stream)
+            nb.energy_forces_virial(model, dsys, nl, ws, out=(e_atom, force, e_tot, vir), stream=stream)
+            f_host.copy_(force, non_blocking=True)
+            e_host.copy_(e_tot, non_blocking=True)
+            v_host.copy_(vir, non_blocking=True)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    e2e_val = world * N * KE / (e2e_ms * 1e-3)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+
+    launches = sum(launches_per_step(k % REBUILD == 0) for k in range(K))
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "atom-steps/s", "n_gpus": world,
+                "steps": K, "warmup": args.warmup, "ms_per_step": ms_max / K,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n_atoms": N, "parallelism": f"replicas x{world}",
+                           "l2": "inputs larger than L2 (neighbour list 0.40 GB, pair scratch 1.4 GB)",
+                           "graph": "K steps captured in one CUDA graph"},
+                "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_val, "unit": "atom-steps/s", "steps": KE,
+                        "h2d_bytes_per_step": 12 * N, "d2h_bytes_per_step": 12 * N + 8 + 72},
+                "gpu_launches": launches, "clocks": clk,
+                "energy": {"e_tot_final": float(e_tot.item())}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

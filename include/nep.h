@@ -1,0 +1,222 @@
+/*
+ * nep.h -- C ABI of libnep: GB300-native (sm_103a) evaluation of the
+ * Neuroevolution Potential (NEP) per atom and its training backward.
+ *
+ * The problem statement follows AI2Pot (arXiv 2607.06969), Section 2:
+ *   positions + species + periodic cell  ->  E_i (Eqs. 1-2), forces (Eq. 3),
+ *   virial (Eq. 4), with NEP descriptors of Eqs. 11-17;
+ *   labelled configurations -> loss (Eqs. 18-21) and its parameter gradient
+ *   (the paper's training operator, Section 3.2).
+ *
+ * Conventions for every call:
+ *   - Units: eV, Angstrom, u, fs.  The virial is in eV, not divided by volume.
+ *   - Every array argument is caller-owned DEVICE memory unless its name ends
+ *     in _host.  The library never frees caller memory.
+ *   - Per-atom arrays are structure-of-arrays: a [3][N] array holds all x,
+ *     then all y, then all z.
+ *   - Hot calls (nep_neighbors, nep_energy_forces_virial, nep_param_grad*,
+ *     nep_md_step) allocate nothing and never synchronise the host; they only
+ *     enqueue kernels on `stream` (a cudaStream_t, NULL = legacy default
+ *     stream).  Scratch memory is the caller's `work` buffer, sized by
+ *     nep_workspace_bytes.
+ *   - Host-detectable argument errors return immediately with a status and a
+ *     message (nep_last_error).  Device-detected conditions (neighbour list
+ *     overflow, non-finite or out-of-box positions, species out of range) set
+ *     flag words in nep_nlist.status; nep_check synchronises and maps them.
+ *   - A model is not thread-safe; different models may be used concurrently.
+ */
+#ifndef NEP_H
+#define NEP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NEP_OK = 0,
+    NEP_ERR_ARG = 1,          /* bad argument (NULL, size, range)              */
+    NEP_ERR_CUDA = 2,         /* a CUDA runtime call failed                     */
+    NEP_ERR_NOMEM = 3,        /* device allocation failed (nep_create only)     */
+    NEP_ERR_CAPACITY = 4,     /* neighbour list capacity exceeded; see status   */
+    NEP_ERR_TIMEOUT = 5,      /* a bounded device wait gave up                  */
+    NEP_ERR_STATE = 6,        /* call made in the wrong order                   */
+    NEP_ERR_UNSUPPORTED = 7,  /* hyper-parameters with no compiled kernel       */
+    NEP_ERR_INPUT = 8         /* device found invalid input (see nep_check)     */
+} nep_status;
+
+/* NEP hyper-parameters (Section 2.3, Table 2).
+ * n_rad, n_ang : radial / angular descriptor counts, n = 0..n-1 (Eqs. 11, 16)
+ * k_rad, k_ang : Chebyshev basis functions N_basis, k = 0..k-1 (Eq. 12)
+ * l_max        : must be 4 (Section 2.3); l runs 1..l_max
+ * has_4body    : 1 adds q4_n = tr(A_n^3), A_n = sum_j g_n (rhat rhat^T - I/3)
+ * n_hidden     : hidden tanh units of the per-species network (N_neurons)
+ * rc_rad/ang   : cutoffs r_max (Eqs. 13-15), rc_ang <= rc_rad
+ * precision    : 0 = FP32 everywhere; 1 = MLP forward and dU/dq in FP16 on
+ *                tensor cores with FP32 accumulation (descriptors FP32);
+ *                2 = same with BF16.
+ * Descriptor dimension D = n_rad + n_ang*l_max + n_ang*has_4body, ordered
+ * [q_0..q_{nR-1}, q_{n,l} (n outer, l = 1..l_max inner), q4_0..q4_{nA-1}]. */
+typedef struct {
+    int n_types;
+    int n_rad, n_ang;
+    int k_rad, k_ang;
+    int l_max;
+    int has_4body;
+    int n_hidden;
+    float rc_rad, rc_ang;
+    int precision;
+} nep_hparams;
+
+typedef struct nep_model nep_model;   /* opaque, library-owned */
+
+/* Number of parameters P.  Flat order (float):
+ *   for t in types: W0[t][H][D], b0[t][H], w1[t][H], b1[t];
+ *   then cR[Zi][Zj][n_rad][k_rad]; then cA[Zi][Zj][n_ang][k_ang]
+ * (c indexed by the ordered species pair, Eqs. 11 and 16).
+ * E_i = sum_h w1[Zi][h] tanh(sum_d W0[Zi][h][d] q_d + b0[Zi][h]) + b1[Zi].
+ * Returns 0 for invalid hyper-parameters. */
+size_t nep_num_params(const nep_hparams* hp);
+
+/* Create a model from hyper-parameters and HOST parameters (P floats).
+ * Allocates the model's device copy on the current device.  Returns
+ * NEP_ERR_UNSUPPORTED when no kernel is compiled for hp (see
+ * nep_supported). */
+nep_status nep_create(const nep_hparams* hp, const float* params_host, size_t n_params,
+                      nep_model** out);
+nep_status nep_destroy(nep_model* m);
+/* 1 if kernels for these hyper-parameters are compiled in, else 0. */
+int nep_supported(const nep_hparams* hp);
+
+/* Replace the parameters from a DEVICE buffer of P floats, stream-ordered
+ * (for optimiser steps that stay on the device). */
+nep_status nep_set_params(nep_model* m, const float* params_dev, void* stream);
+
+/* A batch of B periodic orthorhombic configurations with atoms concatenated.
+ * pos    [3][N] float, each atom of config b inside [0, box[b][a]) for
+ *        nep_neighbors (nep_energy_forces_virial accepts atoms that drifted
+ *        after the list was built: pair vectors use the image stored in the
+ *        list, or the minimum image when the list was built without shifts)
+ * type   [N] int in [0, n_types)
+ * atom_off [B+1] int CSR offsets (atom_off[0] = 0, atom_off[B] = N)
+ * box    [B][3] float edge lengths
+ * atom_off_host, box_host: host copies of the same values (used to plan
+ * launches without a device round trip). */
+typedef struct {
+    int n_atoms;
+    int n_cfg;
+    const float* pos;
+    const int* type;
+    const int* atom_off;
+    const float* box;
+    const int* atom_off_host;
+    const float* box_host;
+} nep_system;
+
+/* Verlet neighbour list, caller-owned.  For each atom i the radial list holds
+ * every (j, image s) != (i, 0) with |r_j + s*L - r_i| < rc_rad + skin, decided
+ * by the FP32 predicate dx = (x_j - x_i) + s_x L_x (and y, z),
+ * d2 = (dx*dx + dy*dy) + dz*dz, d2 < fl32(rc*rc) (the sum over j of Eq. 3).
+ * Its first cnt_ang[i] entries are exactly those with d < rc_ang + skin.
+ *   nbr   [cap][N] int   slot-major: nbr[s*N + i] = j
+ *   shift [cap][N] int   packed image (int8 sx | sy << 8 | sz << 16); may be
+ *                        NULL when every box edge >= 2*(rc_rad+skin)+1e-3,
+ *                        in which case the minimum image is used
+ *   rev   [cap_ang][N]   slot of i in j's angular prefix, for pair (i, s)
+ *   cnt, cnt_ang [N]
+ *   status [4] int: [0] overflow flag, [1] radial count needed,
+ *                   [2] angular count needed, [3] invalid-input flag
+ * nep_neighbors fills every array and the host fields skin and min_image.
+ * If a count exceeds cap (cap_ang) the list is truncated, status[0] is set
+ * and status[1..2] hold the capacity needed; nep_check returns
+ * NEP_ERR_CAPACITY and the caller resizes and rebuilds. */
+typedef struct {
+    int cap, cap_ang;
+    int* cnt;
+    int* cnt_ang;
+    int* nbr;
+    int* shift;
+    int* rev;
+    int* status;
+    float skin;     /* written by nep_neighbors */
+    int min_image;  /* written by nep_neighbors */
+} nep_nlist;
+
+/* Scratch bytes needed by the hot calls for a system of N atoms, B configs,
+ * and a list with capacities cap/cap_ang.  One buffer of this size serves
+ * every hot call of the model. */
+size_t nep_workspace_bytes(const nep_model* m, int n_atoms, int n_cfg, int cap, int cap_ang);
+
+/* Build the cell-list Verlet list (counting sort into cells of edge
+ * >= rc + skin, 27-cell or wider image stencil, then a reverse index).
+ * Deterministic: list order is fixed by cell order and atom index. */
+nep_status nep_neighbors(nep_model* m, const nep_system* sys, float skin, nep_nlist* nl,
+                         void* work, size_t work_bytes, void* stream);
+
+/* Energies, forces and virial (Eqs. 1-4, 11-17).
+ * e_atom [N] float (may be NULL), force [3][N] float,
+ * e_tot [B] double, virial [B][9] double (row-major V_ab, Eq. 4).
+ * Sums over atoms are FP64 in a fixed order: results are bitwise
+ * reproducible run to run. */
+nep_status nep_energy_forces_virial(nep_model* m, const nep_system* sys, const nep_nlist* nl,
+                                    float* e_atom, float* force, double* e_tot, double* virial,
+                                    void* work, size_t work_bytes, void* stream);
+
+/* Loss and its gradient with respect to all P parameters (Eqs. 18-21).
+ * e_lbl [B] double, f_lbl [3][N] float, v_lbl [B][9] double,
+ * w_host[3] = (wE, wF, wV).
+ * loss_mode 0: L = 1/B sum_b [wE (dE_b/N_b)^2 + wF/(3N_b) sum_i |dF_i|^2
+ *                             + wV/9 sum_ab (dV_b,ab/N_b)^2]
+ * loss_mode 1: Eqs. 19-21 per configuration, averaged over the batch:
+ *              1/B sum_b [wE dE_b^2/N_b + wF/(3N_b) sum |dF|^2 + wV/(9N_b) sum dV^2]
+ * grad [P] float (overwritten), loss [1] double (may be NULL).
+ * Per-pair derivatives are recomputed; nothing is cached across calls. */
+nep_status nep_param_grad(nep_model* m, const nep_system* sys, const nep_nlist* nl,
+                          const double* e_lbl, const float* f_lbl, const double* v_lbl,
+                          const float* w_host, int loss_mode, float* grad, double* loss,
+                          void* work, size_t work_bytes, void* stream);
+
+/* Gradient of Phi = sum_b a_e[b] E_b + sum_i lam[:,i] . F_i + sum_b mu[b] : V_b
+ * with the adjoints held fixed (the vector-Jacobian product used by an
+ * autograd backward).  a_e [B] double, lam [3][N] float, mu [B][9] double.
+ * grad [P] float (overwritten). */
+nep_status nep_param_grad_adjoint(nep_model* m, const nep_system* sys, const nep_nlist* nl,
+                                  const double* a_e, const float* lam, const double* mu,
+                                  float* grad, void* work, size_t work_bytes, void* stream);
+
+/* One velocity-Verlet step (dt in fs, masses_host[n_types] in u):
+ *   v += dt/2 F/m; x += dt v; [wrap + rebuild list if rebuild != 0];
+ *   F = force(x); v += dt/2 F/m.
+ * pos is updated in place (sys->pos is treated as writable), vel [3][N],
+ * force [3][N] must hold the forces of the current positions on entry
+ * (call nep_energy_forces_virial once before the first step).
+ * e_tot/virial receive the new step's values. */
+nep_status nep_md_step(nep_model* m, const nep_system* sys, nep_nlist* nl, float* vel,
+                       float* force, double* e_tot, double* virial, const float* masses_host,
+                       float dt, float skin, int rebuild, void* work, size_t work_bytes,
+                       void* stream);
+
+/* Profiling hook: the next nep_energy_forces_virial / nep_md_step call of
+ * this model records events[0] before the descriptor kernel, events[1]
+ * between the descriptor and force kernels and events[2] after the force
+ * kernel, on the call's stream (events are caller-created cudaEvent_t, n = 3;
+ * n = 0 clears).  One-shot: the events are forgotten after that call.  The
+ * records are ordinary stream work and can be captured into a CUDA graph. */
+nep_status nep_set_timing_events(nep_model* m, void* const* events, int n);
+
+/* Synchronise `stream` and map the list's device flags to a status:
+ * NEP_ERR_CAPACITY (status[0]), NEP_ERR_INPUT (status[3]) or NEP_OK.
+ * nl may be NULL (then only the stream is synchronised). */
+nep_status nep_check(const nep_nlist* nl, void* stream);
+
+/* Thread-local message of the last failed call ("" if none). */
+const char* nep_last_error(void);
+
+/* Library version string. */
+const char* nep_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NEP_H */

@@ -1,0 +1,273 @@
+"""Python binding of libnep's C ABI (include/nep.h).
+
+Argument marshalling only: every step of the path runs in libnep's CUDA
+kernels.  PyTorch provides device memory and streams.  If libnep.so is
+missing, lib() raises; nothing falls back to another implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnep.so")
+
+NEP_OK, NEP_ERR_ARG, NEP_ERR_CUDA, NEP_ERR_NOMEM, NEP_ERR_CAPACITY, NEP_ERR_TIMEOUT, \
+    NEP_ERR_STATE, NEP_ERR_UNSUPPORTED, NEP_ERR_INPUT = range(9)
+
+# names of every entry point declared in include/nep.h
+ENTRY_POINTS = (
+    "nep_num_params", "nep_create", "nep_destroy", "nep_supported", "nep_set_params",
+    "nep_workspace_bytes", "nep_neighbors", "nep_energy_forces_virial", "nep_param_grad",
+    "nep_param_grad_adjoint", "nep_md_step", "nep_set_timing_events", "nep_check",
+    "nep_last_error", "nep_version",
+)
+
+
+class Hparams(ctypes.Structure):
+    _fields_ = [("n_types", ctypes.c_int), ("n_rad", ctypes.c_int), ("n_ang", ctypes.c_int),
+                ("k_rad", ctypes.c_int), ("k_ang", ctypes.c_int), ("l_max", ctypes.c_int),
+                ("has_4body", ctypes.c_int), ("n_hidden", ctypes.c_int),
+                ("rc_rad", ctypes.c_float), ("rc_ang", ctypes.c_float),
+                ("precision", ctypes.c_int)]
+
+
+class System(ctypes.Structure):
+    _fields_ = [("n_atoms", ctypes.c_int), ("n_cfg", ctypes.c_int),
+                ("pos", ctypes.c_void_p), ("type", ctypes.c_void_p),
+                ("atom_off", ctypes.c_void_p), ("box", ctypes.c_void_p),
+                ("atom_off_host", ctypes.c_void_p), ("box_host", ctypes.c_void_p)]
+
+
+class NList(ctypes.Structure):
+    _fields_ = [("cap", ctypes.c_int), ("cap_ang", ctypes.c_int),
+                ("cnt", ctypes.c_void_p), ("cnt_ang", ctypes.c_void_p),
+                ("nbr", ctypes.c_void_p), ("shift", ctypes.c_void_p),
+                ("rev", ctypes.c_void_p), ("status", ctypes.c_void_p),
+                ("skin", ctypes.c_float), ("min_image", ctypes.c_int)]
+
+
+_LIB = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libnep.so (built in-tree by paper_2607_06969_gb300.build)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, f, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_size_t
+    P = ctypes.POINTER
+    L.nep_num_params.argtypes = [P(Hparams)]
+    L.nep_num_params.restype = sz
+    L.nep_supported.argtypes = [P(Hparams)]
+    L.nep_supported.restype = i
+    L.nep_create.argtypes = [P(Hparams), vp, sz, P(vp)]
+    L.nep_destroy.argtypes = [vp]
+    L.nep_set_params.argtypes = [vp, vp, vp]
+    L.nep_workspace_bytes.argtypes = [vp, i, i, i, i]
+    L.nep_workspace_bytes.restype = sz
+    L.nep_neighbors.argtypes = [vp, P(System), f, P(NList), vp, sz, vp]
+    L.nep_energy_forces_virial.argtypes = [vp, P(System), P(NList), vp, vp, vp, vp, vp, sz, vp]
+    L.nep_param_grad.argtypes = [vp, P(System), P(NList), vp, vp, vp, vp, i, vp, vp, vp, sz, vp]
+    L.nep_param_grad_adjoint.argtypes = [vp, P(System), P(NList), vp, vp, vp, vp, vp, sz, vp]
+    L.nep_md_step.argtypes = [vp, P(System), P(NList), vp, vp, vp, vp, vp, f, f, i, vp, sz, vp]
+    L.nep_check.argtypes = [P(NList), vp]
+    L.nep_set_timing_events.argtypes = [vp, P(vp), i]
+    L.nep_last_error.restype = ctypes.c_char_p
+    L.nep_version.restype = ctypes.c_char_p
+    for name in ("nep_create", "nep_destroy", "nep_set_params", "nep_neighbors",
+                 "nep_energy_forces_virial", "nep_param_grad", "nep_param_grad_adjoint",
+                 "nep_md_step", "nep_check", "nep_set_timing_events"):
+        getattr(L, name).restype = i
+    _LIB = L
+    return L
+
+
+class NepError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where} failed with status {status}: {msg}")
+        self.status = status
+
+
+def check(status: int, where: str) -> None:
+    if status != NEP_OK:
+        raise NepError(status, where, lib().nep_last_error().decode())
+
+
+def hparams_of(h, precision: int = 0) -> Hparams:
+    return Hparams(h.n_types, h.n_rad, h.n_ang, h.k_rad, h.k_ang, h.l_max, h.has_4body,
+                   h.n_hidden, float(h.rc_rad), float(h.rc_ang), precision)
+
+
+def num_params(h) -> int:
+    hp = hparams_of(h)
+    return int(lib().nep_num_params(ctypes.byref(hp)))
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream(stream=None) -> ctypes.c_void_p:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Model:
+    """A NEP model on the current CUDA device (nep_create / nep_destroy)."""
+
+    def __init__(self, h, params, precision: int = 0):
+        self.h = h
+        self.hp = hparams_of(h, precision)
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+        self.n_params = p.size
+        handle = ctypes.c_void_p()
+        check(lib().nep_create(ctypes.byref(self.hp), p.ctypes.data_as(ctypes.c_void_p),
+                               p.size, ctypes.byref(handle)), "nep_create")
+        self.handle = handle
+
+    def set_params(self, params_dev, stream=None):
+        assert params_dev.is_cuda and params_dev.dtype.is_floating_point
+        check(lib().nep_set_params(self.handle, _ptr(params_dev), _stream(stream)), "nep_set_params")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().nep_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class DeviceSystem:
+    """A batch of periodic configurations resident on the GPU (nep_system)."""
+
+    def __init__(self, pos, types, box, atom_off, device="cuda"):
+        import torch
+        pos = np.asarray(pos, np.float32)
+        self.n_atoms = int(pos.shape[0])
+        self.n_cfg = int(np.asarray(box).shape[0])
+        self.pos = torch.from_numpy(np.ascontiguousarray(pos.T)).to(device)        # [3][N]
+        self.type = torch.from_numpy(np.asarray(types, np.int32)).to(device)
+        self.atom_off_host = np.ascontiguousarray(np.asarray(atom_off, np.int32))
+        self.box_host = np.ascontiguousarray(np.asarray(box, np.float32))
+        self.atom_off = torch.from_numpy(self.atom_off_host).to(device)
+        self.box = torch.from_numpy(self.box_host).to(device)
+        self.refresh()
+
+    @classmethod
+    def from_inputs(cls, s, device="cuda"):
+        return cls(s.pos32(), s.types, s.box, s.atom_off, device)
+
+    def refresh(self):
+        self.c = System(self.n_atoms, self.n_cfg, self.pos.data_ptr(), self.type.data_ptr(),
+                        self.atom_off.data_ptr(), self.box.data_ptr(),
+                        self.atom_off_host.ctypes.data, self.box_host.ctypes.data)
+        return self.c
+
+
+class NeighborList:
+    """Caller-owned Verlet list (nep_nlist) with capacities cap >= cap_ang."""
+
+    def __init__(self, n_atoms: int, cap: int, cap_ang: int, shifts: bool = True, device="cuda"):
+        import torch
+        self.n_atoms, self.cap, self.cap_ang = n_atoms, cap, cap_ang
+        z = dict(dtype=torch.int32, device=device)
+        self.cnt = torch.zeros(n_atoms, **z)
+        self.cnt_ang = torch.zeros(n_atoms, **z)
+        self.nbr = torch.zeros(cap * n_atoms, **z)
+        self.shift = torch.zeros(cap * n_atoms, **z) if shifts else None
+        self.rev = torch.zeros(cap_ang * n_atoms, **z)
+        self.status = torch.zeros(4, **z)
+        self.c = NList(cap, cap_ang, self.cnt.data_ptr(), self.cnt_ang.data_ptr(),
+                       self.nbr.data_ptr(), 0 if self.shift is None else self.shift.data_ptr(),
+                       self.rev.data_ptr(), self.status.data_ptr(), 0.0, 0)
+
+    def to_pairs(self, box=None):
+        """(i, j, s) arrays of the radial list, and the angular prefix mask."""
+        N = self.n_atoms
+        cnt = self.cnt.cpu().numpy()
+        cnta = self.cnt_ang.cpu().numpy()
+        nbr = self.nbr.cpu().numpy().reshape(self.cap, N)
+        slot = np.arange(self.cap)[:, None]
+        mask = slot < cnt[None, :]
+        ii = np.broadcast_to(np.arange(N)[None, :], (self.cap, N))[mask]
+        jj = nbr[mask]
+        ang = (slot < cnta[None, :])[mask]
+        if self.shift is not None and not self.c.min_image:
+            sh = self.shift.cpu().numpy().reshape(self.cap, N)[mask]
+            s = np.stack([((sh >> (8 * k)) & 0xff).astype(np.int8).astype(np.int64) for k in range(3)], 1)
+        else:
+            s = None
+        return ii.astype(np.int64), jj.astype(np.int64), s, ang
+
+
+class Workspace:
+    def __init__(self, model: Model, n_atoms: int, n_cfg: int, cap: int, cap_ang: int, device="cuda"):
+        import torch
+        self.bytes = int(lib().nep_workspace_bytes(model.handle, n_atoms, n_cfg, cap, cap_ang))
+        if self.bytes == 0:
+            raise NepError(NEP_ERR_ARG, "nep_workspace_bytes", "invalid sizes")
+        self.buf = torch.empty(self.bytes + 256, dtype=torch.uint8, device=device)
+        off = (-self.buf.data_ptr()) % 256
+        self.ptr = ctypes.c_void_p(self.buf.data_ptr() + off)
+
+
+def neighbors(model: Model, dsys: DeviceSystem, nl: NeighborList, skin: float, ws: Workspace,
+              stream=None) -> None:
+    check(lib().nep_neighbors(model.handle, ctypes.byref(dsys.c), float(skin), ctypes.byref(nl.c),
+                              ws.ptr, ws.bytes, _stream(stream)), "nep_neighbors")
+
+
+def energy_forces_virial(model: Model, dsys: DeviceSystem, nl: NeighborList, ws: Workspace,
+                         out=None, stream=None):
+    """Returns (e_atom [N] f32, force [3,N] f32, e_tot [B] f64, virial [B,9] f64)."""
+    import torch
+    dev = dsys.pos.device
+    if out is None:
+        out = (torch.empty(dsys.n_atoms, dtype=torch.float32, device=dev),
+               torch.empty(3, dsys.n_atoms, dtype=torch.float32, device=dev),
+               torch.empty(dsys.n_cfg, dtype=torch.float64, device=dev),
+               torch.empty(dsys.n_cfg, 9, dtype=torch.float64, device=dev))
+    e_atom, force, e_tot, vir = out
+    check(lib().nep_energy_forces_virial(model.handle, ctypes.byref(dsys.c), ctypes.byref(nl.c),
+                                         _ptr(e_atom), _ptr(force), _ptr(e_tot), _ptr(vir),
+                                         ws.ptr, ws.bytes, _stream(stream)),
+          "nep_energy_forces_virial")
+    return out
+
+
+def md_step(model: Model, dsys: DeviceSystem, nl: NeighborList, vel, force, e_tot, virial,
+            masses, dt: float, skin: float, rebuild: bool, ws: Workspace, stream=None) -> None:
+    m = np.ascontiguousarray(np.asarray(masses, np.float32))
+    check(lib().nep_md_step(model.handle, ctypes.byref(dsys.c), ctypes.byref(nl.c), _ptr(vel),
+                            _ptr(force), _ptr(e_tot), _ptr(virial),
+                            m.ctypes.data_as(ctypes.c_void_p), float(dt), float(skin),
+                            1 if rebuild else 0, ws.ptr, ws.bytes, _stream(stream)), "nep_md_step")
+
+
+def set_timing_events(model: Model, events) -> None:
+    """events: three torch.cuda.Event(enable_timing=True) or None to clear."""
+    if events is None:
+        check(lib().nep_set_timing_events(model.handle, None, 0), "nep_set_timing_events")
+        return
+    arr = (ctypes.c_void_p * 3)(*[ctypes.c_void_p(e.cuda_event) for e in events])
+    check(lib().nep_set_timing_events(model.handle, arr, 3), "nep_set_timing_events")
+
+
+def check_list(nl: NeighborList | None, stream=None) -> int:
+    """nep_check: synchronise and return the status (does not raise)."""
+    return int(lib().nep_check(None if nl is None else ctypes.byref(nl.c), _stream(stream)))
+
+
+def last_error() -> str:
+    return lib().nep_last_error().decode()

@@ -1,0 +1,442 @@
+// C ABI of libnep (declared in include/nep.h): argument checks, workspace
+// carving and kernel dispatch.  No allocation and no host synchronisation
+// happens in the hot calls.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "nep_internal.h"
+
+struct nep_model {
+    nep_hparams hp;
+    const nep::KernelSet* ks;
+    nep::ParamLayout lay;
+    float* params;   // device [P]
+    int device;
+    cudaEvent_t timing[3];
+    int n_timing;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+nep_status fail(nep_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+nep_status cuda_fail(cudaError_t e, const char* where) {
+    return fail(NEP_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define NEP_CUDA(call, where)                          \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+    } while (0)
+
+bool hp_valid(const nep_hparams* hp) {
+    return hp && hp->n_types >= 1 && hp->n_types <= nep::kMaxTypes && hp->n_rad >= 1 &&
+           hp->n_ang >= 1 && hp->k_rad >= 1 && hp->k_ang >= 1 && hp->l_max == 4 &&
+           (hp->has_4body == 0 || hp->has_4body == 1) && hp->n_hidden >= 1 &&
+           hp->n_hidden <= 1024 && hp->rc_rad > 0.0f && hp->rc_ang > 0.0f &&
+           hp->rc_ang <= hp->rc_rad && hp->precision >= 0 && hp->precision <= 2 &&
+           std::isfinite(hp->rc_rad) && std::isfinite(hp->rc_ang);
+}
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Byte offsets of the scratch arrays inside the caller's workspace.
+struct WsLayout {
+    size_t pos4, cfg, e_atom, S, pang, Pr, comp, cnt_comp, fin, fpart, wat, chunk_start, partial;
+    size_t plan, cell_of, rank, cell_cnt, cell_start, cell_atoms, scan_tmp;
+    size_t total;
+    int max_chunks, cmax;
+};
+
+WsLayout ws_layout(const nep_model* m, int N, int B, int cap, int cap_ang) {
+    (void)cap;
+    WsLayout w;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = align_up(o + bytes);
+        return at;
+    };
+    const size_t n = (size_t)N;
+    const int NA = m->hp.n_ang, T = m->hp.n_types, KR = m->hp.k_rad;
+    const int NP = NA * (4 + m->hp.has_4body);
+    w.pos4 = take(16 * n);
+    w.cfg = take(4 * n);
+    w.e_atom = take(4 * n);
+    w.S = take(4 * n * NA * nep::kLM);
+    w.pang = take(4 * n * NP);
+    w.Pr = take(4 * n * T * KR);
+    w.comp = take(16 * n * cap_ang);
+    w.cnt_comp = take(4 * n);
+    w.fin = take(16 * n * cap_ang);
+    w.fpart = take(12 * n);
+    w.wat = take(36 * n);
+    w.chunk_start = take(4 * ((size_t)B + 1));
+    w.max_chunks = (int)((n + nep::kChunk - 1) / nep::kChunk) + B;
+    w.partial = take(80 * (size_t)w.max_chunks);
+    w.cmax = (int)nep::nbr_cell_capacity(N, B);
+    w.plan = take(sizeof(nep::CellPlan) * (size_t)B);
+    w.cell_of = take(4 * n);
+    w.rank = take(4 * n);
+    w.cell_cnt = take(4 * ((size_t)w.cmax + 1));
+    w.cell_start = take(4 * ((size_t)w.cmax + 1));
+    w.cell_atoms = take(4 * n);
+    const size_t ntiles = ((size_t)w.cmax + 1 + 2047) / 2048;
+    w.scan_tmp = take(4 * (ntiles + 1));
+    w.total = o;
+    return w;
+}
+
+template <class T>
+T* at(void* base, size_t off) {
+    return reinterpret_cast<T*>(static_cast<char*>(base) + off);
+}
+
+nep_status check_system(const nep_model* m, const nep_system* s) {
+    if (!m) return fail(NEP_ERR_ARG, "model is NULL");
+    if (!s) return fail(NEP_ERR_ARG, "system is NULL");
+    if (s->n_atoms < 0 || s->n_cfg < 1) return fail(NEP_ERR_ARG, "n_atoms < 0 or n_cfg < 1");
+    if (!s->atom_off_host || !s->box_host) return fail(NEP_ERR_ARG, "host copies of atom_off/box are NULL");
+    if (s->atom_off_host[0] != 0 || s->atom_off_host[s->n_cfg] != s->n_atoms)
+        return fail(NEP_ERR_ARG, "atom_off must start at 0 and end at n_atoms");
+    for (int b = 0; b < s->n_cfg; ++b) {
+        if (s->atom_off_host[b + 1] < s->atom_off_host[b])
+            return fail(NEP_ERR_ARG, "atom_off not non-decreasing at config %d", b);
+        for (int d = 0; d < 3; ++d) {
+            const float L = s->box_host[3 * b + d];
+            if (!(L > 0.0f) || !std::isfinite(L))
+                return fail(NEP_ERR_ARG, "box of config %d is not positive and finite", b);
+        }
+    }
+    if (s->n_atoms > 0 && (!s->pos || !s->type)) return fail(NEP_ERR_ARG, "pos or type is NULL");
+    if (!s->atom_off || !s->box) return fail(NEP_ERR_ARG, "atom_off or box is NULL");
+    return NEP_OK;
+}
+
+nep_status check_nlist(const nep_nlist* nl, int N) {
+    if (!nl) return fail(NEP_ERR_ARG, "neighbour list is NULL");
+    if (nl->cap < 1 || nl->cap_ang < 1 || nl->cap_ang > nl->cap)
+        return fail(NEP_ERR_ARG, "need 1 <= cap_ang <= cap (got cap=%d cap_ang=%d)", nl->cap, nl->cap_ang);
+    if ((long long)nl->cap * N >= (1LL << 31))
+        return fail(NEP_ERR_ARG, "cap * n_atoms must stay below 2^31");
+    if ((long long)nl->cap_ang * N >= (1LL << 30))
+        return fail(NEP_ERR_ARG, "cap_ang * n_atoms must stay below 2^30");
+    if (N > 0 && (!nl->cnt || !nl->cnt_ang || !nl->nbr || !nl->rev || !nl->status))
+        return fail(NEP_ERR_ARG, "neighbour list arrays are NULL");
+    return NEP_OK;
+}
+
+bool boxes_allow_min_image(const nep_system* s, float rc_list) {
+    for (int b = 0; b < s->n_cfg; ++b)
+        for (int d = 0; d < 3; ++d)
+            if (s->box_host[3 * b + d] < 2.0f * rc_list + 0.01f) return false;
+    return true;
+}
+
+nep::EvalArgs make_args(const nep_model* m, const nep_system* s, const nep_nlist* nl, void* work,
+                        const WsLayout& w) {
+    nep::EvalArgs a;
+    a.N = s->n_atoms;
+    a.B = s->n_cfg;
+    a.T = m->hp.n_types;
+    a.H = m->hp.n_hidden;
+    a.cap = nl->cap;
+    a.cap_ang = nl->cap_ang;
+    a.min_image = nl->min_image;
+    a.rc_rad = m->hp.rc_rad;
+    a.rc_ang = m->hp.rc_ang;
+    a.pos4 = at<float4>(work, w.pos4);
+    a.cfg = at<int>(work, w.cfg);
+    a.box = s->box;
+    a.cnt = nl->cnt;
+    a.cnt_ang = nl->cnt_ang;
+    a.nbr = nl->nbr;
+    a.shift = nl->shift;
+    a.rev = nl->rev;
+    a.params = m->params;
+    a.e_atom = at<float>(work, w.e_atom);
+    a.S = at<float>(work, w.S);
+    a.pang = at<float>(work, w.pang);
+    a.Pr = at<float>(work, w.Pr);
+    a.comp = at<float4>(work, w.comp);
+    a.cnt_comp = at<int>(work, w.cnt_comp);
+    a.fin = at<float4>(work, w.fin);
+    a.fpart = at<float>(work, w.fpart);
+    a.wat = at<float>(work, w.wat);
+    a.status = nl->status;
+    return a;
+}
+
+nep_status check_work(const nep_model* m, const nep_system* s, const nep_nlist* nl, void* work,
+                      size_t work_bytes, WsLayout* w) {
+    *w = ws_layout(m, s->n_atoms, s->n_cfg, nl->cap, nl->cap_ang);
+    if (work_bytes < w->total)
+        return fail(NEP_ERR_ARG, "workspace too small: %zu bytes given, %zu needed", work_bytes, w->total);
+    if (!work && w->total) return fail(NEP_ERR_ARG, "workspace is NULL");
+    if ((reinterpret_cast<uintptr_t>(work) & 255) != 0)
+        return fail(NEP_ERR_ARG, "workspace must be 256-byte aligned");
+    return NEP_OK;
+}
+
+nep_status efv_impl(nep_model* m, const nep_system* s, const nep_nlist* nl, float* e_atom,
+                    float* force, double* e_tot, double* virial, void* work, const WsLayout& w,
+                    cudaStream_t st) {
+    const int N = s->n_atoms, B = s->n_cfg;
+    NEP_CUDA(nep::launch_pack(s->pos, s->type, s->atom_off, N, B, m->hp.n_types, at<float4>(work, w.pos4),
+                              at<int>(work, w.cfg), nl->status, st),
+             "pack");
+    NEP_CUDA(nep::launch_chunk_plan(s->atom_off, B, at<int>(work, w.chunk_start), st), "chunk plan");
+    const nep::EvalArgs a = make_args(m, s, nl, work, w);
+    const int nt = m->n_timing;
+    m->n_timing = 0;
+    if (nt == 3) NEP_CUDA(cudaEventRecord(m->timing[0], st), "timing event");
+    if (N > 0) NEP_CUDA(m->ks->descriptor(a, st), "descriptor kernel");
+    if (nt == 3) NEP_CUDA(cudaEventRecord(m->timing[1], st), "timing event");
+    if (N > 0) NEP_CUDA(m->ks->force(a, st), "force kernel");
+    if (nt == 3) NEP_CUDA(cudaEventRecord(m->timing[2], st), "timing event");
+    NEP_CUDA(nep::launch_gather_reduce(a, s->atom_off, at<int>(work, w.chunk_start), w.max_chunks,
+                                       at<double>(work, w.partial), force, e_atom, st),
+             "gather");
+    NEP_CUDA(nep::launch_final_reduce(B, at<int>(work, w.chunk_start), at<double>(work, w.partial), e_tot,
+                                      virial, st),
+             "final reduce");
+    return NEP_OK;
+}
+
+nep_status neighbors_impl(nep_model* m, const nep_system* s, float skin, nep_nlist* nl, void* work,
+                          const WsLayout& w, cudaStream_t st) {
+    const int N = s->n_atoms, B = s->n_cfg;
+    const float rc_list = m->hp.rc_rad + skin;
+    const float rc_list_ang = m->hp.rc_ang + skin;
+    const bool mi = boxes_allow_min_image(s, rc_list);
+    if (!mi && !nl->shift)
+        return fail(NEP_ERR_ARG,
+                    "a box edge is shorter than 2*(rc+skin)+0.01; the list needs a shift array");
+    nl->skin = skin;
+    nl->min_image = mi ? 1 : 0;
+    NEP_CUDA(cudaMemsetAsync(nl->status, 0, 4 * sizeof(int), st), "clear status");
+    NEP_CUDA(nep::launch_pack(s->pos, s->type, s->atom_off, N, B, m->hp.n_types, at<float4>(work, w.pos4),
+                              at<int>(work, w.cfg), nl->status, st),
+             "pack");
+    nep::NbrWork nw;
+    nw.plan = at<nep::CellPlan>(work, w.plan);
+    nw.cell_of = at<int>(work, w.cell_of);
+    nw.rank = at<int>(work, w.rank);
+    nw.cell_cnt = at<int>(work, w.cell_cnt);
+    nw.cell_start = at<int>(work, w.cell_start);
+    nw.cell_atoms = at<int>(work, w.cell_atoms);
+    nw.scan_tmp = at<int>(work, w.scan_tmp);
+    nw.cmax = w.cmax;
+    nep_nlist copy = *nl;
+    if (mi) copy.shift = nullptr;
+    NEP_CUDA(nep::launch_neighbors(s->pos, s->atom_off, s->box, at<int>(work, w.cfg), N, B, rc_list,
+                                   rc_list_ang, mi ? 1 : 0, &copy, nw, st),
+             "neighbour build");
+    return NEP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* nep_version(void) { return "libnep 0.1 (sm_103a)"; }
+
+const char* nep_last_error(void) { return g_err.c_str(); }
+
+size_t nep_num_params(const nep_hparams* hp) {
+    if (!hp_valid(hp)) return 0;
+    const nep::ParamLayout L = nep::param_layout(hp->n_types, hp->n_rad, hp->n_ang, hp->k_rad,
+                                                 hp->k_ang, hp->has_4body, hp->n_hidden);
+    return (size_t)L.P;
+}
+
+int nep_supported(const nep_hparams* hp) {
+    if (!hp_valid(hp)) return 0;
+    return nep::find_kernel_set(hp->n_rad, hp->n_ang, hp->k_rad, hp->k_ang, hp->has_4body,
+                                hp->n_types) != nullptr;
+}
+
+nep_status nep_create(const nep_hparams* hp, const float* params_host, size_t n_params,
+                      nep_model** out) {
+    if (!out) return fail(NEP_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!hp_valid(hp)) return fail(NEP_ERR_ARG, "invalid hyper-parameters (l_max must be 4, 1 <= n_types <= 4, rc_ang <= rc_rad)");
+    if (hp->precision != 0)
+        return fail(NEP_ERR_UNSUPPORTED, "precision mode %d is not compiled in", hp->precision);
+    const nep::KernelSet* ks = nep::find_kernel_set(hp->n_rad, hp->n_ang, hp->k_rad, hp->k_ang,
+                                                    hp->has_4body, hp->n_types);
+    if (!ks)
+        return fail(NEP_ERR_UNSUPPORTED,
+                    "no kernel compiled for n_rad=%d n_ang=%d k_rad=%d k_ang=%d 4body=%d types=%d",
+                    hp->n_rad, hp->n_ang, hp->k_rad, hp->k_ang, hp->has_4body, hp->n_types);
+    const size_t P = nep_num_params(hp);
+    if (n_params != P) return fail(NEP_ERR_ARG, "expected %zu parameters, got %zu", P, n_params);
+    if (!params_host) return fail(NEP_ERR_ARG, "params_host is NULL");
+    for (size_t k = 0; k < P; ++k)
+        if (!std::isfinite(params_host[k])) return fail(NEP_ERR_ARG, "parameter %zu is not finite", k);
+    nep_model* m = new nep_model();
+    m->hp = *hp;
+    m->ks = ks;
+    m->lay = nep::param_layout(hp->n_types, hp->n_rad, hp->n_ang, hp->k_rad, hp->k_ang,
+                               hp->has_4body, hp->n_hidden);
+    cudaGetDevice(&m->device);
+    m->n_timing = 0;
+    cudaError_t e = ks->init(hp->n_hidden);
+    if (e != cudaSuccess) {
+        delete m;
+        return cuda_fail(e, "kernel attributes");
+    }
+    e = cudaMalloc(&m->params, sizeof(float) * P);
+    if (e != cudaSuccess) {
+        delete m;
+        return fail(NEP_ERR_NOMEM, "cudaMalloc of %zu parameters: %s", P, cudaGetErrorString(e));
+    }
+    e = cudaMemcpy(m->params, params_host, sizeof(float) * P, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(m->params);
+        delete m;
+        return cuda_fail(e, "copy parameters");
+    }
+    *out = m;
+    return NEP_OK;
+}
+
+nep_status nep_destroy(nep_model* m) {
+    if (!m) return NEP_OK;
+    cudaError_t e = cudaFree(m->params);
+    delete m;
+    if (e != cudaSuccess) return cuda_fail(e, "free parameters");
+    return NEP_OK;
+}
+
+nep_status nep_set_params(nep_model* m, const float* params_dev, void* stream) {
+    if (!m || !params_dev) return fail(NEP_ERR_ARG, "model or params is NULL");
+    NEP_CUDA(cudaMemcpyAsync(m->params, params_dev, sizeof(float) * (size_t)m->lay.P,
+                             cudaMemcpyDeviceToDevice, (cudaStream_t)stream),
+             "set params");
+    return NEP_OK;
+}
+
+size_t nep_workspace_bytes(const nep_model* m, int n_atoms, int n_cfg, int cap, int cap_ang) {
+    if (!m || n_atoms < 0 || n_cfg < 1 || cap < 1 || cap_ang < 1) return 0;
+    return ws_layout(m, n_atoms, n_cfg, cap, cap_ang).total;
+}
+
+nep_status nep_neighbors(nep_model* m, const nep_system* sys, float skin, nep_nlist* nl, void* work,
+                         size_t work_bytes, void* stream) {
+    nep_status s;
+    if ((s = check_system(m, sys)) != NEP_OK) return s;
+    if ((s = check_nlist(nl, sys->n_atoms)) != NEP_OK) return s;
+    if (!(skin >= 0.0f) || !std::isfinite(skin)) return fail(NEP_ERR_ARG, "skin must be finite and >= 0");
+    WsLayout w;
+    if ((s = check_work(m, sys, nl, work, work_bytes, &w)) != NEP_OK) return s;
+    return neighbors_impl(m, sys, skin, nl, work, w, (cudaStream_t)stream);
+}
+
+nep_status nep_energy_forces_virial(nep_model* m, const nep_system* sys, const nep_nlist* nl,
+                                    float* e_atom, float* force, double* e_tot, double* virial,
+                                    void* work, size_t work_bytes, void* stream) {
+    nep_status s;
+    if ((s = check_system(m, sys)) != NEP_OK) return s;
+    if ((s = check_nlist(nl, sys->n_atoms)) != NEP_OK) return s;
+    if (sys->n_atoms > 0 && !force) return fail(NEP_ERR_ARG, "force is NULL");
+    if (!nl->min_image && !nl->shift) return fail(NEP_ERR_STATE, "list was not built (no shifts, not min-image)");
+    WsLayout w;
+    if ((s = check_work(m, sys, nl, work, work_bytes, &w)) != NEP_OK) return s;
+    return efv_impl(m, sys, nl, e_atom, force, e_tot, virial, work, w, (cudaStream_t)stream);
+}
+
+nep_status nep_md_step(nep_model* m, const nep_system* sys, nep_nlist* nl, float* vel, float* force,
+                       double* e_tot, double* virial, const float* masses_host, float dt, float skin,
+                       int rebuild, void* work, size_t work_bytes, void* stream) {
+    nep_status s;
+    if ((s = check_system(m, sys)) != NEP_OK) return s;
+    if ((s = check_nlist(nl, sys->n_atoms)) != NEP_OK) return s;
+    if (!masses_host) return fail(NEP_ERR_ARG, "masses_host is NULL");
+    if (sys->n_atoms > 0 && (!vel || !force)) return fail(NEP_ERR_ARG, "vel or force is NULL");
+    if (!(dt > 0.0f) || !std::isfinite(dt)) return fail(NEP_ERR_ARG, "dt must be positive");
+    WsLayout w;
+    if ((s = check_work(m, sys, nl, work, work_bytes, &w)) != NEP_OK) return s;
+    float inv_m[nep::kMaxTypes] = {0, 0, 0, 0};
+    for (int t = 0; t < m->hp.n_types; ++t) {
+        if (!(masses_host[t] > 0.0f)) return fail(NEP_ERR_ARG, "mass of species %d must be positive", t);
+        inv_m[t] = 1.0f / (masses_host[t] * 103.6427f);
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int N = sys->n_atoms;
+    float* pos = const_cast<float*>(sys->pos);
+    NEP_CUDA(nep::launch_kick(vel, force, sys->type, inv_m, N, 0.5f * dt, pos, dt, st), "kick/drift");
+    if (rebuild) {
+        NEP_CUDA(nep::launch_pack(sys->pos, sys->type, sys->atom_off, N, sys->n_cfg, m->hp.n_types,
+                                  at<float4>(work, w.pos4), at<int>(work, w.cfg), nl->status, st),
+                 "pack");
+        NEP_CUDA(nep::launch_wrap(pos, at<int>(work, w.cfg), sys->box, N, st), "wrap");
+        if ((s = neighbors_impl(m, sys, skin, nl, work, w, st)) != NEP_OK) return s;
+    } else if (!nl->min_image && !nl->shift) {
+        return fail(NEP_ERR_STATE, "list was not built");
+    }
+    if ((s = efv_impl(m, sys, nl, nullptr, force, e_tot, virial, work, w, st)) != NEP_OK) return s;
+    NEP_CUDA(nep::launch_kick(vel, force, sys->type, inv_m, N, 0.5f * dt, nullptr, 0.0f, st), "kick");
+    return NEP_OK;
+}
+
+nep_status nep_param_grad(nep_model* m, const nep_system* sys, const nep_nlist* nl,
+                          const double* e_lbl, const float* f_lbl, const double* v_lbl,
+                          const float* w_host, int loss_mode, float* grad, double* loss, void* work,
+                          size_t work_bytes, void* stream) {
+    (void)m; (void)sys; (void)nl; (void)e_lbl; (void)f_lbl; (void)v_lbl; (void)w_host;
+    (void)loss_mode; (void)grad; (void)loss; (void)work; (void)work_bytes; (void)stream;
+    return fail(NEP_ERR_UNSUPPORTED, "nep_param_grad is not built yet");
+}
+
+nep_status nep_param_grad_adjoint(nep_model* m, const nep_system* sys, const nep_nlist* nl,
+                                  const double* a_e, const float* lam, const double* mu, float* grad,
+                                  void* work, size_t work_bytes, void* stream) {
+    (void)m; (void)sys; (void)nl; (void)a_e; (void)lam; (void)mu; (void)grad; (void)work;
+    (void)work_bytes; (void)stream;
+    return fail(NEP_ERR_UNSUPPORTED, "nep_param_grad_adjoint is not built yet");
+}
+
+nep_status nep_set_timing_events(nep_model* m, void* const* events, int n) {
+    if (!m) return fail(NEP_ERR_ARG, "model is NULL");
+    if (n == 0) {
+        m->n_timing = 0;
+        return NEP_OK;
+    }
+    if (n != 3 || !events) return fail(NEP_ERR_ARG, "need exactly 3 events");
+    for (int k = 0; k < 3; ++k) {
+        if (!events[k]) return fail(NEP_ERR_ARG, "event %d is NULL", k);
+        m->timing[k] = (cudaEvent_t)events[k];
+    }
+    m->n_timing = 3;
+    return NEP_OK;
+}
+
+nep_status nep_check(const nep_nlist* nl, void* stream) {
+    NEP_CUDA(cudaStreamSynchronize((cudaStream_t)stream), "synchronise");
+    if (!nl || !nl->status) return NEP_OK;
+    int st[4];
+    NEP_CUDA(cudaMemcpy(st, nl->status, sizeof st, cudaMemcpyDeviceToHost), "read status");
+    if (st[0]) return fail(NEP_ERR_CAPACITY, "neighbour list overflow: need cap >= %d, cap_ang >= %d", st[1], st[2]);
+    if (st[3]) return fail(NEP_ERR_INPUT, "invalid input: species out of range, non-finite position or atom outside its box");
+    return NEP_OK;
+}
+
+}  // extern "C"

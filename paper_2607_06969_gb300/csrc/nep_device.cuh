@@ -1,0 +1,277 @@
+// Device math of the NEP pair terms: cutoff and Chebyshev basis (Eqs. 12-15),
+// real solid harmonics for l = 1..4 (Eq. 16) and their gradients.
+#pragma once
+#include "nep_internal.h"
+
+#if !defined(__CUDA_ARCH__)
+#include <cmath>
+#endif
+
+namespace nep {
+
+// IEEE single operations that the compiler must not contract into FMAs;
+// the neighbour predicate and the pair vectors are defined with them.
+NEP_HD float add_rn(float a, float b) {
+#if defined(__CUDA_ARCH__)
+    return __fadd_rn(a, b);
+#else
+    volatile float r = a + b;
+    return r;
+#endif
+}
+NEP_HD float mul_rn(float a, float b) {
+#if defined(__CUDA_ARCH__)
+    return __fmul_rn(a, b);
+#else
+    volatile float r = a * b;
+    return r;
+#endif
+}
+NEP_HD float sub_rn(float a, float b) {
+#if defined(__CUDA_ARCH__)
+    return __fsub_rn(a, b);
+#else
+    volatile float r = a - b;
+    return r;
+#endif
+}
+NEP_HD float cospi_f(float x) {
+#if defined(__CUDA_ARCH__)
+    return cospif(x);
+#else
+    return (float)std::cos(3.14159265358979323846 * (double)x);
+#endif
+}
+NEP_HD float sinpi_f(float x) {
+#if defined(__CUDA_ARCH__)
+    return sinpif(x);
+#else
+    return (float)std::sin(3.14159265358979323846 * (double)x);
+#endif
+}
+NEP_HD float tanh_f(float x) {
+#if defined(__CUDA_ARCH__)
+    return tanhf(x);
+#else
+    return (float)std::tanh((double)x);
+#endif
+}
+NEP_HD float sqrt_f(float x) {
+#if defined(__CUDA_ARCH__)
+    return sqrtf(x);
+#else
+    return (float)std::sqrt((double)x);
+#endif
+}
+NEP_HD float rint_f(float x) {
+#if defined(__CUDA_ARCH__)
+    return rintf(x);
+#else
+    return std::nearbyint(x);
+#endif
+}
+NEP_HD int f2i(float x) {
+#if defined(__CUDA_ARCH__)
+    return __float_as_int(x);
+#else
+    int r; memcpy(&r, &x, 4); return r;
+#endif
+}
+NEP_HD float i2f(int x) {
+#if defined(__CUDA_ARCH__)
+    return __int_as_float(x);
+#else
+    float r; memcpy(&r, &x, 4); return r;
+#endif
+}
+
+// Packed image shift: int8 sx | sy << 8 | sz << 16.
+NEP_HD int pack_shift(int sx, int sy, int sz) {
+    return (sx & 0xff) | ((sy & 0xff) << 8) | ((sz & 0xff) << 16);
+}
+NEP_HD void unpack_shift(int v, int& sx, int& sy, int& sz) {
+    sx = (int)(signed char)(v & 0xff);
+    sy = (int)(signed char)((v >> 8) & 0xff);
+    sz = (int)(signed char)((v >> 16) & 0xff);
+}
+
+// Pair vector r_ij = (x_j - x_i) + s * L with the list's image, or with the
+// minimum image when the list carries no shifts.  Same operation order as the
+// neighbour predicate.
+NEP_HD void pair_vector(float4 pi, float4 pj, float Lx, float Ly, float Lz, float iLx, float iLy,
+                        float iLz, int min_image, int packed, float& dx, float& dy, float& dz) {
+    float ux = sub_rn(pj.x, pi.x), uy = sub_rn(pj.y, pi.y), uz = sub_rn(pj.z, pi.z);
+    float sx, sy, sz;
+    if (min_image) {
+        sx = -rint_f(ux * iLx);
+        sy = -rint_f(uy * iLy);
+        sz = -rint_f(uz * iLz);
+    } else {
+        int a, b, c;
+        unpack_shift(packed, a, b, c);
+        sx = (float)a; sy = (float)b; sz = (float)c;
+    }
+    dx = add_rn(ux, mul_rn(sx, Lx));
+    dy = add_rn(uy, mul_rn(sy, Ly));
+    dz = add_rn(uz, mul_rn(sz, Lz));
+}
+
+NEP_HD float dist2(float dx, float dy, float dz) {
+    return add_rn(add_rn(mul_rn(dx, dx), mul_rn(dy, dy)), mul_rn(dz, dz));
+}
+
+// Q_k(r) = (T_k(x)+1)/2 f_c(r), x = 2(r/rc-1)^2-1, f_c = (1+cos(pi r/rc))/2.
+template <int K>
+NEP_HD void basis(float r, float inv_rc, float* f) {
+    float fc2 = 0.25f * (1.0f + cospi_f(r * inv_rc));     // f_c / 2
+    float t = r * inv_rc - 1.0f;
+    float x = 2.0f * t * t - 1.0f;
+    float Tm = 1.0f, Tk = x;
+    f[0] = 2.0f * fc2;
+    if (K > 1) f[1] = (x + 1.0f) * fc2;
+#pragma unroll
+    for (int k = 2; k < K; ++k) {
+        float Tn = 2.0f * x * Tk - Tm;
+        f[k] = (Tn + 1.0f) * fc2;
+        Tm = Tk;
+        Tk = Tn;
+    }
+}
+
+// Q_k and dQ_k/dr.  T'_{k+1} = 2 T_k + 2x T'_k - T'_{k-1}.
+template <int K>
+NEP_HD void basis_d(float r, float inv_rc, float* f, float* fp) {
+    float fc2 = 0.25f * (1.0f + cospi_f(r * inv_rc));
+    float dfc2 = -0.25f * 3.14159265358979f * inv_rc * sinpi_f(r * inv_rc);
+    float t = r * inv_rc - 1.0f;
+    float x = 2.0f * t * t - 1.0f;
+    float dxdr = 4.0f * t * inv_rc;
+    float a = dxdr * fc2;
+    float Tm = 1.0f, Tk = x, dTm = 0.0f, dTk = 1.0f;
+    f[0] = 2.0f * fc2;
+    fp[0] = 2.0f * dfc2;
+    if (K > 1) {
+        f[1] = (x + 1.0f) * fc2;
+        fp[1] = a + (x + 1.0f) * dfc2;
+    }
+#pragma unroll
+    for (int k = 2; k < K; ++k) {
+        float Tn = 2.0f * x * Tk - Tm;
+        float dTn = 2.0f * Tk + 2.0f * x * dTk - dTm;
+        f[k] = (Tn + 1.0f) * fc2;
+        fp[k] = dTn * a + (Tn + 1.0f) * dfc2;
+        Tm = Tk; Tk = Tn; dTm = dTk; dTk = dTn;
+    }
+}
+
+// Weights C_lm such that sum_m C_lm P_lm(a) P_lm(b) = P_l(a.b) for unit a, b,
+// i.e. 4 pi/(2l+1) times the squared normalisation of each real harmonic.
+NEP_HD float clm(int lm) {
+    switch (lm) {
+        case 0: case 1: case 2: return 1.0f;
+        case 3: case 4: case 6: return 3.0f;
+        case 5: return 0.25f;
+        case 7: return 0.75f;
+        case 8: case 14: return 0.625f;
+        case 9: return 15.0f;
+        case 10: case 12: return 0.375f;
+        case 11: return 0.25f;
+        case 13: return 3.75f;
+        case 15: return 8.75f;
+        case 16: case 22: return 4.375f;
+        case 17: return 1.25f;
+        case 18: case 20: return 0.625f;
+        case 19: return 1.0f / 64.0f;
+        case 21: return 0.3125f;
+        default: return 35.0f / 64.0f;   // 23
+    }
+}
+NEP_HD int lm_l(int lm) { return lm < 3 ? 1 : (lm < 8 ? 2 : (lm < 15 ? 3 : 4)); }
+
+// Real solid harmonics P_lm(u) of a unit vector (homogeneous polynomials of
+// degree l evaluated on the unit sphere), order as in clm().
+NEP_HD void harmonics(float x, float y, float z, float* Y) {
+    float xx = x * x, yy = y * y, zz = z * z, xy = x * y, xz = x * z, yz = y * z;
+    Y[0] = y; Y[1] = z; Y[2] = x;
+    Y[3] = xy; Y[4] = yz; Y[5] = 3.0f * zz - 1.0f; Y[6] = xz; Y[7] = xx - yy;
+    float a5 = 5.0f * zz - 1.0f;
+    Y[8] = y * (3.0f * xx - yy);
+    Y[9] = xy * z;
+    Y[10] = y * a5;
+    Y[11] = z * (5.0f * zz - 3.0f);
+    Y[12] = x * a5;
+    Y[13] = z * (xx - yy);
+    Y[14] = x * (xx - 3.0f * yy);
+    float b7 = 7.0f * zz - 1.0f, c7 = 7.0f * zz - 3.0f;
+    Y[15] = xy * (xx - yy);
+    Y[16] = yz * (3.0f * xx - yy);
+    Y[17] = xy * b7;
+    Y[18] = yz * c7;
+    Y[19] = (35.0f * zz - 30.0f) * zz + 3.0f;
+    Y[20] = xz * c7;
+    Y[21] = (xx - yy) * b7;
+    Y[22] = xz * (xx - 3.0f * yy);
+    Y[23] = xx * (xx - 3.0f * yy) - yy * (3.0f * xx - yy);
+}
+
+// g = sum_lm a_lm grad P_lm(u) (gradient of the homogeneous polynomials).
+NEP_HD void harmonics_grad_contract(float x, float y, float z, const float* a, float& gx,
+                                    float& gy, float& gz) {
+    float xx = x * x, yy = y * y, zz = z * z, xy = x * y, xz = x * z, yz = y * z;
+    float xyz = xy * z;
+    // l = 1
+    gx = a[2];
+    gy = a[0];
+    gz = a[1];
+    // l = 2
+    gx += a[3] * y - 2.0f * a[5] * x + a[6] * z + 2.0f * a[7] * x;
+    gy += a[3] * x + a[4] * z - 2.0f * a[5] * y - 2.0f * a[7] * y;
+    gz += a[4] * y + 4.0f * a[5] * z + a[6] * x;
+    // l = 3
+    float d3 = 3.0f * (xx - yy);
+    gx += a[8] * 6.0f * xy + a[9] * yz - a[10] * 2.0f * xy - a[11] * 6.0f * xz
+          + a[12] * (4.0f * zz - 3.0f * xx - yy) + a[13] * 2.0f * xz + a[14] * d3;
+    gy += a[8] * d3 + a[9] * xz + a[10] * (4.0f * zz - xx - 3.0f * yy) - a[11] * 6.0f * yz
+          - a[12] * 2.0f * xy - a[13] * 2.0f * yz - a[14] * 6.0f * xy;
+    gz += a[9] * xy + a[10] * 8.0f * yz + a[11] * (6.0f * zz - 3.0f * xx - 3.0f * yy)
+          + a[12] * 8.0f * xz + a[13] * (xx - yy);
+    // l = 4
+    float e1 = 3.0f * xx - yy, e2 = xx - 3.0f * yy, e3 = xx + yy - 4.0f * zz;
+    gx += a[15] * y * e1 + a[16] * 6.0f * xyz - a[17] * y * (3.0f * xx + yy - 6.0f * zz)
+          - a[18] * 6.0f * xyz + a[19] * 12.0f * x * e3 - a[20] * z * (9.0f * xx + 3.0f * yy - 4.0f * zz)
+          - a[21] * 4.0f * x * (xx - 3.0f * zz) + a[22] * 3.0f * z * (xx - yy) + a[23] * 4.0f * x * e2;
+    gy += a[15] * x * e2 + a[16] * 3.0f * z * (xx - yy) - a[17] * x * (xx + 3.0f * yy - 6.0f * zz)
+          - a[18] * z * (3.0f * xx + 9.0f * yy - 4.0f * zz) + a[19] * 12.0f * y * e3
+          - a[20] * 6.0f * xyz + a[21] * 4.0f * y * (yy - 3.0f * zz) - a[22] * 6.0f * xyz
+          - a[23] * 4.0f * y * e1;
+    gz += a[16] * y * e1 + a[17] * 12.0f * xyz - a[18] * 3.0f * y * e3
+          - a[19] * 16.0f * z * (3.0f * xx + 3.0f * yy - 2.0f * zz) - a[20] * 3.0f * x * e3
+          + a[21] * 12.0f * z * (xx - yy) + a[22] * x * e2;
+}
+
+// 4-body term from the l = 2 block s[0..4] = (xy, yz, 2zz-xx-yy, xz, xx-yy)
+// sums: A = sum_j g (u u^T - I/3) is traceless symmetric with
+// A_xy = s0, A_yz = s1, A_zz = s2/3, A_xz = s3, A_xx - A_yy = s4.
+// q4 = tr(A^3); dq4/ds returned in ds.
+NEP_HD float fourbody(const float* s, float* ds) {
+    float axy = s[0], ayz = s[1], azz = s[2] * (1.0f / 3.0f), axz = s[3];
+    float axx = 0.5f * (s[4] - azz), ayy = -0.5f * (s[4] + azz);
+    // B = A^2 (symmetric)
+    float bxx = axx * axx + axy * axy + axz * axz;
+    float byy = axy * axy + ayy * ayy + ayz * ayz;
+    float bzz = axz * axz + ayz * ayz + azz * azz;
+    float bxy = axx * axy + axy * ayy + axz * ayz;
+    float bxz = axx * axz + axy * ayz + axz * azz;
+    float byz = axy * axz + ayy * ayz + ayz * azz;
+    float q4 = axx * bxx + ayy * byy + azz * bzz + 2.0f * (axy * bxy + axz * bxz + ayz * byz);
+    if (ds) {
+        ds[0] = 6.0f * bxy;
+        ds[1] = 6.0f * byz;
+        ds[2] = bzz - 0.5f * (bxx + byy);
+        ds[3] = 6.0f * bxz;
+        ds[4] = 1.5f * (bxx - byy);
+    }
+    return q4;
+}
+
+}  // namespace nep

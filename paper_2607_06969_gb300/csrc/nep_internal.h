@@ -1,0 +1,117 @@
+// Internal declarations shared by the translation units of libnep.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/nep.h"
+
+#if defined(__CUDACC__)
+#define NEP_HD __host__ __device__ __forceinline__
+#else
+#define NEP_HD inline
+#endif
+
+namespace nep {
+
+constexpr int kMaxTypes = 4;
+constexpr int kLM = 24;          // real solid harmonics for l = 1..4: 3+5+7+9
+constexpr int kChunk = 1024;     // atoms per reduction chunk (one CTA)
+constexpr int kBlock = 128;      // threads per block of the per-atom kernels
+
+// Stencil/cell plan of one configuration for the neighbour build.
+struct CellPlan {
+    int nc[3];     // cells per edge
+    int half[3];   // stencil half-width per edge
+    int base;      // first global cell id
+    int pad;
+};
+
+// Everything the per-atom kernels read or write.  All pointers are device
+// pointers (or host pointers when the same code runs in a host emulation).
+struct EvalArgs {
+    int N, B, T, H;
+    int cap, cap_ang;
+    int min_image;
+    float rc_rad, rc_ang;          // physics cutoffs
+    const float4* pos4;            // [N] x, y, z, type bits
+    const int* cfg;                // [N] configuration of each atom
+    const float* box;              // [B][3]
+    const int* cnt;                // [N]
+    const int* cnt_ang;            // [N]
+    const int* nbr;                // [cap][N]
+    const int* shift;              // [cap][N] or null
+    const int* rev;                // [cap_ang][N]
+    const float* params;           // [P] flat model parameters
+    // per-atom scratch
+    float* e_atom;                 // [N]
+    float* S;                      // [NA*24][N]
+    float* pang;                   // [NA*(4+H4)][N]  dE/dq of angular and 4-body entries
+    float* Pr;                     // [N][T][KR]      sum_n dE/dq_n cR[Zi][t][n][k]
+    float4* comp;                  // [cap_ang][N]    compacted angular pairs
+    int* cnt_comp;                 // [N]
+    float4* fin;                   // [cap_ang][N]    incoming angular pair forces
+    float* fpart;                  // [3][N]
+    float* wat;                    // [9][N]          per-atom virial
+    int* status;                   // [4] flags (may be null)
+};
+
+// Offsets of the parameter blocks in the flat vector.
+struct ParamLayout {
+    int D, P;
+    int mlp_stride;   // per type: H*D + 2H + 1
+    int off_cR, off_cA;
+};
+
+NEP_HD ParamLayout param_layout(int T, int NR, int NA, int KR, int KA, int H4, int H) {
+    ParamLayout L;
+    L.D = NR + NA * 4 + (H4 ? NA : 0);
+    L.mlp_stride = H * L.D + 2 * H + 1;
+    L.off_cR = T * L.mlp_stride;
+    L.off_cA = L.off_cR + T * T * NR * KR;
+    L.P = L.off_cA + T * T * NA * KA;
+    return L;
+}
+
+// A compiled hyper-parameter instance: launchers for its kernels.
+struct KernelSet {
+    int n_rad, n_ang, k_rad, k_ang, has_4body, n_types;
+    size_t (*smem_bytes)(int H);
+    cudaError_t (*init)(int H);   // set kernel attributes (dynamic shared memory)
+    cudaError_t (*descriptor)(const EvalArgs&, cudaStream_t);
+    cudaError_t (*force)(const EvalArgs&, cudaStream_t);
+};
+
+const KernelSet* find_kernel_set(int n_rad, int n_ang, int k_rad, int k_ang, int has_4body,
+                                 int n_types);
+
+// runtime kernels (nep_runtime.cu)
+cudaError_t launch_pack(const float* pos, const int* type, const int* atom_off, int N, int B,
+                        int T, float4* pos4, int* cfg, int* status, cudaStream_t st);
+cudaError_t launch_chunk_plan(const int* atom_off, int B, int* chunk_start, cudaStream_t st);
+cudaError_t launch_gather_reduce(const EvalArgs& a, const int* atom_off, const int* chunk_start,
+                                 int max_chunks, double* partial, float* force, float* e_out,
+                                 cudaStream_t st);
+cudaError_t launch_final_reduce(int B, const int* chunk_start, const double* partial,
+                                double* e_tot, double* virial, cudaStream_t st);
+
+struct NbrWork {
+    CellPlan* plan;        // [B]
+    int* cell_of;          // [N]
+    int* rank;             // [N]
+    int* cell_cnt;         // [Cmax]
+    int* cell_start;       // [Cmax+1]
+    int* cell_atoms;       // [N]
+    int* scan_tmp;         // [ceil(Cmax/2048)+1]
+    int cmax;
+};
+size_t nbr_cell_capacity(int N, int B);
+cudaError_t launch_neighbors(const float* pos, const int* atom_off, const float* box,
+                             const int* cfg, int N, int B, float rc_list, float rc_list_ang,
+                             int min_image, nep_nlist* nl, const NbrWork& w, cudaStream_t st);
+
+cudaError_t launch_kick(float* vel, const float* force, const int* type, const float* inv_mass,
+                        int N, float half_dt, float* pos, float dt, cudaStream_t st);
+cudaError_t launch_wrap(float* pos, const int* cfg, const float* box, int N, cudaStream_t st);
+
+}  // namespace nep

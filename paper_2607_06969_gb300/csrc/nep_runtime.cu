@@ -1,0 +1,528 @@
+// Model-independent kernels of libnep: input packing, the cell-list
+// neighbour build, the deterministic force gather with FP64 reductions, and
+// the velocity-Verlet updates.
+#include <cuda_runtime.h>
+
+#include "nep_device.cuh"
+#include "nep_internal.h"
+
+namespace nep {
+
+namespace {
+
+__device__ __forceinline__ void set_flag(int* status, int k) {
+    if (status) atomicExch(status + k, 1);
+}
+
+// binary search: largest b with off[b] <= x, for off[0..B]
+__device__ __forceinline__ int find_segment(const int* off, int B, int x) {
+    int lo = 0, hi = B;   // invariant off[lo] <= x < off[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (off[mid] <= x) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// ------------------------------------------------------------------ packing
+__global__ void k_pack(const float* __restrict__ pos, const int* __restrict__ type,
+                       const int* __restrict__ atom_off, int N, int B, int T, float4* pos4,
+                       int* cfg, int* status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int t = type[i];
+    if (t < 0 || t >= T) {
+        set_flag(status, 3);
+        t = 0;
+    }
+    const float x = pos[i], y = pos[N + i], z = pos[2 * N + i];
+    if (!(isfinite(x) && isfinite(y) && isfinite(z))) set_flag(status, 3);
+    pos4[i] = make_float4(x, y, z, __int_as_float(t));
+    cfg[i] = find_segment(atom_off, B, i);
+}
+
+// exclusive scan of per-configuration chunk counts (one CTA)
+__global__ void k_chunk_plan(const int* __restrict__ atom_off, int B, int* chunk_start) {
+    __shared__ int carry;
+    __shared__ int warp_sums[32];
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < B; base += blockDim.x) {
+        const int b = base + threadIdx.x;
+        int v = 0;
+        if (b < B) {
+            const int n = atom_off[b + 1] - atom_off[b];
+            v = (n + kChunk - 1) / kChunk;
+        }
+        // block inclusive scan
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        int x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_sums[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int s = (lane < (int)(blockDim.x >> 5)) ? warp_sums[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += y;
+            }
+            warp_sums[lane] = s;
+        }
+        __syncthreads();
+        const int incl = x + (w > 0 ? warp_sums[w - 1] : 0);
+        if (b < B) chunk_start[b] = carry + incl - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry += incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) chunk_start[B] = carry;
+}
+
+// --------------------------------------------------- gather + FP64 partials
+constexpr int kRedThreads = 256;
+
+__global__ void __launch_bounds__(kRedThreads) k_gather_reduce(
+    const EvalArgs a, const int* __restrict__ atom_off, const int* __restrict__ chunk_start,
+    double* __restrict__ partial, float* __restrict__ force, float* __restrict__ e_out) {
+    const int k = blockIdx.x;
+    const int B = a.B, N = a.N;
+    const int total = chunk_start[B];
+    if (k >= total) return;
+    const int b = find_segment(chunk_start, B, k);
+    const int a0 = atom_off[b] + (k - chunk_start[b]) * kChunk;
+    const int a1 = min(atom_off[b + 1], a0 + kChunk);
+    double acc[10];
+#pragma unroll
+    for (int c = 0; c < 10; ++c) acc[c] = 0.0;
+    for (int i = a0 + threadIdx.x; i < a1; i += kRedThreads) {
+        float fx = a.fpart[i], fy = a.fpart[N + i], fz = a.fpart[2 * N + i];
+        const int na = a.cnt_ang[i];
+        for (int s = 0; s < na; ++s) {
+            const float4 g = a.fin[(size_t)s * N + i];
+            fx -= g.x; fy -= g.y; fz -= g.z;
+        }
+        force[i] = fx;
+        force[N + i] = fy;
+        force[2 * N + i] = fz;
+        const float e = a.e_atom[i];
+        if (e_out) e_out[i] = e;
+        acc[0] += (double)e;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) acc[1 + c] += (double)a.wat[(size_t)c * N + i];
+    }
+    __shared__ double red[kRedThreads];
+    for (int c = 0; c < 10; ++c) {
+        red[threadIdx.x] = acc[c];
+        __syncthreads();
+        for (int o = kRedThreads / 2; o > 0; o >>= 1) {
+            if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) partial[(size_t)k * 10 + c] = red[0];
+        __syncthreads();
+    }
+}
+
+__global__ void k_final_reduce(int B, const int* __restrict__ chunk_start,
+                               const double* __restrict__ partial, double* e_tot, double* virial) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    double acc[10];
+    for (int c = 0; c < 10; ++c) acc[c] = 0.0;
+    for (int k = chunk_start[b]; k < chunk_start[b + 1]; ++k)
+        for (int c = 0; c < 10; ++c) acc[c] += partial[(size_t)k * 10 + c];
+    if (e_tot) e_tot[b] = acc[0];
+    if (virial)
+        for (int c = 0; c < 9; ++c) virial[(size_t)b * 9 + c] = acc[1 + c];
+}
+
+// ------------------------------------------------------- neighbour build
+// Cells per edge: floor(L / (rc + 1e-3)) (at least 1), reduced while the cell
+// count of a configuration exceeds 2 N_b + 27.  The stencil half-width is the
+// number of cells needed to reach rc + 1e-3 (1 unless a cell is shorter than
+// the cutoff).  An atom in cell c sees cells c + d, d in [-half, half], with
+// image shift floor((c + d) / nc): every (j, image) within the cutoff is
+// visited exactly once.
+constexpr float kCellMargin = 1e-3f;
+
+__global__ void k_cell_plan(const float* __restrict__ box, const int* __restrict__ atom_off, int B,
+                            float rc, CellPlan* plan, int* status) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const int nb = atom_off[b + 1] - atom_off[b];
+    float L[3] = {box[3 * b], box[3 * b + 1], box[3 * b + 2]};
+    int nc[3];
+    for (int d = 0; d < 3; ++d) {
+        if (!(L[d] > 0.0f) || !isfinite(L[d])) {
+            set_flag(status, 3);
+            L[d] = 1.0f;
+        }
+        const float r = floorf(L[d] / (rc + kCellMargin));
+        nc[d] = r < 1.0f ? 1 : (r > 1024.0f ? 1024 : (int)r);
+    }
+    const long long cap = 2LL * nb + 27;
+    while ((long long)nc[0] * nc[1] * nc[2] > cap) {
+        int m = 0;
+        if (nc[1] > nc[m]) m = 1;
+        if (nc[2] > nc[m]) m = 2;
+        nc[m] -= 1;
+    }
+    CellPlan p;
+    for (int d = 0; d < 3; ++d) {
+        p.nc[d] = nc[d];
+        const float cs = L[d] / (float)nc[d];
+        p.half[d] = (int)ceilf((rc + kCellMargin) / cs);
+        if (p.half[d] < 1) p.half[d] = 1;
+    }
+    p.base = nc[0] * nc[1] * nc[2];   // count here, prefix in k_plan_scan
+    p.pad = 0;
+    plan[b] = p;
+}
+
+__global__ void k_plan_scan(CellPlan* plan, int B) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int acc = 0;
+    for (int b = 0; b < B; ++b) {
+        const int c = plan[b].base;
+        plan[b].base = acc;
+        acc += c;
+    }
+}
+
+__device__ __forceinline__ void cell_coords(const CellPlan& p, float x, float y, float z,
+                                            const float* L, int* c) {
+    const float v[3] = {x, y, z};
+    for (int d = 0; d < 3; ++d) {
+        int ci = (int)(v[d] * ((float)p.nc[d] / L[d]));
+        ci = ci < 0 ? 0 : (ci >= p.nc[d] ? p.nc[d] - 1 : ci);
+        c[d] = ci;
+    }
+}
+
+__global__ void k_bin(const float* __restrict__ pos, const int* __restrict__ cfg,
+                      const float* __restrict__ box, const CellPlan* __restrict__ plan, int N,
+                      int* cell_of, int* rank, int* cell_cnt, int* status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int b = cfg[i];
+    const CellPlan p = plan[b];
+    const float L[3] = {box[3 * b], box[3 * b + 1], box[3 * b + 2]};
+    const float x = pos[i], y = pos[N + i], z = pos[2 * N + i];
+    if (!(x >= 0.0f && x < L[0] && y >= 0.0f && y < L[1] && z >= 0.0f && z < L[2]))
+        set_flag(status, 3);
+    int c[3];
+    cell_coords(p, x, y, z, L, c);
+    const int id = p.base + (c[0] * p.nc[1] + c[1]) * p.nc[2] + c[2];
+    cell_of[i] = id;
+    rank[i] = atomicAdd(cell_cnt + id, 1);
+}
+
+// exclusive scan in tiles of 2048 (1024 threads x 2)
+constexpr int kScanTile = 2048;
+
+__device__ int block_excl_scan_1024(int v, int* warp_sums, int* total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int s = warp_sums[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        warp_sums[lane] = s;
+    }
+    __syncthreads();
+    const int incl = x + (w > 0 ? warp_sums[w - 1] : 0);
+    *total = warp_sums[31];
+    __syncthreads();
+    return incl - v;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_tiles(const int* __restrict__ in, int n,
+                                                     int* __restrict__ out, int* tile_sum) {
+    __shared__ int ws[32];
+    const int base = blockIdx.x * kScanTile;
+    const int i0 = base + 2 * threadIdx.x;
+    const int v0 = i0 < n ? in[i0] : 0;
+    const int v1 = i0 + 1 < n ? in[i0 + 1] : 0;
+    int total;
+    const int ex = block_excl_scan_1024(v0 + v1, ws, &total);
+    if (i0 < n) out[i0] = ex;
+    if (i0 + 1 < n) out[i0 + 1] = ex + v0;
+    if (threadIdx.x == 0) tile_sum[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_sums(int* tile_sum, int ntiles, int* grand) {
+    __shared__ int ws[32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < ntiles; base += 1024) {
+        const int t = base + threadIdx.x;
+        const int v = t < ntiles ? tile_sum[t] : 0;
+        int total;
+        const int ex = block_excl_scan_1024(v, ws, &total);
+        if (t < ntiles) tile_sum[t] = carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *grand = carry;
+}
+
+__global__ void k_scan_add(int* out, int n, const int* tile_sum) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += tile_sum[i / kScanTile];
+}
+
+__global__ void k_fill(const int* __restrict__ cell_of, const int* __restrict__ rank,
+                       const int* __restrict__ cell_start, int N, int* cell_atoms) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    cell_atoms[cell_start[cell_of[i]] + rank[i]] = i;
+}
+
+// order each cell's atoms by index so that lists do not depend on the order
+// in which atomics handed out ranks
+__global__ void k_sort_cells(const int* __restrict__ cell_start, int ncell, int* cell_atoms) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    const int s0 = cell_start[c], s1 = cell_start[c + 1];
+    for (int a = s0 + 1; a < s1; ++a) {
+        const int v = cell_atoms[a];
+        int b = a - 1;
+        while (b >= s0 && cell_atoms[b] > v) {
+            cell_atoms[b + 1] = cell_atoms[b];
+            --b;
+        }
+        cell_atoms[b + 1] = v;
+    }
+}
+
+__device__ __forceinline__ int floor_div(int a, int b) {
+    int q = a / b;
+    if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
+    return q;
+}
+
+__global__ void __launch_bounds__(128) k_build(const float* __restrict__ pos,
+                                               const int* __restrict__ cfg,
+                                               const float* __restrict__ box,
+                                               const CellPlan* __restrict__ plan,
+                                               const int* __restrict__ cell_of,
+                                               const int* __restrict__ cell_start,
+                                               const int* __restrict__ cell_atoms, int N,
+                                               float rc2_rad, float rc2_ang, nep_nlist nl) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int b = cfg[i];
+    const CellPlan p = plan[b];
+    const float L[3] = {box[3 * b], box[3 * b + 1], box[3 * b + 2]};
+    const float xi = pos[i], yi = pos[N + i], zi = pos[2 * N + i];
+    int c = cell_of[i] - p.base;
+    const int cz = c % p.nc[2];
+    c /= p.nc[2];
+    const int cy = c % p.nc[1];
+    const int cx = c / p.nc[1];
+    // pass 0 writes the angular candidates (d < rc_ang + skin) into the list
+    // prefix, pass 1 appends the remaining radial ones
+    int n_ang = 0, n_rest = 0;
+    int slot = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int ox = -p.half[0]; ox <= p.half[0]; ++ox) {
+            const int ux = cx + ox, sx = floor_div(ux, p.nc[0]), wx = ux - sx * p.nc[0];
+            for (int oy = -p.half[1]; oy <= p.half[1]; ++oy) {
+                const int uy = cy + oy, sy = floor_div(uy, p.nc[1]), wy = uy - sy * p.nc[1];
+                for (int oz = -p.half[2]; oz <= p.half[2]; ++oz) {
+                    const int uz = cz + oz, sz = floor_div(uz, p.nc[2]), wz = uz - sz * p.nc[2];
+                    const int cell = p.base + (wx * p.nc[1] + wy) * p.nc[2] + wz;
+                    const float fx = mul_rn((float)sx, L[0]);
+                    const float fy = mul_rn((float)sy, L[1]);
+                    const float fz = mul_rn((float)sz, L[2]);
+                    const bool zero_img = (sx == 0 && sy == 0 && sz == 0);
+                    for (int q = cell_start[cell]; q < cell_start[cell + 1]; ++q) {
+                        const int j = cell_atoms[q];
+                        if (j == i && zero_img) continue;
+                        const float dx = add_rn(sub_rn(pos[j], xi), fx);
+                        const float dy = add_rn(sub_rn(pos[N + j], yi), fy);
+                        const float dz = add_rn(sub_rn(pos[2 * N + j], zi), fz);
+                        const float d2 = dist2(dx, dy, dz);
+                        bool take;
+                        if (pass == 0) {
+                            take = d2 < rc2_ang;
+                            if (take) {
+                                ++n_ang;
+                                if (n_ang > nl.cap_ang) take = false;
+                            }
+                        } else {
+                            take = d2 >= rc2_ang && d2 < rc2_rad;
+                            if (take) {
+                                ++n_rest;
+                                if (slot >= nl.cap) take = false;
+                            }
+                        }
+                        if (!take) continue;
+                        nl.nbr[(size_t)slot * N + i] = j;
+                        if (nl.shift) nl.shift[(size_t)slot * N + i] = pack_shift(sx, sy, sz);
+                        ++slot;
+                    }
+                }
+            }
+        }
+    }
+    const int n_total = n_ang + n_rest;
+    if (n_total > nl.cap || n_ang > nl.cap_ang) {
+        set_flag(nl.status, 0);
+        atomicMax(nl.status + 1, n_total);
+        atomicMax(nl.status + 2, n_ang);
+    }
+    nl.cnt[i] = slot;
+    nl.cnt_ang[i] = min(n_ang, nl.cap_ang);
+}
+
+__global__ void k_rev(int N, nep_nlist nl) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int na = nl.cnt_ang[i];
+    for (int s = 0; s < na; ++s) {
+        const int j = nl.nbr[(size_t)s * N + i];
+        int want = 0;
+        if (nl.shift) {
+            int a, b, c;
+            unpack_shift(nl.shift[(size_t)s * N + i], a, b, c);
+            want = pack_shift(-a, -b, -c);
+        }
+        const int nj = nl.cnt_ang[j];
+        int found = -1;
+        for (int t = 0; t < nj; ++t) {
+            if (nl.nbr[(size_t)t * N + j] == i &&
+                (!nl.shift || nl.shift[(size_t)t * N + j] == want)) {
+                found = t;
+                break;
+            }
+        }
+        if (found < 0) {
+            set_flag(nl.status, 0);
+            found = 0;
+        }
+        nl.rev[(size_t)s * N + i] = found;
+    }
+}
+
+// ------------------------------------------------------------ integrator
+struct InvMass {
+    float v[kMaxTypes];
+};
+
+__global__ void k_kick(float* __restrict__ vel, const float* __restrict__ force,
+                       const int* __restrict__ type, InvMass im, int N, float half_dt,
+                       float* __restrict__ pos, float dt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float s = half_dt * im.v[type[i] & (kMaxTypes - 1)];
+    for (int d = 0; d < 3; ++d) {
+        float v = vel[(size_t)d * N + i] + s * force[(size_t)d * N + i];
+        vel[(size_t)d * N + i] = v;
+        if (pos) pos[(size_t)d * N + i] += dt * v;
+    }
+}
+
+__global__ void k_wrap(float* pos, const int* __restrict__ cfg, const float* __restrict__ box,
+                       int N) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int b = cfg[i];
+    for (int d = 0; d < 3; ++d) {
+        const float L = box[3 * b + d];
+        float x = pos[(size_t)d * N + i];
+        x = x - L * floorf(x / L);
+        if (x >= L) x -= L;
+        if (x < 0.0f) x += L;
+        if (!(x < L)) x = 0.0f;
+        pos[(size_t)d * N + i] = x;
+    }
+}
+
+inline int blocks(int n, int t) { return (n + t - 1) / t; }
+
+}  // namespace
+
+// ------------------------------------------------------------ launchers
+cudaError_t launch_pack(const float* pos, const int* type, const int* atom_off, int N, int B,
+                        int T, float4* pos4, int* cfg, int* status, cudaStream_t st) {
+    if (N > 0) k_pack<<<blocks(N, 256), 256, 0, st>>>(pos, type, atom_off, N, B, T, pos4, cfg, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_chunk_plan(const int* atom_off, int B, int* chunk_start, cudaStream_t st) {
+    k_chunk_plan<<<1, 1024, 0, st>>>(atom_off, B, chunk_start);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_reduce(const EvalArgs& a, const int* atom_off, const int* chunk_start,
+                                 int max_chunks, double* partial, float* force, float* e_out,
+                                 cudaStream_t st) {
+    if (max_chunks > 0)
+        k_gather_reduce<<<max_chunks, kRedThreads, 0, st>>>(a, atom_off, chunk_start, partial, force,
+                                                            e_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_final_reduce(int B, const int* chunk_start, const double* partial,
+                                double* e_tot, double* virial, cudaStream_t st) {
+    if (B > 0) k_final_reduce<<<blocks(B, 128), 128, 0, st>>>(B, chunk_start, partial, e_tot, virial);
+    return cudaGetLastError();
+}
+
+size_t nbr_cell_capacity(int N, int B) { return 2 * (size_t)N + 27 * (size_t)B; }
+
+cudaError_t launch_neighbors(const float* pos, const int* atom_off, const float* box,
+                             const int* cfg, int N, int B, float rc_list, float rc_list_ang,
+                             int min_image, nep_nlist* nl, const NbrWork& w, cudaStream_t st) {
+    cudaError_t e;
+    (void)min_image;
+    if (N == 0) return cudaSuccess;
+    const int cmax = w.cmax;
+    k_cell_plan<<<blocks(B, 128), 128, 0, st>>>(box, atom_off, B, rc_list, w.plan, nl->status);
+    k_plan_scan<<<1, 32, 0, st>>>(w.plan, B);
+    if ((e = cudaMemsetAsync(w.cell_cnt, 0, sizeof(int) * (size_t)(cmax + 1), st)) != cudaSuccess)
+        return e;
+    k_bin<<<blocks(N, 256), 256, 0, st>>>(pos, cfg, box, w.plan, N, w.cell_of, w.rank, w.cell_cnt,
+                                          nl->status);
+    const int n = cmax + 1;
+    const int ntiles = blocks(n, kScanTile);
+    k_scan_tiles<<<ntiles, 1024, 0, st>>>(w.cell_cnt, n, w.cell_start, w.scan_tmp);
+    k_scan_sums<<<1, 1024, 0, st>>>(w.scan_tmp, ntiles, w.scan_tmp + ntiles);
+    k_scan_add<<<blocks(n, 256), 256, 0, st>>>(w.cell_start, n, w.scan_tmp);
+    k_fill<<<blocks(N, 256), 256, 0, st>>>(w.cell_of, w.rank, w.cell_start, N, w.cell_atoms);
+    k_sort_cells<<<blocks(cmax, 128), 128, 0, st>>>(w.cell_start, cmax, w.cell_atoms);
+    const float rr = rc_list * rc_list, ra = rc_list_ang * rc_list_ang;
+    k_build<<<blocks(N, 128), 128, 0, st>>>(pos, cfg, box, w.plan, w.cell_of, w.cell_start,
+                                            w.cell_atoms, N, rr, ra, *nl);
+    k_rev<<<blocks(N, 128), 128, 0, st>>>(N, *nl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kick(float* vel, const float* force, const int* type, const float* inv_mass,
+                        int N, float half_dt, float* pos, float dt, cudaStream_t st) {
+    InvMass im;
+    for (int t = 0; t < kMaxTypes; ++t) im.v[t] = inv_mass[t];
+    if (N > 0) k_kick<<<blocks(N, 256), 256, 0, st>>>(vel, force, type, im, N, half_dt, pos, dt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wrap(float* pos, const int* cfg, const float* box, int N, cudaStream_t st) {
+    if (N > 0) k_wrap<<<blocks(N, 256), 256, 0, st>>>(pos, cfg, box, N);
+    return cudaGetLastError();
+}
+
+}  // namespace nep

@@ -1,0 +1,59 @@
+"""The C ABI library builds, loads without a GPU, and exports every entry
+point include/nep.h declares; host-side argument checks need no GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from oracle import nep_oracle as O
+from paper_2607_06969_gb300 import binding as nb
+from paper_2607_06969_gb300 import build as B
+from paper_2607_06969_gb300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    B.build()
+    return nb.lib()
+
+
+def header_functions():
+    txt = open(os.path.join(ROOT, "include", "nep.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    txt = re.sub(r"//[^\n]*", "", txt)
+    return set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_]\w*\s*\**\s*(nep_\w+)\s*\(", txt, flags=re.M))
+
+
+def test_header_and_binding_agree():
+    assert header_functions() == set(nb.ENTRY_POINTS)
+
+
+def test_library_exports_every_declared_symbol(L):
+    for name in header_functions():
+        assert hasattr(L, name), name
+    assert L.nep_version().decode().startswith("libnep")
+
+
+@pytest.mark.parametrize("hyp", [I.HYPER_SMALL, I.HYPER_LARGE, I.HYPER_TABLE2,
+                                 I.Hyper(n_rad=3, n_ang=2, k_rad=4, k_ang=3, n_hidden=4)])
+def test_num_params_matches_oracle(L, hyp):
+    assert nb.num_params(hyp) == O.param_count(hyp)
+    hp = nb.hparams_of(hyp)
+    assert L.nep_supported(ctypes.byref(hp)) == 1
+
+
+def test_create_rejects_bad_arguments_before_touching_the_gpu(L):
+    bad = nb.hparams_of(I.HYPER_SMALL)
+    bad.l_max = 3
+    out = ctypes.c_void_p()
+    assert L.nep_create(ctypes.byref(bad), None, 0, ctypes.byref(out)) == nb.NEP_ERR_ARG
+    assert "l_max" in nb.last_error()
+    uns = nb.hparams_of(I.Hyper(n_rad=5))
+    assert L.nep_supported(ctypes.byref(uns)) == 0
+    assert L.nep_create(ctypes.byref(uns), None, 0, ctypes.byref(out)) == nb.NEP_ERR_UNSUPPORTED
+    ok = nb.hparams_of(I.HYPER_SMALL)
+    assert L.nep_create(ctypes.byref(ok), None, 3, ctypes.byref(out)) == nb.NEP_ERR_ARG
+    assert L.nep_num_params(ctypes.byref(bad)) == 0
