@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncell", type=int, default=50,
+                    help="rock-salt cells per edge (50 = the 900k-atom workload; smaller for profiling)")
     return ap.parse_args()
 
 
@@ -117,9 +119,9 @@ def algorithmic_flops(h, nbar_rad: float, nbar_ang: float) -> dict:
 
 
 def launches_per_step(rebuild: bool) -> int:
-    # kick, [pack, wrap, cell plan, plan scan, bin, 3 scan, fill, sort, build, rev],
+    # kick, [pack, wrap, pack, cell plan, plan scan, bin, 3 scan, fill, sort, build, rev],
     # pack, chunk plan, descriptor, force, gather, final reduce, kick
-    return 8 + (12 if rebuild else 0)
+    return 8 + (13 if rebuild else 0)
 
 
 # --------------------------------------------------------------- cpu legs
@@ -198,7 +200,10 @@ def main():
     from paper_2607_06969_gb300 import binding as nb
     from paper_2607_06969_gb300 import inputs as I
 
-    s, h = I.workload_md900k()
+    if args.ncell == 50:
+        s, h = I.workload_md900k()
+    else:
+        s, h = I.rocksalt(args.ncell, vacancy=0.2, tag=1), I.HYPER_SMALL
     N = s.n_atoms
     theta = I.init_params(h).astype(np.float32)
     vel0 = I.maxwell_boltzmann(s.types, 900.0).astype(np.float32)
@@ -263,6 +268,10 @@ def main():
     # capture the K timed steps, with events around the two pair kernels of every step
     K = args.steps
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    for trio in evs:            # torch creates the underlying cudaEvent on first record
+        for e in trio:
+            e.record(stream)
+    stream.synchronize()
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=stream):
         for k in range(K):

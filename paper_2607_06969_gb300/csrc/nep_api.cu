@@ -206,11 +206,11 @@ nep_status efv_impl(nep_model* m, const nep_system* s, const nep_nlist* nl, floa
     const nep::EvalArgs a = make_args(m, s, nl, work, w);
     const int nt = m->n_timing;
     m->n_timing = 0;
-    if (nt == 3) NEP_CUDA(cudaEventRecord(m->timing[0], st), "timing event");
+    if (nt == 3) NEP_CUDA(cudaEventRecordWithFlags(m->timing[0], st, cudaEventRecordExternal), "timing event");
     if (N > 0) NEP_CUDA(m->ks->descriptor(a, st), "descriptor kernel");
-    if (nt == 3) NEP_CUDA(cudaEventRecord(m->timing[1], st), "timing event");
+    if (nt == 3) NEP_CUDA(cudaEventRecordWithFlags(m->timing[1], st, cudaEventRecordExternal), "timing event");
     if (N > 0) NEP_CUDA(m->ks->force(a, st), "force kernel");
-    if (nt == 3) NEP_CUDA(cudaEventRecord(m->timing[2], st), "timing event");
+    if (nt == 3) NEP_CUDA(cudaEventRecordWithFlags(m->timing[2], st, cudaEventRecordExternal), "timing event");
     NEP_CUDA(nep::launch_gather_reduce(a, s->atom_off, at<int>(work, w.chunk_start), w.max_chunks,
                                        at<double>(work, w.partial), force, e_atom, st),
              "gather");

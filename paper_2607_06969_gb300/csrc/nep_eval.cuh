@@ -12,6 +12,14 @@
 
 namespace nep {
 
+// Keeps the compiler from hoisting every shared-memory load of a fully
+// unrolled contraction ahead of its FMAs (which costs registers and spills).
+#if defined(__CUDA_ARCH__)
+#define NEP_SCHED_BARRIER() asm volatile("" ::: "memory")
+#else
+#define NEP_SCHED_BARRIER() ((void)0)
+#endif
+
 NEP_HD constexpr int odd_up(int x) { return (x % 2) ? x : x + 1; }
 NEP_HD int stride_1mod32(int x) { return x + ((33 - (x % 32)) % 32); }
 
@@ -158,6 +166,7 @@ NEP_HD void desc_atom(const EvalArgs& a, const float* sm, int i) {
             for (int k = 0; k < KR; ++k) acc = fmaf(c[k], fb[t][k], acc);
         }
         q[n] = acc;
+        NEP_SCHED_BARRIER();
     }
 
     // angular: S_nlm = sum_j g_n(r_ij) P_lm(rhat_ij)
@@ -235,6 +244,7 @@ NEP_HD void desc_atom(const EvalArgs& a, const float* sm, int i) {
 #pragma unroll
             for (int n = 0; n < NR; ++n) acc = fmaf(p[n], c[n * KR + k], acc);
             a.Pr[(i * T + t) * KR + k] = acc;
+            NEP_SCHED_BARRIER();
         }
     }
 }

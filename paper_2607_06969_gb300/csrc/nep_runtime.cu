@@ -126,17 +126,36 @@ __global__ void __launch_bounds__(kRedThreads) k_gather_reduce(
     }
 }
 
-__global__ void k_final_reduce(int B, const int* __restrict__ chunk_start,
-                               const double* __restrict__ partial, double* e_tot, double* virial) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+// one block per configuration: threads take chunk partials k = t, t+256, ...
+// and a fixed tree combines them, so the sum order never changes
+__global__ void __launch_bounds__(kRedThreads) k_final_reduce(int B, const int* __restrict__ chunk_start,
+                                                              const double* __restrict__ partial,
+                                                              double* e_tot, double* virial) {
+    const int b = blockIdx.x;
     if (b >= B) return;
     double acc[10];
+#pragma unroll
     for (int c = 0; c < 10; ++c) acc[c] = 0.0;
-    for (int k = chunk_start[b]; k < chunk_start[b + 1]; ++k)
+    for (int k = chunk_start[b] + threadIdx.x; k < chunk_start[b + 1]; k += kRedThreads)
+#pragma unroll
         for (int c = 0; c < 10; ++c) acc[c] += partial[(size_t)k * 10 + c];
-    if (e_tot) e_tot[b] = acc[0];
-    if (virial)
-        for (int c = 0; c < 9; ++c) virial[(size_t)b * 9 + c] = acc[1 + c];
+    __shared__ double red[kRedThreads];
+    for (int c = 0; c < 10; ++c) {
+        red[threadIdx.x] = acc[c];
+        __syncthreads();
+        for (int o = kRedThreads / 2; o > 0; o >>= 1) {
+            if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            if (c == 0) {
+                if (e_tot) e_tot[b] = red[0];
+            } else if (virial) {
+                virial[(size_t)b * 9 + c - 1] = red[0];
+            }
+        }
+        __syncthreads();
+    }
 }
 
 // ------------------------------------------------------- neighbour build
@@ -479,7 +498,7 @@ cudaError_t launch_gather_reduce(const EvalArgs& a, const int* atom_off, const i
 
 cudaError_t launch_final_reduce(int B, const int* chunk_start, const double* partial,
                                 double* e_tot, double* virial, cudaStream_t st) {
-    if (B > 0) k_final_reduce<<<blocks(B, 128), 128, 0, st>>>(B, chunk_start, partial, e_tot, virial);
+    if (B > 0) k_final_reduce<<<B, kRedThreads, 0, st>>>(B, chunk_start, partial, e_tot, virial);
     return cudaGetLastError();
 }
 
