@@ -12,7 +12,7 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libnep.so")
+LIB_PATH = os.environ.get("NEP_LIB_PATH") or os.path.join(HERE, "libnep.so")
 
 NEP_OK, NEP_ERR_ARG, NEP_ERR_CUDA, NEP_ERR_NOMEM, NEP_ERR_CAPACITY, NEP_ERR_TIMEOUT, \
     NEP_ERR_STATE, NEP_ERR_UNSUPPORTED, NEP_ERR_INPUT = range(9)

@@ -59,14 +59,14 @@ size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Byte offsets of the scratch arrays inside the caller's workspace.
 struct WsLayout {
-    size_t pos4, cfg, e_atom, S, pang, Pr, comp, cnt_comp, fin, fpart, wat, chunk_start, partial;
+    size_t pos4, cfg, e_atom, S, pang, Pr, comp, cnt_comp, compr, cnt_compr, fin, fpart, wat, chunk_start,
+        partial;
     size_t plan, cell_of, rank, cell_cnt, cell_start, cell_atoms, scan_tmp;
     size_t total;
     int max_chunks, cmax;
 };
 
 WsLayout ws_layout(const nep_model* m, int N, int B, int cap, int cap_ang) {
-    (void)cap;
     WsLayout w;
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -85,6 +85,8 @@ WsLayout ws_layout(const nep_model* m, int N, int B, int cap, int cap_ang) {
     w.Pr = take(4 * n * T * KR);
     w.comp = take(16 * n * cap_ang);
     w.cnt_comp = take(4 * n);
+    w.compr = take(16 * n * cap);
+    w.cnt_compr = take(4 * n);
     w.fin = take(16 * n * cap_ang);
     w.fpart = take(12 * n);
     w.wat = take(36 * n);
@@ -177,6 +179,8 @@ nep::EvalArgs make_args(const nep_model* m, const nep_system* s, const nep_nlist
     a.Pr = at<float>(work, w.Pr);
     a.comp = at<float4>(work, w.comp);
     a.cnt_comp = at<int>(work, w.cnt_comp);
+    a.compr = at<float4>(work, w.compr);
+    a.cnt_compr = at<int>(work, w.cnt_compr);
     a.fin = at<float4>(work, w.fin);
     a.fpart = at<float>(work, w.fpart);
     a.wat = at<float>(work, w.wat);
@@ -206,11 +210,16 @@ nep_status efv_impl(nep_model* m, const nep_system* s, const nep_nlist* nl, floa
     const nep::EvalArgs a = make_args(m, s, nl, work, w);
     const int nt = m->n_timing;
     m->n_timing = 0;
-    if (nt == 3) NEP_CUDA(cudaEventRecordWithFlags(m->timing[0], st, cudaEventRecordExternal), "timing event");
+    // inside stream capture an event record must be marked external to become
+    // a timing node of the graph; outside capture the flag is not accepted
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (nt == 3) NEP_CUDA(cudaStreamIsCapturing(st, &cap), "capture status");
+    const unsigned rec_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
+    if (nt == 3) NEP_CUDA(cudaEventRecordWithFlags(m->timing[0], st, rec_flags), "timing event");
     if (N > 0) NEP_CUDA(m->ks->descriptor(a, st), "descriptor kernel");
-    if (nt == 3) NEP_CUDA(cudaEventRecordWithFlags(m->timing[1], st, cudaEventRecordExternal), "timing event");
+    if (nt == 3) NEP_CUDA(cudaEventRecordWithFlags(m->timing[1], st, rec_flags), "timing event");
     if (N > 0) NEP_CUDA(m->ks->force(a, st), "force kernel");
-    if (nt == 3) NEP_CUDA(cudaEventRecordWithFlags(m->timing[2], st, cudaEventRecordExternal), "timing event");
+    if (nt == 3) NEP_CUDA(cudaEventRecordWithFlags(m->timing[2], st, rec_flags), "timing event");
     NEP_CUDA(nep::launch_gather_reduce(a, s->atom_off, at<int>(work, w.chunk_start), w.max_chunks,
                                        at<double>(work, w.partial), force, e_atom, st),
              "gather");
@@ -246,7 +255,7 @@ nep_status neighbors_impl(nep_model* m, const nep_system* s, float skin, nep_nli
     nw.cmax = w.cmax;
     nep_nlist copy = *nl;
     if (mi) copy.shift = nullptr;
-    NEP_CUDA(nep::launch_neighbors(s->pos, s->atom_off, s->box, at<int>(work, w.cfg), N, B, rc_list,
+    NEP_CUDA(nep::launch_neighbors(s->pos, at<float4>(work, w.pos4), s->atom_off, s->box, at<int>(work, w.cfg), N, B, rc_list,
                                    rc_list_ang, mi ? 1 : 0, &copy, nw, st),
              "neighbour build");
     return NEP_OK;

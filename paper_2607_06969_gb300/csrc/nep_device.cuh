@@ -49,6 +49,22 @@ NEP_HD float sinpi_f(float x) {
     return (float)std::sin(3.14159265358979323846 * (double)x);
 #endif
 }
+NEP_HD void sincospi_f(float x, float* s, float* c) {
+#if defined(__CUDA_ARCH__)
+    sincospif(x, s, c);
+#else
+    *s = (float)std::sin(3.14159265358979323846 * (double)x);
+    *c = (float)std::cos(3.14159265358979323846 * (double)x);
+#endif
+}
+// correctly rounded reciprocal
+NEP_HD float rcp_f(float x) {
+#if defined(__CUDA_ARCH__)
+    return __frcp_rn(x);
+#else
+    return 1.0f / x;
+#endif
+}
 NEP_HD float tanh_f(float x) {
 #if defined(__CUDA_ARCH__)
     return tanhf(x);
@@ -141,8 +157,10 @@ NEP_HD void basis(float r, float inv_rc, float* f) {
 // Q_k and dQ_k/dr.  T'_{k+1} = 2 T_k + 2x T'_k - T'_{k-1}.
 template <int K>
 NEP_HD void basis_d(float r, float inv_rc, float* f, float* fp) {
-    float fc2 = 0.25f * (1.0f + cospi_f(r * inv_rc));
-    float dfc2 = -0.25f * 3.14159265358979f * inv_rc * sinpi_f(r * inv_rc);
+    float sp, cp;
+    sincospi_f(r * inv_rc, &sp, &cp);
+    float fc2 = 0.25f * (1.0f + cp);
+    float dfc2 = (-0.25f * 3.14159265358979f) * inv_rc * sp;
     float t = r * inv_rc - 1.0f;
     float x = 2.0f * t * t - 1.0f;
     float dxdr = 4.0f * t * inv_rc;
@@ -212,6 +230,50 @@ NEP_HD void harmonics(float x, float y, float z, float* Y) {
     Y[21] = (xx - yy) * b7;
     Y[22] = xz * (xx - 3.0f * yy);
     Y[23] = xx * (xx - 3.0f * yy) - yy * (3.0f * xx - yy);
+}
+
+// Component m of the real solid harmonics: value P_m(u) on the unit sphere
+// and the gradient of the homogeneous polynomial at u.  With m a
+// compile-time constant the switch folds away.
+struct HarmTerms {
+    float x, y, z, xx, yy, zz, xy, xz, yz;
+};
+NEP_HD HarmTerms harm_terms(float x, float y, float z) {
+    HarmTerms t;
+    t.x = x; t.y = y; t.z = z;
+    t.xx = x * x; t.yy = y * y; t.zz = z * z;
+    t.xy = x * y; t.xz = x * z; t.yz = y * z;
+    return t;
+}
+NEP_HD void harm_m(int m, const HarmTerms& t, float& Y, float& gx, float& gy, float& gz) {
+    const float x = t.x, y = t.y, z = t.z, xx = t.xx, yy = t.yy, zz = t.zz;
+    const float xy = t.xy, xz = t.xz, yz = t.yz;
+    switch (m) {
+        case 0: Y = y; gx = 0.0f; gy = 1.0f; gz = 0.0f; break;
+        case 1: Y = z; gx = 0.0f; gy = 0.0f; gz = 1.0f; break;
+        case 2: Y = x; gx = 1.0f; gy = 0.0f; gz = 0.0f; break;
+        case 3: Y = xy; gx = y; gy = x; gz = 0.0f; break;
+        case 4: Y = yz; gx = 0.0f; gy = z; gz = y; break;
+        case 5: Y = 3.0f * zz - 1.0f; gx = -2.0f * x; gy = -2.0f * y; gz = 4.0f * z; break;
+        case 6: Y = xz; gx = z; gy = 0.0f; gz = x; break;
+        case 7: Y = xx - yy; gx = 2.0f * x; gy = -2.0f * y; gz = 0.0f; break;
+        case 8: Y = y * (3.0f * xx - yy); gx = 6.0f * xy; gy = 3.0f * (xx - yy); gz = 0.0f; break;
+        case 9: Y = xy * z; gx = yz; gy = xz; gz = xy; break;
+        case 10: Y = y * (5.0f * zz - 1.0f); gx = -2.0f * xy; gy = 4.0f * zz - xx - 3.0f * yy; gz = 8.0f * yz; break;
+        case 11: Y = z * (5.0f * zz - 3.0f); gx = -6.0f * xz; gy = -6.0f * yz; gz = 6.0f * zz - 3.0f * xx - 3.0f * yy; break;
+        case 12: Y = x * (5.0f * zz - 1.0f); gx = 4.0f * zz - 3.0f * xx - yy; gy = -2.0f * xy; gz = 8.0f * xz; break;
+        case 13: Y = z * (xx - yy); gx = 2.0f * xz; gy = -2.0f * yz; gz = xx - yy; break;
+        case 14: Y = x * (xx - 3.0f * yy); gx = 3.0f * (xx - yy); gy = -6.0f * xy; gz = 0.0f; break;
+        case 15: Y = xy * (xx - yy); gx = y * (3.0f * xx - yy); gy = x * (xx - 3.0f * yy); gz = 0.0f; break;
+        case 16: Y = yz * (3.0f * xx - yy); gx = 6.0f * xy * z; gy = 3.0f * z * (xx - yy); gz = y * (3.0f * xx - yy); break;
+        case 17: Y = xy * (7.0f * zz - 1.0f); gx = -y * (3.0f * xx + yy - 6.0f * zz); gy = -x * (xx + 3.0f * yy - 6.0f * zz); gz = 12.0f * xy * z; break;
+        case 18: Y = yz * (7.0f * zz - 3.0f); gx = -6.0f * xy * z; gy = -z * (3.0f * xx + 9.0f * yy - 4.0f * zz); gz = -3.0f * y * (xx + yy - 4.0f * zz); break;
+        case 19: Y = (35.0f * zz - 30.0f) * zz + 3.0f; gx = 12.0f * x * (xx + yy - 4.0f * zz); gy = 12.0f * y * (xx + yy - 4.0f * zz); gz = -16.0f * z * (3.0f * xx + 3.0f * yy - 2.0f * zz); break;
+        case 20: Y = xz * (7.0f * zz - 3.0f); gx = -z * (9.0f * xx + 3.0f * yy - 4.0f * zz); gy = -6.0f * xy * z; gz = -3.0f * x * (xx + yy - 4.0f * zz); break;
+        case 21: Y = (xx - yy) * (7.0f * zz - 1.0f); gx = -4.0f * x * (xx - 3.0f * zz); gy = 4.0f * y * (yy - 3.0f * zz); gz = 12.0f * z * (xx - yy); break;
+        case 22: Y = xz * (xx - 3.0f * yy); gx = 3.0f * z * (xx - yy); gy = -6.0f * xy * z; gz = x * (xx - 3.0f * yy); break;
+        default: Y = xx * (xx - 3.0f * yy) - yy * (3.0f * xx - yy); gx = 4.0f * x * (xx - 3.0f * yy); gy = -4.0f * y * (3.0f * xx - yy); gz = 0.0f; break;
+    }
 }
 
 // g = sum_lm a_lm grad P_lm(u) (gradient of the homogeneous polynomials).

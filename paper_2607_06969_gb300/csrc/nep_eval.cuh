@@ -123,16 +123,29 @@ NEP_HD void desc_atom(const EvalArgs& a, const float* sm, int i) {
 #pragma unroll
         for (int k = 0; k < KR; ++k) fb[t][k] = 0.0f;
     const int cnt = a.cnt[i], cnt_ang = a.cnt_ang[i];
-    int nc = 0;
+    int nc = 0, ncr = 0;
+    // software pipeline: neighbour index two slots ahead, its position one ahead
+    int j_nx = cnt > 0 ? a.nbr[i] : 0;
+    int j_nx2 = cnt > 1 ? a.nbr[N + i] : 0;
+    float4 p_nx = a.pos4[j_nx];
+    int sh_nx = (!MINIMG && cnt > 0) ? a.shift[i] : 0;
     for (int s = 0; s < cnt; ++s) {
-        const int j = a.nbr[s * N + i];
-        const float4 pj = a.pos4[j];
-        const int sh = MINIMG ? 0 : a.shift[s * N + i];
+        const int j = j_nx;
+        const float4 pj = p_nx;
+        const int sh = sh_nx;
+        if (s + 1 < cnt) {
+            j_nx = j_nx2;
+            p_nx = a.pos4[j_nx];
+            if (!MINIMG) sh_nx = a.shift[(s + 1) * N + i];
+            if (s + 2 < cnt) j_nx2 = a.nbr[(s + 2) * N + i];
+        }
         float dx, dy, dz;
         pair_vector(fr.pi, pj, fr.Lx, fr.Ly, fr.Lz, fr.iLx, fr.iLy, fr.iLz, MINIMG, sh, dx, dy, dz);
         const float d2 = dist2(dx, dy, dz);
         const int tj = f2i(pj.w);
         if (d2 < rcR2) {
+            a.compr[ncr * N + i] = make_float4(dx, dy, dz, i2f((int)(((unsigned)j << 2) | (unsigned)tj)));
+            ++ncr;
             float f[KR];
             basis<KR>(sqrt_f(d2), irR, f);
 #pragma unroll
@@ -154,6 +167,7 @@ NEP_HD void desc_atom(const EvalArgs& a, const float* sm, int i) {
         }
     }
     a.cnt_comp[i] = nc;
+    a.cnt_compr[i] = ncr;
 
     float q[D];
 #pragma unroll
@@ -175,11 +189,13 @@ NEP_HD void desc_atom(const EvalArgs& a, const float* sm, int i) {
     for (int n = 0; n < NA; ++n)
 #pragma unroll
         for (int m = 0; m < kLM; ++m) S[n][m] = 0.0f;
+    float4 e_nx = nc > 0 ? a.comp[i] : make_float4(1.0f, 0.0f, 0.0f, 0.0f);
     for (int c = 0; c < nc; ++c) {
-        const float4 e = a.comp[c * N + i];
+        const float4 e = e_nx;
+        if (c + 1 < nc) e_nx = a.comp[(c + 1) * N + i];
         const int tj = f2i(e.w) & 3;
         const float r = sqrt_f(dist2(e.x, e.y, e.z));
-        const float ir = 1.0f / r;
+        const float ir = rcp_f(r);
         float f[KA];
         basis<KA>(r, irA, f);
         const float* cc = sm + sl.cA + (ti * T + tj) * C::SA;
@@ -191,12 +207,14 @@ NEP_HD void desc_atom(const EvalArgs& a, const float* sm, int i) {
             for (int k = 0; k < KA; ++k) acc = fmaf(cc[n * KA + k], f[k], acc);
             g[n] = acc;
         }
-        float Y[kLM];
-        harmonics(e.x * ir, e.y * ir, e.z * ir, Y);
+        const HarmTerms ht = harm_terms(e.x * ir, e.y * ir, e.z * ir);
 #pragma unroll
-        for (int n = 0; n < NA; ++n)
+        for (int m = 0; m < kLM; ++m) {
+            float Y, gx, gy, gz;
+            harm_m(m, ht, Y, gx, gy, gz);
 #pragma unroll
-            for (int m = 0; m < kLM; ++m) S[n][m] = fmaf(g[n], Y[m], S[n][m]);
+            for (int n = 0; n < NA; ++n) S[n][m] = fmaf(g[n], Y, S[n][m]);
+        }
     }
 #pragma unroll
     for (int n = 0; n < NA; ++n) {
@@ -260,7 +278,6 @@ NEP_HD void force_atom(const EvalArgs& a, const float* sm, int i) {
     const int N = a.N;
     const AtomFrame fr = atom_frame(a, i);
     const int ti = fr.ti;
-    const float rcR2 = a.rc_rad * a.rc_rad;
     const float irR = 1.0f / a.rc_rad, irA = 1.0f / a.rc_ang;
 
     float Fx = 0.0f, Fy = 0.0f, Fz = 0.0f;
@@ -294,34 +311,37 @@ NEP_HD void force_atom(const EvalArgs& a, const float* sm, int i) {
     // angular pairs (compacted by desc): owner-side force, scattered to the
     // reverse slot for the gather of F_j
     const int nc = a.cnt_comp[i];
+    float4 e_nx = nc > 0 ? a.comp[i] : make_float4(1.0f, 0.0f, 0.0f, 0.0f);
     for (int c = 0; c < nc; ++c) {
-        const float4 e = a.comp[c * N + i];
+        const float4 e = e_nx;
+        if (c + 1 < nc) e_nx = a.comp[(c + 1) * N + i];
         const int bits = f2i(e.w);
         const int tj = bits & 3;
         const int addr = (int)((unsigned)bits >> 2);
         const float r = sqrt_f(dist2(e.x, e.y, e.z));
-        const float ir = 1.0f / r;
-        const float ux = e.x * ir, uy = e.y * ir, uz = e.z * ir;
-        float f[KA], fp[KA];
-        basis_d<KA>(r, irA, f, fp);
-        const float* cc = sm + sl.cA + (ti * T + tj) * C::SA;
+        const float ir = rcp_f(r);
         float g[NA], gp[NA];
+        {
+            float f[KA], fp[KA];
+            basis_d<KA>(r, irA, f, fp);
+            const float* cc = sm + sl.cA + (ti * T + tj) * C::SA;
 #pragma unroll
-        for (int n = 0; n < NA; ++n) {
-            float u = 0.0f, v = 0.0f;
+            for (int n = 0; n < NA; ++n) {
+                float u = 0.0f, v = 0.0f;
 #pragma unroll
-            for (int k = 0; k < KA; ++k) {
-                const float cv = cc[n * KA + k];
-                u = fmaf(cv, f[k], u);
-                v = fmaf(cv, fp[k], v);
+                for (int k = 0; k < KA; ++k) {
+                    const float cv = cc[n * KA + k];
+                    u = fmaf(cv, f[k], u);
+                    v = fmaf(cv, fp[k], v);
+                }
+                g[n] = u;
+                gp[n] = v;
             }
-            g[n] = u;
-            gp[n] = v;
         }
-        float Y[kLM];
-        harmonics(ux, uy, uz, Y);
-        float A[kLM];
-        float rad = 0.0f;
+        const HarmTerms ht = harm_terms(e.x * ir, e.y * ir, e.z * ir);
+        // f_ij = u sum_m (b_m - l a_m / r) Y_m + (1/r) sum_m a_m grad P_m(u),
+        // a_m = sum_n Sb[n][m] g_n, b_m = sum_n Sb[n][m] g'_n
+        float rad = 0.0f, Gx = 0.0f, Gy = 0.0f, Gz = 0.0f;
 #pragma unroll
         for (int m = 0; m < kLM; ++m) {
             float am = 0.0f, bm = 0.0f;
@@ -330,14 +350,16 @@ NEP_HD void force_atom(const EvalArgs& a, const float* sm, int i) {
                 am = fmaf(Sb[n][m], g[n], am);
                 bm = fmaf(Sb[n][m], gp[n], bm);
             }
-            A[m] = am;
-            rad = fmaf(bm - (float)lm_l(m) * ir * am, Y[m], rad);
+            float Y, hx, hy, hz;
+            harm_m(m, ht, Y, hx, hy, hz);
+            rad = fmaf(fmaf(-(float)lm_l(m) * ir, am, bm), Y, rad);
+            Gx = fmaf(am, hx, Gx);
+            Gy = fmaf(am, hy, Gy);
+            Gz = fmaf(am, hz, Gz);
         }
-        float gx, gy, gz;
-        harmonics_grad_contract(ux, uy, uz, A, gx, gy, gz);
-        const float fx = fmaf(ux, rad, gx * ir);
-        const float fy = fmaf(uy, rad, gy * ir);
-        const float fz = fmaf(uz, rad, gz * ir);
+        const float fx = fmaf(ht.x, rad, Gx * ir);
+        const float fy = fmaf(ht.y, rad, Gy * ir);
+        const float fz = fmaf(ht.z, rad, Gz * ir);
         Fx += fx; Fy += fy; Fz += fz;
         W[0] -= fx * e.x; W[1] -= fx * e.y; W[2] -= fx * e.z;
         W[3] -= fy * e.x; W[4] -= fy * e.y; W[5] -= fy * e.z;
@@ -352,39 +374,51 @@ NEP_HD void force_atom(const EvalArgs& a, const float* sm, int i) {
     for (int t = 0; t < T; ++t)
 #pragma unroll
         for (int k = 0; k < KR; ++k) Pi[t][k] = a.Pr[(i * T + t) * KR + k];
-    const int cnt = a.cnt[i];
-    for (int s = 0; s < cnt; ++s) {
-        const int j = a.nbr[s * N + i];
-        const float4 pj = a.pos4[j];
-        const int sh = MINIMG ? 0 : a.shift[s * N + i];
-        float dx, dy, dz;
-        pair_vector(fr.pi, pj, fr.Lx, fr.Ly, fr.Lz, fr.iLx, fr.iLy, fr.iLz, MINIMG, sh, dx, dy, dz);
-        const float d2 = dist2(dx, dy, dz);
-        if (d2 < rcR2) {
-            const int tj = f2i(pj.w);
-            const float r = sqrt_f(d2);
-            const float ir = 1.0f / r;
-            float f[KR], fp[KR];
-            basis_d<KR>(r, irR, f, fp);
-            const float* Pj = a.Pr + (j * T + ti) * KR;
-            float dEi = 0.0f, dEj = 0.0f;
+    // compacted radial pairs (all inside rc_rad): no divergence on the cutoff
+    float Wr[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};   // xx yy zz xy xz yz
+    const int ncr = a.cnt_compr[i];
+    float4 q_nx = ncr > 0 ? a.compr[i] : make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+    for (int s = 0; s < ncr; ++s) {
+        const float4 e = q_nx;
+        if (s + 1 < ncr) q_nx = a.compr[(s + 1) * N + i];
+        const int bits = f2i(e.w);
+        const int tj = bits & 3;
+        const int j = (int)((unsigned)bits >> 2);
+        const float4* Pj4 = reinterpret_cast<const float4*>(a.Pr + (j * T + ti) * KR);
+        const float r = sqrt_f(dist2(e.x, e.y, e.z));
+        const float ir = rcp_f(r);
+        float f[KR], fp[KR];
+        basis_d<KR>(r, irR, f, fp);
+        float dEi = 0.0f, dEj = 0.0f;
 #pragma unroll
-            for (int k = 0; k < KR; ++k) {
-                float pk = Pi[0][k];
-#pragma unroll
-                for (int t = 1; t < T; ++t) pk = (tj == t) ? Pi[t][k] : pk;
-                dEi = fmaf(pk, fp[k], dEi);
-                dEj = fmaf(Pj[k], fp[k], dEj);
-            }
-            const float ux = dx * ir, uy = dy * ir, uz = dz * ir;
-            const float tot = dEi + dEj;
-            Fx = fmaf(tot, ux, Fx); Fy = fmaf(tot, uy, Fy); Fz = fmaf(tot, uz, Fz);
-            const float fx = dEi * ux, fy = dEi * uy, fz = dEi * uz;
-            W[0] -= fx * dx; W[1] -= fx * dy; W[2] -= fx * dz;
-            W[3] -= fy * dx; W[4] -= fy * dy; W[5] -= fy * dz;
-            W[6] -= fz * dx; W[7] -= fz * dy; W[8] -= fz * dz;
+        for (int k4 = 0; k4 < KR / 4; ++k4) {
+            const float4 pj = Pj4[k4];
+            dEj = fmaf(pj.x, fp[4 * k4 + 0], dEj);
+            dEj = fmaf(pj.y, fp[4 * k4 + 1], dEj);
+            dEj = fmaf(pj.z, fp[4 * k4 + 2], dEj);
+            dEj = fmaf(pj.w, fp[4 * k4 + 3], dEj);
         }
+#pragma unroll
+        for (int k = (KR / 4) * 4; k < KR; ++k) dEj = fmaf(a.Pr[(j * T + ti) * KR + k], fp[k], dEj);
+#pragma unroll
+        for (int k = 0; k < KR; ++k) {
+            float pk = Pi[0][k];
+#pragma unroll
+            for (int t = 1; t < T; ++t) pk = (tj == t) ? Pi[t][k] : pk;
+            dEi = fmaf(pk, fp[k], dEi);
+        }
+        const float tot = (dEi + dEj) * ir;
+        Fx = fmaf(tot, e.x, Fx); Fy = fmaf(tot, e.y, Fy); Fz = fmaf(tot, e.z, Fz);
+        // W -= f_ij (x) r_ij with f_ij = dE_i/dr rhat: symmetric part only
+        const float w = dEi * ir;
+        const float wx = w * e.x, wy = w * e.y, wz = w * e.z;
+        Wr[0] = fmaf(wx, e.x, Wr[0]); Wr[1] = fmaf(wy, e.y, Wr[1]); Wr[2] = fmaf(wz, e.z, Wr[2]);
+        Wr[3] = fmaf(wx, e.y, Wr[3]); Wr[4] = fmaf(wx, e.z, Wr[4]); Wr[5] = fmaf(wy, e.z, Wr[5]);
     }
+    W[0] -= Wr[0]; W[4] -= Wr[1]; W[8] -= Wr[2];
+    W[1] -= Wr[3]; W[3] -= Wr[3];
+    W[2] -= Wr[4]; W[6] -= Wr[4];
+    W[5] -= Wr[5]; W[7] -= Wr[5];
     a.fpart[i] = Fx;
     a.fpart[N + i] = Fy;
     a.fpart[2 * N + i] = Fz;
@@ -396,8 +430,17 @@ NEP_HD void force_atom(const EvalArgs& a, const float* sm, int i) {
 // kernels and launchers
 // ---------------------------------------------------------------------------
 #if defined(__CUDACC__)
+// Resident blocks per SM the register allocation is sized for: the force
+// kernel keeps dE/dS (n_ang x 24 floats) live across its angular loop and
+// needs the 255-register budget of two blocks to avoid spills.
+#ifndef NEP_DESC_MINB
+#define NEP_DESC_MINB 3
+#endif
+#ifndef NEP_FORCE_MINB
+#define NEP_FORCE_MINB 2
+#endif
 template <class C, bool MINIMG>
-__global__ void __launch_bounds__(kBlock, 3) k_desc(const EvalArgs a) {
+__global__ void __launch_bounds__(kBlock, NEP_DESC_MINB) k_desc(const EvalArgs a) {
     extern __shared__ float sm[];
     load_model<C>(sm, a.params, a.H, threadIdx.x, blockDim.x);
     __syncthreads();
@@ -406,7 +449,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_desc(const EvalArgs a) {
 }
 
 template <class C, bool MINIMG>
-__global__ void __launch_bounds__(kBlock, 3) k_force(const EvalArgs a) {
+__global__ void __launch_bounds__(kBlock, NEP_FORCE_MINB) k_force(const EvalArgs a) {
     extern __shared__ float sm[];
     load_model<C>(sm, a.params, a.H, threadIdx.x, blockDim.x);
     __syncthreads();

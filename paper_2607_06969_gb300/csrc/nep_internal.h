@@ -50,6 +50,8 @@ struct EvalArgs {
     float* Pr;                     // [N][T][KR]      sum_n dE/dq_n cR[Zi][t][n][k]
     float4* comp;                  // [cap_ang][N]    compacted angular pairs
     int* cnt_comp;                 // [N]
+    float4* compr;                 // [cap][N]        compacted radial pairs (r_ij, j|tj)
+    int* cnt_compr;                // [N]
     float4* fin;                   // [cap_ang][N]    incoming angular pair forces
     float* fpart;                  // [3][N]
     float* wat;                    // [9][N]          per-atom virial
@@ -106,7 +108,7 @@ struct NbrWork {
     int cmax;
 };
 size_t nbr_cell_capacity(int N, int B);
-cudaError_t launch_neighbors(const float* pos, const int* atom_off, const float* box,
+cudaError_t launch_neighbors(const float* pos, const float4* pos4, const int* atom_off, const float* box,
                              const int* cfg, int N, int B, float rc_list, float rc_list_ang,
                              int min_image, nep_nlist* nl, const NbrWork& w, cudaStream_t st);
 

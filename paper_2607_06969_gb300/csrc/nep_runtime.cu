@@ -333,7 +333,11 @@ __device__ __forceinline__ int floor_div(int a, int b) {
     return q;
 }
 
-__global__ void __launch_bounds__(128) k_build(const float* __restrict__ pos,
+// One pass over the stencil: angular candidates (d < rc_ang + skin) fill the
+// list from slot 0 up, the remaining radial candidates fill it from slot
+// cap-1 down and are moved behind the angular prefix at the end, so the
+// final order is [angular in visit order, radial-only in visit order].
+__global__ void __launch_bounds__(128) k_build(const float4* __restrict__ pos4,
                                                const int* __restrict__ cfg,
                                                const float* __restrict__ box,
                                                const CellPlan* __restrict__ plan,
@@ -346,66 +350,73 @@ __global__ void __launch_bounds__(128) k_build(const float* __restrict__ pos,
     const int b = cfg[i];
     const CellPlan p = plan[b];
     const float L[3] = {box[3 * b], box[3 * b + 1], box[3 * b + 2]};
-    const float xi = pos[i], yi = pos[N + i], zi = pos[2 * N + i];
+    const float4 pi = pos4[i];
     int c = cell_of[i] - p.base;
     const int cz = c % p.nc[2];
     c /= p.nc[2];
     const int cy = c % p.nc[1];
     const int cx = c / p.nc[1];
-    // pass 0 writes the angular candidates (d < rc_ang + skin) into the list
-    // prefix, pass 1 appends the remaining radial ones
-    int n_ang = 0, n_rest = 0;
-    int slot = 0;
-    for (int pass = 0; pass < 2; ++pass) {
-        for (int ox = -p.half[0]; ox <= p.half[0]; ++ox) {
-            const int ux = cx + ox, sx = floor_div(ux, p.nc[0]), wx = ux - sx * p.nc[0];
-            for (int oy = -p.half[1]; oy <= p.half[1]; ++oy) {
-                const int uy = cy + oy, sy = floor_div(uy, p.nc[1]), wy = uy - sy * p.nc[1];
-                for (int oz = -p.half[2]; oz <= p.half[2]; ++oz) {
-                    const int uz = cz + oz, sz = floor_div(uz, p.nc[2]), wz = uz - sz * p.nc[2];
-                    const int cell = p.base + (wx * p.nc[1] + wy) * p.nc[2] + wz;
-                    const float fx = mul_rn((float)sx, L[0]);
-                    const float fy = mul_rn((float)sy, L[1]);
-                    const float fz = mul_rn((float)sz, L[2]);
-                    const bool zero_img = (sx == 0 && sy == 0 && sz == 0);
-                    for (int q = cell_start[cell]; q < cell_start[cell + 1]; ++q) {
-                        const int j = cell_atoms[q];
-                        if (j == i && zero_img) continue;
-                        const float dx = add_rn(sub_rn(pos[j], xi), fx);
-                        const float dy = add_rn(sub_rn(pos[N + j], yi), fy);
-                        const float dz = add_rn(sub_rn(pos[2 * N + j], zi), fz);
-                        const float d2 = dist2(dx, dy, dz);
-                        bool take;
-                        if (pass == 0) {
-                            take = d2 < rc2_ang;
-                            if (take) {
-                                ++n_ang;
-                                if (n_ang > nl.cap_ang) take = false;
-                            }
-                        } else {
-                            take = d2 >= rc2_ang && d2 < rc2_rad;
-                            if (take) {
-                                ++n_rest;
-                                if (slot >= nl.cap) take = false;
-                            }
-                        }
-                        if (!take) continue;
-                        nl.nbr[(size_t)slot * N + i] = j;
-                        if (nl.shift) nl.shift[(size_t)slot * N + i] = pack_shift(sx, sy, sz);
-                        ++slot;
+    int n_ang = 0, n_rest = 0, w_ang = 0;
+    const int cap = nl.cap, cap_ang = nl.cap_ang;
+    for (int ox = -p.half[0]; ox <= p.half[0]; ++ox) {
+        const int ux = cx + ox, sx = floor_div(ux, p.nc[0]), wx = ux - sx * p.nc[0];
+        for (int oy = -p.half[1]; oy <= p.half[1]; ++oy) {
+            const int uy = cy + oy, sy = floor_div(uy, p.nc[1]), wy = uy - sy * p.nc[1];
+            for (int oz = -p.half[2]; oz <= p.half[2]; ++oz) {
+                const int uz = cz + oz, sz = floor_div(uz, p.nc[2]), wz = uz - sz * p.nc[2];
+                const int cell = p.base + (wx * p.nc[1] + wy) * p.nc[2] + wz;
+                const float fx = mul_rn((float)sx, L[0]);
+                const float fy = mul_rn((float)sy, L[1]);
+                const float fz = mul_rn((float)sz, L[2]);
+                const bool zero_img = (sx == 0 && sy == 0 && sz == 0);
+                const int q1 = cell_start[cell + 1];
+                for (int q = cell_start[cell]; q < q1; ++q) {
+                    const int j = cell_atoms[q];
+                    if (j == i && zero_img) continue;
+                    const float4 pj = pos4[j];
+                    const float dx = add_rn(sub_rn(pj.x, pi.x), fx);
+                    const float dy = add_rn(sub_rn(pj.y, pi.y), fy);
+                    const float dz = add_rn(sub_rn(pj.z, pi.z), fz);
+                    const float d2 = dist2(dx, dy, dz);
+                    if (!(d2 < rc2_rad)) continue;
+                    int slot;
+                    if (d2 < rc2_ang) {
+                        slot = n_ang < cap_ang && n_ang + n_rest < cap ? n_ang : -1;
+                        ++n_ang;
+                        if (slot >= 0) w_ang = n_ang;
+                    } else {
+                        slot = n_ang + n_rest < cap ? cap - 1 - n_rest : -1;
+                        ++n_rest;
                     }
+                    if (slot < 0) continue;
+                    nl.nbr[(size_t)slot * N + i] = j;
+                    if (nl.shift) nl.shift[(size_t)slot * N + i] = pack_shift(sx, sy, sz);
                 }
             }
         }
     }
     const int n_total = n_ang + n_rest;
-    if (n_total > nl.cap || n_ang > nl.cap_ang) {
+    const bool over = n_total > cap || n_ang > cap_ang;
+    if (over) {
         set_flag(nl.status, 0);
         atomicMax(nl.status + 1, n_total);
         atomicMax(nl.status + 2, n_ang);
     }
-    nl.cnt[i] = slot;
-    nl.cnt_ang[i] = min(n_ang, nl.cap_ang);
+    // on overflow only the contiguous angular prefix that was written is kept
+    const int kept_ang = over ? w_ang : n_ang;
+    // move the radial-only entries (stored downward from cap-1) behind the prefix
+    int kept_rest = 0;
+    if (!over) {
+        kept_rest = n_rest;
+        for (int k = 0; k < n_rest; ++k) {
+            const size_t from = (size_t)(cap - 1 - k) * N + i, to = (size_t)(kept_ang + k) * N + i;
+            if (from == to) continue;   // only when the list is exactly full at the meeting point
+            nl.nbr[to] = nl.nbr[from];
+            if (nl.shift) nl.shift[to] = nl.shift[from];
+        }
+    }
+    nl.cnt[i] = kept_ang + kept_rest;
+    nl.cnt_ang[i] = kept_ang;
 }
 
 __global__ void k_rev(int N, nep_nlist nl) {
@@ -504,7 +515,7 @@ cudaError_t launch_final_reduce(int B, const int* chunk_start, const double* par
 
 size_t nbr_cell_capacity(int N, int B) { return 2 * (size_t)N + 27 * (size_t)B; }
 
-cudaError_t launch_neighbors(const float* pos, const int* atom_off, const float* box,
+cudaError_t launch_neighbors(const float* pos, const float4* pos4, const int* atom_off, const float* box,
                              const int* cfg, int N, int B, float rc_list, float rc_list_ang,
                              int min_image, nep_nlist* nl, const NbrWork& w, cudaStream_t st) {
     cudaError_t e;
@@ -525,7 +536,7 @@ cudaError_t launch_neighbors(const float* pos, const int* atom_off, const float*
     k_fill<<<blocks(N, 256), 256, 0, st>>>(w.cell_of, w.rank, w.cell_start, N, w.cell_atoms);
     k_sort_cells<<<blocks(cmax, 128), 128, 0, st>>>(w.cell_start, cmax, w.cell_atoms);
     const float rr = rc_list * rc_list, ra = rc_list_ang * rc_list_ang;
-    k_build<<<blocks(N, 128), 128, 0, st>>>(pos, cfg, box, w.plan, w.cell_of, w.cell_start,
+    k_build<<<blocks(N, 128), 128, 0, st>>>(pos4, cfg, box, w.plan, w.cell_of, w.cell_start,
                                             w.cell_atoms, N, rr, ra, *nl);
     k_rev<<<blocks(N, 128), 128, 0, st>>>(N, *nl);
     return cudaGetLastError();
