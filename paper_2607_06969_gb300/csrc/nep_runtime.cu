@@ -404,15 +404,30 @@ __global__ void __launch_bounds__(128) k_build(const float4* __restrict__ pos4,
     }
     // on overflow only the contiguous angular prefix that was written is kept
     const int kept_ang = over ? w_ang : n_ang;
-    // move the radial-only entries (stored downward from cap-1) behind the prefix
+    // move the radial-only entries (stored downward from cap-1) behind the
+    // prefix: reverse the block in place, then copy it down (the target never
+    // starts above the source, so an ascending copy is safe)
     int kept_rest = 0;
     if (!over) {
         kept_rest = n_rest;
-        for (int k = 0; k < n_rest; ++k) {
-            const size_t from = (size_t)(cap - 1 - k) * N + i, to = (size_t)(kept_ang + k) * N + i;
-            if (from == to) continue;   // only when the list is exactly full at the meeting point
-            nl.nbr[to] = nl.nbr[from];
-            if (nl.shift) nl.shift[to] = nl.shift[from];
+        const int base = cap - n_rest;
+        for (int k = 0; k < n_rest / 2; ++k) {
+            const size_t x = (size_t)(base + k) * N + i, y = (size_t)(cap - 1 - k) * N + i;
+            const int t = nl.nbr[x];
+            nl.nbr[x] = nl.nbr[y];
+            nl.nbr[y] = t;
+            if (nl.shift) {
+                const int u = nl.shift[x];
+                nl.shift[x] = nl.shift[y];
+                nl.shift[y] = u;
+            }
+        }
+        if (base != kept_ang) {
+            for (int k = 0; k < n_rest; ++k) {
+                const size_t from = (size_t)(base + k) * N + i, to = (size_t)(kept_ang + k) * N + i;
+                nl.nbr[to] = nl.nbr[from];
+                if (nl.shift) nl.shift[to] = nl.shift[from];
+            }
         }
     }
     nl.cnt[i] = kept_ang + kept_rest;
