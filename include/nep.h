@@ -163,6 +163,34 @@ nep_status nep_energy_forces_virial(nep_model* m, const nep_system* sys, const n
                                     float* e_atom, float* force, double* e_tot, double* virial,
                                     void* work, size_t work_bytes, void* stream);
 
+/* nep_energy_forces_virial without a caller workspace.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory at all -- for example a force plugin inside a host MD code
+ * whose engine reserves the device memory and hands plugins no scratch
+ * buffers, or a real-time loop that forbids allocator calls after start-up
+ * because cudaMalloc/cudaFree may synchronise the whole device.
+ *
+ * Scratch comes from one file-scope device array of NEP_NOALLOC_SCRATCH_BYTES
+ * (32 MiB) that every GPU loading the library holds until the process exits.
+ * The call allocates nothing: no cudaMalloc, no cudaFree, no allocating
+ * library routine.  Inputs, the neighbour list and the outputs are the
+ * caller's, exactly as for nep_energy_forces_virial, and the results are the
+ * same.  A system whose scratch (nep_workspace_bytes) exceeds the array is
+ * rejected with NEP_ERR_ARG and a message giving both sizes.
+ *
+ * The first call on a device looks up the array's device address for that
+ * device (cudaGetSymbolAddress, once per device, with the caller's device
+ * current); make that first call before any stream capture.  Every call
+ * shares the one array and leaves its contents behind; the computation
+ * writes every scratch word it later reads, so nothing needs clearing
+ * between calls.  Calls whose GPU work overlaps (different streams, or
+ * several host threads) race on the array and must be serialised by the
+ * caller. */
+#define NEP_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+nep_status nep_energy_forces_virial_noalloc(nep_model* m, const nep_system* sys,
+                                            const nep_nlist* nl, float* e_atom, float* force,
+                                            double* e_tot, double* virial, void* stream);
+
 /* Loss and its gradient with respect to all P parameters (Eqs. 18-21).
  * e_lbl [B] double, f_lbl [3][N] float, v_lbl [B][9] double,
  * w_host[3] = (wE, wF, wV).

@@ -20,7 +20,8 @@ NEP_OK, NEP_ERR_ARG, NEP_ERR_CUDA, NEP_ERR_NOMEM, NEP_ERR_CAPACITY, NEP_ERR_TIME
 # names of every entry point declared in include/nep.h
 ENTRY_POINTS = (
     "nep_num_params", "nep_create", "nep_destroy", "nep_supported", "nep_set_params",
-    "nep_workspace_bytes", "nep_neighbors", "nep_energy_forces_virial", "nep_param_grad",
+    "nep_workspace_bytes", "nep_neighbors", "nep_energy_forces_virial",
+    "nep_energy_forces_virial_noalloc", "nep_param_grad",
     "nep_param_grad_adjoint", "nep_md_step", "nep_set_timing_events", "nep_check",
     "nep_last_error", "nep_version",
 )
@@ -73,6 +74,7 @@ def lib() -> ctypes.CDLL:
     L.nep_workspace_bytes.restype = sz
     L.nep_neighbors.argtypes = [vp, P(System), f, P(NList), vp, sz, vp]
     L.nep_energy_forces_virial.argtypes = [vp, P(System), P(NList), vp, vp, vp, vp, vp, sz, vp]
+    L.nep_energy_forces_virial_noalloc.argtypes = [vp, P(System), P(NList), vp, vp, vp, vp, vp]
     L.nep_param_grad.argtypes = [vp, P(System), P(NList), vp, vp, vp, vp, i, vp, vp, vp, sz, vp]
     L.nep_param_grad_adjoint.argtypes = [vp, P(System), P(NList), vp, vp, vp, vp, vp, sz, vp]
     L.nep_md_step.argtypes = [vp, P(System), P(NList), vp, vp, vp, vp, vp, f, f, i, vp, sz, vp]
@@ -81,7 +83,8 @@ def lib() -> ctypes.CDLL:
     L.nep_last_error.restype = ctypes.c_char_p
     L.nep_version.restype = ctypes.c_char_p
     for name in ("nep_create", "nep_destroy", "nep_set_params", "nep_neighbors",
-                 "nep_energy_forces_virial", "nep_param_grad", "nep_param_grad_adjoint",
+                 "nep_energy_forces_virial", "nep_energy_forces_virial_noalloc",
+                 "nep_param_grad", "nep_param_grad_adjoint",
                  "nep_md_step", "nep_check", "nep_set_timing_events"):
         getattr(L, name).restype = i
     _LIB = L
@@ -243,6 +246,30 @@ def energy_forces_virial(model: Model, dsys: DeviceSystem, nl: NeighborList, ws:
                                          _ptr(e_atom), _ptr(force), _ptr(e_tot), _ptr(vir),
                                          ws.ptr, ws.bytes, _stream(stream)),
           "nep_energy_forces_virial")
+    return out
+
+
+NOALLOC_SCRATCH_BYTES = 32 << 20
+
+
+def energy_forces_virial_noalloc(model: Model, dsys: DeviceSystem, nl: NeighborList, out=None,
+                                 stream=None):
+    """nep_energy_forces_virial_noalloc: the same outputs as
+    energy_forces_virial, with scratch taken from the library's static
+    device array instead of a caller workspace (for callers that cannot
+    allocate device memory).  Returns (e_atom, force [3,N], e_tot, virial)."""
+    import torch
+    dev = dsys.pos.device
+    if out is None:
+        out = (torch.empty(dsys.n_atoms, dtype=torch.float32, device=dev),
+               torch.empty(3, dsys.n_atoms, dtype=torch.float32, device=dev),
+               torch.empty(dsys.n_cfg, dtype=torch.float64, device=dev),
+               torch.empty(dsys.n_cfg, 9, dtype=torch.float64, device=dev))
+    e_atom, force, e_tot, vir = out
+    check(lib().nep_energy_forces_virial_noalloc(model.handle, ctypes.byref(dsys.c),
+                                                 ctypes.byref(nl.c), _ptr(e_atom), _ptr(force),
+                                                 _ptr(e_tot), _ptr(vir), _stream(stream)),
+          "nep_energy_forces_virial_noalloc")
     return out
 
 

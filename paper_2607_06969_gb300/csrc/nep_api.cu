@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <mutex>
+
 #include "nep_internal.h"
 
 struct nep_model {
@@ -404,6 +406,56 @@ nep_status nep_md_step(nep_model* m, const nep_system* sys, nep_nlist* nl, float
     if ((s = efv_impl(m, sys, nl, nullptr, force, e_tot, virial, work, w, st)) != NEP_OK) return s;
     NEP_CUDA(nep::launch_kick(vel, force, sys->type, inv_m, N, 0.5f * dt, nullptr, 0.0f, st), "kick");
     return NEP_OK;
+}
+
+}  // extern "C"
+
+// Scratch of nep_energy_forces_virial_noalloc: one fixed device array per
+// GPU, created when the module loads and never freed before exit.  In host
+// code g_noalloc_scratch names a host-side stand-in, not device memory, so
+// its device address is looked up per device and passed to the kernels.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NEP_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+nep_status noalloc_scratch(void** out) {
+    int dev = 0;
+    NEP_CUDA(cudaGetDevice(&dev), "current device");
+    if (dev < 0 || dev >= kMaxDevices) return fail(NEP_ERR_ARG, "device index %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        NEP_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch), "address of the static scratch array");
+        if (!p) return fail(NEP_ERR_CUDA, "static scratch array has no device address");
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return NEP_OK;
+}
+}  // namespace
+
+extern "C" {
+
+nep_status nep_energy_forces_virial_noalloc(nep_model* m, const nep_system* sys,
+                                            const nep_nlist* nl, float* e_atom, float* force,
+                                            double* e_tot, double* virial, void* stream) {
+    nep_status s;
+    if ((s = check_system(m, sys)) != NEP_OK) return s;
+    if ((s = check_nlist(nl, sys->n_atoms)) != NEP_OK) return s;
+    if (sys->n_atoms > 0 && !force) return fail(NEP_ERR_ARG, "force is NULL");
+    if (!nl->min_image && !nl->shift) return fail(NEP_ERR_STATE, "list was not built (no shifts, not min-image)");
+    const WsLayout w = ws_layout(m, sys->n_atoms, sys->n_cfg, nl->cap, nl->cap_ang);
+    if (w.total > NEP_NOALLOC_SCRATCH_BYTES)
+        return fail(NEP_ERR_ARG,
+                    "system needs %zu bytes of scratch, the static array holds %zu "
+                    "(use nep_energy_forces_virial with a caller workspace)",
+                    w.total, (size_t)NEP_NOALLOC_SCRATCH_BYTES);
+    void* work = nullptr;
+    if ((s = noalloc_scratch(&work)) != NEP_OK) return s;
+    return efv_impl(m, sys, nl, e_atom, force, e_tot, virial, work, w, (cudaStream_t)stream);
 }
 
 nep_status nep_param_grad(nep_model* m, const nep_system* sys, const nep_nlist* nl,
