@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-train", action="store_true", help="skip the training-step leg")
     ap.add_argument("--ncell", type=int, default=50,
                     help="rock-salt cells per edge (50 = the 900k-atom workload; smaller for profiling)")
     return ap.parse_args()
@@ -287,6 +288,41 @@ def run_md(args, nb, torch, dist, world, local, s, h, model, theta, vel0, masses
             vir, stream, pos_host0)
 
 
+def train_leg(nb, torch, I, local) -> dict:
+    """Secondary leg: one batched loss+gradient step (nep_param_grad) on the
+    128-configuration training batch (N ~ U{24..512}); labels from a teacher
+    NEP evaluated by the same library (seed 2 weights)."""
+    s, h = I.workload_train128()
+    th = I.init_params(h).astype(np.float32)
+    teacher = nb.Model(h, I.init_params(h, seed=I.SEED_TEACHER).astype(np.float32))
+    model = nb.Model(h, th)
+    dsys = nb.DeviceSystem.from_inputs(s)
+    cap, cap_ang = 112, 56
+    nl = nb.NeighborList(s.n_atoms, cap, cap_ang)
+    ws = nb.Workspace(model, s.n_atoms, s.n_cfg, cap, cap_ang, train=True)
+    nb.neighbors(model, dsys, nl, 0.0, ws)
+    if nb.check_list(nl) != nb.NEP_OK:
+        raise RuntimeError(nb.last_error())
+    _, F, E, V = nb.energy_forces_virial(teacher, dsys, nl, ws)
+    grad = torch.empty(model.n_params, dtype=torch.float32, device="cuda")
+    loss = torch.empty(1, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        nb.param_grad(model, dsys, nl, ws, E, F.contiguous(), V, (1.0, 1.0, 0.1), 0, grad, loss)
+    torch.cuda.synchronize()
+    K = 20
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(K):
+        nb.param_grad(model, dsys, nl, ws, E, F.contiguous(), V, (1.0, 1.0, 0.1), 0, grad, loss)
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / K
+    return {"workload": "train128: 128 random packings, N ~ U{24..512} (%d atoms), loss+grad of %d "
+                        "parameters, FP32" % (s.n_atoms, model.n_params),
+            "configs_per_s": s.n_cfg / (ms * 1e-3), "ms_per_step": ms, "loss": float(loss.item()),
+            "steps": K}
+
+
 # ------------------------------------------------------------------ our arm
 def main():
     args = parse()
@@ -366,6 +402,8 @@ def main():
     e2e_ms = e0.elapsed_time(e1)
     e2e_val = world * N * KE / (e2e_ms * 1e-3)
 
+    train = None if args.no_train else train_leg(nb, torch, I, local)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
@@ -382,7 +420,7 @@ def main():
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_val, "unit": "atom-steps/s", "steps": KE,
                         "h2d_bytes_per_step": 12 * N, "d2h_bytes_per_step": 12 * N + 8 + 72},
-                "gpu_launches": launches, "clocks": clk,
+                "gpu_launches": launches, "clocks": clk, "train": train,
                 "energy": {"e_tot_final": float(e_tot.item())}}
         print(json.dumps(line), flush=True)
     if world > 1:

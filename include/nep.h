@@ -191,6 +191,11 @@ nep_status nep_energy_forces_virial_noalloc(nep_model* m, const nep_system* sys,
                                             const nep_nlist* nl, float* e_atom, float* force,
                                             double* e_tot, double* virial, void* stream);
 
+/* Scratch bytes of nep_param_grad / nep_param_grad_adjoint (the evaluation
+ * scratch plus the training intermediates: descriptors, their tangents,
+ * per-pair adjoint coefficients and per-chunk gradient partials). */
+size_t nep_train_workspace_bytes(const nep_model* m, int n_atoms, int n_cfg, int cap, int cap_ang);
+
 /* Loss and its gradient with respect to all P parameters (Eqs. 18-21).
  * e_lbl [B] double, f_lbl [3][N] float, v_lbl [B][9] double,
  * w_host[3] = (wE, wF, wV).
@@ -199,7 +204,10 @@ nep_status nep_energy_forces_virial_noalloc(nep_model* m, const nep_system* sys,
  * loss_mode 1: Eqs. 19-21 per configuration, averaged over the batch:
  *              1/B sum_b [wE dE_b^2/N_b + wF/(3N_b) sum |dF|^2 + wV/(9N_b) sum dV^2]
  * grad [P] float (overwritten), loss [1] double (may be NULL).
- * Per-pair derivatives are recomputed; nothing is cached across calls. */
+ * work: nep_train_workspace_bytes bytes.  The gradient is that of the FP32
+ * forward; sums over atoms and chunks are fixed-order (FP64 across chunks),
+ * so results are bitwise reproducible.  Per-pair derivatives are
+ * recomputed; nothing is cached across calls. */
 nep_status nep_param_grad(nep_model* m, const nep_system* sys, const nep_nlist* nl,
                           const double* e_lbl, const float* f_lbl, const double* v_lbl,
                           const float* w_host, int loss_mode, float* grad, double* loss,
@@ -208,7 +216,7 @@ nep_status nep_param_grad(nep_model* m, const nep_system* sys, const nep_nlist* 
 /* Gradient of Phi = sum_b a_e[b] E_b + sum_i lam[:,i] . F_i + sum_b mu[b] : V_b
  * with the adjoints held fixed (the vector-Jacobian product used by an
  * autograd backward).  a_e [B] double, lam [3][N] float, mu [B][9] double.
- * grad [P] float (overwritten). */
+ * grad [P] float (overwritten).  work: nep_train_workspace_bytes bytes. */
 nep_status nep_param_grad_adjoint(nep_model* m, const nep_system* sys, const nep_nlist* nl,
                                   const double* a_e, const float* lam, const double* mu,
                                   float* grad, void* work, size_t work_bytes, void* stream);

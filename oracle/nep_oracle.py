@@ -129,6 +129,23 @@ def neighbor_pairs(pos32: np.ndarray, box: np.ndarray, atom_off: np.ndarray, cut
                          for z in range(-S[2], S[2] + 1)], np.int64)
         ncell = [int(np.floor(float(L32[a]) / (float(rc32) + 0.01))) for a in range(3)]
         use_bins = min(ncell) >= 3 and n > 4096
+        # every edge longer than 2 rc: at most one image of j lies within rc,
+        # the minimum image, so that single image is tested
+        single = (not use_bins) and all(float(L32[a]) > 2.0 * float(rc32) + 0.01 for a in range(3))
+        if single:
+            for c0 in range(0, ci.size, 64):
+                ii = ci[c0:c0 + 64]
+                I = np.repeat(ii, n)
+                J = np.tile(np.arange(n), ii.size)
+                d = P[J].astype(np.float64) - P[I].astype(np.float64)
+                Sx = -np.rint(d / L32.astype(np.float64)).astype(np.int64)
+                keep = ~((I == J) & (Sx == 0).all(1))
+                I, J, Sx = I[keep], J[keep], Sx[keep]
+                m = _pred_f32(P[I], P[J], Sx, L32, rc2)
+                out_i.append(I[m] + a0)
+                out_j.append(J[m] + a0)
+                out_s.append(Sx[m])
+            continue
         if use_bins:
             cs = np.array([float(L32[a]) / ncell[a] for a in range(3)])
             cidx = np.minimum((P.astype(np.float64) / cs).astype(np.int64), np.array(ncell) - 1)

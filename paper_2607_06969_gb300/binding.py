@@ -20,7 +20,7 @@ NEP_OK, NEP_ERR_ARG, NEP_ERR_CUDA, NEP_ERR_NOMEM, NEP_ERR_CAPACITY, NEP_ERR_TIME
 # names of every entry point declared in include/nep.h
 ENTRY_POINTS = (
     "nep_num_params", "nep_create", "nep_destroy", "nep_supported", "nep_set_params",
-    "nep_workspace_bytes", "nep_neighbors", "nep_energy_forces_virial",
+    "nep_workspace_bytes", "nep_train_workspace_bytes", "nep_neighbors", "nep_energy_forces_virial",
     "nep_energy_forces_virial_noalloc", "nep_param_grad",
     "nep_param_grad_adjoint", "nep_md_step", "nep_set_timing_events", "nep_check",
     "nep_last_error", "nep_version",
@@ -72,6 +72,8 @@ def lib() -> ctypes.CDLL:
     L.nep_set_params.argtypes = [vp, vp, vp]
     L.nep_workspace_bytes.argtypes = [vp, i, i, i, i]
     L.nep_workspace_bytes.restype = sz
+    L.nep_train_workspace_bytes.argtypes = [vp, i, i, i, i]
+    L.nep_train_workspace_bytes.restype = sz
     L.nep_neighbors.argtypes = [vp, P(System), f, P(NList), vp, sz, vp]
     L.nep_energy_forces_virial.argtypes = [vp, P(System), P(NList), vp, vp, vp, vp, vp, sz, vp]
     L.nep_energy_forces_virial_noalloc.argtypes = [vp, P(System), P(NList), vp, vp, vp, vp, vp]
@@ -215,9 +217,14 @@ class NeighborList:
 
 
 class Workspace:
-    def __init__(self, model: Model, n_atoms: int, n_cfg: int, cap: int, cap_ang: int, device="cuda"):
+    """Device scratch for the hot calls (nep_workspace_bytes, or
+    nep_train_workspace_bytes with train=True)."""
+
+    def __init__(self, model: Model, n_atoms: int, n_cfg: int, cap: int, cap_ang: int, device="cuda",
+                 train: bool = False):
         import torch
-        self.bytes = int(lib().nep_workspace_bytes(model.handle, n_atoms, n_cfg, cap, cap_ang))
+        fn = lib().nep_train_workspace_bytes if train else lib().nep_workspace_bytes
+        self.bytes = int(fn(model.handle, n_atoms, n_cfg, cap, cap_ang))
         if self.bytes == 0:
             raise NepError(NEP_ERR_ARG, "nep_workspace_bytes", "invalid sizes")
         self.buf = torch.empty(self.bytes + 256, dtype=torch.uint8, device=device)
@@ -247,6 +254,38 @@ def energy_forces_virial(model: Model, dsys: DeviceSystem, nl: NeighborList, ws:
                                          ws.ptr, ws.bytes, _stream(stream)),
           "nep_energy_forces_virial")
     return out
+
+
+def param_grad(model: Model, dsys: DeviceSystem, nl: NeighborList, ws: Workspace, e_lbl, f_lbl,
+               v_lbl, w=(1.0, 1.0, 0.1), loss_mode: int = 0, grad=None, loss=None, stream=None):
+    """nep_param_grad: loss (Eqs. 18-21) and its gradient over all parameters.
+    e_lbl [B] f64, f_lbl [3,N] f32, v_lbl [B,9] f64 on the device; ws must be a
+    training workspace.  Returns (grad [P] f32, loss [1] f64)."""
+    import torch
+    dev = dsys.pos.device
+    if grad is None:
+        grad = torch.empty(model.n_params, dtype=torch.float32, device=dev)
+    if loss is None:
+        loss = torch.empty(1, dtype=torch.float64, device=dev)
+    wh = np.ascontiguousarray(np.asarray(w, np.float32))
+    check(lib().nep_param_grad(model.handle, ctypes.byref(dsys.c), ctypes.byref(nl.c), _ptr(e_lbl),
+                               _ptr(f_lbl), _ptr(v_lbl), wh.ctypes.data_as(ctypes.c_void_p),
+                               int(loss_mode), _ptr(grad), _ptr(loss), ws.ptr, ws.bytes, _stream(stream)),
+          "nep_param_grad")
+    return grad, loss
+
+
+def param_grad_adjoint(model: Model, dsys: DeviceSystem, nl: NeighborList, ws: Workspace, a_e, lam, mu,
+                       grad=None, stream=None):
+    """nep_param_grad_adjoint: d/dtheta of sum a_e E + lam . F + mu : V.
+    a_e [B] f64, lam [3,N] f32, mu [B,9] f64.  Returns grad [P] f32."""
+    import torch
+    if grad is None:
+        grad = torch.empty(model.n_params, dtype=torch.float32, device=dsys.pos.device)
+    check(lib().nep_param_grad_adjoint(model.handle, ctypes.byref(dsys.c), ctypes.byref(nl.c),
+                                       _ptr(a_e), _ptr(lam), _ptr(mu), _ptr(grad), ws.ptr, ws.bytes,
+                                       _stream(stream)), "nep_param_grad_adjoint")
+    return grad
 
 
 NOALLOC_SCRATCH_BYTES = 32 << 20

@@ -108,6 +108,49 @@ WsLayout ws_layout(const nep_model* m, int N, int B, int cap, int cap_ang) {
     return w;
 }
 
+// Training scratch placed after the evaluation scratch.
+struct TrainLayout {
+    WsLayout w;
+    size_t q, p, fb, lam4, aE, mu, partialF, etot, vir, force, dq, dS, df, coef, rho, xz, bins, gpart,
+        loss;
+    size_t total;
+};
+
+TrainLayout train_layout(const nep_model* m, int N, int B, int cap, int cap_ang) {
+    TrainLayout t;
+    t.w = ws_layout(m, N, B, cap, cap_ang);
+    size_t o = t.w.total;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = align_up(o + bytes);
+        return at;
+    };
+    const size_t n = (size_t)N;
+    const int D = m->lay.D, NA = m->hp.n_ang, T = m->hp.n_types, KR = m->hp.k_rad, KA = m->hp.k_ang;
+    const int H = m->hp.n_hidden;
+    t.q = take(4 * n * D);
+    t.p = take(4 * n * D);
+    t.fb = take(4 * n * T * KR);
+    t.lam4 = take(16 * n);
+    t.aE = take(4 * (size_t)B);
+    t.mu = take(36 * (size_t)B);
+    t.partialF = take(8 * (size_t)t.w.max_chunks);
+    t.etot = take(8 * (size_t)B);
+    t.vir = take(72 * (size_t)B);
+    t.force = take(12 * n);
+    t.dq = take(4 * n * D);
+    t.dS = take(4 * n * NA * nep::kLM);
+    t.df = take(4 * n * T * KR);
+    t.coef = take(4 * n * 3 * H);
+    t.rho = take(4 * n * D);
+    t.xz = take(4 * n * 2 * NA * (size_t)cap_ang);
+    t.bins = take(4 * n * T * NA * KA);
+    t.gpart = take(4 * (size_t)m->ks->grad_chunks(N) * m->lay.P);
+    t.loss = take(8);
+    t.total = o;
+    return t;
+}
+
 template <class T>
 T* at(void* base, size_t off) {
     return reinterpret_cast<T*>(static_cast<char*>(base) + off);
@@ -187,6 +230,9 @@ nep::EvalArgs make_args(const nep_model* m, const nep_system* s, const nep_nlist
     a.fpart = at<float>(work, w.fpart);
     a.wat = at<float>(work, w.wat);
     a.status = nl->status;
+    a.q_out = nullptr;
+    a.p_out = nullptr;
+    a.fb_out = nullptr;
     return a;
 }
 
@@ -228,6 +274,73 @@ nep_status efv_impl(nep_model* m, const nep_system* s, const nep_nlist* nl, floa
     NEP_CUDA(nep::launch_final_reduce(B, at<int>(work, w.chunk_start), at<double>(work, w.partial), e_tot,
                                       virial, st),
              "final reduce");
+    return NEP_OK;
+}
+
+nep_status train_impl(nep_model* m, const nep_system* s, const nep_nlist* nl, const double* e_lbl,
+                      const float* f_lbl, const double* v_lbl, const float* w_host, int loss_mode,
+                      const double* a_e, const float* lam, const double* mu, float* grad,
+                      double* loss, void* work, const TrainLayout& tl, cudaStream_t st) {
+    const int N = s->n_atoms, B = s->n_cfg;
+    const WsLayout& w = tl.w;
+    NEP_CUDA(nep::launch_pack(s->pos, s->type, s->atom_off, N, B, m->hp.n_types, at<float4>(work, w.pos4),
+                              at<int>(work, w.cfg), nl->status, st),
+             "pack");
+    NEP_CUDA(nep::launch_chunk_plan(s->atom_off, B, at<int>(work, w.chunk_start), st), "chunk plan");
+    nep::EvalArgs a = make_args(m, s, nl, work, w);
+    a.q_out = at<float>(work, tl.q);
+    a.p_out = at<float>(work, tl.p);
+    a.fb_out = at<float>(work, tl.fb);
+    if (N > 0) NEP_CUDA(m->ks->descriptor(a, st), "descriptor kernel");
+    if (e_lbl) {
+        // forward forces, energies and virials, then the loss and its adjoints
+        if (N > 0) NEP_CUDA(m->ks->force(a, st), "force kernel");
+        NEP_CUDA(nep::launch_gather_reduce(a, s->atom_off, at<int>(work, w.chunk_start), w.max_chunks,
+                                           at<double>(work, w.partial), at<float>(work, tl.force),
+                                           nullptr, st),
+                 "gather");
+        NEP_CUDA(nep::launch_final_reduce(B, at<int>(work, w.chunk_start), at<double>(work, w.partial),
+                                          at<double>(work, tl.etot), at<double>(work, tl.vir), st),
+                 "final reduce");
+        NEP_CUDA(nep::launch_loss(N, B, s->atom_off, at<int>(work, w.chunk_start), w.max_chunks,
+                                  at<float>(work, tl.force), f_lbl, at<double>(work, tl.etot),
+                                  at<double>(work, tl.vir), e_lbl, v_lbl, w_host, loss_mode,
+                                  at<float4>(work, tl.lam4), at<float>(work, tl.aE),
+                                  at<float>(work, tl.mu), at<double>(work, tl.partialF),
+                                  loss ? loss : at<double>(work, tl.loss), st),
+                 "loss");
+    } else {
+        NEP_CUDA(nep::launch_pack_adjoint(N, B, lam, a_e, mu, at<float4>(work, tl.lam4),
+                                          at<float>(work, tl.aE), at<float>(work, tl.mu), st),
+                 "adjoints");
+    }
+    nep::TrainArgs t;
+    t.e = a;
+    t.lam4 = at<float4>(work, tl.lam4);
+    t.aE = at<float>(work, tl.aE);
+    t.mu = at<float>(work, tl.mu);
+    t.dq = at<float>(work, tl.dq);
+    t.dS = at<float>(work, tl.dS);
+    t.df = at<float>(work, tl.df);
+    t.coef = at<float>(work, tl.coef);
+    t.rho = at<float>(work, tl.rho);
+    t.xz = at<float>(work, tl.xz);
+    t.bins = at<float>(work, tl.bins);
+    t.gpart = at<float>(work, tl.gpart);
+    t.grad = grad;
+    NEP_CUDA(m->ks->train(t, st), "gradient kernels");
+    return NEP_OK;
+}
+
+nep_status check_train_work(const nep_model* m, const nep_system* s, const nep_nlist* nl, void* work,
+                            size_t work_bytes, TrainLayout* tl) {
+    *tl = train_layout(m, s->n_atoms, s->n_cfg, nl->cap, nl->cap_ang);
+    if (work_bytes < tl->total)
+        return fail(NEP_ERR_ARG, "training workspace too small: %zu bytes given, %zu needed "
+                    "(nep_train_workspace_bytes)", work_bytes, tl->total);
+    if (!work) return fail(NEP_ERR_ARG, "workspace is NULL");
+    if ((reinterpret_cast<uintptr_t>(work) & 255) != 0)
+        return fail(NEP_ERR_ARG, "workspace must be 256-byte aligned");
     return NEP_OK;
 }
 
@@ -310,6 +423,7 @@ nep_status nep_create(const nep_hparams* hp, const float* params_host, size_t n_
     cudaGetDevice(&m->device);
     m->n_timing = 0;
     cudaError_t e = ks->init(hp->n_hidden);
+    if (e == cudaSuccess) e = ks->train_init(hp->n_hidden);
     if (e != cudaSuccess) {
         delete m;
         return cuda_fail(e, "kernel attributes");
@@ -458,21 +572,42 @@ nep_status nep_energy_forces_virial_noalloc(nep_model* m, const nep_system* sys,
     return efv_impl(m, sys, nl, e_atom, force, e_tot, virial, work, w, (cudaStream_t)stream);
 }
 
+size_t nep_train_workspace_bytes(const nep_model* m, int n_atoms, int n_cfg, int cap, int cap_ang) {
+    if (!m || n_atoms < 0 || n_cfg < 1 || cap < 1 || cap_ang < 1) return 0;
+    return train_layout(m, n_atoms, n_cfg, cap, cap_ang).total;
+}
+
 nep_status nep_param_grad(nep_model* m, const nep_system* sys, const nep_nlist* nl,
                           const double* e_lbl, const float* f_lbl, const double* v_lbl,
                           const float* w_host, int loss_mode, float* grad, double* loss, void* work,
                           size_t work_bytes, void* stream) {
-    (void)m; (void)sys; (void)nl; (void)e_lbl; (void)f_lbl; (void)v_lbl; (void)w_host;
-    (void)loss_mode; (void)grad; (void)loss; (void)work; (void)work_bytes; (void)stream;
-    return fail(NEP_ERR_UNSUPPORTED, "nep_param_grad is not built yet");
+    nep_status s;
+    if ((s = check_system(m, sys)) != NEP_OK) return s;
+    if ((s = check_nlist(nl, sys->n_atoms)) != NEP_OK) return s;
+    if (!e_lbl || !v_lbl || (sys->n_atoms > 0 && !f_lbl)) return fail(NEP_ERR_ARG, "labels are NULL");
+    if (!w_host) return fail(NEP_ERR_ARG, "loss weights are NULL");
+    if (loss_mode != 0 && loss_mode != 1) return fail(NEP_ERR_ARG, "loss_mode must be 0 or 1");
+    if (!grad) return fail(NEP_ERR_ARG, "grad is NULL");
+    if (!nl->min_image && !nl->shift) return fail(NEP_ERR_STATE, "list was not built");
+    TrainLayout tl;
+    if ((s = check_train_work(m, sys, nl, work, work_bytes, &tl)) != NEP_OK) return s;
+    return train_impl(m, sys, nl, e_lbl, f_lbl, v_lbl, w_host, loss_mode, nullptr, nullptr, nullptr, grad,
+                      loss, work, tl, (cudaStream_t)stream);
 }
 
 nep_status nep_param_grad_adjoint(nep_model* m, const nep_system* sys, const nep_nlist* nl,
                                   const double* a_e, const float* lam, const double* mu, float* grad,
                                   void* work, size_t work_bytes, void* stream) {
-    (void)m; (void)sys; (void)nl; (void)a_e; (void)lam; (void)mu; (void)grad; (void)work;
-    (void)work_bytes; (void)stream;
-    return fail(NEP_ERR_UNSUPPORTED, "nep_param_grad_adjoint is not built yet");
+    nep_status s;
+    if ((s = check_system(m, sys)) != NEP_OK) return s;
+    if ((s = check_nlist(nl, sys->n_atoms)) != NEP_OK) return s;
+    if (!a_e || !mu || (sys->n_atoms > 0 && !lam)) return fail(NEP_ERR_ARG, "adjoints are NULL");
+    if (!grad) return fail(NEP_ERR_ARG, "grad is NULL");
+    if (!nl->min_image && !nl->shift) return fail(NEP_ERR_STATE, "list was not built");
+    TrainLayout tl;
+    if ((s = check_train_work(m, sys, nl, work, work_bytes, &tl)) != NEP_OK) return s;
+    return train_impl(m, sys, nl, nullptr, nullptr, nullptr, nullptr, 0, a_e, lam, mu, grad, nullptr,
+                      work, tl, (cudaStream_t)stream);
 }
 
 nep_status nep_set_timing_events(nep_model* m, void* const* events, int n) {

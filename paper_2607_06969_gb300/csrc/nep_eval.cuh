@@ -182,6 +182,12 @@ NEP_HD void desc_atom(const EvalArgs& a, const float* sm, int i) {
         q[n] = acc;
         NEP_SCHED_BARRIER();
     }
+    if (a.fb_out) {
+#pragma unroll
+        for (int t = 0; t < T; ++t)
+#pragma unroll
+            for (int k = 0; k < KR; ++k) a.fb_out[(t * KR + k) * N + i] = fb[t][k];
+    }
 
     // angular: S_nlm = sum_j g_n(r_ij) P_lm(rhat_ij)
     float S[NA][kLM];
@@ -251,6 +257,14 @@ NEP_HD void desc_atom(const EvalArgs& a, const float* sm, int i) {
     a.e_atom[i] = E;
 #pragma unroll
     for (int d = NR; d < D; ++d) a.pang[(d - NR) * N + i] = p[d];
+    if (a.q_out) {
+#pragma unroll
+        for (int d = 0; d < D; ++d) a.q_out[d * N + i] = q[d];
+    }
+    if (a.p_out) {
+#pragma unroll
+        for (int d = 0; d < D; ++d) a.p_out[d * N + i] = p[d];
+    }
     // radial adjoint projected on the neighbour species:
     // P[i][t][k] = sum_n dE/dq_n cR[Zi][t][n][k]
 #pragma unroll
@@ -494,11 +508,15 @@ cudaError_t init_t(int H) {
     return cudaFuncSetAttribute(k_force<C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
-#define NEP_DEFINE_KERNEL_SET(NAME, NR, NA, KR, KA, H4, T)                                  \
-    extern const KernelSet NAME = {NR, NA, KR, KA, H4, T, &smem_bytes_of<Cfg<NR, NA, KR, KA, H4, T>>, \
-                                   &init_t<Cfg<NR, NA, KR, KA, H4, T>>,                       \
-                            &launch_desc_t<Cfg<NR, NA, KR, KA, H4, T>>,                       \
-                            &launch_force_t<Cfg<NR, NA, KR, KA, H4, T>>};
+#define NEP_DEFINE_KERNEL_SET(NAME, NR, NA, KR, KA, H4, T)                                    \
+    extern const KernelSet NAME = {NR, NA, KR, KA, H4, T,                                        \
+                                   &smem_bytes_of<Cfg<NR, NA, KR, KA, H4, T>>,                   \
+                                   &init_t<Cfg<NR, NA, KR, KA, H4, T>>,                          \
+                                   &launch_desc_t<Cfg<NR, NA, KR, KA, H4, T>>,                   \
+                                   &launch_force_t<Cfg<NR, NA, KR, KA, H4, T>>,                  \
+                                   &train_init_t<Cfg<NR, NA, KR, KA, H4, T>>,                    \
+                                   &train_t<Cfg<NR, NA, KR, KA, H4, T>>,                         \
+                                   &grad_chunks_t<Cfg<NR, NA, KR, KA, H4, T>>};
 #endif
 
 }  // namespace nep

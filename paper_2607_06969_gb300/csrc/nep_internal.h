@@ -56,6 +56,27 @@ struct EvalArgs {
     float* fpart;                  // [3][N]
     float* wat;                    // [9][N]          per-atom virial
     int* status;                   // [4] flags (may be null)
+    // training outputs of the descriptor kernel (null when not training)
+    float* q_out;                  // [D][N]          descriptors
+    float* p_out;                  // [D][N]          dE/dq
+    float* fb_out;                 // [T*KR][N]       species-resolved radial basis sums
+};
+
+// Inputs and scratch of the training backward (see nep_train.cuh).
+struct TrainArgs {
+    EvalArgs e;
+    const float4* lam4;            // [N]  force adjoint lambda_i = dL/dF_i
+    const float* aE;               // [B]  energy adjoint dL/dE_b
+    const float* mu;               // [B][9] virial adjoint dL/dV_b
+    float* dq;                     // [D][N]   tangent of q along dr
+    float* dS;                     // [NA*24][N]
+    float* df;                     // [T*KR][N]
+    float* coef;                   // [3H][N]  alpha, beta, gamma of the network gradient
+    float* rho;                    // [D][N]   a dE/dq + d(dE/dq . dq)/dq
+    float* xz;                     // [2*NA][cap_ang][N] per angular pair X_n, Z_n
+    float* bins;                   // [T*NA*KA][N] per-atom angular c-gradient
+    float* gpart;                  // [chunks][P] per-chunk gradient partials
+    float* grad;                   // [P] output
 };
 
 // Offsets of the parameter blocks in the flat vector.
@@ -82,6 +103,9 @@ struct KernelSet {
     cudaError_t (*init)(int H);   // set kernel attributes (dynamic shared memory)
     cudaError_t (*descriptor)(const EvalArgs&, cudaStream_t);
     cudaError_t (*force)(const EvalArgs&, cudaStream_t);
+    cudaError_t (*train_init)(int H);
+    cudaError_t (*train)(const TrainArgs&, cudaStream_t);   // tangent ... gradient
+    int (*grad_chunks)(int N);
 };
 
 const KernelSet* find_kernel_set(int n_rad, int n_ang, int k_rad, int k_ang, int has_4body,
@@ -115,5 +139,12 @@ cudaError_t launch_neighbors(const float* pos, const float4* pos4, const int* at
 cudaError_t launch_kick(float* vel, const float* force, const int* type, const float* inv_mass,
                         int N, float half_dt, float* pos, float dt, cudaStream_t st);
 cudaError_t launch_wrap(float* pos, const int* cfg, const float* box, int N, cudaStream_t st);
+cudaError_t launch_loss(int N, int B, const int* atom_off, const int* chunk_start, int max_chunks,
+                        const float* force, const float* f_lbl, const double* e_tot,
+                        const double* vir, const double* e_lbl, const double* v_lbl,
+                        const float* w, int mode, float4* lam4, float* aE, float* mu,
+                        double* partial, double* loss, cudaStream_t st);
+cudaError_t launch_pack_adjoint(int N, int B, const float* lam, const double* a_e, const double* mu_in,
+                                float4* lam4, float* aE, float* mu, cudaStream_t st);
 
 }  // namespace nep

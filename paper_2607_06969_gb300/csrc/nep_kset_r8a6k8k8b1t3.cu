@@ -1,5 +1,5 @@
 // Kernel instance: n_rad=8 n_ang=6 k_rad=8 k_ang=8 has_4body=1 n_types=3.
-#include "nep_eval.cuh"
+#include "nep_train.cuh"
 
 namespace nep {
 NEP_DEFINE_KERNEL_SET(kset_r8a6k8k8b1t3, 8, 6, 8, 8, 1, 3)

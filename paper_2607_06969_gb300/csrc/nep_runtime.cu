@@ -497,6 +497,95 @@ __global__ void k_wrap(float* pos, const int* __restrict__ cfg, const float* __r
     }
 }
 
+// ------------------------------------------------------------- loss adjoints
+// Force residuals per chunk: lam_i = 2 wF (F_i - F_lbl,i) / (3 N_b B) and the
+// FP64 partial sum of |dF|^2 (Eq. 20).
+__global__ void __launch_bounds__(kRedThreads) k_loss_atoms(
+    int N, int B, const int* __restrict__ atom_off, const int* __restrict__ chunk_start,
+    const float* __restrict__ force, const float* __restrict__ f_lbl, float wF, float4* lam4,
+    double* partial) {
+    const int k = blockIdx.x;
+    const int total = chunk_start[B];
+    if (k >= total) return;
+    const int b = find_segment(chunk_start, B, k);
+    const int a0 = atom_off[b] + (k - chunk_start[b]) * kChunk;
+    const int a1 = min(atom_off[b + 1], a0 + kChunk);
+    const int nb = atom_off[b + 1] - atom_off[b];
+    const float cf = 2.0f * wF / (3.0f * (float)nb * (float)B);
+    double acc = 0.0;
+    for (int i = a0 + threadIdx.x; i < a1; i += kRedThreads) {
+        const float dx = force[i] - f_lbl[i];
+        const float dy = force[N + i] - f_lbl[N + i];
+        const float dz = force[2 * N + i] - f_lbl[2 * N + i];
+        lam4[i] = make_float4(cf * dx, cf * dy, cf * dz, 0.0f);
+        acc += (double)dx * dx + (double)dy * dy + (double)dz * dz;
+    }
+    __shared__ double red[kRedThreads];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = kRedThreads / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[k] = red[0];
+}
+
+// Per-configuration loss terms and energy/virial adjoints (Eqs. 18-21), and
+// the batch loss summed in a fixed tree (one CTA).
+__global__ void __launch_bounds__(kRedThreads) k_loss_cfg(
+    int B, const int* __restrict__ atom_off, const int* __restrict__ chunk_start,
+    const double* __restrict__ partial, const double* __restrict__ e_tot,
+    const double* __restrict__ vir, const double* __restrict__ e_lbl,
+    const double* __restrict__ v_lbl, float wE, float wF, float wV, int mode, float* aE, float* mu,
+    double* loss) {
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < B; b += kRedThreads) {
+        const double nb = (double)(atom_off[b + 1] - atom_off[b]);
+        const double n = nb > 0.0 ? nb : 1.0;
+        double sF = 0.0;
+        for (int k = chunk_start[b]; k < chunk_start[b + 1]; ++k) sF += partial[k];
+        const double dE = e_tot[b] - e_lbl[b];
+        double sV = 0.0;
+        for (int c = 0; c < 9; ++c) {
+            const double dv = vir[9 * b + c] - v_lbl[9 * b + c];
+            sV += dv * dv;
+        }
+        double Lb;
+        if (mode == 0) {
+            Lb = wE * (dE / n) * (dE / n) + wF * sF / (3.0 * n) + wV * sV / (9.0 * n * n);
+            aE[b] = (float)(2.0 * wE * dE / (n * n) / B);
+            for (int c = 0; c < 9; ++c)
+                mu[9 * b + c] = (float)(2.0 * wV * (vir[9 * b + c] - v_lbl[9 * b + c]) / (9.0 * n * n) / B);
+        } else {
+            Lb = wE * dE * dE / n + wF * sF / (3.0 * n) + wV * sV / (9.0 * n);
+            aE[b] = (float)(2.0 * wE * dE / n / B);
+            for (int c = 0; c < 9; ++c)
+                mu[9 * b + c] = (float)(2.0 * wV * (vir[9 * b + c] - v_lbl[9 * b + c]) / (9.0 * n) / B);
+        }
+        if (nb > 0.0) acc += Lb;
+    }
+    __shared__ double red[kRedThreads];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = kRedThreads / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && loss) *loss = red[0] / B;
+}
+
+// External adjoints (vector-Jacobian product) into the kernels' layout.
+__global__ void k_pack_adjoint(int N, int B, const float* __restrict__ lam,
+                               const double* __restrict__ a_e, const double* __restrict__ mu_in,
+                               float4* lam4, float* aE, float* mu) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) lam4[i] = make_float4(lam[i], lam[N + i], lam[2 * N + i], 0.0f);
+    if (i < B) {
+        aE[i] = (float)a_e[i];
+        for (int c = 0; c < 9; ++c) mu[9 * i + c] = (float)mu_in[9 * i + c];
+    }
+}
+
 inline int blocks(int n, int t) { return (n + t - 1) / t; }
 
 }  // namespace
@@ -562,6 +651,26 @@ cudaError_t launch_kick(float* vel, const float* force, const int* type, const f
     InvMass im;
     for (int t = 0; t < kMaxTypes; ++t) im.v[t] = inv_mass[t];
     if (N > 0) k_kick<<<blocks(N, 256), 256, 0, st>>>(vel, force, type, im, N, half_dt, pos, dt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_loss(int N, int B, const int* atom_off, const int* chunk_start, int max_chunks,
+                        const float* force, const float* f_lbl, const double* e_tot,
+                        const double* vir, const double* e_lbl, const double* v_lbl,
+                        const float* w, int mode, float4* lam4, float* aE, float* mu,
+                        double* partial, double* loss, cudaStream_t st) {
+    if (max_chunks > 0)
+        k_loss_atoms<<<max_chunks, kRedThreads, 0, st>>>(N, B, atom_off, chunk_start, force, f_lbl, w[1],
+                                                         lam4, partial);
+    k_loss_cfg<<<1, kRedThreads, 0, st>>>(B, atom_off, chunk_start, partial, e_tot, vir, e_lbl, v_lbl,
+                                          w[0], w[1], w[2], mode, aE, mu, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_adjoint(int N, int B, const float* lam, const double* a_e, const double* mu_in,
+                                float4* lam4, float* aE, float* mu, cudaStream_t st) {
+    const int n = N > B ? N : B;
+    if (n > 0) k_pack_adjoint<<<blocks(n, 256), 256, 0, st>>>(N, B, lam, a_e, mu_in, lam4, aE, mu);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,560 @@
+// Training backward: gradient of Phi = sum_b aE_b E_b + sum_i lam_i . F_i
+// + sum_b mu_b : V_b with respect to every parameter (the loss gradient of
+// Eqs. 18-21 when aE, lam, mu are the loss adjoints), without autograd
+// caches; per-pair derivatives are recomputed.
+//
+// With F_i = -dE/dr_i (Eq. 3) and V = -dE/deps (Eq. 4),
+//   Phi = sum_k [ aE E_k + sum_j dE_k/dr_kj . dr_kj ],
+//   dr_kj = -(lam_j - lam_k) - mu r_kj,
+// and sum_j dE_k/dr_kj . dr_kj = p_k . dq_k with p = dE/dq and dq the
+// tangent of the descriptors along dr.  Kernels, one thread per atom:
+//   tangent : dq (radial via species-resolved sums of Q'_k (rhat . dr),
+//             angular via dS_nlm), stored with dS.
+//   mlp2    : network second-order terms: alpha, beta, gamma (network
+//             gradient coefficients) and rho = aE p + d(p . dq)/dq.
+//   xzP/xzR : per angular pair X_n = sum_m P_nm Y_m + sum_m R_nm dY_m . dr and
+//             Z_n = (rhat . dr) sum_m R_nm Y_m, where P = dPhi/dS, R = dPhi/d(dS).
+//   cbins   : per-atom angular c-gradient sum_j Q_k X_n + Q'_k Z_n by species.
+//   grad    : per-chunk sums over atoms of every parameter's contributions,
+//             then an FP64 sum over chunks in fixed order.
+#pragma once
+#include "nep_eval.cuh"
+
+namespace nep {
+
+constexpr int kGradChunk = 32;   // atoms per gradient-partial CTA
+
+NEP_HD int config_of_comp_j(int addr, int N) { return addr - (addr / N) * N; }
+
+NEP_HD void adjoint_frame(const TrainArgs& t, int i, float4& li, float* mu) {
+    li = t.lam4[i];
+    const int b = t.e.cfg[i];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) mu[k] = t.mu[9 * b + k];
+}
+
+// dr_ij = -(lam_j - lam_i) - mu r_ij
+NEP_HD void pair_tangent(const float* mu, float4 li, float4 lj, float rx, float ry, float rz,
+                         float& dx, float& dy, float& dz) {
+    dx = -(lj.x - li.x) - (mu[0] * rx + mu[1] * ry + mu[2] * rz);
+    dy = -(lj.y - li.y) - (mu[3] * rx + mu[4] * ry + mu[5] * rz);
+    dz = -(lj.z - li.z) - (mu[6] * rx + mu[7] * ry + mu[8] * rz);
+}
+
+// ---------------------------------------------------------------------------
+template <class C>
+NEP_HD void tangent_atom(const TrainArgs& t, const float* sm, int i) {
+    constexpr int NR = C::NR, NA = C::NA, KR = C::KR, KA = C::KA, T = C::T, D = C::D;
+    const EvalArgs& a = t.e;
+    const SmemLayout sl = smem_layout<C>(a.H);
+    const int N = a.N;
+    const int ti = f2i(a.pos4[i].w);
+    const float irR = 1.0f / a.rc_rad, irA = 1.0f / a.rc_ang;
+    float4 li;
+    float mu[9];
+    adjoint_frame(t, i, li, mu);
+
+    // radial: DF[t][k] = sum_{j of species t} Q'_k(r) (rhat . dr)
+    float df[T][KR];
+#pragma unroll
+    for (int s = 0; s < T; ++s)
+#pragma unroll
+        for (int k = 0; k < KR; ++k) df[s][k] = 0.0f;
+    const int ncr = a.cnt_compr[i];
+    for (int s = 0; s < ncr; ++s) {
+        const float4 e = a.compr[s * N + i];
+        const int bits = f2i(e.w);
+        const int tj = bits & 3;
+        const int j = (int)((unsigned)bits >> 2);
+        float drx, dry, drz;
+        pair_tangent(mu, li, t.lam4[j], e.x, e.y, e.z, drx, dry, drz);
+        const float r = sqrt_f(dist2(e.x, e.y, e.z));
+        const float ir = rcp_f(r);
+        const float udr = (e.x * drx + e.y * dry + e.z * drz) * ir;
+        float f[KR], fp[KR];
+        basis_d<KR>(r, irR, f, fp);
+#pragma unroll
+        for (int s2 = 0; s2 < T; ++s2) {
+            const float w = (tj == s2) ? udr : 0.0f;
+#pragma unroll
+            for (int k = 0; k < KR; ++k) df[s2][k] = fmaf(w, fp[k], df[s2][k]);
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < T; ++s)
+#pragma unroll
+        for (int k = 0; k < KR; ++k) t.df[(s * KR + k) * N + i] = df[s][k];
+#pragma unroll
+    for (int n = 0; n < NR; ++n) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int s = 0; s < T; ++s) {
+            const float* c = sm + sl.cR + (ti * T + s) * C::SR + n * KR;
+#pragma unroll
+            for (int k = 0; k < KR; ++k) acc = fmaf(c[k], df[s][k], acc);
+        }
+        t.dq[n * N + i] = acc;
+        NEP_SCHED_BARRIER();
+    }
+
+    // angular: dS_nlm = sum_j [g'_n (rhat.dr) Y_m + g_n (grad P_m . dr - l Y_m rhat.dr)/r]
+    float dS[NA][kLM];
+#pragma unroll
+    for (int n = 0; n < NA; ++n)
+#pragma unroll
+        for (int m = 0; m < kLM; ++m) dS[n][m] = 0.0f;
+    const int nc = a.cnt_comp[i];
+    for (int c = 0; c < nc; ++c) {
+        const float4 e = a.comp[c * N + i];
+        const int bits = f2i(e.w);
+        const int tj = bits & 3;
+        const int j = config_of_comp_j((int)((unsigned)bits >> 2), N);
+        float drx, dry, drz;
+        pair_tangent(mu, li, t.lam4[j], e.x, e.y, e.z, drx, dry, drz);
+        const float r = sqrt_f(dist2(e.x, e.y, e.z));
+        const float ir = rcp_f(r);
+        const HarmTerms ht = harm_terms(e.x * ir, e.y * ir, e.z * ir);
+        const float udr = ht.x * drx + ht.y * dry + ht.z * drz;
+        float g[NA], gp[NA];
+        {
+            float f[KA], fp[KA];
+            basis_d<KA>(r, irA, f, fp);
+            const float* cc = sm + sl.cA + (ti * T + tj) * C::SA;
+#pragma unroll
+            for (int n = 0; n < NA; ++n) {
+                float u = 0.0f, v = 0.0f;
+#pragma unroll
+                for (int k = 0; k < KA; ++k) {
+                    u = fmaf(cc[n * KA + k], f[k], u);
+                    v = fmaf(cc[n * KA + k], fp[k], v);
+                }
+                g[n] = u;
+                gp[n] = v;
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < kLM; ++m) {
+            float Y, hx, hy, hz;
+            harm_m(m, ht, Y, hx, hy, hz);
+            const float gdr = (hx * drx + hy * dry + hz * drz) * ir;
+            const float yu = Y * udr;
+            const float lr = (float)lm_l(m) * ir;
+#pragma unroll
+            for (int n = 0; n < NA; ++n)
+                dS[n][m] = fmaf(yu, fmaf(-lr, g[n], gp[n]), fmaf(g[n], gdr, dS[n][m]));
+        }
+    }
+#pragma unroll
+    for (int n = 0; n < NA; ++n) {
+        float S[kLM];
+#pragma unroll
+        for (int m = 0; m < kLM; ++m) {
+            S[m] = a.S[(n * kLM + m) * N + i];
+            t.dS[(n * kLM + m) * N + i] = dS[n][m];
+        }
+        float dql[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int m = 0; m < kLM; ++m) dql[lm_l(m) - 1] = fmaf(2.0f * clm(m) * S[m], dS[n][m], dql[lm_l(m) - 1]);
+#pragma unroll
+        for (int l = 0; l < 4; ++l) t.dq[(NR + n * 4 + l) * N + i] = dql[l];
+        if (C::H4) {
+            float J[5], S2[5] = {S[3], S[4], S[5], S[6], S[7]};
+            fourbody(S2, J);
+            float v = 0.0f;
+#pragma unroll
+            for (int m = 0; m < 5; ++m) v = fmaf(J[m], dS[n][3 + m], v);
+            t.dq[(NR + NA * 4 + n) * N + i] = v;
+        }
+        NEP_SCHED_BARRIER();
+    }
+    (void)D;
+}
+
+// ---------------------------------------------------------------------------
+template <class C>
+NEP_HD void mlp2_atom(const TrainArgs& t, const float* sm, int i) {
+    constexpr int D = C::D;
+    const EvalArgs& a = t.e;
+    const SmemLayout sl = smem_layout<C>(a.H);
+    const int N = a.N, H = a.H;
+    const int ti = f2i(a.pos4[i].w);
+    const float aE = t.aE[a.cfg[i]];
+    const float* W0 = sm + sl.W0 + ti * sl.SW;
+    const float* b0 = sm + sl.b0 + ti * sl.HS;
+    const float* w1 = sm + sl.w1 + ti * sl.HS;
+    float q[D], dq[D], p2[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        q[d] = a.q_out[d * N + i];
+        dq[d] = t.dq[d * N + i];
+        p2[d] = 0.0f;
+    }
+    for (int h = 0; h < H; ++h) {
+        const float* w = W0 + h * D;
+        float z = b0[h], u = 0.0f;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            z = fmaf(w[d], q[d], z);
+            u = fmaf(w[d], dq[d], u);
+        }
+        const float th = tanh_f(z);
+        const float s = 1.0f - th * th;
+        const float wh = w1[h];
+        const float c2 = -2.0f * wh * u * th * s;     // d(w1 s u)/dz
+        t.coef[h * N + i] = aE * wh * s + c2;          // alpha: coefficient of q in dW0, and db0
+        t.coef[(H + h) * N + i] = wh * s;              // beta: coefficient of dq in dW0
+        t.coef[(2 * H + h) * N + i] = aE * th + s * u; // gamma: dw1
+#pragma unroll
+        for (int d = 0; d < D; ++d) p2[d] = fmaf(c2, w[d], p2[d]);
+    }
+#pragma unroll
+    for (int d = 0; d < D; ++d) t.rho[d * N + i] = fmaf(aE, a.p_out[d * N + i], p2[d]);
+}
+
+// ---------------------------------------------------------------------------
+// X_n from P = dPhi/dS (pass 1)
+template <class C>
+NEP_HD void xzp_atom(const TrainArgs& t, const float* sm, int i) {
+    constexpr int NR = C::NR, NA = C::NA;
+    const EvalArgs& a = t.e;
+    const int N = a.N, capA = a.cap_ang;
+    float P[NA][kLM];
+#pragma unroll
+    for (int n = 0; n < NA; ++n) {
+        float rl[4], pl[4];
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            rl[l] = t.rho[(NR + n * 4 + l) * N + i];
+            pl[l] = a.p_out[(NR + n * 4 + l) * N + i];
+        }
+        float S2[5], dS2[5];
+#pragma unroll
+        for (int m = 0; m < kLM; ++m) {
+            const float S = a.S[(n * kLM + m) * N + i];
+            const float dS = t.dS[(n * kLM + m) * N + i];
+            if (m >= 3 && m < 8) { S2[m - 3] = S; dS2[m - 3] = dS; }
+            P[n][m] = 2.0f * clm(m) * fmaf(rl[lm_l(m) - 1], S, pl[lm_l(m) - 1] * dS);
+        }
+        if (C::H4) {
+            const float r4 = t.rho[(NR + NA * 4 + n) * N + i];
+            const float p4 = a.p_out[(NR + NA * 4 + n) * N + i];
+            float J[5], dJ[5];
+            fourbody_jvp(S2, dS2, J, dJ);
+#pragma unroll
+            for (int m = 0; m < 5; ++m) P[n][3 + m] = fmaf(r4, J[m], fmaf(p4, dJ[m], P[n][3 + m]));
+        }
+    }
+    const int nc = a.cnt_comp[i];
+    for (int c = 0; c < nc; ++c) {
+        const float4 e = a.comp[c * N + i];
+        const float ir = rcp_f(sqrt_f(dist2(e.x, e.y, e.z)));
+        const HarmTerms ht = harm_terms(e.x * ir, e.y * ir, e.z * ir);
+        float X[NA];
+#pragma unroll
+        for (int n = 0; n < NA; ++n) X[n] = 0.0f;
+#pragma unroll
+        for (int m = 0; m < kLM; ++m) {
+            float Y, hx, hy, hz;
+            harm_m(m, ht, Y, hx, hy, hz);
+#pragma unroll
+            for (int n = 0; n < NA; ++n) X[n] = fmaf(P[n][m], Y, X[n]);
+        }
+#pragma unroll
+        for (int n = 0; n < NA; ++n) t.xz[((size_t)n * capA + c) * N + i] = X[n];
+    }
+}
+
+// X_n += sum_m R dY_m . dr, Z_n = (rhat.dr) sum_m R Y_m with R = dPhi/d(dS) (pass 2)
+template <class C>
+NEP_HD void xzr_atom(const TrainArgs& t, const float* sm, int i) {
+    constexpr int NR = C::NR, NA = C::NA;
+    (void)sm;
+    const EvalArgs& a = t.e;
+    const int N = a.N, capA = a.cap_ang;
+    float R[NA][kLM];
+#pragma unroll
+    for (int n = 0; n < NA; ++n) {
+        float pl[4];
+#pragma unroll
+        for (int l = 0; l < 4; ++l) pl[l] = a.p_out[(NR + n * 4 + l) * N + i];
+        float S2[5];
+#pragma unroll
+        for (int m = 0; m < kLM; ++m) {
+            const float S = a.S[(n * kLM + m) * N + i];
+            if (m >= 3 && m < 8) S2[m - 3] = S;
+            R[n][m] = 2.0f * clm(m) * pl[lm_l(m) - 1] * S;
+        }
+        if (C::H4) {
+            const float p4 = a.p_out[(NR + NA * 4 + n) * N + i];
+            float J[5];
+            fourbody(S2, J);
+#pragma unroll
+            for (int m = 0; m < 5; ++m) R[n][3 + m] = fmaf(p4, J[m], R[n][3 + m]);
+        }
+    }
+    float4 li;
+    float mu[9];
+    adjoint_frame(t, i, li, mu);
+    const int nc = a.cnt_comp[i];
+    for (int c = 0; c < nc; ++c) {
+        const float4 e = a.comp[c * N + i];
+        const int bits = f2i(e.w);
+        const int j = config_of_comp_j((int)((unsigned)bits >> 2), N);
+        float drx, dry, drz;
+        pair_tangent(mu, li, t.lam4[j], e.x, e.y, e.z, drx, dry, drz);
+        const float ir = rcp_f(sqrt_f(dist2(e.x, e.y, e.z)));
+        const HarmTerms ht = harm_terms(e.x * ir, e.y * ir, e.z * ir);
+        const float udr = ht.x * drx + ht.y * dry + ht.z * drz;
+        float X[NA], Z[NA];
+#pragma unroll
+        for (int n = 0; n < NA; ++n) {
+            X[n] = 0.0f;
+            Z[n] = 0.0f;
+        }
+#pragma unroll
+        for (int m = 0; m < kLM; ++m) {
+            float Y, hx, hy, hz;
+            harm_m(m, ht, Y, hx, hy, hz);
+            const float dY = ((hx * drx + hy * dry + hz * drz) - (float)lm_l(m) * Y * udr) * ir;
+#pragma unroll
+            for (int n = 0; n < NA; ++n) {
+                X[n] = fmaf(R[n][m], dY, X[n]);
+                Z[n] = fmaf(R[n][m], Y, Z[n]);
+            }
+        }
+#pragma unroll
+        for (int n = 0; n < NA; ++n) {
+            const size_t xi = ((size_t)n * capA + c) * N + i;
+            t.xz[xi] += X[n];
+            t.xz[((size_t)(NA + n) * capA + c) * N + i] = udr * Z[n];
+        }
+    }
+}
+
+// per-atom angular c-gradient: bins[t][n][k] = sum_{j of species t} Q_k X_n + Q'_k Z_n
+template <class C>
+NEP_HD void cbins_atom(const TrainArgs& t, const float* sm, int i) {
+    constexpr int NA = C::NA, KA = C::KA, T = C::T;
+    (void)sm;
+    const EvalArgs& a = t.e;
+    const int N = a.N, capA = a.cap_ang;
+    const float irA = 1.0f / a.rc_ang;
+    float bins[T][NA][KA];
+#pragma unroll
+    for (int s = 0; s < T; ++s)
+#pragma unroll
+        for (int n = 0; n < NA; ++n)
+#pragma unroll
+            for (int k = 0; k < KA; ++k) bins[s][n][k] = 0.0f;
+    const int nc = a.cnt_comp[i];
+    for (int c = 0; c < nc; ++c) {
+        const float4 e = a.comp[c * N + i];
+        const int tj = f2i(e.w) & 3;
+        const float r = sqrt_f(dist2(e.x, e.y, e.z));
+        float f[KA], fp[KA];
+        basis_d<KA>(r, irA, f, fp);
+        float X[NA], Z[NA];
+#pragma unroll
+        for (int n = 0; n < NA; ++n) {
+            X[n] = t.xz[((size_t)n * capA + c) * N + i];
+            Z[n] = t.xz[((size_t)(NA + n) * capA + c) * N + i];
+        }
+#pragma unroll
+        for (int s = 0; s < T; ++s) {
+            if (tj == s) {
+#pragma unroll
+                for (int n = 0; n < NA; ++n)
+#pragma unroll
+                    for (int k = 0; k < KA; ++k) bins[s][n][k] = fmaf(f[k], X[n], fmaf(fp[k], Z[n], bins[s][n][k]));
+            }
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < T; ++s)
+#pragma unroll
+        for (int n = 0; n < NA; ++n)
+#pragma unroll
+            for (int k = 0; k < KA; ++k) t.bins[((s * NA + n) * KA + k) * N + i] = bins[s][n][k];
+}
+
+// ---------------------------------------------------------------------------
+// Gradient partial of one chunk of kGradChunk atoms: every parameter's
+// contribution summed over the chunk in atom order.
+template <class C>
+struct GradStage {
+    static constexpr int NR = C::NR, NA = C::NA, KR = C::KR, KA = C::KA, T = C::T, D = C::D;
+    // per-atom layout in shared memory (floats)
+    static NEP_HD int width(int H) { return 2 + 2 * D + 3 * H + 2 * NR + 2 * T * KR + T * NA * KA; }
+    static NEP_HD int o_q() { return 2; }
+    static NEP_HD int o_dq() { return 2 + D; }
+    static NEP_HD int o_coef() { return 2 + 2 * D; }
+    static NEP_HD int o_rho(int H) { return 2 + 2 * D + 3 * H; }
+    static NEP_HD int o_p(int H) { return o_rho(H) + NR; }
+    static NEP_HD int o_fb(int H) { return o_p(H) + NR; }
+    static NEP_HD int o_df(int H) { return o_fb(H) + T * KR; }
+    static NEP_HD int o_bins(int H) { return o_df(H) + T * KR; }
+};
+
+template <class C>
+NEP_HD void stage_atom(const TrainArgs& t, float* row, int i) {
+    using G = GradStage<C>;
+    constexpr int NR = C::NR, NA = C::NA, KR = C::KR, KA = C::KA, T = C::T, D = C::D;
+    const EvalArgs& a = t.e;
+    const int N = a.N, H = a.H;
+    row[0] = i2f(f2i(a.pos4[i].w));
+    row[1] = t.aE[a.cfg[i]];
+    for (int d = 0; d < D; ++d) {
+        row[G::o_q() + d] = a.q_out[d * N + i];
+        row[G::o_dq() + d] = t.dq[d * N + i];
+    }
+    for (int h = 0; h < 3 * H; ++h) row[G::o_coef() + h] = t.coef[h * N + i];
+    for (int n = 0; n < NR; ++n) {
+        row[G::o_rho(H) + n] = t.rho[n * N + i];
+        row[G::o_p(H) + n] = a.p_out[n * N + i];
+    }
+    for (int k = 0; k < T * KR; ++k) {
+        row[G::o_fb(H) + k] = a.fb_out[k * N + i];
+        row[G::o_df(H) + k] = t.df[k * N + i];
+    }
+    for (int k = 0; k < T * NA * KA; ++k) row[G::o_bins(H) + k] = t.bins[k * N + i];
+}
+
+// sum over the staged atoms of parameter p's contribution
+template <class C>
+NEP_HD float param_partial(const float* stage, int natoms, int H, int p) {
+    using G = GradStage<C>;
+    constexpr int NR = C::NR, NA = C::NA, KR = C::KR, KA = C::KA, T = C::T, D = C::D;
+    const int W = G::width(H);
+    const ParamLayout L = param_layout(T, NR, NA, KR, KA, C::H4, H);
+    float acc = 0.0f;
+    if (p < L.off_cR) {
+        const int sp = p / L.mlp_stride, r = p % L.mlp_stride;
+        const int HD = H * D;
+        for (int a = 0; a < natoms; ++a) {
+            const float* row = stage + a * W;
+            if (f2i(row[0]) != sp) continue;
+            if (r < HD) {
+                const int h = r / D, d = r % D;
+                acc = fmaf(row[G::o_coef() + h], row[G::o_q() + d], acc);
+                acc = fmaf(row[G::o_coef() + H + h], row[G::o_dq() + d], acc);
+            } else if (r < HD + H) {
+                acc += row[G::o_coef() + (r - HD)];
+            } else if (r < HD + 2 * H) {
+                acc += row[G::o_coef() + 2 * H + (r - HD - H)];
+            } else {
+                acc += row[1];
+            }
+        }
+    } else if (p < L.off_cA) {
+        const int x = p - L.off_cR;
+        const int t1 = x / (T * NR * KR), t2 = (x / (NR * KR)) % T, n = (x / KR) % NR, k = x % KR;
+        for (int a = 0; a < natoms; ++a) {
+            const float* row = stage + a * W;
+            if (f2i(row[0]) != t1) continue;
+            acc = fmaf(row[G::o_rho(H) + n], row[G::o_fb(H) + t2 * KR + k], acc);
+            acc = fmaf(row[G::o_p(H) + n], row[G::o_df(H) + t2 * KR + k], acc);
+        }
+    } else {
+        const int x = p - L.off_cA;
+        const int t1 = x / (T * NA * KA), rest = x % (T * NA * KA);
+        for (int a = 0; a < natoms; ++a) {
+            const float* row = stage + a * W;
+            if (f2i(row[0]) != t1) continue;
+            acc += row[G::o_bins(H) + rest];
+        }
+    }
+    return acc;
+}
+
+#if defined(__CUDACC__)
+template <class C>
+__global__ void __launch_bounds__(kBlock, 2) k_tangent(const TrainArgs t) {
+    extern __shared__ float sm[];
+    load_model<C>(sm, t.e.params, t.e.H, threadIdx.x, blockDim.x);
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < t.e.N) tangent_atom<C>(t, sm, i);
+}
+template <class C>
+__global__ void __launch_bounds__(kBlock, 2) k_mlp2(const TrainArgs t) {
+    extern __shared__ float sm[];
+    load_model<C>(sm, t.e.params, t.e.H, threadIdx.x, blockDim.x);
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < t.e.N) mlp2_atom<C>(t, sm, i);
+}
+template <class C>
+__global__ void __launch_bounds__(kBlock, 2) k_xzp(const TrainArgs t) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < t.e.N) xzp_atom<C>(t, nullptr, i);
+}
+template <class C>
+__global__ void __launch_bounds__(kBlock, 2) k_xzr(const TrainArgs t) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < t.e.N) xzr_atom<C>(t, nullptr, i);
+}
+template <class C>
+__global__ void __launch_bounds__(kBlock, 2) k_cbins(const TrainArgs t) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < t.e.N) cbins_atom<C>(t, nullptr, i);
+}
+constexpr int kGradThreads = 256;
+template <class C>
+__global__ void __launch_bounds__(kGradThreads) k_grad_partial(const TrainArgs t) {
+    extern __shared__ float stage[];
+    const int H = t.e.H, N = t.e.N;
+    const int W = GradStage<C>::width(H);
+    const int a0 = blockIdx.x * kGradChunk;
+    const int na = min(kGradChunk, N - a0);
+    for (int a = threadIdx.x; a < na; a += blockDim.x) stage_atom<C>(t, stage + a * W, a0 + a);
+    __syncthreads();
+    const ParamLayout L = param_layout(C::T, C::NR, C::NA, C::KR, C::KA, C::H4, H);
+    for (int p = threadIdx.x; p < L.P; p += blockDim.x)
+        t.gpart[(size_t)blockIdx.x * L.P + p] = param_partial<C>(stage, na, H, p);
+}
+template <class C>
+__global__ void k_grad_final(const TrainArgs t, int nchunk) {
+    const ParamLayout L = param_layout(C::T, C::NR, C::NA, C::KR, C::KA, C::H4, t.e.H);
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= L.P) return;
+    double acc = 0.0;
+    for (int k = 0; k < nchunk; ++k) acc += (double)t.gpart[(size_t)k * L.P + p];
+    t.grad[p] = (float)acc;
+}
+
+template <class C>
+size_t grad_stage_bytes(int H) { return sizeof(float) * (size_t)kGradChunk * GradStage<C>::width(H); }
+
+template <class C>
+cudaError_t train_init_t(int H) {
+    const int smem = (int)smem_bytes_of<C>(H);
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_tangent<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
+    if ((e = cudaFuncSetAttribute(k_mlp2<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
+    return cudaFuncSetAttribute(k_grad_partial<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)grad_stage_bytes<C>(H));
+}
+
+template <class C>
+int grad_chunks_t(int N) { return (N + kGradChunk - 1) / kGradChunk; }
+
+template <class C>
+cudaError_t train_t(const TrainArgs& t, cudaStream_t st) {
+    const int N = t.e.N;
+    const size_t smem = smem_bytes_of<C>(t.e.H);
+    if (N > 0) {
+        const int grid = (N + kBlock - 1) / kBlock;
+        k_tangent<C><<<grid, kBlock, smem, st>>>(t);
+        k_mlp2<C><<<grid, kBlock, smem, st>>>(t);
+        k_xzp<C><<<grid, kBlock, 0, st>>>(t);
+        k_xzr<C><<<grid, kBlock, 0, st>>>(t);
+        k_cbins<C><<<grid, kBlock, 0, st>>>(t);
+        k_grad_partial<C><<<grad_chunks_t<C>(N), kGradThreads, grad_stage_bytes<C>(t.e.H), st>>>(t);
+    }
+    const ParamLayout L = param_layout(C::T, C::NR, C::NA, C::KR, C::KA, C::H4, t.e.H);
+    k_grad_final<C><<<(L.P + 255) / 256, 256, 0, st>>>(t, grad_chunks_t<C>(N));
+    return cudaGetLastError();
+}
+#endif
+
+}  // namespace nep
