@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-train", action="store_true", help="skip the training-step leg")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision leg")
+    ap.add_argument("--no-replicas", action="store_true", help="skip the batched-replica leg")
     ap.add_argument("--ncell", type=int, default=50,
                     help="rock-salt cells per edge (50 = the 900k-atom workload; smaller for profiling)")
     return ap.parse_args()
@@ -323,6 +325,132 @@ def train_leg(nb, torch, I, local) -> dict:
             "steps": K}
 
 
+def mixed_leg(nb, torch, I) -> dict:
+    """Secondary leg: E+F+V of the 3,686,400-atom rock-salt system (80^3
+    cells, 20% cation vacancies) with the larger NEP (n_R=12, n_A=8, 4-body,
+    D=52, MLP 52-64-1), plain FP32 against the FP16 and BF16 tensor-core
+    network; errors of the mixed forms are measured against the FP32 form,
+    which itself matches FP64 to 1e-6 eV/atom and 1e-4 eV/A."""
+    s, h = I.workload_mixed3m7()
+    th = I.init_params(h).astype(np.float32)
+    dsys = nb.DeviceSystem.from_inputs(s)
+    cap, cap_ang = 80, 40
+    nl = nb.NeighborList(s.n_atoms, cap, cap_ang, shifts=False)
+    out = {"workload": "mixed3m7: 3,686,400 atoms, 80^3 rock-salt cells, NEP n_R=12 n_A=8 +4-body "
+                       "(D=52), MLP 52-64-1, one E+F+V per step", "n_atoms": s.n_atoms}
+    ref = None
+    for prec, name in ((0, "fp32"), (1, "fp16"), (2, "bf16")):
+        model = nb.Model(h, th, precision=prec)
+        ws = nb.Workspace(model, s.n_atoms, 1, cap, cap_ang)
+        nb.neighbors(model, dsys, nl, 0.0, ws)
+        if nb.check_list(nl) != nb.NEP_OK:
+            raise RuntimeError(nb.last_error())
+        res = nb.energy_forces_virial(model, dsys, nl, ws)
+        for _ in range(2):
+            nb.energy_forces_virial(model, dsys, nl, ws, out=res)
+        torch.cuda.synchronize()
+        K = 10
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(K):
+            nb.energy_forces_virial(model, dsys, nl, ws, out=res)
+        t1.record()
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1) / K
+        e_atom, force, e_tot, vir = [x.clone() for x in res]
+        entry = {"ms_per_step": ms, "atom_steps_per_s": s.n_atoms / (ms * 1e-3)}
+        if ref is None:
+            ref = (e_atom, force, e_tot)
+        else:
+            entry["force_rms_vs_fp32_eV_per_A"] = float(torch.sqrt(((force - ref[1]) ** 2).mean()))
+            entry["energy_vs_fp32_eV_per_atom"] = float(abs(e_tot - ref[2]).item() / s.n_atoms)
+            entry["energy_rms_per_atom_eV"] = float(torch.sqrt(((e_atom - ref[0]) ** 2).mean()))
+            entry["speedup_vs_fp32"] = out["fp32"]["ms_per_step"] / ms
+        out[name] = entry
+        del ws, model
+        torch.cuda.empty_cache()
+    return out
+
+
+def replicas_leg(nb, torch, I, K: int = 20) -> dict:
+    """Secondary leg: 1,024 independent periodic packings, N log-uniform in
+    [64, 4096] (~975k atoms), config-0 NEP with the FP16 tensor-core network,
+    900 K velocity Verlet (dt 2 fs, rebuild every 10 steps, skin 1 A).  All
+    replicas advance in one launch per kernel, K steps captured in one CUDA
+    graph, kernel variants autotuned; compared with a loop that launches each
+    replica separately."""
+    s, h = I.workload_replicas1024()
+    N, B = s.n_atoms, s.n_cfg
+    th = I.init_params(h).astype(np.float32)
+    masses = I.MASSES.astype(np.float32)
+    model = nb.Model(h, th, precision=1)
+    dsys = nb.DeviceSystem.from_inputs(s)
+    cap, cap_ang = 160, 80
+    nl = nb.NeighborList(N, cap, cap_ang, shifts=True)
+    ws = nb.Workspace(model, N, B, cap, cap_ang)
+    nb.neighbors(model, dsys, nl, SKIN, ws)
+    if nb.check_list(nl) != nb.NEP_OK:
+        raise RuntimeError(nb.last_error())
+    chosen = nb.autotune(model, dsys, nl, ws)
+    e_atom, force, e_tot, vir = nb.energy_forces_virial(model, dsys, nl, ws)
+    vel = torch.from_numpy(np.ascontiguousarray(
+        I.maxwell_boltzmann(s.types, 900.0, atom_off=s.atom_off).astype(np.float32).T)).cuda()
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for k in range(3):
+            nb.md_step(model, dsys, nl, vel, force, e_tot, vir, masses, DT, SKIN, k == 0, ws, stream=stream)
+    stream.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        for k in range(K):
+            nb.md_step(model, dsys, nl, vel, force, e_tot, vir, masses, DT, SKIN, k % REBUILD == 0, ws,
+                       stream=stream)
+    g.replay()
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        t0.record(stream)
+        g.replay()
+        t1.record(stream)
+    torch.cuda.synchronize()
+    if nb.check_list(nl, stream) != nb.NEP_OK:
+        raise RuntimeError("replica list overflow: " + nb.last_error())
+    ms = t0.elapsed_time(t1) / K
+    del g
+
+    # per-replica launch loop over the same replicas (same model, kernels, caps)
+    reps = []
+    for b in range(B):
+        a0, a1 = int(s.atom_off[b]), int(s.atom_off[b + 1])
+        sb = I.System(pos=s.pos[a0:a1], types=s.types[a0:a1], box=s.box[b:b + 1],
+                      atom_off=np.array([0, a1 - a0]))
+        d = nb.DeviceSystem.from_inputs(sb)
+        l = nb.NeighborList(sb.n_atoms, cap, cap_ang, shifts=True)
+        w = nb.Workspace(model, sb.n_atoms, 1, cap, cap_ang)
+        nb.neighbors(model, d, l, SKIN, w)
+        out = nb.energy_forces_virial(model, d, l, w)
+        v = vel[:, a0:a1].contiguous()
+        reps.append((d, l, w, v, out))
+    torch.cuda.synchronize()
+    KL = 3
+    l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0.record()
+    for k in range(KL):
+        for d, l, w, v, (_, f, et, vr) in reps:
+            nb.md_step(model, d, l, v, f, et, vr, masses, DT, SKIN, k == 0, w)
+    l1.record()
+    torch.cuda.synchronize()
+    ms_loop = l0.elapsed_time(l1) / KL
+    return {"workload": "replicas1024: 1,024 packings, N log-uniform [64, 4096] (%d atoms), FP16 "
+                        "tensor-core network, 900 K velocity Verlet" % N,
+            "replica_steps_per_s": B / (ms * 1e-3), "atom_steps_per_s": N / (ms * 1e-3),
+            "ms_per_step": ms, "steps": K,
+            "per_replica_loop": {"ms_per_step": ms_loop, "replica_steps_per_s": B / (ms_loop * 1e-3),
+                                 "steps": KL},
+            "speedup_vs_loop": ms_loop / ms, "autotuned_variants": {"desc": chosen[0], "force": chosen[1]}}
+
+
 # ------------------------------------------------------------------ our arm
 def main():
     args = parse()
@@ -403,6 +531,8 @@ def main():
     e2e_val = world * N * KE / (e2e_ms * 1e-3)
 
     train = None if args.no_train else train_leg(nb, torch, I, local)
+    mixed = None if args.no_mixed else mixed_leg(nb, torch, I)
+    replicas = None if args.no_replicas else replicas_leg(nb, torch, I)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -420,7 +550,7 @@ def main():
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_val, "unit": "atom-steps/s", "steps": KE,
                         "h2d_bytes_per_step": 12 * N, "d2h_bytes_per_step": 12 * N + 8 + 72},
-                "gpu_launches": launches, "clocks": clk, "train": train,
+                "gpu_launches": launches, "clocks": clk, "train": train, "mixed": mixed, "replicas": replicas,
                 "energy": {"e_tot_final": float(e_tot.item())}}
         print(json.dumps(line), flush=True)
     if world > 1:

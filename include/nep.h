@@ -233,6 +233,17 @@ nep_status nep_md_step(nep_model* m, const nep_system* sys, nep_nlist* nl, float
                        float dt, float skin, int rebuild, void* work, size_t work_bytes,
                        void* stream);
 
+/* Autotuner: times every compiled variant of the descriptor and force
+ * kernels (register budgets for 2, 3 or 4 resident blocks of 128 threads per
+ * SM) on this system and list, `reps` timed launches each after one untimed
+ * launch, and stores the fastest pair in the model for the system's size
+ * class (log2 of the mean atom count per configuration).  Later hot calls on
+ * systems of that class use it.  Not a hot call: it synchronises `stream`.
+ * chosen[2] (may be NULL) receives the descriptor and force variant indices
+ * (0, 1, 2 = 2, 3, 4 blocks per SM); the defaults are 1 and 0. */
+nep_status nep_autotune(nep_model* m, const nep_system* sys, const nep_nlist* nl, void* work,
+                        size_t work_bytes, void* stream, int reps, int* chosen);
+
 /* Profiling hook: the next nep_energy_forces_virial / nep_md_step call of
  * this model records events[0] before the descriptor kernel, events[1]
  * between the descriptor and force kernels and events[2] after the force

@@ -22,7 +22,7 @@ ENTRY_POINTS = (
     "nep_num_params", "nep_create", "nep_destroy", "nep_supported", "nep_set_params",
     "nep_workspace_bytes", "nep_train_workspace_bytes", "nep_neighbors", "nep_energy_forces_virial",
     "nep_energy_forces_virial_noalloc", "nep_param_grad",
-    "nep_param_grad_adjoint", "nep_md_step", "nep_set_timing_events", "nep_check",
+    "nep_param_grad_adjoint", "nep_md_step", "nep_autotune", "nep_set_timing_events", "nep_check",
     "nep_last_error", "nep_version",
 )
 
@@ -82,6 +82,8 @@ def lib() -> ctypes.CDLL:
     L.nep_md_step.argtypes = [vp, P(System), P(NList), vp, vp, vp, vp, vp, f, f, i, vp, sz, vp]
     L.nep_check.argtypes = [P(NList), vp]
     L.nep_set_timing_events.argtypes = [vp, P(vp), i]
+    L.nep_autotune.argtypes = [vp, P(System), P(NList), vp, sz, vp, i, P(ctypes.c_int)]
+    L.nep_autotune.restype = i
     L.nep_last_error.restype = ctypes.c_char_p
     L.nep_version.restype = ctypes.c_char_p
     for name in ("nep_create", "nep_destroy", "nep_set_params", "nep_neighbors",
@@ -328,6 +330,16 @@ def set_timing_events(model: Model, events) -> None:
         return
     arr = (ctypes.c_void_p * 3)(*[ctypes.c_void_p(e.cuda_event) for e in events])
     check(lib().nep_set_timing_events(model.handle, arr, 3), "nep_set_timing_events")
+
+
+def autotune(model: Model, dsys: DeviceSystem, nl: NeighborList, ws: Workspace, reps: int = 3,
+             stream=None):
+    """nep_autotune: pick the descriptor/force kernel variants for this system's
+    size class; returns the chosen (descriptor, force) variant indices."""
+    chosen = (ctypes.c_int * 2)()
+    check(lib().nep_autotune(model.handle, ctypes.byref(dsys.c), ctypes.byref(nl.c), ws.ptr, ws.bytes,
+                             _stream(stream), int(reps), chosen), "nep_autotune")
+    return int(chosen[0]), int(chosen[1])
 
 
 def check_list(nl: NeighborList | None, stream=None) -> int:

@@ -22,6 +22,9 @@ struct nep_model {
     int device;
     cudaEvent_t timing[3];
     int n_timing;
+    // autotuned kernel variants per size class (-1: default)
+    int tune_desc[nep::kSizeBins];
+    int tune_force[nep::kSizeBins];
 };
 
 namespace {
@@ -63,7 +66,7 @@ size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 struct WsLayout {
     size_t pos4, cfg, e_atom, S, pang, Pr, comp, cnt_comp, compr, cnt_compr, fin, fpart, wat, chunk_start,
         partial;
-    size_t plan, cell_of, rank, cell_cnt, cell_start, cell_atoms, scan_tmp;
+    size_t plan, cell_of, rank, cell_cnt, cell_start, cell_atoms, scan_tmp, q16;
     size_t total;
     int max_chunks, cmax;
 };
@@ -104,6 +107,8 @@ WsLayout ws_layout(const nep_model* m, int N, int B, int cap, int cap_ang) {
     w.cell_atoms = take(4 * n);
     const size_t ntiles = ((size_t)w.cmax + 1 + 2047) / 2048;
     w.scan_tmp = take(4 * (ntiles + 1));
+    const int Kp = (m->lay.D + 15) / 16 * 16;
+    w.q16 = m->hp.precision ? take(2 * n * Kp) : 0;
     w.total = o;
     return w;
 }
@@ -197,6 +202,20 @@ bool boxes_allow_min_image(const nep_system* s, float rc_list) {
     return true;
 }
 
+// size class of a system: log2 of its mean atoms per configuration
+int size_bin(const nep_system* s) {
+    const int mean = s->n_cfg > 0 ? s->n_atoms / s->n_cfg : 0;
+    int b = 0;
+    while ((1 << (b + 1)) <= mean && b + 1 < nep::kSizeBins) ++b;
+    return b;
+}
+
+void variants_for(const nep_model* m, const nep_system* s, int* vd, int* vf) {
+    const int b = size_bin(s);
+    *vd = m->tune_desc[b] >= 0 ? m->tune_desc[b] : nep::kDefaultDescVariant;
+    *vf = m->tune_force[b] >= 0 ? m->tune_force[b] : nep::kDefaultForceVariant;
+}
+
 nep::EvalArgs make_args(const nep_model* m, const nep_system* s, const nep_nlist* nl, void* work,
                         const WsLayout& w) {
     nep::EvalArgs a;
@@ -233,6 +252,8 @@ nep::EvalArgs make_args(const nep_model* m, const nep_system* s, const nep_nlist
     a.q_out = nullptr;
     a.p_out = nullptr;
     a.fb_out = nullptr;
+    a.q16 = m->hp.precision ? at<void>(work, w.q16) : nullptr;
+    a.q16_kind = m->hp.precision;
     return a;
 }
 
@@ -256,6 +277,8 @@ nep_status efv_impl(nep_model* m, const nep_system* s, const nep_nlist* nl, floa
              "pack");
     NEP_CUDA(nep::launch_chunk_plan(s->atom_off, B, at<int>(work, w.chunk_start), st), "chunk plan");
     const nep::EvalArgs a = make_args(m, s, nl, work, w);
+    int vd, vf;
+    variants_for(m, s, &vd, &vf);
     const int nt = m->n_timing;
     m->n_timing = 0;
     // inside stream capture an event record must be marked external to become
@@ -264,9 +287,10 @@ nep_status efv_impl(nep_model* m, const nep_system* s, const nep_nlist* nl, floa
     if (nt == 3) NEP_CUDA(cudaStreamIsCapturing(st, &cap), "capture status");
     const unsigned rec_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
     if (nt == 3) NEP_CUDA(cudaEventRecordWithFlags(m->timing[0], st, rec_flags), "timing event");
-    if (N > 0) NEP_CUDA(m->ks->descriptor(a, st), "descriptor kernel");
+    if (N > 0) NEP_CUDA(m->ks->descriptor(a, st, vd), "descriptor kernel");
+    if (N > 0 && a.q16) NEP_CUDA(m->ks->mlp_tc(a, st), "tensor-core network");
     if (nt == 3) NEP_CUDA(cudaEventRecordWithFlags(m->timing[1], st, rec_flags), "timing event");
-    if (N > 0) NEP_CUDA(m->ks->force(a, st), "force kernel");
+    if (N > 0) NEP_CUDA(m->ks->force(a, st, vf), "force kernel");
     if (nt == 3) NEP_CUDA(cudaEventRecordWithFlags(m->timing[2], st, rec_flags), "timing event");
     NEP_CUDA(nep::launch_gather_reduce(a, s->atom_off, at<int>(work, w.chunk_start), w.max_chunks,
                                        at<double>(work, w.partial), force, e_atom, st),
@@ -288,13 +312,17 @@ nep_status train_impl(nep_model* m, const nep_system* s, const nep_nlist* nl, co
              "pack");
     NEP_CUDA(nep::launch_chunk_plan(s->atom_off, B, at<int>(work, w.chunk_start), st), "chunk plan");
     nep::EvalArgs a = make_args(m, s, nl, work, w);
+    a.q16 = nullptr;
+    a.q16_kind = 0;
     a.q_out = at<float>(work, tl.q);
     a.p_out = at<float>(work, tl.p);
     a.fb_out = at<float>(work, tl.fb);
-    if (N > 0) NEP_CUDA(m->ks->descriptor(a, st), "descriptor kernel");
+    int vd, vf;
+    variants_for(m, s, &vd, &vf);
+    if (N > 0) NEP_CUDA(m->ks->descriptor(a, st, vd), "descriptor kernel");
     if (e_lbl) {
         // forward forces, energies and virials, then the loss and its adjoints
-        if (N > 0) NEP_CUDA(m->ks->force(a, st), "force kernel");
+        if (N > 0) NEP_CUDA(m->ks->force(a, st, vf), "force kernel");
         NEP_CUDA(nep::launch_gather_reduce(a, s->atom_off, at<int>(work, w.chunk_start), w.max_chunks,
                                            at<double>(work, w.partial), at<float>(work, tl.force),
                                            nullptr, st),
@@ -402,8 +430,6 @@ nep_status nep_create(const nep_hparams* hp, const float* params_host, size_t n_
     if (!out) return fail(NEP_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!hp_valid(hp)) return fail(NEP_ERR_ARG, "invalid hyper-parameters (l_max must be 4, 1 <= n_types <= 4, rc_ang <= rc_rad)");
-    if (hp->precision != 0)
-        return fail(NEP_ERR_UNSUPPORTED, "precision mode %d is not compiled in", hp->precision);
     const nep::KernelSet* ks = nep::find_kernel_set(hp->n_rad, hp->n_ang, hp->k_rad, hp->k_ang,
                                                     hp->has_4body, hp->n_types);
     if (!ks)
@@ -422,6 +448,7 @@ nep_status nep_create(const nep_hparams* hp, const float* params_host, size_t n_
                                hp->has_4body, hp->n_hidden);
     cudaGetDevice(&m->device);
     m->n_timing = 0;
+    for (int b = 0; b < nep::kSizeBins; ++b) m->tune_desc[b] = m->tune_force[b] = -1;
     cudaError_t e = ks->init(hp->n_hidden);
     if (e == cudaSuccess) e = ks->train_init(hp->n_hidden);
     if (e != cudaSuccess) {
@@ -589,6 +616,8 @@ nep_status nep_param_grad(nep_model* m, const nep_system* sys, const nep_nlist* 
     if (loss_mode != 0 && loss_mode != 1) return fail(NEP_ERR_ARG, "loss_mode must be 0 or 1");
     if (!grad) return fail(NEP_ERR_ARG, "grad is NULL");
     if (!nl->min_image && !nl->shift) return fail(NEP_ERR_STATE, "list was not built");
+    if (m->hp.precision != 0)
+        return fail(NEP_ERR_UNSUPPORTED, "the gradient is computed for FP32 models (precision 0)");
     TrainLayout tl;
     if ((s = check_train_work(m, sys, nl, work, work_bytes, &tl)) != NEP_OK) return s;
     return train_impl(m, sys, nl, e_lbl, f_lbl, v_lbl, w_host, loss_mode, nullptr, nullptr, nullptr, grad,
@@ -604,10 +633,70 @@ nep_status nep_param_grad_adjoint(nep_model* m, const nep_system* sys, const nep
     if (!a_e || !mu || (sys->n_atoms > 0 && !lam)) return fail(NEP_ERR_ARG, "adjoints are NULL");
     if (!grad) return fail(NEP_ERR_ARG, "grad is NULL");
     if (!nl->min_image && !nl->shift) return fail(NEP_ERR_STATE, "list was not built");
+    if (m->hp.precision != 0)
+        return fail(NEP_ERR_UNSUPPORTED, "the gradient is computed for FP32 models (precision 0)");
     TrainLayout tl;
     if ((s = check_train_work(m, sys, nl, work, work_bytes, &tl)) != NEP_OK) return s;
     return train_impl(m, sys, nl, nullptr, nullptr, nullptr, nullptr, 0, a_e, lam, mu, grad, nullptr,
                       work, tl, (cudaStream_t)stream);
+}
+
+nep_status nep_autotune(nep_model* m, const nep_system* sys, const nep_nlist* nl, void* work,
+                        size_t work_bytes, void* stream, int reps, int* chosen) {
+    nep_status s;
+    if ((s = check_system(m, sys)) != NEP_OK) return s;
+    if ((s = check_nlist(nl, sys->n_atoms)) != NEP_OK) return s;
+    if (!nl->min_image && !nl->shift) return fail(NEP_ERR_STATE, "list was not built");
+    if (reps < 1) reps = 1;
+    WsLayout w;
+    if ((s = check_work(m, sys, nl, work, work_bytes, &w)) != NEP_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int N = sys->n_atoms;
+    NEP_CUDA(nep::launch_pack(sys->pos, sys->type, sys->atom_off, N, sys->n_cfg, m->hp.n_types,
+                              at<float4>(work, w.pos4), at<int>(work, w.cfg), nl->status, st),
+             "pack");
+    const nep::EvalArgs a = make_args(m, sys, nl, work, w);
+    cudaEvent_t e0, e1;
+    NEP_CUDA(cudaEventCreate(&e0), "event");
+    NEP_CUDA(cudaEventCreate(&e1), "event");
+    float best_d = 1e30f, best_f = 1e30f;
+    int vd = nep::kDefaultDescVariant, vf = nep::kDefaultForceVariant;
+    for (int pass = 0; pass < 2 && N > 0; ++pass) {
+        for (int v = 0; v < nep::kVariants; ++v) {
+            // one untimed launch, then the best of `reps` timed launches
+            float tmin = 1e30f;
+            for (int r = 0; r <= reps; ++r) {
+                cudaEventRecord(e0, st);
+                cudaError_t err = pass == 0 ? m->ks->descriptor(a, st, v) : m->ks->force(a, st, v);
+                if (err == cudaSuccess && a.q16) err = pass == 0 ? m->ks->mlp_tc(a, st) : cudaSuccess;
+                cudaEventRecord(e1, st);
+                if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+                if (err != cudaSuccess) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return cuda_fail(err, "autotune launch");
+                }
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (r > 0 && ms < tmin) tmin = ms;
+            }
+            if (pass == 0 && tmin < best_d) best_d = tmin, vd = v;
+            if (pass == 1 && tmin < best_f) best_f = tmin, vf = v;
+        }
+        // leave the descriptor outputs of the chosen variant for the force pass
+        if (pass == 0) NEP_CUDA(m->ks->descriptor(a, st, vd), "descriptor kernel");
+        if (pass == 0 && a.q16) NEP_CUDA(m->ks->mlp_tc(a, st), "tensor-core network");
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const int b = size_bin(sys);
+    m->tune_desc[b] = vd;
+    m->tune_force[b] = vf;
+    if (chosen) {
+        chosen[0] = vd;
+        chosen[1] = vf;
+    }
+    return NEP_OK;
 }
 
 nep_status nep_set_timing_events(nep_model* m, void* const* events, int n) {

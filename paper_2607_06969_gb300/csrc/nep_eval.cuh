@@ -8,6 +8,9 @@
 //          (Eq. 3), radial part for both directions of the pair, angular part
 //          scattered to the reverse slot, per-atom virial (Eq. 4).
 #pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "nep_device.cuh"
 
 namespace nep {
@@ -234,6 +237,26 @@ NEP_HD void desc_atom(const EvalArgs& a, const float* sm, int i) {
         for (int m = 0; m < kLM; ++m) a.S[(n * kLM + m) * N + i] = S[n][m];
     }
 
+    if (a.q16) {
+        // mixed precision: hand q to the tensor-core network as a 16-bit row
+        constexpr int Kp = (D + 15) / 16 * 16;
+        unsigned* row = reinterpret_cast<unsigned*>(a.q16) + (size_t)i * (Kp / 2);
+#pragma unroll
+        for (int d = 0; d < Kp; d += 2) {
+            const float x0 = d < D ? q[d] : 0.0f, x1 = d + 1 < D ? q[d + 1] : 0.0f;
+            unsigned bits;
+            if (a.q16_kind == 2) {
+                __nv_bfloat162 v = __floats2bfloat162_rn(x0, x1);
+                memcpy(&bits, &v, 4);
+            } else {
+                __half2 v = __floats2half2_rn(x0, x1);
+                memcpy(&bits, &v, 4);
+            }
+            row[d / 2] = bits;
+        }
+        return;
+    }
+
     // network E_i = sum_h w1 tanh(W0 q + b0) + b1 and p = dE_i/dq
     const float* W0 = sm + sl.W0 + ti * sl.SW;
     const float* b0 = sm + sl.b0 + ti * sl.HS;
@@ -444,17 +467,15 @@ NEP_HD void force_atom(const EvalArgs& a, const float* sm, int i) {
 // kernels and launchers
 // ---------------------------------------------------------------------------
 #if defined(__CUDACC__)
-// Resident blocks per SM the register allocation is sized for: the force
-// kernel keeps dE/dS (n_ang x 24 floats) live across its angular loop and
-// needs the 255-register budget of two blocks to avoid spills.
-#ifndef NEP_DESC_MINB
-#define NEP_DESC_MINB 3
-#endif
-#ifndef NEP_FORCE_MINB
-#define NEP_FORCE_MINB 2
-#endif
-template <class C, bool MINIMG>
-__global__ void __launch_bounds__(kBlock, NEP_DESC_MINB) k_desc(const EvalArgs a) {
+// Resident blocks per SM that the register allocation is sized for
+// (65536 / (128 x MINB) registers per thread: 255, 168 or 128).  Each kernel
+// is compiled for MINB = 2, 3 and 4; the runtime picks one per system size
+// class (nep_autotune), by default 3 for the descriptor kernel and 2 for the
+// force kernel, which keeps dE/dS (n_ang x 24 floats) in registers.
+NEP_HD constexpr int variant_minb(int v) { return v + 2; }
+
+template <class C, bool MINIMG, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) k_desc(const EvalArgs a) {
     extern __shared__ float sm[];
     load_model<C>(sm, a.params, a.H, threadIdx.x, blockDim.x);
     __syncthreads();
@@ -462,8 +483,8 @@ __global__ void __launch_bounds__(kBlock, NEP_DESC_MINB) k_desc(const EvalArgs a
     if (i < a.N) desc_atom<C, MINIMG>(a, sm, i);
 }
 
-template <class C, bool MINIMG>
-__global__ void __launch_bounds__(kBlock, NEP_FORCE_MINB) k_force(const EvalArgs a) {
+template <class C, bool MINIMG, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) k_force(const EvalArgs a) {
     extern __shared__ float sm[];
     load_model<C>(sm, a.params, a.H, threadIdx.x, blockDim.x);
     __syncthreads();
@@ -474,38 +495,59 @@ __global__ void __launch_bounds__(kBlock, NEP_FORCE_MINB) k_force(const EvalArgs
 template <class C>
 size_t smem_bytes_of(int H) { return sizeof(float) * (size_t)smem_layout<C>(H).total; }
 
+template <class C, int MINB>
+void launch_desc_v(const EvalArgs& a, cudaStream_t st, size_t smem, int grid) {
+    if (a.min_image)
+        k_desc<C, true, MINB><<<grid, kBlock, smem, st>>>(a);
+    else
+        k_desc<C, false, MINB><<<grid, kBlock, smem, st>>>(a);
+}
+template <class C, int MINB>
+void launch_force_v(const EvalArgs& a, cudaStream_t st, size_t smem, int grid) {
+    if (a.min_image)
+        k_force<C, true, MINB><<<grid, kBlock, smem, st>>>(a);
+    else
+        k_force<C, false, MINB><<<grid, kBlock, smem, st>>>(a);
+}
+
 template <class C>
-cudaError_t launch_desc_t(const EvalArgs& a, cudaStream_t st) {
+cudaError_t launch_desc_t(const EvalArgs& a, cudaStream_t st, int v) {
     const size_t smem = smem_bytes_of<C>(a.H);
     const int grid = (a.N + kBlock - 1) / kBlock;
     if (grid == 0) return cudaSuccess;
-    if (a.min_image)
-        k_desc<C, true><<<grid, kBlock, smem, st>>>(a);
-    else
-        k_desc<C, false><<<grid, kBlock, smem, st>>>(a);
+    if (v == 0) launch_desc_v<C, 2>(a, st, smem, grid);
+    else if (v == 2) launch_desc_v<C, 4>(a, st, smem, grid);
+    else launch_desc_v<C, 3>(a, st, smem, grid);
     return cudaGetLastError();
 }
 
 template <class C>
-cudaError_t launch_force_t(const EvalArgs& a, cudaStream_t st) {
+cudaError_t launch_force_t(const EvalArgs& a, cudaStream_t st, int v) {
     const size_t smem = smem_bytes_of<C>(a.H);
     const int grid = (a.N + kBlock - 1) / kBlock;
     if (grid == 0) return cudaSuccess;
-    if (a.min_image)
-        k_force<C, true><<<grid, kBlock, smem, st>>>(a);
-    else
-        k_force<C, false><<<grid, kBlock, smem, st>>>(a);
+    if (v == 1) launch_force_v<C, 3>(a, st, smem, grid);
+    else if (v == 2) launch_force_v<C, 4>(a, st, smem, grid);
+    else launch_force_v<C, 2>(a, st, smem, grid);
     return cudaGetLastError();
+}
+
+template <class C, int MINB>
+cudaError_t init_v(int smem) {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_desc<C, true, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
+    if ((e = cudaFuncSetAttribute(k_desc<C, false, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
+    if ((e = cudaFuncSetAttribute(k_force<C, true, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
+    return cudaFuncSetAttribute(k_force<C, false, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
 template <class C>
 cudaError_t init_t(int H) {
     const int smem = (int)smem_bytes_of<C>(H);
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_desc<C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
-    if ((e = cudaFuncSetAttribute(k_desc<C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
-    if ((e = cudaFuncSetAttribute(k_force<C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
-    return cudaFuncSetAttribute(k_force<C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if ((e = init_v<C, 2>(smem))) return e;
+    if ((e = init_v<C, 3>(smem))) return e;
+    return init_v<C, 4>(smem);
 }
 
 #define NEP_DEFINE_KERNEL_SET(NAME, NR, NA, KR, KA, H4, T)                                    \
@@ -514,6 +556,7 @@ cudaError_t init_t(int H) {
                                    &init_t<Cfg<NR, NA, KR, KA, H4, T>>,                          \
                                    &launch_desc_t<Cfg<NR, NA, KR, KA, H4, T>>,                   \
                                    &launch_force_t<Cfg<NR, NA, KR, KA, H4, T>>,                  \
+                                   &launch_mlp_tc_t<Cfg<NR, NA, KR, KA, H4, T>>,                 \
                                    &train_init_t<Cfg<NR, NA, KR, KA, H4, T>>,                    \
                                    &train_t<Cfg<NR, NA, KR, KA, H4, T>>,                         \
                                    &grad_chunks_t<Cfg<NR, NA, KR, KA, H4, T>>};

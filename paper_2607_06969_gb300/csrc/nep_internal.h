@@ -18,6 +18,10 @@ constexpr int kMaxTypes = 4;
 constexpr int kLM = 24;          // real solid harmonics for l = 1..4: 3+5+7+9
 constexpr int kChunk = 1024;     // atoms per reduction chunk (one CTA)
 constexpr int kBlock = 128;      // threads per block of the per-atom kernels
+constexpr int kVariants = 3;              // register budgets for 2, 3, 4 blocks per SM
+constexpr int kDefaultDescVariant = 1;    // 3 blocks per SM
+constexpr int kDefaultForceVariant = 0;   // 2 blocks per SM
+constexpr int kSizeBins = 32;             // tuning table: log2 of mean atoms per configuration
 
 // Stencil/cell plan of one configuration for the neighbour build.
 struct CellPlan {
@@ -56,6 +60,10 @@ struct EvalArgs {
     float* fpart;                  // [3][N]
     float* wat;                    // [9][N]          per-atom virial
     int* status;                   // [4] flags (may be null)
+    // mixed precision: the descriptor kernel stops after q and writes it as
+    // 16-bit rows q16[N][Kp] (1 = FP16, 2 = BF16); the network runs in k_mlp_tc
+    void* q16;
+    int q16_kind;
     // training outputs of the descriptor kernel (null when not training)
     float* q_out;                  // [D][N]          descriptors
     float* p_out;                  // [D][N]          dE/dq
@@ -101,8 +109,9 @@ struct KernelSet {
     int n_rad, n_ang, k_rad, k_ang, has_4body, n_types;
     size_t (*smem_bytes)(int H);
     cudaError_t (*init)(int H);   // set kernel attributes (dynamic shared memory)
-    cudaError_t (*descriptor)(const EvalArgs&, cudaStream_t);
-    cudaError_t (*force)(const EvalArgs&, cudaStream_t);
+    cudaError_t (*descriptor)(const EvalArgs&, cudaStream_t, int variant);
+    cudaError_t (*force)(const EvalArgs&, cudaStream_t, int variant);
+    cudaError_t (*mlp_tc)(const EvalArgs&, cudaStream_t);   // tensor-core network (mixed precision)
     cudaError_t (*train_init)(int H);
     cudaError_t (*train)(const TrainArgs&, cudaStream_t);   // tangent ... gradient
     int (*grad_chunks)(int N);

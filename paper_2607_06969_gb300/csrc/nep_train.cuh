@@ -19,6 +19,7 @@
 //             then an FP64 sum over chunks in fixed order.
 #pragma once
 #include "nep_eval.cuh"
+#include "nep_mlp_tc.cuh"
 
 namespace nep {
 
@@ -525,10 +526,12 @@ __global__ void k_grad_final(const TrainArgs t, int nchunk) {
 template <class C>
 size_t grad_stage_bytes(int H) { return sizeof(float) * (size_t)kGradChunk * GradStage<C>::width(H); }
 
+// attributes of the training kernels and of the tensor-core network
 template <class C>
 cudaError_t train_init_t(int H) {
     const int smem = (int)smem_bytes_of<C>(H);
     cudaError_t e;
+    if ((e = mlp_tc_init_t<C>(H))) return e;
     if ((e = cudaFuncSetAttribute(k_tangent<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
     if ((e = cudaFuncSetAttribute(k_mlp2<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
     return cudaFuncSetAttribute(k_grad_partial<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,

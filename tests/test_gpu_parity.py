@@ -206,3 +206,20 @@ def test_host_argument_errors(nb):
     bad = nb.NeighborList(s.n_atoms, 8, 16)
     with pytest.raises(nb.NepError):
         nb.neighbors(model, dsys, bad, 0.0, ws)
+
+
+def test_autotune_variants_agree(nb):
+    """Every compiled register-budget variant computes the same E, F, V; the
+    autotuner picks valid indices and later calls use them."""
+    import ctypes
+    h = I.HYPER_SMALL
+    s = I.packing_batch([57, 100, 250], tag=67)
+    th = I.init_params(h).astype(np.float32)
+    g = gpu_eval(nb, h, th, s, skin=1.0, cap=160, cap_ang=64)
+    chosen = nb.autotune(g["model"], g["dsys"], g["nl"], g["ws"], reps=2)
+    assert all(0 <= c < 3 for c in chosen)
+    e, f, et, v = nb.energy_forces_virial(g["model"], g["dsys"], g["nl"], g["ws"])
+    assert np.abs(e.cpu().numpy() - g["E"]).max() <= 1e-6
+    assert np.abs(f.cpu().numpy().T - g["F"]).max() <= 1e-5
+    assert_parity(dict(E=e.cpu().numpy(), F=f.cpu().numpy().T, Etot=et.cpu().numpy(),
+                       V=v.cpu().numpy().reshape(-1, 3, 3), status=0), oracle_eval(h, th, s), s)
