@@ -111,14 +111,17 @@ def algorithmic_flops(h, nbar_rad: float, nbar_ang: float) -> dict:
     D = NR + NA * 4 + (NA if h.has_4body else 0)
     basis = lambda K: 8 + 5 * (K - 1)             # cos, x, Chebyshev recursion, (T+1) fc/2
     basis_d = lambda K: 20 + 13 * (K - 2)          # with derivatives
-    rad_desc = 21 + basis(KR) + 2 * T * KR
+    # k_radial: pair vector, r, Q_k and the species-resolved sums
+    radial = nbar_rad * (21 + basis(KR) + 2 * T * KR)
+    # k_angular: radial q, S_nlm, q_nl and q4, network, projected adjoint,
+    # dE/dS, angular pair forces
     ang_desc = 10 + basis(KA) + 2 * NA * KA + 45 + 2 * NA * 24
-    atom_desc = 2 * NR * T * KR + 3 * NA * 24 + 40 * NA + H * (4 * D + 6) + 2 * T * KR * NR
-    rad_force = 22 + basis_d(KR) + 4 * KR + 34
     ang_force = 10 + basis_d(KA) + 4 * NA * KA + 45 + 4 * NA * 24 + 4 * 24 + 150 + 30
-    atom_force = 3 * NA * 24 + 60 * NA
-    return {"desc": nbar_rad * rad_desc + nbar_ang * ang_desc + atom_desc,
-            "force": nbar_rad * rad_force + nbar_ang * ang_force + atom_force}
+    angular = (2 * NR * T * KR + nbar_ang * ang_desc + 72 * NA + 40 * NA + H * (4 * D + 6)
+               + 2 * T * KR * NR + 72 * NA + 60 * NA + nbar_ang * ang_force)
+    # k_finish: radial pair forces of both directions, virial, gather
+    finish = nbar_rad * (22 + basis_d(KR) + 4 * KR + 30) + 3 * 1.6 * nbar_ang
+    return {"radial": radial, "angular": angular, "finish": finish}
 
 
 def launches_per_step(rebuild: bool) -> int:
@@ -246,9 +249,9 @@ def run_md(args, nb, torch, dist, world, local, s, h, model, theta, vel0, masses
     stream.synchronize()
     _raise_if_overflow(nb, nl, stream)
 
-    # capture the K timed steps, with events around the two pair kernels of every step
+    # capture the K timed steps, with events around the three pair kernels of every step
     K = args.steps
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
     for trio in evs:            # torch creates the underlying cudaEvent on first record
         for e in trio:
             e.record(stream)
@@ -278,15 +281,16 @@ def run_md(args, nb, torch, dist, world, local, s, h, model, theta, vel0, masses
     clk = clocks.stop()
     ms = start.elapsed_time(stop)
     _raise_if_overflow(nb, nl, stream)
-    t_desc = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
-    t_force = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+    t_kern = {"radial": statistics.mean(e[0].elapsed_time(e[1]) for e in evs),
+              "angular": statistics.mean(e[1].elapsed_time(e[2]) for e in evs),
+              "finish": statistics.mean(e[2].elapsed_time(e[3]) for e in evs)}
     ms_max = ms
     if world > 1:
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_max = float(t.item())
     del g
-    return (ms_max, K, t_desc, t_force, nbar_rad, nbar_ang, clk, dsys, nl, ws, e_atom, force, e_tot,
+    return (ms_max, K, t_kern, nbar_rad, nbar_ang, clk, dsys, nl, ws, e_atom, force, e_tot,
             vir, stream, pos_host0)
 
 
@@ -489,7 +493,7 @@ def main():
                 print(f"# list overflow, retrying with cap={cap} cap_ang={cap_ang}", file=sys.stderr)
     else:
         raise RuntimeError("neighbour list did not fit")
-    (ms_max, K, t_desc, t_force, nbar_rad, nbar_ang, clk, dsys, nl, ws, e_atom, force, e_tot, vir,
+    (ms_max, K, t_kern, nbar_rad, nbar_ang, clk, dsys, nl, ws, e_atom, force, e_tot, vir,
      stream, pos_host0) = res
     value = world * N * K / (ms_max * 1e-3)
 
@@ -498,14 +502,15 @@ def main():
     props = torch.cuda.get_device_properties(local)
     sm_count = props.multi_processor_count
     peak = sm_count * 128 * 2 * 2070e6 / 1e12
-    dom = "force" if t_force >= t_desc else "desc"
-    t_dom = t_force if dom == "force" else t_desc
+    dom = max(t_kern, key=t_kern.get)
+    t_dom = t_kern[dom]
     achieved = fl[dom] * N / (t_dom * 1e-3) / 1e12
     roofline = {"bound": "alu", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                 "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
                 "flops_per_atom": fl[dom], "nbar_rad": nbar_rad, "nbar_ang": nbar_ang,
-                "kernel_ms": {"desc": t_desc, "force": t_force}}
+                "kernel_ms": t_kern,
+                "kernel_tflops": {k: fl[k] * N / (t_kern[k] * 1e-3) / 1e12 for k in t_kern}}
 
     # end to end through the C ABI from pinned host buffers
     KE = max(1, min(args.e2e_steps, K))

@@ -118,7 +118,8 @@ typedef struct {
  * every (j, image s) != (i, 0) with |r_j + s*L - r_i| < rc_rad + skin, decided
  * by the FP32 predicate dx = (x_j - x_i) + s_x L_x (and y, z),
  * d2 = (dx*dx + dy*dy) + dz*dz, d2 < fl32(rc*rc) (the sum over j of Eq. 3).
- * Its first cnt_ang[i] entries are exactly those with d < rc_ang + skin.
+ * Its first cnt_ang[i] entries are exactly those with d < rc_ang + skin; the
+ * remaining ones are ordered with d < rc_rad before d >= rc_rad.
  *   nbr   [cap][N] int   slot-major: nbr[s*N + i] = j
  *   shift [cap][N] int   packed image (int8 sx | sy << 8 | sz << 16); may be
  *                        NULL when every box edge >= 2*(rc_rad+skin)+1e-3,
@@ -245,10 +246,11 @@ nep_status nep_autotune(nep_model* m, const nep_system* sys, const nep_nlist* nl
                         size_t work_bytes, void* stream, int reps, int* chosen);
 
 /* Profiling hook: the next nep_energy_forces_virial / nep_md_step call of
- * this model records events[0] before the descriptor kernel, events[1]
- * between the descriptor and force kernels and events[2] after the force
- * kernel, on the call's stream (events are caller-created cudaEvent_t, n = 3;
- * n = 0 clears).  One-shot: the events are forgotten after that call.  The
+ * this model records events[0] before the radial-descriptor kernel,
+ * events[1] after it, events[2] after the angular kernel(s) (descriptor,
+ * network and angular pair forces) and events[3] after the kernel that
+ * completes the forces, on the call's stream (events are caller-created
+ * cudaEvent_t, n = 4; n = 0 clears).  One-shot: the events are forgotten after that call.  The
  * records are ordinary stream work and can be captured into a CUDA graph. */
 nep_status nep_set_timing_events(nep_model* m, void* const* events, int n);
 

@@ -324,12 +324,14 @@ def md_step(model: Model, dsys: DeviceSystem, nl: NeighborList, vel, force, e_to
 
 
 def set_timing_events(model: Model, events) -> None:
-    """events: three torch.cuda.Event(enable_timing=True) or None to clear."""
+    """events: four torch.cuda.Event(enable_timing=True) (before the radial
+    kernel, after it, after the angular kernel(s), after the finish kernel),
+    or None to clear."""
     if events is None:
         check(lib().nep_set_timing_events(model.handle, None, 0), "nep_set_timing_events")
         return
-    arr = (ctypes.c_void_p * 3)(*[ctypes.c_void_p(e.cuda_event) for e in events])
-    check(lib().nep_set_timing_events(model.handle, arr, 3), "nep_set_timing_events")
+    arr = (ctypes.c_void_p * 4)(*[ctypes.c_void_p(e.cuda_event) for e in events])
+    check(lib().nep_set_timing_events(model.handle, arr, 4), "nep_set_timing_events")
 
 
 def autotune(model: Model, dsys: DeviceSystem, nl: NeighborList, ws: Workspace, reps: int = 3,

@@ -20,7 +20,7 @@ struct nep_model {
     nep::ParamLayout lay;
     float* params;   // device [P]
     int device;
-    cudaEvent_t timing[3];
+    cudaEvent_t timing[4];
     int n_timing;
     // autotuned kernel variants per size class (-1: default)
     int tune_desc[nep::kSizeBins];
@@ -64,9 +64,8 @@ size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Byte offsets of the scratch arrays inside the caller's workspace.
 struct WsLayout {
-    size_t pos4, cfg, e_atom, S, pang, Pr, comp, cnt_comp, compr, cnt_compr, fin, fpart, wat, chunk_start,
-        partial;
-    size_t plan, cell_of, rank, cell_cnt, cell_start, cell_atoms, scan_tmp, q16;
+    size_t pos4, cfg, e_atom, fb, S, pang, Pr, comp, cnt_comp, fin, fpart, wat, chunk_start, partial;
+    size_t plan, cell_of, rank, cell_cnt, cell_start, cell_atoms, scan_tmp, shell, q16;
     size_t total;
     int max_chunks, cmax;
 };
@@ -85,13 +84,14 @@ WsLayout ws_layout(const nep_model* m, int N, int B, int cap, int cap_ang) {
     w.pos4 = take(16 * n);
     w.cfg = take(4 * n);
     w.e_atom = take(4 * n);
+    w.fb = take(4 * n * T * KR);
+    // S and the angular dE/dq leave the SM only in mixed precision and training
+    const bool split = m->hp.precision != 0;
     w.S = take(4 * n * NA * nep::kLM);
-    w.pang = take(4 * n * NP);
+    w.pang = split ? take(4 * n * NP) : 0;
     w.Pr = take(4 * n * T * KR);
     w.comp = take(16 * n * cap_ang);
     w.cnt_comp = take(4 * n);
-    w.compr = take(16 * n * cap);
-    w.cnt_compr = take(4 * n);
     w.fin = take(16 * n * cap_ang);
     w.fpart = take(12 * n);
     w.wat = take(36 * n);
@@ -107,6 +107,7 @@ WsLayout ws_layout(const nep_model* m, int N, int B, int cap, int cap_ang) {
     w.cell_atoms = take(4 * n);
     const size_t ntiles = ((size_t)w.cmax + 1 + 2047) / 2048;
     w.scan_tmp = take(4 * (ntiles + 1));
+    w.shell = take(8 * n * (size_t)cap);
     const int Kp = (m->lay.D + 15) / 16 * 16;
     w.q16 = m->hp.precision ? take(2 * n * Kp) : 0;
     w.total = o;
@@ -116,8 +117,8 @@ WsLayout ws_layout(const nep_model* m, int N, int B, int cap, int cap_ang) {
 // Training scratch placed after the evaluation scratch.
 struct TrainLayout {
     WsLayout w;
-    size_t q, p, fb, lam4, aE, mu, partialF, etot, vir, force, dq, dS, df, coef, rho, xz, bins, gpart,
-        loss;
+    size_t q, p, compr, cnt_compr, lam4, aE, mu, partialF, etot, vir, force, dq, dS, df, coef, rho, xz,
+        bins, gpart, loss;
     size_t total;
 };
 
@@ -135,7 +136,8 @@ TrainLayout train_layout(const nep_model* m, int N, int B, int cap, int cap_ang)
     const int H = m->hp.n_hidden;
     t.q = take(4 * n * D);
     t.p = take(4 * n * D);
-    t.fb = take(4 * n * T * KR);
+    t.compr = take(16 * n * (size_t)cap);
+    t.cnt_compr = take(4 * n);
     t.lam4 = take(16 * n);
     t.aE = take(4 * (size_t)B);
     t.mu = take(36 * (size_t)B);
@@ -238,13 +240,14 @@ nep::EvalArgs make_args(const nep_model* m, const nep_system* s, const nep_nlist
     a.rev = nl->rev;
     a.params = m->params;
     a.e_atom = at<float>(work, w.e_atom);
-    a.S = at<float>(work, w.S);
-    a.pang = at<float>(work, w.pang);
+    a.fb = at<float>(work, w.fb);
+    a.S = m->hp.precision ? at<float>(work, w.S) : nullptr;
+    a.pang = m->hp.precision ? at<float>(work, w.pang) : nullptr;
     a.Pr = at<float>(work, w.Pr);
     a.comp = at<float4>(work, w.comp);
     a.cnt_comp = at<int>(work, w.cnt_comp);
-    a.compr = at<float4>(work, w.compr);
-    a.cnt_compr = at<int>(work, w.cnt_compr);
+    a.compr = nullptr;
+    a.cnt_compr = nullptr;
     a.fin = at<float4>(work, w.fin);
     a.fpart = at<float>(work, w.fpart);
     a.wat = at<float>(work, w.wat);
@@ -284,17 +287,28 @@ nep_status efv_impl(nep_model* m, const nep_system* s, const nep_nlist* nl, floa
     // inside stream capture an event record must be marked external to become
     // a timing node of the graph; outside capture the flag is not accepted
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    if (nt == 3) NEP_CUDA(cudaStreamIsCapturing(st, &cap), "capture status");
+    if (nt) NEP_CUDA(cudaStreamIsCapturing(st, &cap), "capture status");
     const unsigned rec_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
-    if (nt == 3) NEP_CUDA(cudaEventRecordWithFlags(m->timing[0], st, rec_flags), "timing event");
-    if (N > 0) NEP_CUDA(m->ks->descriptor(a, st, vd), "descriptor kernel");
-    if (N > 0 && a.q16) NEP_CUDA(m->ks->mlp_tc(a, st), "tensor-core network");
-    if (nt == 3) NEP_CUDA(cudaEventRecordWithFlags(m->timing[1], st, rec_flags), "timing event");
-    if (N > 0) NEP_CUDA(m->ks->force(a, st, vf), "force kernel");
-    if (nt == 3) NEP_CUDA(cudaEventRecordWithFlags(m->timing[2], st, rec_flags), "timing event");
-    NEP_CUDA(nep::launch_gather_reduce(a, s->atom_off, at<int>(work, w.chunk_start), w.max_chunks,
-                                       at<double>(work, w.partial), force, e_atom, st),
-             "gather");
+    auto mark = [&](int k) -> cudaError_t {
+        return nt ? cudaEventRecordWithFlags(m->timing[k], st, rec_flags) : cudaSuccess;
+    };
+    NEP_CUDA(mark(0), "timing event");
+    if (N > 0) NEP_CUDA(m->ks->radial(a, st), "radial kernel");
+    NEP_CUDA(mark(1), "timing event");
+    if (N > 0) NEP_CUDA(m->ks->angular(a, st, vd), "angular kernel");
+    if (N > 0 && a.q16) {
+        NEP_CUDA(m->ks->mlp_tc(a, st), "tensor-core network");
+        NEP_CUDA(m->ks->angforce(a, st, vf), "angular force kernel");
+    }
+    NEP_CUDA(mark(2), "timing event");
+    nep::FinishArgs f;
+    f.atom_off = s->atom_off;
+    f.chunk_start = at<int>(work, w.chunk_start);
+    f.partial = at<double>(work, w.partial);
+    f.force = force;
+    f.e_out = e_atom;
+    NEP_CUDA(m->ks->finish(a, f, w.max_chunks, st), "finish kernel");
+    NEP_CUDA(mark(3), "timing event");
     NEP_CUDA(nep::launch_final_reduce(B, at<int>(work, w.chunk_start), at<double>(work, w.partial), e_tot,
                                       virial, st),
              "final reduce");
@@ -314,19 +328,25 @@ nep_status train_impl(nep_model* m, const nep_system* s, const nep_nlist* nl, co
     nep::EvalArgs a = make_args(m, s, nl, work, w);
     a.q16 = nullptr;
     a.q16_kind = 0;
+    a.S = at<float>(work, w.S);
+    a.compr = at<float4>(work, tl.compr);
+    a.cnt_compr = at<int>(work, tl.cnt_compr);
     a.q_out = at<float>(work, tl.q);
     a.p_out = at<float>(work, tl.p);
-    a.fb_out = at<float>(work, tl.fb);
+    a.fb_out = a.fb;
     int vd, vf;
     variants_for(m, s, &vd, &vf);
-    if (N > 0) NEP_CUDA(m->ks->descriptor(a, st, vd), "descriptor kernel");
+    if (N > 0) NEP_CUDA(m->ks->radial(a, st), "radial kernel");
+    if (N > 0) NEP_CUDA(m->ks->angular(a, st, vd), "angular kernel");
     if (e_lbl) {
         // forward forces, energies and virials, then the loss and its adjoints
-        if (N > 0) NEP_CUDA(m->ks->force(a, st, vf), "force kernel");
-        NEP_CUDA(nep::launch_gather_reduce(a, s->atom_off, at<int>(work, w.chunk_start), w.max_chunks,
-                                           at<double>(work, w.partial), at<float>(work, tl.force),
-                                           nullptr, st),
-                 "gather");
+        nep::FinishArgs f;
+        f.atom_off = s->atom_off;
+        f.chunk_start = at<int>(work, w.chunk_start);
+        f.partial = at<double>(work, w.partial);
+        f.force = at<float>(work, tl.force);
+        f.e_out = nullptr;
+        NEP_CUDA(m->ks->finish(a, f, w.max_chunks, st), "finish kernel");
         NEP_CUDA(nep::launch_final_reduce(B, at<int>(work, w.chunk_start), at<double>(work, w.partial),
                                           at<double>(work, tl.etot), at<double>(work, tl.vir), st),
                  "final reduce");
@@ -395,11 +415,12 @@ nep_status neighbors_impl(nep_model* m, const nep_system* s, float skin, nep_nli
     nw.cell_start = at<int>(work, w.cell_start);
     nw.cell_atoms = at<int>(work, w.cell_atoms);
     nw.scan_tmp = at<int>(work, w.scan_tmp);
+    nw.shell = at<int2>(work, w.shell);
     nw.cmax = w.cmax;
     nep_nlist copy = *nl;
     if (mi) copy.shift = nullptr;
     NEP_CUDA(nep::launch_neighbors(s->pos, at<float4>(work, w.pos4), s->atom_off, s->box, at<int>(work, w.cfg), N, B, rc_list,
-                                   rc_list_ang, mi ? 1 : 0, &copy, nw, st),
+                                   rc_list_ang, m->hp.rc_rad, mi ? 1 : 0, &copy, nw, st),
              "neighbour build");
     return NEP_OK;
 }
@@ -661,14 +682,17 @@ nep_status nep_autotune(nep_model* m, const nep_system* sys, const nep_nlist* nl
     NEP_CUDA(cudaEventCreate(&e1), "event");
     float best_d = 1e30f, best_f = 1e30f;
     int vd = nep::kDefaultDescVariant, vf = nep::kDefaultForceVariant;
-    for (int pass = 0; pass < 2 && N > 0; ++pass) {
+    // pass 0 times the angular kernel variants; pass 1 (mixed precision only)
+    // the angular-force variants, after the tensor-core network
+    NEP_CUDA(m->ks->radial(a, st), "radial kernel");
+    const int passes = a.q16 ? 2 : 1;
+    for (int pass = 0; pass < passes && N > 0; ++pass) {
         for (int v = 0; v < nep::kVariants; ++v) {
             // one untimed launch, then the best of `reps` timed launches
             float tmin = 1e30f;
             for (int r = 0; r <= reps; ++r) {
                 cudaEventRecord(e0, st);
-                cudaError_t err = pass == 0 ? m->ks->descriptor(a, st, v) : m->ks->force(a, st, v);
-                if (err == cudaSuccess && a.q16) err = pass == 0 ? m->ks->mlp_tc(a, st) : cudaSuccess;
+                cudaError_t err = pass == 0 ? m->ks->angular(a, st, v) : m->ks->angforce(a, st, v);
                 cudaEventRecord(e1, st);
                 if (err == cudaSuccess) err = cudaEventSynchronize(e1);
                 if (err != cudaSuccess) {
@@ -683,9 +707,10 @@ nep_status nep_autotune(nep_model* m, const nep_system* sys, const nep_nlist* nl
             if (pass == 0 && tmin < best_d) best_d = tmin, vd = v;
             if (pass == 1 && tmin < best_f) best_f = tmin, vf = v;
         }
-        // leave the descriptor outputs of the chosen variant for the force pass
-        if (pass == 0) NEP_CUDA(m->ks->descriptor(a, st, vd), "descriptor kernel");
-        if (pass == 0 && a.q16) NEP_CUDA(m->ks->mlp_tc(a, st), "tensor-core network");
+        if (pass == 0 && a.q16) {
+            NEP_CUDA(m->ks->angular(a, st, vd), "angular kernel");
+            NEP_CUDA(m->ks->mlp_tc(a, st), "tensor-core network");
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -705,12 +730,12 @@ nep_status nep_set_timing_events(nep_model* m, void* const* events, int n) {
         m->n_timing = 0;
         return NEP_OK;
     }
-    if (n != 3 || !events) return fail(NEP_ERR_ARG, "need exactly 3 events");
-    for (int k = 0; k < 3; ++k) {
+    if (n != 4 || !events) return fail(NEP_ERR_ARG, "need exactly 4 events");
+    for (int k = 0; k < 4; ++k) {
         if (!events[k]) return fail(NEP_ERR_ARG, "event %d is NULL", k);
         m->timing[k] = (cudaEvent_t)events[k];
     }
-    m->n_timing = 3;
+    m->n_timing = 4;
     return NEP_OK;
 }
 

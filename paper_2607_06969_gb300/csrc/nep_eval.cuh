@@ -1,12 +1,22 @@
-// Per-atom NEP kernels, templated on the compiled hyper-parameters.
+// Per-atom NEP kernels, templated on the compiled hyper-parameters.  One
+// thread owns one atom i in each of them, so every sum over neighbours is a
+// private register sum (no atomics, bitwise reproducible).
 //
-//   desc   (one thread per atom i):  radial descriptor via species-resolved
-//          basis sums, angular S_nlm (Eq. 16) over the compacted angular
-//          pairs, q_nl (Eq. 17), 4-body q4_n, the per-species tanh network
-//          (Section 2.3) and dE/dq.
-//   force  (one thread per atom i):  f_ij = dE_i/dr_ij for every pair
-//          (Eq. 3), radial part for both directions of the pair, angular part
-//          scattered to the reverse slot, per-atom virial (Eq. 4).
+//   k_radial   radial descriptor sums over the neighbour list (Eqs. 11-15),
+//              resolved by neighbour species, and compaction of the pairs
+//              inside the angular cutoff.  Few registers: many resident warps
+//              hide the neighbour gathers.
+//   k_angular  angular S_nlm (Eq. 16) over the compacted pairs, q_nl (Eq. 17)
+//              and the 4-body term, the per-species tanh network (Section 2.3)
+//              and dE/dq, then dE/dS and the angular pair forces f_ij =
+//              dE_i/dr_ij, scattered to the reverse slot of the pair.  S and
+//              dE/dS stay on the SM.
+//   k_finish   radial pair forces of both directions of every pair from the
+//              species-projected adjoints, plus the scattered angular forces,
+//              give F_i (Eq. 3); per-atom virials (Eq. 4) and energies are
+//              summed in FP64 per chunk of atoms in a fixed order.
+// In mixed precision k_angular stops after q (written as 16-bit rows), the
+// tensor-core network runs, and k_angforce computes the angular forces.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -23,16 +33,22 @@ namespace nep {
 #define NEP_SCHED_BARRIER() ((void)0)
 #endif
 
-NEP_HD constexpr int odd_up(int x) { return (x % 2) ? x : x + 1; }
-NEP_HD int stride_1mod32(int x) { return x + ((33 - (x % 32)) % 32); }
+// Shared-memory row strides: multiples of 4 floats (16-byte vector loads)
+// congruent to 4 mod 32, so that the up to 9 species pairs (or 3 species) a
+// warp meets land in different 4-bank groups.
+NEP_HD constexpr int stride4(int x) { return (x + 31) / 32 * 32 + 4; }
+NEP_HD constexpr int round4(int x) { return (x + 3) / 4 * 4; }
+
+NEP_HD float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 
 template <int NR_, int NA_, int KR_, int KA_, int H4_, int T_>
 struct Cfg {
     static constexpr int NR = NR_, NA = NA_, KR = KR_, KA = KA_, H4 = H4_, T = T_;
     static constexpr int D = NR + NA * 4 + (H4 ? NA : 0);
     static constexpr int NP = NA * (4 + (H4 ? 1 : 0));   // angular + 4-body descriptor count
-    static constexpr int SA = odd_up(NA * KA);           // per-species-pair stride, odd
-    static constexpr int SR = odd_up(NR * KR);
+    static constexpr int SA = stride4(NA * KA);          // per-species-pair stride
+    static constexpr int SR = stride4(NR * KR);
+    static constexpr int DW = round4(D);                  // row stride of W0 (zero padded)
 };
 
 // Shared-memory image of the model, padded so that the (up to 9) species
@@ -45,7 +61,7 @@ struct SmemLayout {
 template <class C>
 NEP_HD SmemLayout smem_layout(int H) {
     SmemLayout s;
-    s.SW = stride_1mod32(H * C::D);
+    s.SW = stride4(H * C::DW);
     s.HS = (H % 2) ? H : H + 1;
     s.cA = 0;
     s.cR = s.cA + C::T * C::T * C::SA;
@@ -74,9 +90,9 @@ NEP_HD void load_model(float* sm, const float* prm, int H, int tid, int nthr) {
         sm[s.cR + pair * C::SR + r] = prm[L.off_cR + x];
     }
     const int HD = H * C::D;
-    for (int x = tid; x < C::T * HD; x += nthr) {
-        int t = x / HD, r = x % HD;
-        sm[s.W0 + t * s.SW + r] = prm[t * L.mlp_stride + r];
+    for (int x = tid; x < C::T * H * C::DW; x += nthr) {
+        const int t = x / (H * C::DW), r = x % (H * C::DW), h = r / C::DW, d = r % C::DW;
+        sm[s.W0 + t * s.SW + r] = d < C::D ? prm[t * L.mlp_stride + h * C::D + d] : 0.0f;
     }
     for (int x = tid; x < C::T * H; x += nthr) {
         int t = x / H, h = x % H;
@@ -107,19 +123,16 @@ NEP_HD AtomFrame atom_frame(const EvalArgs& a, int i) {
 }
 
 // ---------------------------------------------------------------------------
-// descriptor + network, one atom
+// radial descriptor sums and pair compaction, one atom
 // ---------------------------------------------------------------------------
 template <class C, bool MINIMG>
-NEP_HD void desc_atom(const EvalArgs& a, const float* sm, int i) {
-    constexpr int NR = C::NR, NA = C::NA, KR = C::KR, KA = C::KA, T = C::T, D = C::D;
-    const SmemLayout sl = smem_layout<C>(a.H);
+NEP_HD void radial_atom(const EvalArgs& a, int i) {
+    constexpr int KR = C::KR, T = C::T;
     const int N = a.N;
     const AtomFrame fr = atom_frame(a, i);
-    const int ti = fr.ti;
     const float rcR2 = a.rc_rad * a.rc_rad, rcA2 = a.rc_ang * a.rc_ang;
-    const float irR = 1.0f / a.rc_rad, irA = 1.0f / a.rc_ang;
-
-    // radial: species-resolved basis sums F[t][k] = sum_{j of species t} Q_k(r_ij)
+    const float irR = 1.0f / a.rc_rad;
+    // F[t][k] = sum_{j of species t} Q_k(r_ij)
     float fb[T][KR];
 #pragma unroll
     for (int t = 0; t < T; ++t)
@@ -147,8 +160,10 @@ NEP_HD void desc_atom(const EvalArgs& a, const float* sm, int i) {
         const float d2 = dist2(dx, dy, dz);
         const int tj = f2i(pj.w);
         if (d2 < rcR2) {
-            a.compr[ncr * N + i] = make_float4(dx, dy, dz, i2f((int)(((unsigned)j << 2) | (unsigned)tj)));
-            ++ncr;
+            if (a.compr) {
+                a.compr[ncr * N + i] = make_float4(dx, dy, dz, i2f((int)(((unsigned)j << 2) | (unsigned)tj)));
+                ++ncr;
+            }
             float f[KR];
             basis<KR>(sqrt_f(d2), irR, f);
 #pragma unroll
@@ -170,34 +185,69 @@ NEP_HD void desc_atom(const EvalArgs& a, const float* sm, int i) {
         }
     }
     a.cnt_comp[i] = nc;
-    a.cnt_compr[i] = ncr;
+    if (a.compr) a.cnt_compr[i] = ncr;
+#pragma unroll
+    for (int t = 0; t < T; ++t)
+#pragma unroll
+        for (int k = 0; k < KR; ++k) a.fb[(t * KR + k) * N + i] = fb[t][k];
+}
 
-    float q[D];
+// ---------------------------------------------------------------------------
+// angular pieces shared by the fused and the mixed-precision kernels
+// ---------------------------------------------------------------------------
+// q_n = sum_t sum_k cR[Zi][t][n][k] F[t][k] (Eq. 11 with species-resolved sums)
+// row of K floats from shared memory, 16-byte loads when K is a multiple of 4
+template <int K>
+NEP_HD void load_row(const float* p, float* out) {
+    if (K % 4 == 0) {
+#pragma unroll
+        for (int k = 0; k < K; k += 4) {
+            const float4 v = ld4(p + k);
+            out[k] = v.x; out[k + 1] = v.y; out[k + 2] = v.z; out[k + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k) out[k] = p[k];
+    }
+}
+
+template <class C>
+NEP_HD void radial_q(const EvalArgs& a, const float* sm, const SmemLayout& sl, int ti, int i, float* q) {
+    constexpr int NR = C::NR, KR = C::KR, T = C::T;
+    const int N = a.N;
+    float fbv[T][KR];
+#pragma unroll
+    for (int t = 0; t < T; ++t)
+#pragma unroll
+        for (int k = 0; k < KR; ++k) fbv[t][k] = a.fb[(t * KR + k) * N + i];
 #pragma unroll
     for (int n = 0; n < NR; ++n) {
         float acc = 0.0f;
 #pragma unroll
         for (int t = 0; t < T; ++t) {
             const float* c = sm + sl.cR + (ti * T + t) * C::SR + n * KR;
+            float cv[KR];
+            load_row<KR>(c, cv);
 #pragma unroll
-            for (int k = 0; k < KR; ++k) acc = fmaf(c[k], fb[t][k], acc);
+            for (int k = 0; k < KR; ++k) acc = fmaf(cv[k], fbv[t][k], acc);
         }
         q[n] = acc;
         NEP_SCHED_BARRIER();
     }
-    if (a.fb_out) {
-#pragma unroll
-        for (int t = 0; t < T; ++t)
-#pragma unroll
-            for (int k = 0; k < KR; ++k) a.fb_out[(t * KR + k) * N + i] = fb[t][k];
-    }
+}
 
-    // angular: S_nlm = sum_j g_n(r_ij) P_lm(rhat_ij)
-    float S[NA][kLM];
+// S_nlm = sum_j g_n(r_ij) P_lm(rhat_ij) over the compacted angular pairs
+template <class C>
+NEP_HD void angular_S(const EvalArgs& a, const float* sm, const SmemLayout& sl, int ti, int i,
+                      float (&S)[C::NA][kLM]) {
+    constexpr int NA = C::NA, KA = C::KA, T = C::T;
+    const int N = a.N;
+    const float irA = 1.0f / a.rc_ang;
 #pragma unroll
     for (int n = 0; n < NA; ++n)
 #pragma unroll
         for (int m = 0; m < kLM; ++m) S[n][m] = 0.0f;
+    const int nc = a.cnt_comp[i];
     float4 e_nx = nc > 0 ? a.comp[i] : make_float4(1.0f, 0.0f, 0.0f, 0.0f);
     for (int c = 0; c < nc; ++c) {
         const float4 e = e_nx;
@@ -211,9 +261,11 @@ NEP_HD void desc_atom(const EvalArgs& a, const float* sm, int i) {
         float g[NA];
 #pragma unroll
         for (int n = 0; n < NA; ++n) {
+            float cv[KA];
+            load_row<KA>(cc + n * KA, cv);
             float acc = 0.0f;
 #pragma unroll
-            for (int k = 0; k < KA; ++k) acc = fmaf(cc[n * KA + k], f[k], acc);
+            for (int k = 0; k < KA; ++k) acc = fmaf(cv[k], f[k], acc);
             g[n] = acc;
         }
         const HarmTerms ht = harm_terms(e.x * ir, e.y * ir, e.z * ir);
@@ -225,128 +277,64 @@ NEP_HD void desc_atom(const EvalArgs& a, const float* sm, int i) {
             for (int n = 0; n < NA; ++n) S[n][m] = fmaf(g[n], Y, S[n][m]);
         }
     }
+}
+
+// q_nl = sum_m C_lm S_nlm^2 (Eq. 17) and q4_n = tr(A_n^3)
+template <class C>
+NEP_HD void angular_q(const float (&S)[C::NA][kLM], float* q) {
+    constexpr int NR = C::NR, NA = C::NA;
 #pragma unroll
     for (int n = 0; n < NA; ++n) {
         float ql[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-        for (int m = 0; m < kLM; ++m) ql[lm_l(m) - 1] = fmaf(clm(m) * S[n][m], S[n][m], ql[lm_l(m) - 1]);
+        for (int m = 0; m < 3; ++m) ql[0] = fmaf(clm(m) * S[n][m], S[n][m], ql[0]);
+#pragma unroll
+        for (int m = 3; m < 8; ++m) ql[1] = fmaf(clm(m) * S[n][m], S[n][m], ql[1]);
+#pragma unroll
+        for (int m = 8; m < 15; ++m) ql[2] = fmaf(clm(m) * S[n][m], S[n][m], ql[2]);
+#pragma unroll
+        for (int m = 15; m < 24; ++m) ql[3] = fmaf(clm(m) * S[n][m], S[n][m], ql[3]);
 #pragma unroll
         for (int l = 0; l < 4; ++l) q[NR + n * 4 + l] = ql[l];
-        if (C::H4) q[NR + NA * 4 + n] = fourbody(&S[n][3], nullptr);
-#pragma unroll
-        for (int m = 0; m < kLM; ++m) a.S[(n * kLM + m) * N + i] = S[n][m];
-    }
-
-    if (a.q16) {
-        // mixed precision: hand q to the tensor-core network as a 16-bit row
-        constexpr int Kp = (D + 15) / 16 * 16;
-        unsigned* row = reinterpret_cast<unsigned*>(a.q16) + (size_t)i * (Kp / 2);
-#pragma unroll
-        for (int d = 0; d < Kp; d += 2) {
-            const float x0 = d < D ? q[d] : 0.0f, x1 = d + 1 < D ? q[d + 1] : 0.0f;
-            unsigned bits;
-            if (a.q16_kind == 2) {
-                __nv_bfloat162 v = __floats2bfloat162_rn(x0, x1);
-                memcpy(&bits, &v, 4);
-            } else {
-                __half2 v = __floats2half2_rn(x0, x1);
-                memcpy(&bits, &v, 4);
-            }
-            row[d / 2] = bits;
-        }
-        return;
-    }
-
-    // network E_i = sum_h w1 tanh(W0 q + b0) + b1 and p = dE_i/dq
-    const float* W0 = sm + sl.W0 + ti * sl.SW;
-    const float* b0 = sm + sl.b0 + ti * sl.HS;
-    const float* w1 = sm + sl.w1 + ti * sl.HS;
-    float E = sm[sl.b1 + ti];
-    float p[D];
-#pragma unroll
-    for (int d = 0; d < D; ++d) p[d] = 0.0f;
-    for (int h = 0; h < a.H; ++h) {
-        const float* w = W0 + h * D;
-        float z = b0[h];
-#pragma unroll
-        for (int d = 0; d < D; ++d) z = fmaf(w[d], q[d], z);
-        const float t = tanh_f(z);
-        const float wh = w1[h];
-        E = fmaf(wh, t, E);
-        const float sg = wh * (1.0f - t * t);
-#pragma unroll
-        for (int d = 0; d < D; ++d) p[d] = fmaf(sg, w[d], p[d]);
-    }
-    a.e_atom[i] = E;
-#pragma unroll
-    for (int d = NR; d < D; ++d) a.pang[(d - NR) * N + i] = p[d];
-    if (a.q_out) {
-#pragma unroll
-        for (int d = 0; d < D; ++d) a.q_out[d * N + i] = q[d];
-    }
-    if (a.p_out) {
-#pragma unroll
-        for (int d = 0; d < D; ++d) a.p_out[d * N + i] = p[d];
-    }
-    // radial adjoint projected on the neighbour species:
-    // P[i][t][k] = sum_n dE/dq_n cR[Zi][t][n][k]
-#pragma unroll
-    for (int t = 0; t < T; ++t) {
-        const float* c = sm + sl.cR + (ti * T + t) * C::SR;
-#pragma unroll
-        for (int k = 0; k < KR; ++k) {
-            float acc = 0.0f;
-#pragma unroll
-            for (int n = 0; n < NR; ++n) acc = fmaf(p[n], c[n * KR + k], acc);
-            a.Pr[(i * T + t) * KR + k] = acc;
-            NEP_SCHED_BARRIER();
+        if (C::H4) {
+            const float s2[5] = {S[n][3], S[n][4], S[n][5], S[n][6], S[n][7]};
+            q[NR + NA * 4 + n] = fourbody(s2, nullptr);
         }
     }
 }
 
-// ---------------------------------------------------------------------------
-// pair forces and per-atom virial, one atom
-// ---------------------------------------------------------------------------
-template <class C, bool MINIMG>
-NEP_HD void force_atom(const EvalArgs& a, const float* sm, int i) {
-    constexpr int NR = C::NR, NA = C::NA, KR = C::KR, KA = C::KA, T = C::T;
-    (void)NR;
-    const SmemLayout sl = smem_layout<C>(a.H);
-    const int N = a.N;
-    const AtomFrame fr = atom_frame(a, i);
-    const int ti = fr.ti;
-    const float irR = 1.0f / a.rc_rad, irA = 1.0f / a.rc_ang;
-
-    float Fx = 0.0f, Fy = 0.0f, Fz = 0.0f;
-    float W[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) W[k] = 0.0f;
-
-    // dE_i/dS_nlm = 2 C_lm S_nlm dE/dq_nl (+ the 4-body chain through l = 2)
-    float Sb[NA][kLM];
+// dE_i/dS_nlm = 2 C_lm S_nlm dE/dq_nl (+ the 4-body chain through l = 2);
+// S(n, m) and pl(n, l) are the atom's S and angular dE/dq
+template <class C, class GetS, class GetP>
+NEP_HD void make_Sb(float (&Sb)[C::NA][kLM], GetS S, GetP pl) {
+    constexpr int NA = C::NA;
 #pragma unroll
     for (int n = 0; n < NA; ++n) {
-        float pl[4];
-#pragma unroll
-        for (int l = 0; l < 4; ++l) pl[l] = a.pang[(n * 4 + l) * N + i];
         float s2[5];
 #pragma unroll
         for (int m = 0; m < kLM; ++m) {
-            const float s = a.S[(n * kLM + m) * N + i];
+            const float s = S(n, m);
             if (m >= 3 && m < 8) s2[m - 3] = s;
-            Sb[n][m] = 2.0f * clm(m) * pl[lm_l(m) - 1] * s;
+            Sb[n][m] = 2.0f * clm(m) * pl(n, lm_l(m) - 1) * s;
         }
         if (C::H4) {
-            const float p4 = a.pang[(NA * 4 + n) * N + i];
+            const float p4 = pl(n, 4);
             float ds[5];
             fourbody(s2, ds);
 #pragma unroll
             for (int m = 0; m < 5; ++m) Sb[n][3 + m] = fmaf(p4, ds[m], Sb[n][3 + m]);
         }
     }
+}
 
-    // angular pairs (compacted by desc): owner-side force, scattered to the
-    // reverse slot for the gather of F_j
+// angular pair forces: f_ij = u sum_m (b_m - l a_m / r) Y_m + (1/r) sum_m a_m grad P_m(u),
+// a_m = sum_n Sb[n][m] g_n, b_m = sum_n Sb[n][m] g'_n; owner sums and reverse-slot scatter
+template <class C>
+NEP_HD void angular_force(const EvalArgs& a, const float* sm, const SmemLayout& sl, int ti, int i,
+                          const float (&Sb)[C::NA][kLM], float& Fx, float& Fy, float& Fz, float* W) {
+    constexpr int NA = C::NA, KA = C::KA, T = C::T;
+    const int N = a.N;
+    const float irA = 1.0f / a.rc_ang;
     const int nc = a.cnt_comp[i];
     float4 e_nx = nc > 0 ? a.comp[i] : make_float4(1.0f, 0.0f, 0.0f, 0.0f);
     for (int c = 0; c < nc; ++c) {
@@ -364,20 +352,19 @@ NEP_HD void force_atom(const EvalArgs& a, const float* sm, int i) {
             const float* cc = sm + sl.cA + (ti * T + tj) * C::SA;
 #pragma unroll
             for (int n = 0; n < NA; ++n) {
+                float cv[KA];
+                load_row<KA>(cc + n * KA, cv);
                 float u = 0.0f, v = 0.0f;
 #pragma unroll
                 for (int k = 0; k < KA; ++k) {
-                    const float cv = cc[n * KA + k];
-                    u = fmaf(cv, f[k], u);
-                    v = fmaf(cv, fp[k], v);
+                    u = fmaf(cv[k], f[k], u);
+                    v = fmaf(cv[k], fp[k], v);
                 }
                 g[n] = u;
                 gp[n] = v;
             }
         }
         const HarmTerms ht = harm_terms(e.x * ir, e.y * ir, e.z * ir);
-        // f_ij = u sum_m (b_m - l a_m / r) Y_m + (1/r) sum_m a_m grad P_m(u),
-        // a_m = sum_n Sb[n][m] g_n, b_m = sum_n Sb[n][m] g'_n
         float rad = 0.0f, Gx = 0.0f, Gy = 0.0f, Gz = 0.0f;
 #pragma unroll
         for (int m = 0; m < kLM; ++m) {
@@ -403,59 +390,156 @@ NEP_HD void force_atom(const EvalArgs& a, const float* sm, int i) {
         W[6] -= fz * e.x; W[7] -= fz * e.y; W[8] -= fz * e.z;
         a.fin[addr] = make_float4(fx, fy, fz, 0.0f);
     }
+}
 
-    // radial pairs: dE_i/dr_ij + dE_j/dr_ij along rhat, computed from the
-    // species-projected adjoints P of both atoms
-    float Pi[T][KR];
+// per-species network: E = sum_h w1 tanh(W0 q + b0) + b1, p = dE/dq;
+// writes E, the species-projected radial adjoint P[i][t][k] = sum_n p_n cR[Zi][t][n][k]
+template <class C>
+NEP_HD void network(const EvalArgs& a, const float* sm, const SmemLayout& sl, int ti, int i,
+                    const float* q, float* p) {
+    constexpr int NR = C::NR, KR = C::KR, T = C::T, D = C::D, DW = C::DW;
+    const float* W0 = sm + sl.W0 + ti * sl.SW;
+    const float* b0 = sm + sl.b0 + ti * sl.HS;
+    const float* w1 = sm + sl.w1 + ti * sl.HS;
+    float E = sm[sl.b1 + ti];
+    float qv[DW], pv[DW];
 #pragma unroll
-    for (int t = 0; t < T; ++t)
-#pragma unroll
-        for (int k = 0; k < KR; ++k) Pi[t][k] = a.Pr[(i * T + t) * KR + k];
-    // compacted radial pairs (all inside rc_rad): no divergence on the cutoff
-    float Wr[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};   // xx yy zz xy xz yz
-    const int ncr = a.cnt_compr[i];
-    float4 q_nx = ncr > 0 ? a.compr[i] : make_float4(1.0f, 0.0f, 0.0f, 0.0f);
-    for (int s = 0; s < ncr; ++s) {
-        const float4 e = q_nx;
-        if (s + 1 < ncr) q_nx = a.compr[(s + 1) * N + i];
-        const int bits = f2i(e.w);
-        const int tj = bits & 3;
-        const int j = (int)((unsigned)bits >> 2);
-        const float4* Pj4 = reinterpret_cast<const float4*>(a.Pr + (j * T + ti) * KR);
-        const float r = sqrt_f(dist2(e.x, e.y, e.z));
-        const float ir = rcp_f(r);
-        float f[KR], fp[KR];
-        basis_d<KR>(r, irR, f, fp);
-        float dEi = 0.0f, dEj = 0.0f;
-#pragma unroll
-        for (int k4 = 0; k4 < KR / 4; ++k4) {
-            const float4 pj = Pj4[k4];
-            dEj = fmaf(pj.x, fp[4 * k4 + 0], dEj);
-            dEj = fmaf(pj.y, fp[4 * k4 + 1], dEj);
-            dEj = fmaf(pj.z, fp[4 * k4 + 2], dEj);
-            dEj = fmaf(pj.w, fp[4 * k4 + 3], dEj);
-        }
-#pragma unroll
-        for (int k = (KR / 4) * 4; k < KR; ++k) dEj = fmaf(a.Pr[(j * T + ti) * KR + k], fp[k], dEj);
-#pragma unroll
-        for (int k = 0; k < KR; ++k) {
-            float pk = Pi[0][k];
-#pragma unroll
-            for (int t = 1; t < T; ++t) pk = (tj == t) ? Pi[t][k] : pk;
-            dEi = fmaf(pk, fp[k], dEi);
-        }
-        const float tot = (dEi + dEj) * ir;
-        Fx = fmaf(tot, e.x, Fx); Fy = fmaf(tot, e.y, Fy); Fz = fmaf(tot, e.z, Fz);
-        // W -= f_ij (x) r_ij with f_ij = dE_i/dr rhat: symmetric part only
-        const float w = dEi * ir;
-        const float wx = w * e.x, wy = w * e.y, wz = w * e.z;
-        Wr[0] = fmaf(wx, e.x, Wr[0]); Wr[1] = fmaf(wy, e.y, Wr[1]); Wr[2] = fmaf(wz, e.z, Wr[2]);
-        Wr[3] = fmaf(wx, e.y, Wr[3]); Wr[4] = fmaf(wx, e.z, Wr[4]); Wr[5] = fmaf(wy, e.z, Wr[5]);
+    for (int d = 0; d < DW; ++d) {
+        qv[d] = d < D ? q[d] : 0.0f;
+        pv[d] = 0.0f;
     }
-    W[0] -= Wr[0]; W[4] -= Wr[1]; W[8] -= Wr[2];
-    W[1] -= Wr[3]; W[3] -= Wr[3];
-    W[2] -= Wr[4]; W[6] -= Wr[4];
-    W[5] -= Wr[5]; W[7] -= Wr[5];
+    for (int h = 0; h < a.H; ++h) {
+        float w[DW];
+        load_row<DW>(W0 + h * DW, w);
+        float z = b0[h];
+#pragma unroll
+        for (int d = 0; d < DW; ++d) z = fmaf(w[d], qv[d], z);
+        const float t = tanh_f(z);
+        const float wh = w1[h];
+        E = fmaf(wh, t, E);
+        const float sg = wh * (1.0f - t * t);
+#pragma unroll
+        for (int d = 0; d < DW; ++d) pv[d] = fmaf(sg, w[d], pv[d]);
+    }
+#pragma unroll
+    for (int d = 0; d < D; ++d) p[d] = pv[d];
+    a.e_atom[i] = E;
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        const float* c = sm + sl.cR + (ti * T + t) * C::SR;
+        float acc[KR];
+#pragma unroll
+        for (int k = 0; k < KR; ++k) acc[k] = 0.0f;
+#pragma unroll
+        for (int n = 0; n < NR; ++n) {
+            float cv[KR];
+            load_row<KR>(c + n * KR, cv);
+#pragma unroll
+            for (int k = 0; k < KR; ++k) acc[k] = fmaf(p[n], cv[k], acc[k]);
+        }
+        if (KR % 4 == 0) {
+            float4* dst = reinterpret_cast<float4*>(a.Pr + (i * T + t) * KR);
+#pragma unroll
+            for (int k = 0; k < KR; k += 4) dst[k / 4] = make_float4(acc[k], acc[k + 1], acc[k + 2], acc[k + 3]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < KR; ++k) a.Pr[(i * T + t) * KR + k] = acc[k];
+        }
+        NEP_SCHED_BARRIER();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// fused angular descriptor + network + angular forces, one atom.  `stage`
+// points at this thread's column of a [NA*24][blockDim] shared array where S
+// waits while the network runs (stride `sstride` floats between entries).
+// ---------------------------------------------------------------------------
+template <class C>
+NEP_HD void angular_atom(const EvalArgs& a, const float* sm, float* stage, int sstride, int i) {
+    constexpr int NR = C::NR, NA = C::NA, D = C::D;
+    const SmemLayout sl = smem_layout<C>(a.H);
+    const int N = a.N;
+    const int ti = f2i(a.pos4[i].w);
+    float q[D];
+    radial_q<C>(a, sm, sl, ti, i, q);
+    {
+        float S[NA][kLM];
+        angular_S<C>(a, sm, sl, ti, i, S);
+        angular_q<C>(S, q);
+        if (a.q16) {
+            // mixed precision: S and 16-bit q for the tensor-core network
+#pragma unroll
+            for (int n = 0; n < NA; ++n)
+#pragma unroll
+                for (int m = 0; m < kLM; ++m) a.S[(n * kLM + m) * N + i] = S[n][m];
+            constexpr int Kp = (D + 15) / 16 * 16;
+            unsigned* row = reinterpret_cast<unsigned*>(a.q16) + (size_t)i * (Kp / 2);
+#pragma unroll
+            for (int d = 0; d < Kp; d += 2) {
+                const float x0 = d < D ? q[d] : 0.0f, x1 = d + 1 < D ? q[d + 1] : 0.0f;
+                unsigned bits;
+                if (a.q16_kind == 2) {
+                    __nv_bfloat162 v = __floats2bfloat162_rn(x0, x1);
+                    memcpy(&bits, &v, 4);
+                } else {
+                    __half2 v = __floats2half2_rn(x0, x1);
+                    memcpy(&bits, &v, 4);
+                }
+                row[d / 2] = bits;
+            }
+            return;
+        }
+        if (a.S) {
+#pragma unroll
+            for (int n = 0; n < NA; ++n)
+#pragma unroll
+                for (int m = 0; m < kLM; ++m) a.S[(n * kLM + m) * N + i] = S[n][m];
+        }
+#pragma unroll
+        for (int n = 0; n < NA; ++n)
+#pragma unroll
+            for (int m = 0; m < kLM; ++m) stage[(n * kLM + m) * sstride] = S[n][m];
+    }
+    float p[D];
+    network<C>(a, sm, sl, ti, i, q, p);
+    if (a.q_out) {
+#pragma unroll
+        for (int d = 0; d < D; ++d) a.q_out[d * N + i] = q[d];
+    }
+    if (a.p_out) {
+#pragma unroll
+        for (int d = 0; d < D; ++d) a.p_out[d * N + i] = p[d];
+    }
+    float Sb[NA][kLM];
+    make_Sb<C>(Sb, [&](int n, int m) { return stage[(n * kLM + m) * sstride]; },
+               [&](int n, int l) { return p[NR + (l < 4 ? n * 4 + l : NA * 4 + n)]; });
+    float Fx = 0.0f, Fy = 0.0f, Fz = 0.0f;
+    float W[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) W[k] = 0.0f;
+    angular_force<C>(a, sm, sl, ti, i, Sb, Fx, Fy, Fz, W);
+    a.fpart[i] = Fx;
+    a.fpart[N + i] = Fy;
+    a.fpart[2 * N + i] = Fz;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) a.wat[k * N + i] = W[k];
+}
+
+// angular forces of the mixed-precision path (S and dE/dq from memory)
+template <class C>
+NEP_HD void angforce_atom(const EvalArgs& a, const float* sm, int i) {
+    constexpr int NA = C::NA;
+    const SmemLayout sl = smem_layout<C>(a.H);
+    const int N = a.N;
+    const int ti = f2i(a.pos4[i].w);
+    float Sb[NA][kLM];
+    make_Sb<C>(Sb, [&](int n, int m) { return a.S[(n * kLM + m) * N + i]; },
+               [&](int n, int l) { return a.pang[(l < 4 ? n * 4 + l : NA * 4 + n) * N + i]; });
+    float Fx = 0.0f, Fy = 0.0f, Fz = 0.0f;
+    float W[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) W[k] = 0.0f;
+    angular_force<C>(a, sm, sl, ti, i, Sb, Fx, Fy, Fz, W);
     a.fpart[i] = Fx;
     a.fpart[N + i] = Fy;
     a.fpart[2 * N + i] = Fz;
@@ -464,98 +548,237 @@ NEP_HD void force_atom(const EvalArgs& a, const float* sm, int i) {
 }
 
 // ---------------------------------------------------------------------------
+// radial pair forces of both directions: dE_i/dr_ij + dE_j/dr_ij along rhat,
+// from P of atom i (neighbour species row) and P of atom j (row Zi); returns
+// F_i's radial part and the symmetric radial virial (xx yy zz xy xz yz)
+// ---------------------------------------------------------------------------
+template <class C, bool MINIMG>
+NEP_HD void radial_force_atom(const EvalArgs& a, int i, float& Fx, float& Fy, float& Fz, float* Wr) {
+    constexpr int KR = C::KR, T = C::T;
+    const int N = a.N;
+    const AtomFrame fr = atom_frame(a, i);
+    const int ti = fr.ti;
+    const float rcR2 = a.rc_rad * a.rc_rad;
+    const float irR = 1.0f / a.rc_rad;
+    float Pi[T][KR];
+#pragma unroll
+    for (int t = 0; t < T; ++t)
+#pragma unroll
+        for (int k = 0; k < KR; ++k) Pi[t][k] = a.Pr[(i * T + t) * KR + k];
+    // one pair: both directions of the radial force along r_ij, and the
+    // owner's symmetric radial virial
+    auto pair = [&](int j, int tj, float dx, float dy, float dz, float d2) {
+        const float r = sqrt_f(d2);
+        const float ir = rcp_f(r);
+        float f[KR], fp[KR];
+        basis_d<KR>(r, irR, f, fp);
+        float Pj[KR];
+        if (KR % 4 == 0) {
+            const float4* src = reinterpret_cast<const float4*>(a.Pr + (j * T + ti) * KR);
+#pragma unroll
+            for (int k = 0; k < KR; k += 4) {
+                const float4 v = src[k / 4];
+                Pj[k] = v.x; Pj[k + 1] = v.y; Pj[k + 2] = v.z; Pj[k + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < KR; ++k) Pj[k] = a.Pr[(j * T + ti) * KR + k];
+        }
+        float dEi = 0.0f, dEj = 0.0f;
+#pragma unroll
+        for (int k = 0; k < KR; ++k) {
+            float pk = Pi[0][k];
+#pragma unroll
+            for (int t = 1; t < T; ++t) pk = (tj == t) ? Pi[t][k] : pk;
+            dEi = fmaf(pk, fp[k], dEi);
+            dEj = fmaf(Pj[k], fp[k], dEj);
+        }
+        const float tot = (dEi + dEj) * ir;
+        Fx = fmaf(tot, dx, Fx); Fy = fmaf(tot, dy, Fy); Fz = fmaf(tot, dz, Fz);
+        const float w = dEi * ir;
+        const float wx = w * dx, wy = w * dy, wz = w * dz;
+        Wr[0] = fmaf(wx, dx, Wr[0]); Wr[1] = fmaf(wy, dy, Wr[1]); Wr[2] = fmaf(wz, dz, Wr[2]);
+        Wr[3] = fmaf(wx, dy, Wr[3]); Wr[4] = fmaf(wx, dz, Wr[4]); Wr[5] = fmaf(wy, dz, Wr[5]);
+    };
+    if (a.compr) {
+        // pairs inside rc_rad, compacted by the radial-descriptor kernel
+        const int ncr = a.cnt_compr[i];
+        float4 q_nx = ncr > 0 ? a.compr[i] : make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+        for (int s = 0; s < ncr; ++s) {
+            const float4 e = q_nx;
+            if (s + 1 < ncr) q_nx = a.compr[(s + 1) * N + i];
+            const int bits = f2i(e.w);
+            pair((int)((unsigned)bits >> 2), bits & 3, e.x, e.y, e.z, dist2(e.x, e.y, e.z));
+        }
+        return;
+    }
+    const int cnt = a.cnt[i];
+    int j_nx = cnt > 0 ? a.nbr[i] : 0;
+    int j_nx2 = cnt > 1 ? a.nbr[N + i] : 0;
+    float4 p_nx = a.pos4[j_nx];
+    int sh_nx = (!MINIMG && cnt > 0) ? a.shift[i] : 0;
+    for (int s = 0; s < cnt; ++s) {
+        const int j = j_nx;
+        const float4 pj = p_nx;
+        const int sh = sh_nx;
+        if (s + 1 < cnt) {
+            j_nx = j_nx2;
+            p_nx = a.pos4[j_nx];
+            if (!MINIMG) sh_nx = a.shift[(s + 1) * N + i];
+            if (s + 2 < cnt) j_nx2 = a.nbr[(s + 2) * N + i];
+        }
+        float dx, dy, dz;
+        pair_vector(fr.pi, pj, fr.Lx, fr.Ly, fr.Lz, fr.iLx, fr.iLy, fr.iLz, MINIMG, sh, dx, dy, dz);
+        const float d2 = dist2(dx, dy, dz);
+        if (d2 < rcR2) pair(j, f2i(pj.w), dx, dy, dz, d2);
+    }
+}
+
+// F_i = radial part + angular owner part - sum of the scattered incoming
+// angular pair forces; the per-atom virial (angular owner part minus the
+// radial part) is written back for the FP64 reduction
+template <class C, bool MINIMG>
+NEP_HD void finish_atom(const EvalArgs& a, int i, float* force, float* e_out) {
+    const int N = a.N;
+    float Fx = a.fpart[i], Fy = a.fpart[N + i], Fz = a.fpart[2 * N + i];
+    float Wr[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    radial_force_atom<C, MINIMG>(a, i, Fx, Fy, Fz, Wr);
+    const int na = a.cnt_ang[i];
+    for (int s = 0; s < na; ++s) {
+        const float4 g = a.fin[(size_t)s * N + i];
+        Fx -= g.x; Fy -= g.y; Fz -= g.z;
+    }
+    force[i] = Fx;
+    force[N + i] = Fy;
+    force[2 * N + i] = Fz;
+    if (e_out) e_out[i] = a.e_atom[i];
+    const float Wsym[9] = {Wr[0], Wr[3], Wr[4], Wr[3], Wr[1], Wr[5], Wr[4], Wr[5], Wr[2]};
+#pragma unroll
+    for (int c = 0; c < 9; ++c) a.wat[(size_t)c * N + i] -= Wsym[c];
+}
+
+// ---------------------------------------------------------------------------
 // kernels and launchers
 // ---------------------------------------------------------------------------
 #if defined(__CUDACC__)
-// Resident blocks per SM that the register allocation is sized for
-// (65536 / (128 x MINB) registers per thread: 255, 168 or 128).  Each kernel
-// is compiled for MINB = 2, 3 and 4; the runtime picks one per system size
-// class (nep_autotune), by default 3 for the descriptor kernel and 2 for the
-// force kernel, which keeps dE/dS (n_ang x 24 floats) in registers.
+// Resident blocks per SM that the register allocation of k_angular is sized
+// for (65536 / (128 x MINB) registers per thread: 255, 168 or 128).  It is
+// compiled for MINB = 2, 3 and 4; the runtime picks one per system size class
+// (nep_autotune).  Variant 0 (255 registers) keeps S and dE/dS on chip
+// without spills and is the default.
 NEP_HD constexpr int variant_minb(int v) { return v + 2; }
+constexpr int kRadialBlock = 256;
+constexpr int kFinishThreads = 128;
 
-template <class C, bool MINIMG, int MINB>
-__global__ void __launch_bounds__(kBlock, MINB) k_desc(const EvalArgs a) {
-    extern __shared__ float sm[];
-    load_model<C>(sm, a.params, a.H, threadIdx.x, blockDim.x);
-    __syncthreads();
+template <class C, bool MINIMG>
+__global__ void __launch_bounds__(kRadialBlock) k_radial(const EvalArgs a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < a.N) desc_atom<C, MINIMG>(a, sm, i);
+    if (i < a.N) radial_atom<C, MINIMG>(a, i);
 }
 
-template <class C, bool MINIMG, int MINB>
-__global__ void __launch_bounds__(kBlock, MINB) k_force(const EvalArgs a) {
+template <class C, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) k_angular(const EvalArgs a) {
+    extern __shared__ float sm[];
+    const SmemLayout sl = smem_layout<C>(a.H);
+    load_model<C>(sm, a.params, a.H, threadIdx.x, blockDim.x);
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < a.N) angular_atom<C>(a, sm, sm + sl.total + threadIdx.x, kBlock, i);
+}
+
+template <class C, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) k_angforce(const EvalArgs a) {
     extern __shared__ float sm[];
     load_model<C>(sm, a.params, a.H, threadIdx.x, blockDim.x);
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < a.N) force_atom<C, MINIMG>(a, sm, i);
+    if (i < a.N) angforce_atom<C>(a, sm, i);
+}
+
+template <class C, bool MINIMG>
+__global__ void __launch_bounds__(kFinishThreads) k_finish(const EvalArgs a, float* force, float* e_out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < a.N) finish_atom<C, MINIMG>(a, i, force, e_out);
 }
 
 template <class C>
 size_t smem_bytes_of(int H) { return sizeof(float) * (size_t)smem_layout<C>(H).total; }
-
-template <class C, int MINB>
-void launch_desc_v(const EvalArgs& a, cudaStream_t st, size_t smem, int grid) {
-    if (a.min_image)
-        k_desc<C, true, MINB><<<grid, kBlock, smem, st>>>(a);
-    else
-        k_desc<C, false, MINB><<<grid, kBlock, smem, st>>>(a);
-}
-template <class C, int MINB>
-void launch_force_v(const EvalArgs& a, cudaStream_t st, size_t smem, int grid) {
-    if (a.min_image)
-        k_force<C, true, MINB><<<grid, kBlock, smem, st>>>(a);
-    else
-        k_force<C, false, MINB><<<grid, kBlock, smem, st>>>(a);
+template <class C>
+size_t angular_smem_bytes(int H) {
+    return sizeof(float) * ((size_t)smem_layout<C>(H).total + (size_t)C::NA * kLM * kBlock);
 }
 
 template <class C>
-cudaError_t launch_desc_t(const EvalArgs& a, cudaStream_t st, int v) {
-    const size_t smem = smem_bytes_of<C>(a.H);
-    const int grid = (a.N + kBlock - 1) / kBlock;
+cudaError_t launch_radial_t(const EvalArgs& a, cudaStream_t st) {
+    const int grid = (a.N + kRadialBlock - 1) / kRadialBlock;
     if (grid == 0) return cudaSuccess;
-    if (v == 0) launch_desc_v<C, 2>(a, st, smem, grid);
-    else if (v == 2) launch_desc_v<C, 4>(a, st, smem, grid);
-    else launch_desc_v<C, 3>(a, st, smem, grid);
+    if (a.min_image)
+        k_radial<C, true><<<grid, kRadialBlock, 0, st>>>(a);
+    else
+        k_radial<C, false><<<grid, kRadialBlock, 0, st>>>(a);
     return cudaGetLastError();
 }
 
 template <class C>
-cudaError_t launch_force_t(const EvalArgs& a, cudaStream_t st, int v) {
-    const size_t smem = smem_bytes_of<C>(a.H);
+cudaError_t launch_angular_t(const EvalArgs& a, cudaStream_t st, int v) {
     const int grid = (a.N + kBlock - 1) / kBlock;
     if (grid == 0) return cudaSuccess;
-    if (v == 1) launch_force_v<C, 3>(a, st, smem, grid);
-    else if (v == 2) launch_force_v<C, 4>(a, st, smem, grid);
-    else launch_force_v<C, 2>(a, st, smem, grid);
+    const size_t smem = angular_smem_bytes<C>(a.H);
+    if (v == 1) k_angular<C, 3><<<grid, kBlock, smem, st>>>(a);
+    else if (v == 2) k_angular<C, 4><<<grid, kBlock, smem, st>>>(a);
+    else k_angular<C, 2><<<grid, kBlock, smem, st>>>(a);
     return cudaGetLastError();
 }
 
+template <class C>
+cudaError_t launch_angforce_t(const EvalArgs& a, cudaStream_t st, int v) {
+    const int grid = (a.N + kBlock - 1) / kBlock;
+    if (grid == 0) return cudaSuccess;
+    const size_t smem = smem_bytes_of<C>(a.H);
+    if (v == 1) k_angforce<C, 3><<<grid, kBlock, smem, st>>>(a);
+    else if (v == 2) k_angforce<C, 4><<<grid, kBlock, smem, st>>>(a);
+    else k_angforce<C, 2><<<grid, kBlock, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <class C>
+cudaError_t launch_finish_t(const EvalArgs& a, const FinishArgs& f, int max_chunks, cudaStream_t st) {
+    const int grid = (a.N + kFinishThreads - 1) / kFinishThreads;
+    if (grid > 0) {
+        if (a.min_image)
+            k_finish<C, true><<<grid, kFinishThreads, 0, st>>>(a, f.force, f.e_out);
+        else
+            k_finish<C, false><<<grid, kFinishThreads, 0, st>>>(a, f.force, f.e_out);
+    }
+    return launch_chunk_reduce(a, f, max_chunks, st);
+}
+
 template <class C, int MINB>
-cudaError_t init_v(int smem) {
+cudaError_t init_v(int H) {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_desc<C, true, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
-    if ((e = cudaFuncSetAttribute(k_desc<C, false, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
-    if ((e = cudaFuncSetAttribute(k_force<C, true, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
-    return cudaFuncSetAttribute(k_force<C, false, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if ((e = cudaFuncSetAttribute(k_angular<C, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)angular_smem_bytes<C>(H))))
+        return e;
+    return cudaFuncSetAttribute(k_angforce<C, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_bytes_of<C>(H));
 }
 
 template <class C>
 cudaError_t init_t(int H) {
-    const int smem = (int)smem_bytes_of<C>(H);
     cudaError_t e;
-    if ((e = init_v<C, 2>(smem))) return e;
-    if ((e = init_v<C, 3>(smem))) return e;
-    return init_v<C, 4>(smem);
+    if ((e = init_v<C, 2>(H))) return e;
+    if ((e = init_v<C, 3>(H))) return e;
+    return init_v<C, 4>(H);
 }
 
 #define NEP_DEFINE_KERNEL_SET(NAME, NR, NA, KR, KA, H4, T)                                    \
     extern const KernelSet NAME = {NR, NA, KR, KA, H4, T,                                        \
                                    &smem_bytes_of<Cfg<NR, NA, KR, KA, H4, T>>,                   \
                                    &init_t<Cfg<NR, NA, KR, KA, H4, T>>,                          \
-                                   &launch_desc_t<Cfg<NR, NA, KR, KA, H4, T>>,                   \
-                                   &launch_force_t<Cfg<NR, NA, KR, KA, H4, T>>,                  \
+                                   &launch_radial_t<Cfg<NR, NA, KR, KA, H4, T>>,                 \
+                                   &launch_angular_t<Cfg<NR, NA, KR, KA, H4, T>>,                \
+                                   &launch_angforce_t<Cfg<NR, NA, KR, KA, H4, T>>,               \
+                                   &launch_finish_t<Cfg<NR, NA, KR, KA, H4, T>>,                 \
                                    &launch_mlp_tc_t<Cfg<NR, NA, KR, KA, H4, T>>,                 \
                                    &train_init_t<Cfg<NR, NA, KR, KA, H4, T>>,                    \
                                    &train_t<Cfg<NR, NA, KR, KA, H4, T>>,                         \

@@ -4,7 +4,7 @@
 #include <stddef.h>
 #include <stdint.h>
 
-#include "../../include/nep.h"
+#include "nep.h"
 
 #if defined(__CUDACC__)
 #define NEP_HD __host__ __device__ __forceinline__
@@ -19,8 +19,8 @@ constexpr int kLM = 24;          // real solid harmonics for l = 1..4: 3+5+7+9
 constexpr int kChunk = 1024;     // atoms per reduction chunk (one CTA)
 constexpr int kBlock = 128;      // threads per block of the per-atom kernels
 constexpr int kVariants = 3;              // register budgets for 2, 3, 4 blocks per SM
-constexpr int kDefaultDescVariant = 1;    // 3 blocks per SM
-constexpr int kDefaultForceVariant = 0;   // 2 blocks per SM
+constexpr int kDefaultDescVariant = 0;    // fused angular kernel: 2 blocks per SM
+constexpr int kDefaultForceVariant = 0;   // angular force kernel (mixed precision): 2 blocks per SM
 constexpr int kSizeBins = 32;             // tuning table: log2 of mean atoms per configuration
 
 // Stencil/cell plan of one configuration for the neighbour build.
@@ -49,12 +49,13 @@ struct EvalArgs {
     const float* params;           // [P] flat model parameters
     // per-atom scratch
     float* e_atom;                 // [N]
-    float* S;                      // [NA*24][N]
-    float* pang;                   // [NA*(4+H4)][N]  dE/dq of angular and 4-body entries
+    float* fb;                     // [T*KR][N]       species-resolved radial basis sums
+    float* S;                      // [NA*24][N]      S_nlm (mixed precision and training only)
+    float* pang;                   // [NA*(4+H4)][N]  dE/dq of angular and 4-body entries (mixed)
     float* Pr;                     // [N][T][KR]      sum_n dE/dq_n cR[Zi][t][n][k]
     float4* comp;                  // [cap_ang][N]    compacted angular pairs
     int* cnt_comp;                 // [N]
-    float4* compr;                 // [cap][N]        compacted radial pairs (r_ij, j|tj)
+    float4* compr;                 // [cap][N]        compacted radial pairs (r_ij, j|tj), training only
     int* cnt_compr;                // [N]
     float4* fin;                   // [cap_ang][N]    incoming angular pair forces
     float* fpart;                  // [3][N]
@@ -87,6 +88,15 @@ struct TrainArgs {
     float* grad;                   // [P] output
 };
 
+// Outputs of the force-completion kernel.
+struct FinishArgs {
+    const int* atom_off;           // [B+1]
+    const int* chunk_start;        // [B+1] reduction chunks per configuration
+    double* partial;               // [chunks][10] FP64 E and virial per chunk
+    float* force;                  // [3][N]
+    float* e_out;                  // [N] or null
+};
+
 // Offsets of the parameter blocks in the flat vector.
 struct ParamLayout {
     int D, P;
@@ -109,8 +119,10 @@ struct KernelSet {
     int n_rad, n_ang, k_rad, k_ang, has_4body, n_types;
     size_t (*smem_bytes)(int H);
     cudaError_t (*init)(int H);   // set kernel attributes (dynamic shared memory)
-    cudaError_t (*descriptor)(const EvalArgs&, cudaStream_t, int variant);
-    cudaError_t (*force)(const EvalArgs&, cudaStream_t, int variant);
+    cudaError_t (*radial)(const EvalArgs&, cudaStream_t);
+    cudaError_t (*angular)(const EvalArgs&, cudaStream_t, int variant);
+    cudaError_t (*angforce)(const EvalArgs&, cudaStream_t, int variant);
+    cudaError_t (*finish)(const EvalArgs&, const FinishArgs&, int max_chunks, cudaStream_t);
     cudaError_t (*mlp_tc)(const EvalArgs&, cudaStream_t);   // tensor-core network (mixed precision)
     cudaError_t (*train_init)(int H);
     cudaError_t (*train)(const TrainArgs&, cudaStream_t);   // tangent ... gradient
@@ -124,9 +136,8 @@ const KernelSet* find_kernel_set(int n_rad, int n_ang, int k_rad, int k_ang, int
 cudaError_t launch_pack(const float* pos, const int* type, const int* atom_off, int N, int B,
                         int T, float4* pos4, int* cfg, int* status, cudaStream_t st);
 cudaError_t launch_chunk_plan(const int* atom_off, int B, int* chunk_start, cudaStream_t st);
-cudaError_t launch_gather_reduce(const EvalArgs& a, const int* atom_off, const int* chunk_start,
-                                 int max_chunks, double* partial, float* force, float* e_out,
-                                 cudaStream_t st);
+// FP64 sums of E_i and the per-atom virials per reduction chunk
+cudaError_t launch_chunk_reduce(const EvalArgs& a, const FinishArgs& f, int max_chunks, cudaStream_t st);
 cudaError_t launch_final_reduce(int B, const int* chunk_start, const double* partial,
                                 double* e_tot, double* virial, cudaStream_t st);
 
@@ -138,11 +149,12 @@ struct NbrWork {
     int* cell_start;       // [Cmax+1]
     int* cell_atoms;       // [N]
     int* scan_tmp;         // [ceil(Cmax/2048)+1]
+    int2* shell;           // [cap][N] scratch for the list entries beyond rc_rad
     int cmax;
 };
 size_t nbr_cell_capacity(int N, int B);
 cudaError_t launch_neighbors(const float* pos, const float4* pos4, const int* atom_off, const float* box,
-                             const int* cfg, int N, int B, float rc_list, float rc_list_ang,
+                             const int* cfg, int N, int B, float rc_list, float rc_list_ang, float rc_phys,
                              int min_image, nep_nlist* nl, const NbrWork& w, cudaStream_t st);
 
 cudaError_t launch_kick(float* vel, const float* force, const int* type, const float* inv_mass,

@@ -81,48 +81,40 @@ __global__ void k_chunk_plan(const int* __restrict__ atom_off, int B, int* chunk
     if (threadIdx.x == 0) chunk_start[B] = carry;
 }
 
-// --------------------------------------------------- gather + FP64 partials
 constexpr int kRedThreads = 256;
 
-__global__ void __launch_bounds__(kRedThreads) k_gather_reduce(
-    const EvalArgs a, const int* __restrict__ atom_off, const int* __restrict__ chunk_start,
-    double* __restrict__ partial, float* __restrict__ force, float* __restrict__ e_out) {
+// one CTA per reduction chunk (atoms of one configuration): FP64 sums of the
+// energies and per-atom virials, each thread over a fixed atom subset, then a
+// fixed tree
+__global__ void __launch_bounds__(kRedThreads) k_chunk_reduce(const EvalArgs a, FinishArgs f) {
     const int k = blockIdx.x;
     const int B = a.B, N = a.N;
-    const int total = chunk_start[B];
+    const int total = f.chunk_start[B];
     if (k >= total) return;
-    const int b = find_segment(chunk_start, B, k);
-    const int a0 = atom_off[b] + (k - chunk_start[b]) * kChunk;
-    const int a1 = min(atom_off[b + 1], a0 + kChunk);
+    const int b = find_segment(f.chunk_start, B, k);
+    const int a0 = f.atom_off[b] + (k - f.chunk_start[b]) * kChunk;
+    const int a1 = min(f.atom_off[b + 1], a0 + kChunk);
     double acc[10];
 #pragma unroll
     for (int c = 0; c < 10; ++c) acc[c] = 0.0;
     for (int i = a0 + threadIdx.x; i < a1; i += kRedThreads) {
-        float fx = a.fpart[i], fy = a.fpart[N + i], fz = a.fpart[2 * N + i];
-        const int na = a.cnt_ang[i];
-        for (int s = 0; s < na; ++s) {
-            const float4 g = a.fin[(size_t)s * N + i];
-            fx -= g.x; fy -= g.y; fz -= g.z;
-        }
-        force[i] = fx;
-        force[N + i] = fy;
-        force[2 * N + i] = fz;
-        const float e = a.e_atom[i];
-        if (e_out) e_out[i] = e;
-        acc[0] += (double)e;
+        acc[0] += (double)a.e_atom[i];
 #pragma unroll
         for (int c = 0; c < 9; ++c) acc[1 + c] += (double)a.wat[(size_t)c * N + i];
     }
-    __shared__ double red[kRedThreads];
+    __shared__ double red[10][kRedThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
     for (int c = 0; c < 10; ++c) {
-        red[threadIdx.x] = acc[c];
-        __syncthreads();
-        for (int o = kRedThreads / 2; o > 0; o >>= 1) {
-            if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) partial[(size_t)k * 10 + c] = red[0];
-        __syncthreads();
+        double v = acc[c];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[c][w] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 10) {
+        double v = 0.0;
+        for (int q = 0; q < kRedThreads / 32; ++q) v += red[threadIdx.x][q];
+        f.partial[(size_t)k * 10 + threadIdx.x] = v;
     }
 }
 
@@ -333,10 +325,14 @@ __device__ __forceinline__ int floor_div(int a, int b) {
     return q;
 }
 
-// One pass over the stencil: angular candidates (d < rc_ang + skin) fill the
-// list from slot 0 up, the remaining radial candidates fill it from slot
-// cap-1 down and are moved behind the angular prefix at the end, so the
-// final order is [angular in visit order, radial-only in visit order].
+// One pass over the stencil.  The list is written in three groups:
+// [d < rc_ang + skin] (the angular prefix) | [d < rc_rad] | [rc_rad <= d <
+// rc_rad + skin].  Angular candidates fill it from slot 0 up, radial ones
+// inside rc_rad from slot cap-1 down, the shell beyond rc_rad goes to a
+// scratch buffer; at the end the downward block is reversed and moved behind
+// the prefix and the shell appended, all in visit order.  With the pairs
+// inside the cutoff first, a warp's late iterations are mostly outside the
+// cutoff for all of its lanes and skip the pair work together.
 __global__ void __launch_bounds__(128) k_build(const float4* __restrict__ pos4,
                                                const int* __restrict__ cfg,
                                                const float* __restrict__ box,
@@ -344,7 +340,8 @@ __global__ void __launch_bounds__(128) k_build(const float4* __restrict__ pos4,
                                                const int* __restrict__ cell_of,
                                                const int* __restrict__ cell_start,
                                                const int* __restrict__ cell_atoms, int N,
-                                               float rc2_rad, float rc2_ang, nep_nlist nl) {
+                                               float rc2_rad, float rc2_ang, float rc2_phys,
+                                               int2* __restrict__ shell, nep_nlist nl) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int b = cfg[i];
@@ -356,7 +353,7 @@ __global__ void __launch_bounds__(128) k_build(const float4* __restrict__ pos4,
     c /= p.nc[2];
     const int cy = c % p.nc[1];
     const int cx = c / p.nc[1];
-    int n_ang = 0, n_rest = 0, w_ang = 0;
+    int n_ang = 0, n_in = 0, n_out = 0, w_ang = 0;
     const int cap = nl.cap, cap_ang = nl.cap_ang;
     for (int ox = -p.half[0]; ox <= p.half[0]; ++ox) {
         const int ux = cx + ox, sx = floor_div(ux, p.nc[0]), wx = ux - sx * p.nc[0];
@@ -379,59 +376,70 @@ __global__ void __launch_bounds__(128) k_build(const float4* __restrict__ pos4,
                     const float dz = add_rn(sub_rn(pj.z, pi.z), fz);
                     const float d2 = dist2(dx, dy, dz);
                     if (!(d2 < rc2_rad)) continue;
-                    int slot;
+                    const int sh = pack_shift(sx, sy, sz);
                     if (d2 < rc2_ang) {
-                        slot = n_ang < cap_ang && n_ang + n_rest < cap ? n_ang : -1;
+                        const int slot = n_ang < cap_ang && n_ang + n_in < cap ? n_ang : -1;
                         ++n_ang;
-                        if (slot >= 0) w_ang = n_ang;
+                        if (slot < 0) continue;
+                        w_ang = n_ang;
+                        nl.nbr[(size_t)slot * N + i] = j;
+                        if (nl.shift) nl.shift[(size_t)slot * N + i] = sh;
+                    } else if (d2 < rc2_phys) {
+                        const int slot = n_ang + n_in < cap ? cap - 1 - n_in : -1;
+                        ++n_in;
+                        if (slot < 0) continue;
+                        nl.nbr[(size_t)slot * N + i] = j;
+                        if (nl.shift) nl.shift[(size_t)slot * N + i] = sh;
                     } else {
-                        slot = n_ang + n_rest < cap ? cap - 1 - n_rest : -1;
-                        ++n_rest;
+                        if (n_out < cap) shell[(size_t)n_out * N + i] = make_int2(j, sh);
+                        ++n_out;
                     }
-                    if (slot < 0) continue;
-                    nl.nbr[(size_t)slot * N + i] = j;
-                    if (nl.shift) nl.shift[(size_t)slot * N + i] = pack_shift(sx, sy, sz);
                 }
             }
         }
     }
+    const int n_rest = n_in + n_out;
     const int n_total = n_ang + n_rest;
     const bool over = n_total > cap || n_ang > cap_ang;
     if (over) {
         set_flag(nl.status, 0);
         atomicMax(nl.status + 1, n_total);
         atomicMax(nl.status + 2, n_ang);
+        // only the contiguous angular prefix that was written is kept
+        nl.cnt[i] = w_ang;
+        nl.cnt_ang[i] = w_ang;
+        return;
     }
-    // on overflow only the contiguous angular prefix that was written is kept
-    const int kept_ang = over ? w_ang : n_ang;
-    // move the radial-only entries (stored downward from cap-1) behind the
-    // prefix: reverse the block in place, then copy it down (the target never
-    // starts above the source, so an ascending copy is safe)
-    int kept_rest = 0;
-    if (!over) {
-        kept_rest = n_rest;
-        const int base = cap - n_rest;
-        for (int k = 0; k < n_rest / 2; ++k) {
-            const size_t x = (size_t)(base + k) * N + i, y = (size_t)(cap - 1 - k) * N + i;
-            const int t = nl.nbr[x];
-            nl.nbr[x] = nl.nbr[y];
-            nl.nbr[y] = t;
-            if (nl.shift) {
-                const int u = nl.shift[x];
-                nl.shift[x] = nl.shift[y];
-                nl.shift[y] = u;
-            }
-        }
-        if (base != kept_ang) {
-            for (int k = 0; k < n_rest; ++k) {
-                const size_t from = (size_t)(base + k) * N + i, to = (size_t)(kept_ang + k) * N + i;
-                nl.nbr[to] = nl.nbr[from];
-                if (nl.shift) nl.shift[to] = nl.shift[from];
-            }
+    // the inside block sits reversed at [cap - n_in, cap): reverse it in
+    // place, then copy it down behind the prefix (ascending copy, target
+    // never above source), then append the shell
+    const int base = cap - n_in;
+    for (int k = 0; k < n_in / 2; ++k) {
+        const size_t x = (size_t)(base + k) * N + i, y = (size_t)(cap - 1 - k) * N + i;
+        const int t = nl.nbr[x];
+        nl.nbr[x] = nl.nbr[y];
+        nl.nbr[y] = t;
+        if (nl.shift) {
+            const int u = nl.shift[x];
+            nl.shift[x] = nl.shift[y];
+            nl.shift[y] = u;
         }
     }
-    nl.cnt[i] = kept_ang + kept_rest;
-    nl.cnt_ang[i] = kept_ang;
+    if (base != n_ang) {
+        for (int k = 0; k < n_in; ++k) {
+            const size_t from = (size_t)(base + k) * N + i, to = (size_t)(n_ang + k) * N + i;
+            nl.nbr[to] = nl.nbr[from];
+            if (nl.shift) nl.shift[to] = nl.shift[from];
+        }
+    }
+    for (int k = 0; k < n_out; ++k) {
+        const int2 e = shell[(size_t)k * N + i];
+        const size_t to = (size_t)(n_ang + n_in + k) * N + i;
+        nl.nbr[to] = e.x;
+        if (nl.shift) nl.shift[to] = e.y;
+    }
+    nl.cnt[i] = n_total;
+    nl.cnt_ang[i] = n_ang;
 }
 
 __global__ void k_rev(int N, nep_nlist nl) {
@@ -602,12 +610,8 @@ cudaError_t launch_chunk_plan(const int* atom_off, int B, int* chunk_start, cuda
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather_reduce(const EvalArgs& a, const int* atom_off, const int* chunk_start,
-                                 int max_chunks, double* partial, float* force, float* e_out,
-                                 cudaStream_t st) {
-    if (max_chunks > 0)
-        k_gather_reduce<<<max_chunks, kRedThreads, 0, st>>>(a, atom_off, chunk_start, partial, force,
-                                                            e_out);
+cudaError_t launch_chunk_reduce(const EvalArgs& a, const FinishArgs& f, int max_chunks, cudaStream_t st) {
+    if (max_chunks > 0) k_chunk_reduce<<<max_chunks, kRedThreads, 0, st>>>(a, f);
     return cudaGetLastError();
 }
 
@@ -620,7 +624,7 @@ cudaError_t launch_final_reduce(int B, const int* chunk_start, const double* par
 size_t nbr_cell_capacity(int N, int B) { return 2 * (size_t)N + 27 * (size_t)B; }
 
 cudaError_t launch_neighbors(const float* pos, const float4* pos4, const int* atom_off, const float* box,
-                             const int* cfg, int N, int B, float rc_list, float rc_list_ang,
+                             const int* cfg, int N, int B, float rc_list, float rc_list_ang, float rc_phys,
                              int min_image, nep_nlist* nl, const NbrWork& w, cudaStream_t st) {
     cudaError_t e;
     (void)min_image;
@@ -639,9 +643,9 @@ cudaError_t launch_neighbors(const float* pos, const float4* pos4, const int* at
     k_scan_add<<<blocks(n, 256), 256, 0, st>>>(w.cell_start, n, w.scan_tmp);
     k_fill<<<blocks(N, 256), 256, 0, st>>>(w.cell_of, w.rank, w.cell_start, N, w.cell_atoms);
     k_sort_cells<<<blocks(cmax, 128), 128, 0, st>>>(w.cell_start, cmax, w.cell_atoms);
-    const float rr = rc_list * rc_list, ra = rc_list_ang * rc_list_ang;
+    const float rr = rc_list * rc_list, ra = rc_list_ang * rc_list_ang, rp = rc_phys * rc_phys;
     k_build<<<blocks(N, 128), 128, 0, st>>>(pos4, cfg, box, w.plan, w.cell_of, w.cell_start,
-                                            w.cell_atoms, N, rr, ra, *nl);
+                                            w.cell_atoms, N, rr, ra, rp, w.shell, *nl);
     k_rev<<<blocks(N, 128), 128, 0, st>>>(N, *nl);
     return cudaGetLastError();
 }

@@ -191,7 +191,7 @@ NEP_HD void mlp2_atom(const TrainArgs& t, const float* sm, int i) {
         p2[d] = 0.0f;
     }
     for (int h = 0; h < H; ++h) {
-        const float* w = W0 + h * D;
+        const float* w = W0 + h * C::DW;
         float z = b0[h], u = 0.0f;
 #pragma unroll
         for (int d = 0; d < D; ++d) {
