@@ -126,8 +126,8 @@ def algorithmic_flops(h, nbar_rad: float, nbar_ang: float) -> dict:
 
 def launches_per_step(rebuild: bool) -> int:
     # kick, [pack, wrap, pack, cell plan, plan scan, bin, 3 scan, fill, sort, build, rev],
-    # pack, chunk plan, descriptor, force, gather, final reduce, kick
-    return 8 + (13 if rebuild else 0)
+    # pack, chunk plan, radial, angular, finish, chunk reduce, final reduce, kick
+    return 9 + (13 if rebuild else 0)
 
 
 # --------------------------------------------------------------- cpu legs

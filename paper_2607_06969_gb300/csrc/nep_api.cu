@@ -64,8 +64,8 @@ size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Byte offsets of the scratch arrays inside the caller's workspace.
 struct WsLayout {
-    size_t pos4, cfg, e_atom, fb, S, pang, Pr, comp, cnt_comp, fin, fpart, wat, chunk_start, partial;
-    size_t plan, cell_of, rank, cell_cnt, cell_start, cell_atoms, scan_tmp, shell, q16;
+    size_t pos4, cfg, e_atom, fb, S, Pr, comp, cnt_comp, fin, fpart, wat, chunk_start, partial;
+    size_t plan, cell_of, rank, cell_cnt, cell_start, cell_atoms, scan_tmp, shell;
     size_t total;
     int max_chunks, cmax;
 };
@@ -86,9 +86,7 @@ WsLayout ws_layout(const nep_model* m, int N, int B, int cap, int cap_ang) {
     w.e_atom = take(4 * n);
     w.fb = take(4 * n * T * KR);
     // S and the angular dE/dq leave the SM only in mixed precision and training
-    const bool split = m->hp.precision != 0;
     w.S = take(4 * n * NA * nep::kLM);
-    w.pang = split ? take(4 * n * NP) : 0;
     w.Pr = take(4 * n * T * KR);
     w.comp = take(16 * n * cap_ang);
     w.cnt_comp = take(4 * n);
@@ -108,8 +106,6 @@ WsLayout ws_layout(const nep_model* m, int N, int B, int cap, int cap_ang) {
     const size_t ntiles = ((size_t)w.cmax + 1 + 2047) / 2048;
     w.scan_tmp = take(4 * (ntiles + 1));
     w.shell = take(8 * n * (size_t)cap);
-    const int Kp = (m->lay.D + 15) / 16 * 16;
-    w.q16 = m->hp.precision ? take(2 * n * Kp) : 0;
     w.total = o;
     return w;
 }
@@ -242,7 +238,6 @@ nep::EvalArgs make_args(const nep_model* m, const nep_system* s, const nep_nlist
     a.e_atom = at<float>(work, w.e_atom);
     a.fb = at<float>(work, w.fb);
     a.S = m->hp.precision ? at<float>(work, w.S) : nullptr;
-    a.pang = m->hp.precision ? at<float>(work, w.pang) : nullptr;
     a.Pr = at<float>(work, w.Pr);
     a.comp = at<float4>(work, w.comp);
     a.cnt_comp = at<int>(work, w.cnt_comp);
@@ -255,7 +250,6 @@ nep::EvalArgs make_args(const nep_model* m, const nep_system* s, const nep_nlist
     a.q_out = nullptr;
     a.p_out = nullptr;
     a.fb_out = nullptr;
-    a.q16 = m->hp.precision ? at<void>(work, w.q16) : nullptr;
     a.q16_kind = m->hp.precision;
     return a;
 }
@@ -296,10 +290,6 @@ nep_status efv_impl(nep_model* m, const nep_system* s, const nep_nlist* nl, floa
     if (N > 0) NEP_CUDA(m->ks->radial(a, st), "radial kernel");
     NEP_CUDA(mark(1), "timing event");
     if (N > 0) NEP_CUDA(m->ks->angular(a, st, vd), "angular kernel");
-    if (N > 0 && a.q16) {
-        NEP_CUDA(m->ks->mlp_tc(a, st), "tensor-core network");
-        NEP_CUDA(m->ks->angforce(a, st, vf), "angular force kernel");
-    }
     NEP_CUDA(mark(2), "timing event");
     nep::FinishArgs f;
     f.atom_off = s->atom_off;
@@ -326,7 +316,6 @@ nep_status train_impl(nep_model* m, const nep_system* s, const nep_nlist* nl, co
              "pack");
     NEP_CUDA(nep::launch_chunk_plan(s->atom_off, B, at<int>(work, w.chunk_start), st), "chunk plan");
     nep::EvalArgs a = make_args(m, s, nl, work, w);
-    a.q16 = nullptr;
     a.q16_kind = 0;
     a.S = at<float>(work, w.S);
     a.compr = at<float4>(work, tl.compr);
@@ -682,36 +671,28 @@ nep_status nep_autotune(nep_model* m, const nep_system* sys, const nep_nlist* nl
     NEP_CUDA(cudaEventCreate(&e1), "event");
     float best_d = 1e30f, best_f = 1e30f;
     int vd = nep::kDefaultDescVariant, vf = nep::kDefaultForceVariant;
-    // pass 0 times the angular kernel variants; pass 1 (mixed precision only)
-    // the angular-force variants, after the tensor-core network
+    // time the angular kernel variants (the one register-heavy kernel)
     NEP_CUDA(m->ks->radial(a, st), "radial kernel");
-    const int passes = a.q16 ? 2 : 1;
-    for (int pass = 0; pass < passes && N > 0; ++pass) {
-        for (int v = 0; v < nep::kVariants; ++v) {
-            // one untimed launch, then the best of `reps` timed launches
-            float tmin = 1e30f;
-            for (int r = 0; r <= reps; ++r) {
-                cudaEventRecord(e0, st);
-                cudaError_t err = pass == 0 ? m->ks->angular(a, st, v) : m->ks->angforce(a, st, v);
-                cudaEventRecord(e1, st);
-                if (err == cudaSuccess) err = cudaEventSynchronize(e1);
-                if (err != cudaSuccess) {
-                    cudaEventDestroy(e0);
-                    cudaEventDestroy(e1);
-                    return cuda_fail(err, "autotune launch");
-                }
-                float ms = 0.0f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (r > 0 && ms < tmin) tmin = ms;
+    for (int v = 0; v < nep::kVariants && N > 0; ++v) {
+        // one untimed launch, then the best of `reps` timed launches
+        float tmin = 1e30f;
+        for (int r = 0; r <= reps; ++r) {
+            cudaEventRecord(e0, st);
+            cudaError_t err = m->ks->angular(a, st, v);
+            cudaEventRecord(e1, st);
+            if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+            if (err != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return cuda_fail(err, "autotune launch");
             }
-            if (pass == 0 && tmin < best_d) best_d = tmin, vd = v;
-            if (pass == 1 && tmin < best_f) best_f = tmin, vf = v;
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (r > 0 && ms < tmin) tmin = ms;
         }
-        if (pass == 0 && a.q16) {
-            NEP_CUDA(m->ks->angular(a, st, vd), "angular kernel");
-            NEP_CUDA(m->ks->mlp_tc(a, st), "tensor-core network");
-        }
+        if (tmin < best_d) best_d = tmin, vd = v;
     }
+    (void)best_f;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     const int b = size_bin(sys);

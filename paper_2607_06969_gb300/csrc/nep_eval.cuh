@@ -15,8 +15,8 @@
 //              species-projected adjoints, plus the scattered angular forces,
 //              give F_i (Eq. 3); per-atom virials (Eq. 4) and energies are
 //              summed in FP64 per chunk of atoms in a fixed order.
-// In mixed precision k_angular stops after q (written as 16-bit rows), the
-// tensor-core network runs, and k_angforce computes the angular forces.
+// In mixed precision k_angular_tc (nep_mlp_tc.cuh) takes k_angular's place
+// with the network on the tensor cores.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -466,29 +466,6 @@ NEP_HD void angular_atom(const EvalArgs& a, const float* sm, float* stage, int s
         float S[NA][kLM];
         angular_S<C>(a, sm, sl, ti, i, S);
         angular_q<C>(S, q);
-        if (a.q16) {
-            // mixed precision: S and 16-bit q for the tensor-core network
-#pragma unroll
-            for (int n = 0; n < NA; ++n)
-#pragma unroll
-                for (int m = 0; m < kLM; ++m) a.S[(n * kLM + m) * N + i] = S[n][m];
-            constexpr int Kp = (D + 15) / 16 * 16;
-            unsigned* row = reinterpret_cast<unsigned*>(a.q16) + (size_t)i * (Kp / 2);
-#pragma unroll
-            for (int d = 0; d < Kp; d += 2) {
-                const float x0 = d < D ? q[d] : 0.0f, x1 = d + 1 < D ? q[d + 1] : 0.0f;
-                unsigned bits;
-                if (a.q16_kind == 2) {
-                    __nv_bfloat162 v = __floats2bfloat162_rn(x0, x1);
-                    memcpy(&bits, &v, 4);
-                } else {
-                    __half2 v = __floats2half2_rn(x0, x1);
-                    memcpy(&bits, &v, 4);
-                }
-                row[d / 2] = bits;
-            }
-            return;
-        }
         if (a.S) {
 #pragma unroll
             for (int n = 0; n < NA; ++n)
@@ -513,28 +490,6 @@ NEP_HD void angular_atom(const EvalArgs& a, const float* sm, float* stage, int s
     float Sb[NA][kLM];
     make_Sb<C>(Sb, [&](int n, int m) { return stage[(n * kLM + m) * sstride]; },
                [&](int n, int l) { return p[NR + (l < 4 ? n * 4 + l : NA * 4 + n)]; });
-    float Fx = 0.0f, Fy = 0.0f, Fz = 0.0f;
-    float W[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) W[k] = 0.0f;
-    angular_force<C>(a, sm, sl, ti, i, Sb, Fx, Fy, Fz, W);
-    a.fpart[i] = Fx;
-    a.fpart[N + i] = Fy;
-    a.fpart[2 * N + i] = Fz;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) a.wat[k * N + i] = W[k];
-}
-
-// angular forces of the mixed-precision path (S and dE/dq from memory)
-template <class C>
-NEP_HD void angforce_atom(const EvalArgs& a, const float* sm, int i) {
-    constexpr int NA = C::NA;
-    const SmemLayout sl = smem_layout<C>(a.H);
-    const int N = a.N;
-    const int ti = f2i(a.pos4[i].w);
-    float Sb[NA][kLM];
-    make_Sb<C>(Sb, [&](int n, int m) { return a.S[(n * kLM + m) * N + i]; },
-               [&](int n, int l) { return a.pang[(l < 4 ? n * 4 + l : NA * 4 + n) * N + i]; });
     float Fx = 0.0f, Fy = 0.0f, Fz = 0.0f;
     float W[9];
 #pragma unroll
@@ -676,23 +631,40 @@ __global__ void __launch_bounds__(kRadialBlock) k_radial(const EvalArgs a) {
     if (i < a.N) radial_atom<C, MINIMG>(a, i);
 }
 
+// Persistent: one CTA per resident slot, the model image staged once, then a
+// grid-stride loop over tiles of 128 atoms.
 template <class C, int MINB>
 __global__ void __launch_bounds__(kBlock, MINB) k_angular(const EvalArgs a) {
     extern __shared__ float sm[];
     const SmemLayout sl = smem_layout<C>(a.H);
     load_model<C>(sm, a.params, a.H, threadIdx.x, blockDim.x);
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < a.N) angular_atom<C>(a, sm, sm + sl.total + threadIdx.x, kBlock, i);
+    const int ntiles = (a.N + kBlock - 1) / kBlock;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int i = tile * kBlock + threadIdx.x;
+        if (i < a.N) angular_atom<C>(a, sm, sm + sl.total + threadIdx.x, kBlock, i);
+    }
 }
 
-template <class C, int MINB>
-__global__ void __launch_bounds__(kBlock, MINB) k_angforce(const EvalArgs a) {
-    extern __shared__ float sm[];
-    load_model<C>(sm, a.params, a.H, threadIdx.x, blockDim.x);
-    __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < a.N) angforce_atom<C>(a, sm, i);
+// resident CTAs per SM of a kernel variant, measured once at model creation
+template <class C, int MINB, int KIND>
+int& resident_blocks() {
+    static int b = 1;
+    return b;
+}
+inline int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+inline int persistent_grid(int ntiles, int per_sm) {
+    const int g = sm_count() * (per_sm > 0 ? per_sm : 1);
+    return ntiles < g ? ntiles : g;
 }
 
 template <class C, bool MINIMG>
@@ -721,23 +693,15 @@ cudaError_t launch_radial_t(const EvalArgs& a, cudaStream_t st) {
 
 template <class C>
 cudaError_t launch_angular_t(const EvalArgs& a, cudaStream_t st, int v) {
-    const int grid = (a.N + kBlock - 1) / kBlock;
-    if (grid == 0) return cudaSuccess;
+    const int ntiles = (a.N + kBlock - 1) / kBlock;
+    if (ntiles == 0) return cudaSuccess;
     const size_t smem = angular_smem_bytes<C>(a.H);
-    if (v == 1) k_angular<C, 3><<<grid, kBlock, smem, st>>>(a);
-    else if (v == 2) k_angular<C, 4><<<grid, kBlock, smem, st>>>(a);
-    else k_angular<C, 2><<<grid, kBlock, smem, st>>>(a);
-    return cudaGetLastError();
-}
-
-template <class C>
-cudaError_t launch_angforce_t(const EvalArgs& a, cudaStream_t st, int v) {
-    const int grid = (a.N + kBlock - 1) / kBlock;
-    if (grid == 0) return cudaSuccess;
-    const size_t smem = smem_bytes_of<C>(a.H);
-    if (v == 1) k_angforce<C, 3><<<grid, kBlock, smem, st>>>(a);
-    else if (v == 2) k_angforce<C, 4><<<grid, kBlock, smem, st>>>(a);
-    else k_angforce<C, 2><<<grid, kBlock, smem, st>>>(a);
+    if (v == 1)
+        k_angular<C, 3><<<persistent_grid(ntiles, resident_blocks<C, 3, 0>()), kBlock, smem, st>>>(a);
+    else if (v == 2)
+        k_angular<C, 4><<<persistent_grid(ntiles, resident_blocks<C, 4, 0>()), kBlock, smem, st>>>(a);
+    else
+        k_angular<C, 2><<<persistent_grid(ntiles, resident_blocks<C, 2, 0>()), kBlock, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -755,12 +719,12 @@ cudaError_t launch_finish_t(const EvalArgs& a, const FinishArgs& f, int max_chun
 
 template <class C, int MINB>
 cudaError_t init_v(int H) {
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_angular<C, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)angular_smem_bytes<C>(H))))
-        return e;
-    return cudaFuncSetAttribute(k_angforce<C, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_bytes_of<C>(H));
+    const int smem = (int)angular_smem_bytes<C>(H);
+    cudaError_t e = cudaFuncSetAttribute(k_angular<C, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e) return e;
+    sm_count();
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident_blocks<C, MINB, 0>(), k_angular<C, MINB>,
+                                                         kBlock, smem);
 }
 
 template <class C>
@@ -776,10 +740,8 @@ cudaError_t init_t(int H) {
                                    &smem_bytes_of<Cfg<NR, NA, KR, KA, H4, T>>,                   \
                                    &init_t<Cfg<NR, NA, KR, KA, H4, T>>,                          \
                                    &launch_radial_t<Cfg<NR, NA, KR, KA, H4, T>>,                 \
-                                   &launch_angular_t<Cfg<NR, NA, KR, KA, H4, T>>,                \
-                                   &launch_angforce_t<Cfg<NR, NA, KR, KA, H4, T>>,               \
+                                   &launch_angular_any_t<Cfg<NR, NA, KR, KA, H4, T>>,            \
                                    &launch_finish_t<Cfg<NR, NA, KR, KA, H4, T>>,                 \
-                                   &launch_mlp_tc_t<Cfg<NR, NA, KR, KA, H4, T>>,                 \
                                    &train_init_t<Cfg<NR, NA, KR, KA, H4, T>>,                    \
                                    &train_t<Cfg<NR, NA, KR, KA, H4, T>>,                         \
                                    &grad_chunks_t<Cfg<NR, NA, KR, KA, H4, T>>};

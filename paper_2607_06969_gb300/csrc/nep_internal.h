@@ -20,7 +20,7 @@ constexpr int kChunk = 1024;     // atoms per reduction chunk (one CTA)
 constexpr int kBlock = 128;      // threads per block of the per-atom kernels
 constexpr int kVariants = 3;              // register budgets for 2, 3, 4 blocks per SM
 constexpr int kDefaultDescVariant = 0;    // fused angular kernel: 2 blocks per SM
-constexpr int kDefaultForceVariant = 0;   // angular force kernel (mixed precision): 2 blocks per SM
+constexpr int kDefaultForceVariant = 0;   // reserved
 constexpr int kSizeBins = 32;             // tuning table: log2 of mean atoms per configuration
 
 // Stencil/cell plan of one configuration for the neighbour build.
@@ -51,7 +51,6 @@ struct EvalArgs {
     float* e_atom;                 // [N]
     float* fb;                     // [T*KR][N]       species-resolved radial basis sums
     float* S;                      // [NA*24][N]      S_nlm (mixed precision and training only)
-    float* pang;                   // [NA*(4+H4)][N]  dE/dq of angular and 4-body entries (mixed)
     float* Pr;                     // [N][T][KR]      sum_n dE/dq_n cR[Zi][t][n][k]
     float4* comp;                  // [cap_ang][N]    compacted angular pairs
     int* cnt_comp;                 // [N]
@@ -61,9 +60,7 @@ struct EvalArgs {
     float* fpart;                  // [3][N]
     float* wat;                    // [9][N]          per-atom virial
     int* status;                   // [4] flags (may be null)
-    // mixed precision: the descriptor kernel stops after q and writes it as
-    // 16-bit rows q16[N][Kp] (1 = FP16, 2 = BF16); the network runs in k_mlp_tc
-    void* q16;
+    // network precision: 0 FP32 (CUDA cores), 1 FP16, 2 BF16 (tensor cores)
     int q16_kind;
     // training outputs of the descriptor kernel (null when not training)
     float* q_out;                  // [D][N]          descriptors
@@ -120,10 +117,8 @@ struct KernelSet {
     size_t (*smem_bytes)(int H);
     cudaError_t (*init)(int H);   // set kernel attributes (dynamic shared memory)
     cudaError_t (*radial)(const EvalArgs&, cudaStream_t);
-    cudaError_t (*angular)(const EvalArgs&, cudaStream_t, int variant);
-    cudaError_t (*angforce)(const EvalArgs&, cudaStream_t, int variant);
+    cudaError_t (*angular)(const EvalArgs&, cudaStream_t, int variant);   // FP32 or tensor-core network
     cudaError_t (*finish)(const EvalArgs&, const FinishArgs&, int max_chunks, cudaStream_t);
-    cudaError_t (*mlp_tc)(const EvalArgs&, cudaStream_t);   // tensor-core network (mixed precision)
     cudaError_t (*train_init)(int H);
     cudaError_t (*train)(const TrainArgs&, cudaStream_t);   // tangent ... gradient
     int (*grad_chunks)(int N);
