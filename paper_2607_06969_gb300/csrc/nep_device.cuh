@@ -86,6 +86,26 @@ NEP_HD float rint_f(float x) {
     return std::nearbyint(x);
 #endif
 }
+// eight consecutive floats from a 32-byte aligned global address that no
+// thread writes during the kernel: one 256-bit load on the device
+NEP_HD void load8_ro(const float* p, float* v) {
+#if defined(__CUDA_ARCH__)
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+        : "l"(p));
+#else
+    for (int k = 0; k < 8; ++k) v[k] = p[k];
+#endif
+}
+
+// index of the lowest set bit of a non-zero word
+NEP_HD int low_bit(unsigned long long m) {
+#if defined(__CUDA_ARCH__)
+    return __ffsll((long long)m) - 1;
+#else
+    return __builtin_ctzll(m);
+#endif
+}
 NEP_HD int f2i(float x) {
 #if defined(__CUDA_ARCH__)
     return __float_as_int(x);

@@ -122,6 +122,49 @@ NEP_HD AtomFrame atom_frame(const EvalArgs& a, int i) {
     return f;
 }
 
+// Walk over one atom's skin list with the gathers in flight ahead of use:
+// neighbour indices DEPTH + 1 slots ahead, their positions (and image
+// shifts) DEPTH slots ahead.  Every index read stays below cnt <= cap.
+template <bool MINIMG, int DEPTH>
+struct NbrStream {
+    int j[DEPTH + 1];    // slots s .. s + DEPTH
+    float4 p[DEPTH];     // slots s .. s + DEPTH - 1
+    int sh[DEPTH];
+    NEP_HD NbrStream(const EvalArgs& a, int i, int cnt) {
+        const int N = a.N;
+#pragma unroll
+        for (int d = 0; d <= DEPTH; ++d) j[d] = cnt > d ? a.nbr[d * N + i] : 0;
+#pragma unroll
+        for (int d = 0; d < DEPTH; ++d) {
+            p[d] = a.pos4[j[d]];
+            sh[d] = (!MINIMG && cnt > d) ? a.shift[d * N + i] : 0;
+        }
+    }
+    // move from slot s to slot s + 1
+    NEP_HD void advance(const EvalArgs& a, int i, int cnt, int s) {
+        const int N = a.N;
+#pragma unroll
+        for (int d = 0; d + 1 < DEPTH; ++d) {
+            p[d] = p[d + 1];
+            sh[d] = sh[d + 1];
+        }
+#pragma unroll
+        for (int d = 0; d < DEPTH; ++d) j[d] = j[d + 1];
+        if (s + DEPTH < cnt) {
+            p[DEPTH - 1] = a.pos4[j[DEPTH - 1]];
+            if (!MINIMG) sh[DEPTH - 1] = a.shift[(s + DEPTH) * N + i];
+        }
+        if (s + DEPTH + 1 < cnt) j[DEPTH] = a.nbr[(s + DEPTH + 1) * N + i];
+    }
+};
+
+#ifndef NEP_RADIAL_DEPTH
+#define NEP_RADIAL_DEPTH 2
+#endif
+#ifndef NEP_FINISH_DEPTH
+#define NEP_FINISH_DEPTH 1
+#endif
+
 // ---------------------------------------------------------------------------
 // radial descriptor sums and pair compaction, one atom
 // ---------------------------------------------------------------------------
@@ -140,21 +183,12 @@ NEP_HD void radial_atom(const EvalArgs& a, int i) {
         for (int k = 0; k < KR; ++k) fb[t][k] = 0.0f;
     const int cnt = a.cnt[i], cnt_ang = a.cnt_ang[i];
     int nc = 0, ncr = 0;
-    // software pipeline: neighbour index two slots ahead, its position one ahead
-    int j_nx = cnt > 0 ? a.nbr[i] : 0;
-    int j_nx2 = cnt > 1 ? a.nbr[N + i] : 0;
-    float4 p_nx = a.pos4[j_nx];
-    int sh_nx = (!MINIMG && cnt > 0) ? a.shift[i] : 0;
+    NbrStream<MINIMG, NEP_RADIAL_DEPTH> ns(a, i, cnt);
     for (int s = 0; s < cnt; ++s) {
-        const int j = j_nx;
-        const float4 pj = p_nx;
-        const int sh = sh_nx;
-        if (s + 1 < cnt) {
-            j_nx = j_nx2;
-            p_nx = a.pos4[j_nx];
-            if (!MINIMG) sh_nx = a.shift[(s + 1) * N + i];
-            if (s + 2 < cnt) j_nx2 = a.nbr[(s + 2) * N + i];
-        }
+        const int j = ns.j[0];
+        const float4 pj = ns.p[0];
+        const int sh = ns.sh[0];
+        ns.advance(a, i, cnt, s);
         float dx, dy, dz;
         pair_vector(fr.pi, pj, fr.Lx, fr.Ly, fr.Lz, fr.iLx, fr.iLy, fr.iLz, MINIMG, sh, dx, dy, dz);
         const float d2 = dist2(dx, dy, dz);
@@ -179,7 +213,9 @@ NEP_HD void radial_atom(const EvalArgs& a, int i) {
                 a.comp[nc * N + i] =
                     make_float4(dx, dy, dz, i2f((int)(((unsigned)addr << 2) | (unsigned)tj)));
                 ++nc;
-            } else {
+            } else if (a.compr) {
+                // the compacted-record force pass reads every angular slot;
+                // the list walk of k_finish reads only the slots inside rc_A
                 a.fin[addr] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             }
         }
@@ -516,10 +552,22 @@ NEP_HD void radial_force_atom(const EvalArgs& a, int i, float& Fx, float& Fy, fl
     const float rcR2 = a.rc_rad * a.rc_rad;
     const float irR = 1.0f / a.rc_rad;
     float Pi[T][KR];
+    if ((T * KR) % 4 == 0) {
+        const float4* src = reinterpret_cast<const float4*>(a.Pr + i * T * KR);
 #pragma unroll
-    for (int t = 0; t < T; ++t)
+        for (int x = 0; x < T * KR; x += 4) {
+            const float4 v = src[x / 4];
+            Pi[x / KR][x % KR] = v.x;
+            Pi[(x + 1) / KR][(x + 1) % KR] = v.y;
+            Pi[(x + 2) / KR][(x + 2) % KR] = v.z;
+            Pi[(x + 3) / KR][(x + 3) % KR] = v.w;
+        }
+    } else {
 #pragma unroll
-        for (int k = 0; k < KR; ++k) Pi[t][k] = a.Pr[(i * T + t) * KR + k];
+        for (int t = 0; t < T; ++t)
+#pragma unroll
+            for (int k = 0; k < KR; ++k) Pi[t][k] = a.Pr[(i * T + t) * KR + k];
+    }
     // one pair: both directions of the radial force along r_ij, and the
     // owner's symmetric radial virial
     auto pair = [&](int j, int tj, float dx, float dy, float dz, float d2) {
@@ -528,7 +576,11 @@ NEP_HD void radial_force_atom(const EvalArgs& a, int i, float& Fx, float& Fy, fl
         float f[KR], fp[KR];
         basis_d<KR>(r, irR, f, fp);
         float Pj[KR];
-        if (KR % 4 == 0) {
+        if (KR % 8 == 0) {
+            // rows of K_R floats start on 32-byte boundaries (256-byte aligned base)
+#pragma unroll
+            for (int k = 0; k < KR; k += 8) load8_ro(a.Pr + (j * T + ti) * KR + k, Pj + k);
+        } else if (KR % 4 == 0) {
             const float4* src = reinterpret_cast<const float4*>(a.Pr + (j * T + ti) * KR);
 #pragma unroll
             for (int k = 0; k < KR; k += 4) {
@@ -565,32 +617,62 @@ NEP_HD void radial_force_atom(const EvalArgs& a, int i, float& Fx, float& Fy, fl
             const int bits = f2i(e.w);
             pair((int)((unsigned)bits >> 2), bits & 3, e.x, e.y, e.z, dist2(e.x, e.y, e.z));
         }
+        // incoming angular pair forces: every slot of the angular prefix
+        const int na = a.cnt_ang[i];
+        for (int s = 0; s < na; ++s) {
+            const float4 g = a.fin[(size_t)s * N + i];
+            Fx -= g.x; Fy -= g.y; Fz -= g.z;
+        }
         return;
     }
-    const int cnt = a.cnt[i];
-    int j_nx = cnt > 0 ? a.nbr[i] : 0;
-    int j_nx2 = cnt > 1 ? a.nbr[N + i] : 0;
-    float4 p_nx = a.pos4[j_nx];
-    int sh_nx = (!MINIMG && cnt > 0) ? a.shift[i] : 0;
+    // list walk: radial pairs, and which angular-prefix slots lie inside
+    // rc_A.  The pair vector seen from j is the exact negation of the one
+    // seen from i, so j's angular kernel wrote the incoming force of slot s
+    // exactly when d2 < rc_A^2 here; only those slots are read.  Slots below
+    // 64 are marked in a bit mask and read afterwards in batches of four
+    // independent loads, ascending; any later slot is read in the walk.
+    const float rcA2 = a.rc_ang * a.rc_ang;
+    const int cnt = a.cnt[i], cnt_ang = a.cnt_ang[i];
+    unsigned long long amask = 0ull;
+    NbrStream<MINIMG, NEP_FINISH_DEPTH> ns(a, i, cnt);
     for (int s = 0; s < cnt; ++s) {
-        const int j = j_nx;
-        const float4 pj = p_nx;
-        const int sh = sh_nx;
-        if (s + 1 < cnt) {
-            j_nx = j_nx2;
-            p_nx = a.pos4[j_nx];
-            if (!MINIMG) sh_nx = a.shift[(s + 1) * N + i];
-            if (s + 2 < cnt) j_nx2 = a.nbr[(s + 2) * N + i];
-        }
+        const int j = ns.j[0];
+        const float4 pj = ns.p[0];
+        const int sh = ns.sh[0];
+        ns.advance(a, i, cnt, s);
         float dx, dy, dz;
         pair_vector(fr.pi, pj, fr.Lx, fr.Ly, fr.Lz, fr.iLx, fr.iLy, fr.iLz, MINIMG, sh, dx, dy, dz);
         const float d2 = dist2(dx, dy, dz);
+        if (s < cnt_ang && d2 < rcA2) {
+            if (s < 64) {
+                amask |= 1ull << s;
+            } else {
+                const float4 g = a.fin[(size_t)s * N + i];
+                Fx -= g.x; Fy -= g.y; Fz -= g.z;
+            }
+        }
         if (d2 < rcR2) pair(j, f2i(pj.w), dx, dy, dz, d2);
+    }
+    while (amask) {
+        int sl[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            sl[u] = amask ? low_bit(amask) : -1;
+            amask &= amask - 1ull;
+        }
+        float4 g[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            g[u] = sl[u] >= 0 ? a.fin[(size_t)sl[u] * N + i] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (sl[u] >= 0) { Fx -= g[u].x; Fy -= g[u].y; Fz -= g[u].z; }
+        }
     }
 }
 
 // F_i = radial part + angular owner part - sum of the scattered incoming
-// angular pair forces; the per-atom virial (angular owner part minus the
+// angular pair forces (subtracted inside radial_force_atom); the per-atom virial (angular owner part minus the
 // radial part) is written back for the FP64 reduction
 template <class C, bool MINIMG>
 NEP_HD void finish_atom(const EvalArgs& a, int i, float* force, float* e_out) {
@@ -598,11 +680,6 @@ NEP_HD void finish_atom(const EvalArgs& a, int i, float* force, float* e_out) {
     float Fx = a.fpart[i], Fy = a.fpart[N + i], Fz = a.fpart[2 * N + i];
     float Wr[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
     radial_force_atom<C, MINIMG>(a, i, Fx, Fy, Fz, Wr);
-    const int na = a.cnt_ang[i];
-    for (int s = 0; s < na; ++s) {
-        const float4 g = a.fin[(size_t)s * N + i];
-        Fx -= g.x; Fy -= g.y; Fz -= g.z;
-    }
     force[i] = Fx;
     force[N + i] = Fy;
     force[2 * N + i] = Fz;
@@ -625,8 +702,14 @@ NEP_HD constexpr int variant_minb(int v) { return v + 2; }
 constexpr int kRadialBlock = 256;
 constexpr int kFinishThreads = 128;
 
+#ifndef NEP_RADIAL_MINB
+#define NEP_RADIAL_MINB 3
+#endif
+#ifndef NEP_FINISH_MINB
+#define NEP_FINISH_MINB 6
+#endif
 template <class C, bool MINIMG>
-__global__ void __launch_bounds__(kRadialBlock) k_radial(const EvalArgs a) {
+__global__ void __launch_bounds__(kRadialBlock, NEP_RADIAL_MINB) k_radial(const EvalArgs a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < a.N) radial_atom<C, MINIMG>(a, i);
 }
@@ -668,7 +751,7 @@ inline int persistent_grid(int ntiles, int per_sm) {
 }
 
 template <class C, bool MINIMG>
-__global__ void __launch_bounds__(kFinishThreads) k_finish(const EvalArgs a, float* force, float* e_out) {
+__global__ void __launch_bounds__(kFinishThreads, NEP_FINISH_MINB) k_finish(const EvalArgs a, float* force, float* e_out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < a.N) finish_atom<C, MINIMG>(a, i, force, e_out);
 }

@@ -130,6 +130,17 @@ def test_efv_batch_small_boxes(nb, skin):
     assert_parity(gpu_eval(nb, h, th, s, skin=skin, cap=160, cap_ang=64), oracle_eval(h, th, s), s)
 
 
+def test_efv_more_than_64_angular_slots(nb):
+    # long angular cutoff: atoms with more than 64 angular-prefix slots, so the
+    # force gather takes both its bit-mask and its in-walk branch
+    h = I.Hyper(n_rad=3, n_ang=2, k_rad=4, k_ang=3, n_hidden=4, rc_rad=8.5, rc_ang=8.0)
+    s = I.packing_batch([150, 200], tag=77)
+    th = I.init_params(h).astype(np.float32)
+    g = gpu_eval(nb, h, th, s, skin=0.5, cap=260, cap_ang=200)
+    assert int(g["nl"].cnt_ang.max().item()) > 64
+    assert_parity(g, oracle_eval(h, th, s), s)
+
+
 def test_efv_degenerate_configs(nb):
     # an empty configuration, a single atom seeing only its own images, an
     # isolated atom (q = 0, E = network(0)) and a normal packing
