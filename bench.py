@@ -124,6 +124,15 @@ def algorithmic_flops(h, nbar_rad: float, nbar_ang: float) -> dict:
     return {"radial": radial, "angular": angular, "finish": finish}
 
 
+# DRAM bytes (read + write) per atom of each evaluation kernel, from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum) of the 460,800-atom
+# case of this workload (40^3 cells), divided by its atom count; traffic grows
+# in proportion to the atoms.  Valid only for the kernels as captured.
+TRAFFIC_PER_ATOM = {"radial": (223.585792e6 + 138.799872e6) / 460800,
+                    "angular": (295.563520e6 + 221.383936e6) / 460800,
+                    "finish": (423.724288e6 + 29.852416e6) / 460800}
+
+
 def launches_per_step(rebuild: bool) -> int:
     # kick, [pack, wrap, pack, cell plan, plan scan, bin, 3 scan, fill, sort, build, rev],
     # pack, chunk plan, radial, angular, finish, chunk reduce, final reduce, kick
@@ -506,7 +515,9 @@ def main():
     t_dom = t_kern[dom]
     achieved = fl[dom] * N / (t_dom * 1e-3) / 1e12
     roofline = {"bound": "alu", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": TRAFFIC_PER_ATOM[dom] * N,
+                "traffic_basis": "ncu dram bytes per atom of the 460,800-atom capture x atoms",
                 "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
                 "flops_per_atom": fl[dom], "nbar_rad": nbar_rad, "nbar_ang": nbar_ang,
                 "kernel_ms": t_kern,
