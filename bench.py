@@ -225,24 +225,24 @@ def run_md(args, nb, torch, dist, world, local, s, h, model, theta, vel0, masses
     torch.cuda.synchronize()
 
     # neighbour statistics inside the cutoffs (for the flop count), from the list
-    with torch.no_grad():
-        cnt = nl.cnt.long()
-        nbr = nl.nbr.view(cap, N).long()
-        valid = torch.arange(cap, device="cuda")[:, None] < cnt[None, :]
-        L = float(s.box[0, 0])
-        nrad = nang = 0.0
-        for a in range(0, N, 100000):
-            sl = slice(a, min(N, a + 100000))
-            d2 = torch.zeros_like(nbr[:, sl], dtype=torch.float32)
-            for c in range(3):
-                d = dsys.pos[c][nbr[:, sl]] - dsys.pos[c][sl][None, :]
-                d = d - L * torch.round(d / L)
-                d2 += d * d
-            v = valid[:, sl]
-            nrad += float(((d2 < h.rc_rad ** 2) & v).sum())
-            nang += float(((d2 < h.rc_ang ** 2) & v).sum())
-        nbar_rad, nbar_ang = nrad / N, nang / N
-        del nbr, valid
+    def neighbour_stats():
+        with torch.no_grad():
+            cnt = nl.cnt.long()
+            nbr = nl.nbr.view(cap, N).long()
+            valid = torch.arange(cap, device="cuda")[:, None] < cnt[None, :]
+            L = float(s.box[0, 0])
+            nrad = nang = 0.0
+            for a in range(0, N, 100000):
+                sl = slice(a, min(N, a + 100000))
+                d2 = torch.zeros_like(nbr[:, sl], dtype=torch.float32)
+                for c in range(3):
+                    d = dsys.pos[c][nbr[:, sl]] - dsys.pos[c][sl][None, :]
+                    d = d - L * torch.round(d / L)
+                    d2 += d * d
+                v = valid[:, sl]
+                nrad += float(((d2 < h.rc_rad ** 2) & v).sum())
+                nang += float(((d2 < h.rc_ang ** 2) & v).sum())
+            return nrad / N, nang / N
 
     vel = torch.from_numpy(np.ascontiguousarray(vel0.T)).cuda()
     stream = torch.cuda.Stream()
@@ -274,6 +274,8 @@ def run_md(args, nb, torch, dist, world, local, s, h, model, theta, vel0, masses
     g.replay()
     torch.cuda.synchronize()
     _raise_if_overflow(nb, nl, stream)
+    nbar_start = neighbour_stats()
+    torch.cuda.synchronize()
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local)
     if world > 1:
@@ -290,6 +292,12 @@ def run_md(args, nb, torch, dist, world, local, s, h, model, theta, vel0, masses
     clk = clocks.stop()
     ms = start.elapsed_time(stop)
     _raise_if_overflow(nb, nl, stream)
+    # the structure evolves during the run (neighbour counts grow as the
+    # lattice heats): the flop count takes the mean of the counts at the
+    # start and at the end of the timed steps
+    nbar_end = neighbour_stats()
+    nbar_rad = 0.5 * (nbar_start[0] + nbar_end[0])
+    nbar_ang = 0.5 * (nbar_start[1] + nbar_end[1])
     t_kern = {"radial": statistics.mean(e[0].elapsed_time(e[1]) for e in evs),
               "angular": statistics.mean(e[1].elapsed_time(e[2]) for e in evs),
               "finish": statistics.mean(e[2].elapsed_time(e[3]) for e in evs)}
@@ -299,8 +307,8 @@ def run_md(args, nb, torch, dist, world, local, s, h, model, theta, vel0, masses
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_max = float(t.item())
     del g
-    return (ms_max, K, t_kern, nbar_rad, nbar_ang, clk, dsys, nl, ws, e_atom, force, e_tot,
-            vir, stream, pos_host0)
+    return (ms_max, K, t_kern, (nbar_rad, nbar_start, nbar_end), nbar_ang, clk, dsys, nl, ws, e_atom,
+            force, e_tot, vir, stream, pos_host0)
 
 
 def train_leg(nb, torch, I, local) -> dict:
@@ -370,8 +378,19 @@ def mixed_leg(nb, torch, I) -> dict:
         t1.record()
         torch.cuda.synchronize()
         ms = t0.elapsed_time(t1) / K
+        # per-kernel split, from separate calls with timing events
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(3)]
+        for quad in evs:            # torch creates the underlying cudaEvent on first record
+            for e in quad:
+                e.record()
+        for quad in evs:
+            nb.set_timing_events(model, quad)
+            nb.energy_forces_virial(model, dsys, nl, ws, out=res)
+        torch.cuda.synchronize()
+        kms = {k: statistics.mean(q[c].elapsed_time(q[c + 1]) for q in evs)
+               for c, k in enumerate(("radial", "angular", "finish"))}
         e_atom, force, e_tot, vir = [x.clone() for x in res]
-        entry = {"ms_per_step": ms, "atom_steps_per_s": s.n_atoms / (ms * 1e-3)}
+        entry = {"ms_per_step": ms, "atom_steps_per_s": s.n_atoms / (ms * 1e-3), "kernel_ms": kms}
         if ref is None:
             ref = (e_atom, force, e_tot)
         else:
@@ -502,8 +521,8 @@ def main():
                 print(f"# list overflow, retrying with cap={cap} cap_ang={cap_ang}", file=sys.stderr)
     else:
         raise RuntimeError("neighbour list did not fit")
-    (ms_max, K, t_kern, nbar_rad, nbar_ang, clk, dsys, nl, ws, e_atom, force, e_tot, vir,
-     stream, pos_host0) = res
+    (ms_max, K, t_kern, (nbar_rad, nbar_start, nbar_end), nbar_ang, clk, dsys, nl, ws, e_atom, force,
+     e_tot, vir, stream, pos_host0) = res
     value = world * N * K / (ms_max * 1e-3)
 
     # roofline of the dominant kernel (FP32 CUDA-core bound)
@@ -520,6 +539,7 @@ def main():
                 "traffic_basis": "ncu dram bytes per atom of the 460,800-atom capture x atoms",
                 "peak_basis": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
                 "flops_per_atom": fl[dom], "nbar_rad": nbar_rad, "nbar_ang": nbar_ang,
+                "nbar_start": list(nbar_start), "nbar_end": list(nbar_end),
                 "kernel_ms": t_kern,
                 "kernel_tflops": {k: fl[k] * N / (t_kern[k] * 1e-3) / 1e12 for k in t_kern}}
 

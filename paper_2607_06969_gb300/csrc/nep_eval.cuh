@@ -18,10 +18,13 @@
 // In mixed precision k_angular_tc (nep_mlp_tc.cuh) takes k_angular's place
 // with the network on the tensor cores.
 #pragma once
+#include <algorithm>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include "nep_device.cuh"
+#include "nep_tmem.cuh"
 
 namespace nep {
 
@@ -538,6 +541,80 @@ NEP_HD void angular_atom(const EvalArgs& a, const float* sm, float* stage, int s
     for (int k = 0; k < 9; ++k) a.wat[k * N + i] = W[k];
 }
 
+// The same atom with S_nlm parked in the thread's TMEM lane (tS: column 0 of
+// the lane) while the network runs.  Every thread of the warp calls it (the
+// TMEM moves are warp-collective); `valid` guards the atom's own work.
+template <class C>
+__device__ void angular_atom_tm(const EvalArgs& a, const float* sm, uint32_t tS, int i, bool valid) {
+    constexpr int NR = C::NR, NA = C::NA, D = C::D;
+    const SmemLayout sl = smem_layout<C>(a.H);
+    const int N = a.N;
+    const int ti = valid ? f2i(a.pos4[i].w) : 0;
+    float q[D];
+    {
+        float S[NA][kLM];
+        if (valid) {
+            radial_q<C>(a, sm, sl, ti, i, q);
+            angular_S<C>(a, sm, sl, ti, i, S);
+        } else {
+#pragma unroll
+            for (int d = 0; d < D; ++d) q[d] = 0.0f;
+#pragma unroll
+            for (int n = 0; n < NA; ++n)
+#pragma unroll
+                for (int m = 0; m < kLM; ++m) S[n][m] = 0.0f;
+        }
+        angular_q<C>(S, q);
+        if (valid && a.S) {
+#pragma unroll
+            for (int n = 0; n < NA; ++n)
+#pragma unroll
+                for (int m = 0; m < kLM; ++m) a.S[(n * kLM + m) * N + i] = S[n][m];
+        }
+        __syncwarp();
+        const float* Sf = &S[0][0];
+#pragma unroll
+        for (int c = 0; c < NA * kLM; c += 8) tc5::st8(tS + c, Sf + c);
+    }
+    float p[D];
+    if (valid) {
+        network<C>(a, sm, sl, ti, i, q, p);
+        if (a.q_out) {
+#pragma unroll
+            for (int d = 0; d < D; ++d) a.q_out[d * N + i] = q[d];
+        }
+        if (a.p_out) {
+#pragma unroll
+            for (int d = 0; d < D; ++d) a.p_out[d * N + i] = p[d];
+        }
+    } else {
+#pragma unroll
+        for (int d = 0; d < D; ++d) p[d] = 0.0f;
+    }
+    float Sb[NA][kLM];
+    __syncwarp();
+    tc5::wait_st();
+    {
+        float* Sf = &Sb[0][0];
+#pragma unroll
+        for (int c = 0; c < NA * kLM; c += 8) tc5::ld8(tS + c, Sf + c);
+        tc5::wait_ld();
+    }
+    if (!valid) return;
+    make_Sb<C>(Sb, [&](int n, int m) { return Sb[n][m]; },
+               [&](int n, int l) { return p[NR + (l < 4 ? n * 4 + l : NA * 4 + n)]; });
+    float Fx = 0.0f, Fy = 0.0f, Fz = 0.0f;
+    float W[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) W[k] = 0.0f;
+    angular_force<C>(a, sm, sl, ti, i, Sb, Fx, Fy, Fz, W);
+    a.fpart[i] = Fx;
+    a.fpart[N + i] = Fy;
+    a.fpart[2 * N + i] = Fz;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) a.wat[k * N + i] = W[k];
+}
+
 // ---------------------------------------------------------------------------
 // radial pair forces of both directions: dE_i/dr_ij + dE_j/dr_ij along rhat,
 // from P of atom i (neighbour species row) and P of atom j (row Zi); returns
@@ -716,16 +793,42 @@ __global__ void __launch_bounds__(kRadialBlock, NEP_RADIAL_MINB) k_radial(const 
 
 // Persistent: one CTA per resident slot, the model image staged once, then a
 // grid-stride loop over tiles of 128 atoms.
+// The 255-register variant (MINB 2) parks S_nlm in tensor memory, NA x 24
+// columns per CTA; the others stage it in shared memory.
+template <int MINB>
+NEP_HD constexpr bool angular_uses_tmem() { return MINB == 2; }
+template <class C>
+NEP_HD constexpr uint32_t angular_tmem_cols() { return tc5::tmem_cols(C::NA * kLM); }
+
 template <class C, int MINB>
 __global__ void __launch_bounds__(kBlock, MINB) k_angular(const EvalArgs a) {
     extern __shared__ float sm[];
     const SmemLayout sl = smem_layout<C>(a.H);
     load_model<C>(sm, a.params, a.H, threadIdx.x, blockDim.x);
-    __syncthreads();
     const int ntiles = (a.N + kBlock - 1) / kBlock;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int i = tile * kBlock + threadIdx.x;
-        if (i < a.N) angular_atom<C>(a, sm, sm + sl.total + threadIdx.x, kBlock, i);
+    if constexpr (angular_uses_tmem<MINB>()) {
+        __shared__ uint32_t tslot;
+        const int warp = threadIdx.x >> 5;
+        if (warp == 0) tc5::alloc(&tslot, angular_tmem_cols<C>());
+        tc5::fence_before();
+        __syncthreads();
+        tc5::fence_after();
+        const uint32_t tbase = tslot;
+        const uint32_t tS = tc5::lane_addr(tbase, warp, 0);
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            const int i = tile * kBlock + threadIdx.x;
+            angular_atom_tm<C>(a, sm, tS, i, i < a.N);
+        }
+        tc5::fence_before();
+        __syncthreads();
+        tc5::fence_after();
+        if (warp == 0) tc5::dealloc(tbase, angular_tmem_cols<C>());
+    } else {
+        __syncthreads();
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            const int i = tile * kBlock + threadIdx.x;
+            if (i < a.N) angular_atom<C>(a, sm, sm + sl.total + threadIdx.x, kBlock, i);
+        }
     }
 }
 
@@ -745,6 +848,32 @@ inline int sm_count() {
     }
     return n;
 }
+// Resident CTAs per SM of a kernel from its registers (allocated per warp
+// in units of 256), shared memory and threads.  The runtime's occupancy
+// query reports one CTA per SM for every kernel that allocates tensor
+// memory, whatever its resources, so those kernels count here and cap the
+// result by their share of the SM's 512 TMEM columns.
+inline int resident_by_resources(const void* fn, int threads, size_t dyn_smem, int tmem_cols_per_cta) {
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) return 1;
+    int dev = 0, regs_sm = 0, smem_sm = 0, thr_sm = 0, blk_sm = 0, smem_rsv = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+    cudaDeviceGetAttribute(&blk_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    const int warps = (threads + 31) / 32;
+    const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;
+    int n = blk_sm;
+    if (regs_warp > 0) n = std::min(n, regs_sm / regs_warp / warps);
+    const size_t smem_blk = fa.sharedSizeBytes + dyn_smem + (size_t)smem_rsv;
+    if (smem_blk > 0) n = std::min(n, (int)((size_t)smem_sm / smem_blk));
+    n = std::min(n, thr_sm / threads);
+    if (tmem_cols_per_cta > 0) n = std::min(n, 512 / tmem_cols_per_cta);
+    return n < 1 ? 1 : n;
+}
+
 inline int persistent_grid(int ntiles, int per_sm) {
     const int g = sm_count() * (per_sm > 0 ? per_sm : 1);
     return ntiles < g ? ntiles : g;
@@ -759,8 +888,8 @@ __global__ void __launch_bounds__(kFinishThreads, NEP_FINISH_MINB) k_finish(cons
 template <class C>
 size_t smem_bytes_of(int H) { return sizeof(float) * (size_t)smem_layout<C>(H).total; }
 template <class C>
-size_t angular_smem_bytes(int H) {
-    return sizeof(float) * ((size_t)smem_layout<C>(H).total + (size_t)C::NA * kLM * kBlock);
+size_t angular_smem_bytes(int H, bool tmem_stage) {
+    return sizeof(float) * ((size_t)smem_layout<C>(H).total + (tmem_stage ? 0 : (size_t)C::NA * kLM * kBlock));
 }
 
 template <class C>
@@ -774,17 +903,22 @@ cudaError_t launch_radial_t(const EvalArgs& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+template <class C, int MINB>
+void launch_angular_v(const EvalArgs& a, cudaStream_t st, int ntiles) {
+    const size_t smem = angular_smem_bytes<C>(a.H, angular_uses_tmem<MINB>());
+    k_angular<C, MINB><<<persistent_grid(ntiles, resident_blocks<C, MINB, 0>()), kBlock, smem, st>>>(a);
+}
+
 template <class C>
 cudaError_t launch_angular_t(const EvalArgs& a, cudaStream_t st, int v) {
     const int ntiles = (a.N + kBlock - 1) / kBlock;
     if (ntiles == 0) return cudaSuccess;
-    const size_t smem = angular_smem_bytes<C>(a.H);
     if (v == 1)
-        k_angular<C, 3><<<persistent_grid(ntiles, resident_blocks<C, 3, 0>()), kBlock, smem, st>>>(a);
+        launch_angular_v<C, 3>(a, st, ntiles);
     else if (v == 2)
-        k_angular<C, 4><<<persistent_grid(ntiles, resident_blocks<C, 4, 0>()), kBlock, smem, st>>>(a);
+        launch_angular_v<C, 4>(a, st, ntiles);
     else
-        k_angular<C, 2><<<persistent_grid(ntiles, resident_blocks<C, 2, 0>()), kBlock, smem, st>>>(a);
+        launch_angular_v<C, 2>(a, st, ntiles);
     return cudaGetLastError();
 }
 
@@ -800,14 +934,21 @@ cudaError_t launch_finish_t(const EvalArgs& a, const FinishArgs& f, int max_chun
     return launch_chunk_reduce(a, f, max_chunks, st);
 }
 
+// resident CTAs per SM of one angular variant; a variant that parks S in
+// tensor memory also fits its allocation into the SM's 512 columns, so that
+// no CTA of the persistent grid waits for another one's columns
 template <class C, int MINB>
 cudaError_t init_v(int H) {
-    const int smem = (int)angular_smem_bytes<C>(H);
+    const int smem = (int)angular_smem_bytes<C>(H, angular_uses_tmem<MINB>());
     cudaError_t e = cudaFuncSetAttribute(k_angular<C, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e) return e;
     sm_count();
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident_blocks<C, MINB, 0>(), k_angular<C, MINB>,
-                                                         kBlock, smem);
+    int& rb = resident_blocks<C, MINB, 0>();
+    if (angular_uses_tmem<MINB>()) {
+        rb = resident_by_resources((const void*)k_angular<C, MINB>, kBlock, smem, (int)angular_tmem_cols<C>());
+        return cudaGetLastError();
+    }
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rb, k_angular<C, MINB>, kBlock, smem);
 }
 
 template <class C>
