@@ -54,8 +54,9 @@ typedef enum {
  * n_hidden     : hidden tanh units of the per-species network (N_neurons)
  * rc_rad/ang   : cutoffs r_max (Eqs. 13-15), rc_ang <= rc_rad
  * precision    : 0 = FP32 everywhere; 1 = MLP forward and dU/dq in FP16 on
- *                tensor cores with FP32 accumulation (descriptors FP32);
- *                2 = same with BF16.
+ *                tensor cores (tcgen05, FP32 accumulation in tensor
+ *                memory; descriptors FP32); 2 = same with BF16.  Precisions
+ *                1 and 2 need n_hidden <= 64 (else NEP_ERR_UNSUPPORTED).
  * Descriptor dimension D = n_rad + n_ang*l_max + n_ang*has_4body, ordered
  * [q_0..q_{nR-1}, q_{n,l} (n outer, l = 1..l_max inner), q4_0..q4_{nA-1}]. */
 typedef struct {
@@ -127,7 +128,8 @@ typedef struct {
  *   rev   [cap_ang][N]   slot of i in j's angular prefix, for pair (i, s)
  *   cnt, cnt_ang [N]
  *   status [4] int: [0] overflow flag, [1] radial count needed,
- *                   [2] angular count needed, [3] invalid-input flag
+ *                   [2] angular count needed, [3] bit 0: invalid input,
+ *                   bit 1: a tensor-core completion wait gave up
  * nep_neighbors fills every array and the host fields skin and min_image.
  * If a count exceeds cap (cap_ang) the list is truncated, status[0] is set
  * and status[1..2] hold the capacity needed; nep_check returns
@@ -234,16 +236,21 @@ nep_status nep_md_step(nep_model* m, const nep_system* sys, nep_nlist* nl, float
                        float dt, float skin, int rebuild, void* work, size_t work_bytes,
                        void* stream);
 
-/* Autotuner: times every compiled variant of the descriptor and force
- * kernels (register budgets for 2, 3 or 4 resident blocks of 128 threads per
- * SM) on this system and list, `reps` timed launches each after one untimed
- * launch, and stores the fastest pair in the model for the system's size
+/* Autotuner: times every compiled register-budget variant of the angular
+ * kernel (the register-heavy one: 2, 3 or 4 resident blocks of 128 threads
+ * per SM) on this system and list, `reps` timed launches each after one
+ * untimed launch, and stores the fastest in the model for the system's size
  * class (log2 of the mean atom count per configuration).  Later hot calls on
  * systems of that class use it.  Not a hot call: it synchronises `stream`.
- * chosen[2] (may be NULL) receives the descriptor and force variant indices
- * (0, 1, 2 = 2, 3, 4 blocks per SM); the defaults are 1 and 0. */
+ * chosen[2] (may be NULL) receives the angular variant index (0, 1, 2 = 2,
+ * 3, 4 blocks per SM) and 0 (reserved).  Untuned classes use variant 0. */
 nep_status nep_autotune(nep_model* m, const nep_system* sys, const nep_nlist* nl, void* work,
                         size_t work_bytes, void* stream, int reps, int* chosen);
+
+/* Pin the angular kernel variant (0, 1, 2 = 2, 3, 4 resident blocks per SM;
+ * -1 = back to the default) for one size class (0..31, as in nep_autotune)
+ * or for all of them (size_class = -1).  Host only, no device work. */
+nep_status nep_set_variant(nep_model* m, int size_class, int variant);
 
 /* Profiling hook: the next nep_energy_forces_virial / nep_md_step call of
  * this model records events[0] before the radial-descriptor kernel,
@@ -255,7 +262,8 @@ nep_status nep_autotune(nep_model* m, const nep_system* sys, const nep_nlist* nl
 nep_status nep_set_timing_events(nep_model* m, void* const* events, int n);
 
 /* Synchronise `stream` and map the list's device flags to a status:
- * NEP_ERR_CAPACITY (status[0]), NEP_ERR_INPUT (status[3]) or NEP_OK.
+ * NEP_ERR_CAPACITY (status[0]), NEP_ERR_TIMEOUT (status[3] bit 1),
+ * NEP_ERR_INPUT (status[3] bit 0) or NEP_OK.
  * nl may be NULL (then only the stream is synchronised). */
 nep_status nep_check(const nep_nlist* nl, void* stream);
 

@@ -22,7 +22,8 @@ ENTRY_POINTS = (
     "nep_num_params", "nep_create", "nep_destroy", "nep_supported", "nep_set_params",
     "nep_workspace_bytes", "nep_train_workspace_bytes", "nep_neighbors", "nep_energy_forces_virial",
     "nep_energy_forces_virial_noalloc", "nep_param_grad",
-    "nep_param_grad_adjoint", "nep_md_step", "nep_autotune", "nep_set_timing_events", "nep_check",
+    "nep_param_grad_adjoint", "nep_md_step", "nep_autotune", "nep_set_variant", "nep_set_timing_events",
+    "nep_check",
     "nep_last_error", "nep_version",
 )
 
@@ -84,6 +85,8 @@ def lib() -> ctypes.CDLL:
     L.nep_set_timing_events.argtypes = [vp, P(vp), i]
     L.nep_autotune.argtypes = [vp, P(System), P(NList), vp, sz, vp, i, P(ctypes.c_int)]
     L.nep_autotune.restype = i
+    L.nep_set_variant.argtypes = [vp, i, i]
+    L.nep_set_variant.restype = i
     L.nep_last_error.restype = ctypes.c_char_p
     L.nep_version.restype = ctypes.c_char_p
     for name in ("nep_create", "nep_destroy", "nep_set_params", "nep_neighbors",
@@ -336,12 +339,18 @@ def set_timing_events(model: Model, events) -> None:
 
 def autotune(model: Model, dsys: DeviceSystem, nl: NeighborList, ws: Workspace, reps: int = 3,
              stream=None):
-    """nep_autotune: pick the descriptor/force kernel variants for this system's
-    size class; returns the chosen (descriptor, force) variant indices."""
+    """nep_autotune: pick the angular kernel variant for this system's size
+    class; returns (chosen variant, 0)."""
     chosen = (ctypes.c_int * 2)()
     check(lib().nep_autotune(model.handle, ctypes.byref(dsys.c), ctypes.byref(nl.c), ws.ptr, ws.bytes,
                              _stream(stream), int(reps), chosen), "nep_autotune")
     return int(chosen[0]), int(chosen[1])
+
+
+def set_variant(model: Model, variant: int, size_class: int = -1) -> None:
+    """nep_set_variant: pin the angular kernel variant (-1 = default) for one
+    size class or all of them."""
+    check(lib().nep_set_variant(model.handle, int(size_class), int(variant)), "nep_set_variant")
 
 
 def check_list(nl: NeighborList | None, stream=None) -> int:

@@ -431,6 +431,7 @@ size_t nep_num_params(const nep_hparams* hp) {
 
 int nep_supported(const nep_hparams* hp) {
     if (!hp_valid(hp)) return 0;
+    if (hp->precision != 0 && hp->n_hidden > nep::kTcMaxHidden) return 0;
     return nep::find_kernel_set(hp->n_rad, hp->n_ang, hp->k_rad, hp->k_ang, hp->has_4body,
                                 hp->n_types) != nullptr;
 }
@@ -446,6 +447,8 @@ nep_status nep_create(const nep_hparams* hp, const float* params_host, size_t n_
         return fail(NEP_ERR_UNSUPPORTED,
                     "no kernel compiled for n_rad=%d n_ang=%d k_rad=%d k_ang=%d 4body=%d types=%d",
                     hp->n_rad, hp->n_ang, hp->k_rad, hp->k_ang, hp->has_4body, hp->n_types);
+    if (hp->precision != 0 && hp->n_hidden > nep::kTcMaxHidden)
+        return fail(NEP_ERR_UNSUPPORTED, "the FP16/BF16 network supports n_hidden <= %d", nep::kTcMaxHidden);
     const size_t P = nep_num_params(hp);
     if (n_params != P) return fail(NEP_ERR_ARG, "expected %zu parameters, got %zu", P, n_params);
     if (!params_host) return fail(NEP_ERR_ARG, "params_host is NULL");
@@ -649,6 +652,17 @@ nep_status nep_param_grad_adjoint(nep_model* m, const nep_system* sys, const nep
     if ((s = check_train_work(m, sys, nl, work, work_bytes, &tl)) != NEP_OK) return s;
     return train_impl(m, sys, nl, nullptr, nullptr, nullptr, nullptr, 0, a_e, lam, mu, grad, nullptr,
                       work, tl, (cudaStream_t)stream);
+}
+
+nep_status nep_set_variant(nep_model* m, int size_class, int variant) {
+    if (!m) return fail(NEP_ERR_ARG, "model is NULL");
+    if (size_class < -1 || size_class >= nep::kSizeBins)
+        return fail(NEP_ERR_ARG, "size_class must be -1 or 0..%d", nep::kSizeBins - 1);
+    if (variant < -1 || variant >= nep::kVariants)
+        return fail(NEP_ERR_ARG, "variant must be -1 or 0..%d", nep::kVariants - 1);
+    for (int b = 0; b < nep::kSizeBins; ++b)
+        if (size_class < 0 || b == size_class) m->tune_desc[b] = variant;
+    return NEP_OK;
 }
 
 nep_status nep_autotune(nep_model* m, const nep_system* sys, const nep_nlist* nl, void* work,

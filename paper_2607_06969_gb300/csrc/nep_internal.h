@@ -14,6 +14,8 @@
 
 namespace nep {
 
+// largest hidden width of the FP16/BF16 tensor-core network
+constexpr int kTcMaxHidden = 64;
 constexpr int kMaxTypes = 4;
 constexpr int kLM = 24;          // real solid harmonics for l = 1..4: 3+5+7+9
 constexpr int kChunk = 1024;     // atoms per reduction chunk (one CTA)

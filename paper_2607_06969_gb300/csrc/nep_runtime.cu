@@ -11,7 +11,7 @@ namespace nep {
 namespace {
 
 __device__ __forceinline__ void set_flag(int* status, int k) {
-    if (status) atomicExch(status + k, 1);
+    if (status) atomicOr(status + k, 1);
 }
 
 // binary search: largest b with off[b] <= x, for off[0..B]

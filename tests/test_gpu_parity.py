@@ -219,6 +219,25 @@ def test_host_argument_errors(nb):
         nb.neighbors(model, dsys, bad, 0.0, ws)
 
 
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_every_angular_variant(nb, variant):
+    """Each register-budget variant of the angular kernel (S_nlm in tensor
+    memory for variant 0, in shared memory for 1 and 2) against the oracle."""
+    h = I.HYPER_SMALL
+    s = I.packing_batch([57, 100, 250], tag=68)
+    th = I.init_params(h).astype(np.float32)
+    model = nb.Model(h, th)
+    nb.set_variant(model, variant)
+    dsys = nb.DeviceSystem.from_inputs(s)
+    nl = nb.NeighborList(s.n_atoms, 160, 64)
+    ws = nb.Workspace(model, s.n_atoms, s.n_cfg, 160, 64)
+    nb.neighbors(model, dsys, nl, 1.0, ws)
+    e, f, et, v = nb.energy_forces_virial(model, dsys, nl, ws)
+    assert_parity(dict(E=e.cpu().numpy(), F=f.cpu().numpy().T, Etot=et.cpu().numpy(),
+                       V=v.cpu().numpy().reshape(-1, 3, 3), status=nb.check_list(nl)),
+                  oracle_eval(h, th, s), s)
+
+
 def test_autotune_variants_agree(nb):
     """Every compiled register-budget variant computes the same E, F, V; the
     autotuner picks valid indices and later calls use them."""
