@@ -9,8 +9,9 @@ rebuild every 10 steps with a 1 A skin.  One bench step = one MD step
 (kick, drift, [rebuild], energy+forces+virial, kick), all in libnep kernels.
 
 value: atom-steps/s over all ranks (device-timed, inputs resident in HBM).
-e2e:   the same metric through the C ABI from pinned host buffers: positions
-       copied in, E/F/V copied out every step.
+e2e:   the same metric through the C ABI with the MD state in pinned host
+       buffers: positions and velocities copied in, nep_md_step, positions,
+       velocities, forces, energy and virial copied out, every step.
 """
 from __future__ import annotations
 
@@ -128,9 +129,9 @@ def algorithmic_flops(h, nbar_rad: float, nbar_ang: float) -> dict:
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the 460,800-atom
 # case of this workload (40^3 cells), divided by its atom count; traffic grows
 # in proportion to the atoms.  Valid only for the kernels as captured.
-TRAFFIC_PER_ATOM = {"radial": (223.585792e6 + 138.799872e6) / 460800,
-                    "angular": (295.563520e6 + 221.383936e6) / 460800,
-                    "finish": (423.724288e6 + 29.852416e6) / 460800}
+TRAFFIC_PER_ATOM = {"radial": (223.652096e6 + 139.176960e6) / 460800,
+                    "angular": (293.204992e6 + 218.010880e6) / 460800,
+                    "finish": (423.694080e6 + 29.356800e6) / 460800}
 
 
 def launches_per_step(rebuild: bool) -> int:
@@ -216,7 +217,6 @@ def _raise_if_overflow(nb, nl, stream=None):
 def run_md(args, nb, torch, dist, world, local, s, h, model, theta, vel0, masses, cap, cap_ang):
     N = s.n_atoms
     dsys = nb.DeviceSystem.from_inputs(s)
-    pos_host0 = np.ascontiguousarray(s.pos32().T)
     nl = nb.NeighborList(N, cap, cap_ang, shifts=False)
     ws = nb.Workspace(model, N, 1, cap, cap_ang)
     nb.neighbors(model, dsys, nl, SKIN, ws)
@@ -308,7 +308,7 @@ def run_md(args, nb, torch, dist, world, local, s, h, model, theta, vel0, masses
         ms_max = float(t.item())
     del g
     return (ms_max, K, t_kern, (nbar_rad, nbar_start, nbar_end), nbar_ang, clk, dsys, nl, ws, e_atom,
-            force, e_tot, vir, stream, pos_host0)
+            force, e_tot, vir, stream, vel)
 
 
 def train_leg(nb, torch, I, local) -> dict:
@@ -480,7 +480,7 @@ def replicas_leg(nb, torch, I, K: int = 20) -> dict:
             "ms_per_step": ms, "steps": K,
             "per_replica_loop": {"ms_per_step": ms_loop, "replica_steps_per_s": B / (ms_loop * 1e-3),
                                  "steps": KL},
-            "speedup_vs_loop": ms_loop / ms, "autotuned_variants": {"desc": chosen[0], "force": chosen[1]}}
+            "speedup_vs_loop": ms_loop / ms, "autotuned_angular_variant": chosen[0]}
 
 
 # ------------------------------------------------------------------ our arm
@@ -522,7 +522,7 @@ def main():
     else:
         raise RuntimeError("neighbour list did not fit")
     (ms_max, K, t_kern, (nbar_rad, nbar_start, nbar_end), nbar_ang, clk, dsys, nl, ws, e_atom, force,
-     e_tot, vir, stream, pos_host0) = res
+     e_tot, vir, stream, vel) = res
     value = world * N * K / (ms_max * 1e-3)
 
     # roofline of the dominant kernel (FP32 CUDA-core bound)
@@ -543,26 +543,34 @@ def main():
                 "kernel_ms": t_kern,
                 "kernel_tflops": {k: fl[k] * N / (t_kern[k] * 1e-3) / 1e12 for k in t_kern}}
 
-    # end to end through the C ABI from pinned host buffers
+    # end to end through the C ABI from pinned host buffers: the MD state
+    # (positions, velocities) lives on the host and continues from the end of
+    # the timed run; every step copies it in, runs nep_md_step, and copies
+    # positions, velocities, forces, energy and virial back out
     KE = max(1, min(args.e2e_steps, K))
-    pos_host = torch.from_numpy(pos_host0).pin_memory()
-    f_host = torch.empty(3, N, dtype=torch.float32).pin_memory()
-    e_host = torch.empty(1, dtype=torch.float64).pin_memory()
-    v_host = torch.empty(1, 9, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    pos_h = dsys.pos.cpu().pin_memory()
+    vel_h = vel.cpu().pin_memory()
+    f_h = torch.empty(3, N, dtype=torch.float32).pin_memory()
+    e_h = torch.empty(1, dtype=torch.float64).pin_memory()
+    v_h = torch.empty(1, 9, dtype=torch.float64).pin_memory()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
         e0.record(stream)
         for k in range(KE):
-            dsys.pos.copy_(pos_host, non_blocking=True)
-            if k % REBUILD == 0:
-                nb.neighbors(model, dsys, nl, SKIN, ws, stream=stream)
-            nb.energy_forces_virial(model, dsys, nl, ws, out=(e_atom, force, e_tot, vir), stream=stream)
-            f_host.copy_(force, non_blocking=True)
-            e_host.copy_(e_tot, non_blocking=True)
-            v_host.copy_(vir, non_blocking=True)
+            dsys.pos.copy_(pos_h, non_blocking=True)
+            vel.copy_(vel_h, non_blocking=True)
+            nb.md_step(model, dsys, nl, vel, force, e_tot, vir, masses, DT, SKIN, k % REBUILD == 0, ws,
+                       stream=stream)
+            pos_h.copy_(dsys.pos, non_blocking=True)
+            vel_h.copy_(vel, non_blocking=True)
+            f_h.copy_(force, non_blocking=True)
+            e_h.copy_(e_tot, non_blocking=True)
+            v_h.copy_(vir, non_blocking=True)
         e1.record(stream)
     torch.cuda.synchronize()
+    _raise_if_overflow(nb, nl, stream)
     e2e_ms = e0.elapsed_time(e1)
     e2e_val = world * N * KE / (e2e_ms * 1e-3)
 
@@ -585,7 +593,7 @@ def main():
                            "graph": "K steps captured in one CUDA graph"},
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_val, "unit": "atom-steps/s", "steps": KE,
-                        "h2d_bytes_per_step": 12 * N, "d2h_bytes_per_step": 12 * N + 8 + 72},
+                        "h2d_bytes_per_step": 24 * N, "d2h_bytes_per_step": 36 * N + 8 + 72},
                 "gpu_launches": launches, "clocks": clk, "train": train, "mixed": mixed, "replicas": replicas,
                 "energy": {"e_tot_final": float(e_tot.item())}}
         print(json.dumps(line), flush=True)
