@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-train", action="store_true", help="skip the training-step leg")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision leg")
     ap.add_argument("--no-replicas", action="store_true", help="skip the batched-replica leg")
+    ap.add_argument("--no-table2", action="store_true", help="skip the paper-model size sweep")
     ap.add_argument("--ncell", type=int, default=50,
                     help="rock-salt cells per edge (50 = the 900k-atom workload; smaller for profiling)")
     return ap.parse_args()
@@ -483,6 +484,70 @@ def replicas_leg(nb, torch, I, K: int = 20) -> dict:
             "speedup_vs_loop": ms_loop / ms, "autotuned_angular_variant": chosen[0]}
 
 
+def md_graph_ms(nb, torch, I, s, model, K: int, cap: int = 160, cap_ang: int = 80) -> float:
+    """ms per velocity-Verlet step (dt 2 fs, 900 K start, rebuild every 10
+    steps, skin 1 A) of one system, K steps captured in one CUDA graph."""
+    masses = I.MASSES.astype(np.float32)
+    N = s.n_atoms
+    for _ in range(3):
+        dsys = nb.DeviceSystem.from_inputs(s)
+        nl = nb.NeighborList(N, cap, cap_ang, shifts=False)
+        ws = nb.Workspace(model, N, s.n_cfg, cap, cap_ang)
+        nb.neighbors(model, dsys, nl, SKIN, ws)
+        e_atom, force, e_tot, vir = nb.energy_forces_virial(model, dsys, nl, ws)
+        vel = torch.from_numpy(np.ascontiguousarray(
+            I.maxwell_boltzmann(s.types, 900.0, atom_off=s.atom_off).astype(np.float32).T)).cuda()
+        stream = torch.cuda.Stream()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            for k in range(3):
+                nb.md_step(model, dsys, nl, vel, force, e_tot, vir, masses, DT, SKIN, k == 0, ws, stream=stream)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            for k in range(K):
+                nb.md_step(model, dsys, nl, vel, force, e_tot, vir, masses, DT, SKIN, k % REBUILD == 0, ws,
+                           stream=stream)
+        g.replay()
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            t0.record(stream)
+            g.replay()
+            t1.record(stream)
+        torch.cuda.synchronize()
+        st = nb.check_list(nl, stream)
+        del g
+        if st == nb.NEP_OK:
+            return t0.elapsed_time(t1) / K
+        cap, cap_ang = cap + 32, cap_ang + 16
+    raise RuntimeError("neighbour list did not fit: " + nb.last_error())
+
+
+# the paper's NEP throughput on one RTX 4090 D in LAMMPS, FP32 (Fig. 11 text)
+PAPER_NEP_KATOM_STEPS = {"189 atoms": 15.3, "55,566 atoms": 807.9, "3.4M atoms (peak)": 923.5}
+
+
+def table2_leg(nb, torch, I) -> dict:
+    """The paper's own NEP variant (2+3-body, n_R=10, n_A=8, K=8, l_max=4,
+    50 hidden units; Table 2) in MD on rock-salt Ge-Sb-Te of 194 to 3.42M
+    atoms (the size range of its Fig. 11), FP32, one graph-captured step per
+    MD step."""
+    h = I.HYPER_TABLE2
+    model = nb.Model(h, I.init_params(h).astype(np.float32))
+    rows = []
+    for ncell, K in ((3, 2000), (10, 1000), (20, 500), (40, 100), (78, 30)):
+        s = I.rocksalt(ncell, vacancy=0.2, tag=1)
+        ms = md_graph_ms(nb, torch, I, s, model, K)
+        rows.append({"n_atoms": s.n_atoms, "ms_per_step": ms, "katom_steps_per_s": s.n_atoms / ms,
+                     "steps": K})
+        del s
+        torch.cuda.empty_cache()
+    return {"workload": "table2: paper's NEP (n_R=10 n_A=8 K=8 l_max=4, no 4-body, D=42, MLP 42-50-1), "
+                        "rock-salt GST 3^3..78^3 cells, 900 K velocity Verlet, FP32",
+            "sizes": rows,
+            "paper_rtx4090d_katom_steps_per_s": PAPER_NEP_KATOM_STEPS}
+
+
 # ------------------------------------------------------------------ our arm
 def main():
     args = parse()
@@ -577,6 +642,7 @@ def main():
     train = None if args.no_train else train_leg(nb, torch, I, local)
     mixed = None if args.no_mixed else mixed_leg(nb, torch, I)
     replicas = None if args.no_replicas else replicas_leg(nb, torch, I)
+    table2 = None if args.no_table2 else table2_leg(nb, torch, I)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -595,6 +661,7 @@ def main():
                 "e2e": {"value": e2e_val, "unit": "atom-steps/s", "steps": KE,
                         "h2d_bytes_per_step": 24 * N, "d2h_bytes_per_step": 36 * N + 8 + 72},
                 "gpu_launches": launches, "clocks": clk, "train": train, "mixed": mixed, "replicas": replicas,
+                "table2": table2,
                 "energy": {"e_tot_final": float(e_tot.item())}}
         print(json.dumps(line), flush=True)
     if world > 1:
