@@ -65,6 +65,7 @@ size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 // Byte offsets of the scratch arrays inside the caller's workspace.
 struct WsLayout {
     size_t pos4, cfg, e_atom, fb, S, Pr, comp, cnt_comp, fin, fpart, wat, chunk_start, partial;
+    size_t rin, rin_sh, cnt_rin;
     size_t plan, cell_of, rank, cell_cnt, cell_start, cell_atoms, scan_tmp, shell;
     size_t total;
     int max_chunks, cmax;
@@ -91,6 +92,9 @@ WsLayout ws_layout(const nep_model* m, int N, int B, int cap, int cap_ang) {
     w.comp = take(16 * n * cap_ang);
     w.cnt_comp = take(4 * n);
     w.fin = take(16 * n * cap_ang);
+    w.rin = take(4 * n * cap);
+    w.rin_sh = take(4 * n * cap);
+    w.cnt_rin = take(4 * n);
     w.fpart = take(12 * n);
     w.wat = take(36 * n);
     w.chunk_start = take(4 * ((size_t)B + 1));
@@ -244,6 +248,12 @@ nep::EvalArgs make_args(const nep_model* m, const nep_system* s, const nep_nlist
     a.compr = nullptr;
     a.cnt_compr = nullptr;
     a.fin = at<float4>(work, w.fin);
+    // the compact list of post-prefix entries inside rc_rad pays off only
+    // when the list carries a shell beyond rc_rad (a skin)
+    const bool use_rin = nl->skin > 0.0f;
+    a.rin = use_rin ? at<int>(work, w.rin) : nullptr;
+    a.rin_sh = use_rin && nl->shift ? at<int>(work, w.rin_sh) : nullptr;
+    a.cnt_rin = use_rin ? at<int>(work, w.cnt_rin) : nullptr;
     a.fpart = at<float>(work, w.fpart);
     a.wat = at<float>(work, w.wat);
     a.status = nl->status;

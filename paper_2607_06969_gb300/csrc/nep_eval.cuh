@@ -125,25 +125,28 @@ NEP_HD AtomFrame atom_frame(const EvalArgs& a, int i) {
     return f;
 }
 
-// Walk over one atom's skin list with the gathers in flight ahead of use:
-// neighbour indices DEPTH + 1 slots ahead, their positions (and image
-// shifts) DEPTH slots ahead.  Every index read stays below cnt <= cap.
+// Walk over one atom's neighbour entries (slot-major arrays nb / sh, entry
+// s of atom i at s * N + i) with the gathers in flight ahead of use:
+// neighbour indices DEPTH + 1 entries ahead, their positions (and image
+// shifts) DEPTH entries ahead.  Every index read stays below cnt.
 template <bool MINIMG, int DEPTH>
 struct NbrStream {
-    int j[DEPTH + 1];    // slots s .. s + DEPTH
-    float4 p[DEPTH];     // slots s .. s + DEPTH - 1
+    int j[DEPTH + 1];    // entries s .. s + DEPTH
+    float4 p[DEPTH];     // entries s .. s + DEPTH - 1
     int sh[DEPTH];
-    NEP_HD NbrStream(const EvalArgs& a, int i, int cnt) {
+    const int* nb;
+    const int* shp;
+    NEP_HD NbrStream(const EvalArgs& a, const int* nb_, const int* sh_, int i, int cnt) : nb(nb_), shp(sh_) {
         const int N = a.N;
 #pragma unroll
-        for (int d = 0; d <= DEPTH; ++d) j[d] = cnt > d ? a.nbr[d * N + i] : 0;
+        for (int d = 0; d <= DEPTH; ++d) j[d] = cnt > d ? nb[d * N + i] : 0;
 #pragma unroll
         for (int d = 0; d < DEPTH; ++d) {
             p[d] = a.pos4[j[d]];
-            sh[d] = (!MINIMG && cnt > d) ? a.shift[d * N + i] : 0;
+            sh[d] = (!MINIMG && cnt > d) ? shp[d * N + i] : 0;
         }
     }
-    // move from slot s to slot s + 1
+    // move from entry s to entry s + 1
     NEP_HD void advance(const EvalArgs& a, int i, int cnt, int s) {
         const int N = a.N;
 #pragma unroll
@@ -155,9 +158,9 @@ struct NbrStream {
         for (int d = 0; d < DEPTH; ++d) j[d] = j[d + 1];
         if (s + DEPTH < cnt) {
             p[DEPTH - 1] = a.pos4[j[DEPTH - 1]];
-            if (!MINIMG) sh[DEPTH - 1] = a.shift[(s + DEPTH) * N + i];
+            if (!MINIMG) sh[DEPTH - 1] = shp[(s + DEPTH) * N + i];
         }
-        if (s + DEPTH + 1 < cnt) j[DEPTH] = a.nbr[(s + DEPTH + 1) * N + i];
+        if (s + DEPTH + 1 < cnt) j[DEPTH] = nb[(s + DEPTH + 1) * N + i];
     }
 };
 
@@ -185,8 +188,8 @@ NEP_HD void radial_atom(const EvalArgs& a, int i) {
 #pragma unroll
         for (int k = 0; k < KR; ++k) fb[t][k] = 0.0f;
     const int cnt = a.cnt[i], cnt_ang = a.cnt_ang[i];
-    int nc = 0, ncr = 0;
-    NbrStream<MINIMG, NEP_RADIAL_DEPTH> ns(a, i, cnt);
+    int nc = 0, ncr = 0, nr = 0;
+    NbrStream<MINIMG, NEP_RADIAL_DEPTH> ns(a, a.nbr, a.shift, i, cnt);
     for (int s = 0; s < cnt; ++s) {
         const int j = ns.j[0];
         const float4 pj = ns.p[0];
@@ -200,6 +203,11 @@ NEP_HD void radial_atom(const EvalArgs& a, int i) {
             if (a.compr) {
                 a.compr[ncr * N + i] = make_float4(dx, dy, dz, i2f((int)(((unsigned)j << 2) | (unsigned)tj)));
                 ++ncr;
+            }
+            if (s >= cnt_ang && a.rin) {
+                a.rin[nr * N + i] = j;
+                if (!MINIMG) a.rin_sh[nr * N + i] = sh;
+                ++nr;
             }
             float f[KR];
             basis<KR>(sqrt_f(d2), irR, f);
@@ -225,6 +233,7 @@ NEP_HD void radial_atom(const EvalArgs& a, int i) {
     }
     a.cnt_comp[i] = nc;
     if (a.compr) a.cnt_compr[i] = ncr;
+    if (a.rin) a.cnt_rin[i] = nr;
 #pragma unroll
     for (int t = 0; t < T; ++t)
 #pragma unroll
@@ -702,33 +711,55 @@ NEP_HD void radial_force_atom(const EvalArgs& a, int i, float& Fx, float& Fy, fl
         }
         return;
     }
-    // list walk: radial pairs, and which angular-prefix slots lie inside
-    // rc_A.  The pair vector seen from j is the exact negation of the one
-    // seen from i, so j's angular kernel wrote the incoming force of slot s
-    // exactly when d2 < rc_A^2 here; only those slots are read.  Slots below
-    // 64 are marked in a bit mask and read afterwards in batches of four
-    // independent loads, ascending; any later slot is read in the walk.
+    // Walk 1, the angular prefix: radial pairs, and which prefix slots lie
+    // inside rc_A.  The pair vector seen from j is the exact negation of the
+    // one seen from i, so j's angular kernel wrote the incoming force of slot
+    // s exactly when d2 < rc_A^2 here; only those slots are read.  Slots
+    // below 64 are marked in a bit mask and read afterwards in batches of
+    // four independent loads, ascending; any later slot is read in the walk.
+    // Walk 2: the entries after the prefix that the radial kernel found
+    // inside rc_rad (the shell beyond rc_rad is not visited again), or with
+    // no skin simply the rest of the list.
     const float rcA2 = a.rc_ang * a.rc_ang;
-    const int cnt = a.cnt[i], cnt_ang = a.cnt_ang[i];
+    const int cnt_ang = a.cnt_ang[i];
     unsigned long long amask = 0ull;
-    NbrStream<MINIMG, NEP_FINISH_DEPTH> ns(a, i, cnt);
-    for (int s = 0; s < cnt; ++s) {
-        const int j = ns.j[0];
-        const float4 pj = ns.p[0];
-        const int sh = ns.sh[0];
-        ns.advance(a, i, cnt, s);
-        float dx, dy, dz;
-        pair_vector(fr.pi, pj, fr.Lx, fr.Ly, fr.Lz, fr.iLx, fr.iLy, fr.iLz, MINIMG, sh, dx, dy, dz);
-        const float d2 = dist2(dx, dy, dz);
-        if (s < cnt_ang && d2 < rcA2) {
-            if (s < 64) {
-                amask |= 1ull << s;
-            } else {
-                const float4 g = a.fin[(size_t)s * N + i];
-                Fx -= g.x; Fy -= g.y; Fz -= g.z;
+    {
+        NbrStream<MINIMG, NEP_FINISH_DEPTH> ns(a, a.nbr, a.shift, i, cnt_ang);
+        for (int s = 0; s < cnt_ang; ++s) {
+            const int j = ns.j[0];
+            const float4 pj = ns.p[0];
+            const int sh = ns.sh[0];
+            ns.advance(a, i, cnt_ang, s);
+            float dx, dy, dz;
+            pair_vector(fr.pi, pj, fr.Lx, fr.Ly, fr.Lz, fr.iLx, fr.iLy, fr.iLz, MINIMG, sh, dx, dy, dz);
+            const float d2 = dist2(dx, dy, dz);
+            if (d2 < rcA2) {
+                if (s < 64) {
+                    amask |= 1ull << s;
+                } else {
+                    const float4 g = a.fin[(size_t)s * N + i];
+                    Fx -= g.x; Fy -= g.y; Fz -= g.z;
+                }
             }
+            if (d2 < rcR2) pair(j, f2i(pj.w), dx, dy, dz, d2);
         }
-        if (d2 < rcR2) pair(j, f2i(pj.w), dx, dy, dz, d2);
+    }
+    {
+        // without a skin the rest of the list is the set inside rc_rad itself
+        const int* nb2 = a.rin ? a.rin : a.nbr + (size_t)cnt_ang * N;
+        const int* sh2 = a.rin ? a.rin_sh : (a.shift ? a.shift + (size_t)cnt_ang * N : nullptr);
+        const int nr = a.rin ? a.cnt_rin[i] : a.cnt[i] - cnt_ang;
+        NbrStream<MINIMG, NEP_FINISH_DEPTH> ns(a, nb2, sh2, i, nr);
+        for (int s = 0; s < nr; ++s) {
+            const int j = ns.j[0];
+            const float4 pj = ns.p[0];
+            const int sh = ns.sh[0];
+            ns.advance(a, i, nr, s);
+            float dx, dy, dz;
+            pair_vector(fr.pi, pj, fr.Lx, fr.Ly, fr.Lz, fr.iLx, fr.iLy, fr.iLz, MINIMG, sh, dx, dy, dz);
+            const float d2 = dist2(dx, dy, dz);
+            if (d2 < rcR2) pair(j, f2i(pj.w), dx, dy, dz, d2);
+        }
     }
     while (amask) {
         int sl[4];

@@ -58,6 +58,9 @@ struct EvalArgs {
     int* cnt_comp;                 // [N]
     float4* compr;                 // [cap][N]        compacted radial pairs (r_ij, j|tj), training only
     int* cnt_compr;                // [N]
+    int* rin;                      // [cap][N]        list entries after the angular prefix that lie
+    int* rin_sh;                   // [cap][N]        inside rc_rad (j; image shift or null), in
+    int* cnt_rin;                  // [N]             list order, written by the radial kernel
     float4* fin;                   // [cap_ang][N]    incoming angular pair forces
     float* fpart;                  // [3][N]
     float* wat;                    // [9][N]          per-atom virial
