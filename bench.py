@@ -313,9 +313,12 @@ def run_md(args, nb, torch, dist, world, local, s, h, model, theta, vel0, masses
 
 
 def train_leg(nb, torch, I, local) -> dict:
-    """Secondary leg: one batched loss+gradient step (nep_param_grad) on the
-    128-configuration training batch (N ~ U{24..512}); labels from a teacher
-    NEP evaluated by the same library (seed 2 weights)."""
+    """Secondary leg: batched training steps on the 128-configuration batch
+    (N ~ U{24..512}); labels from a teacher NEP evaluated by the same library
+    (seed 2 weights).  One step = loss and gradient (nep_param_grad) plus the
+    Adam update of all parameters (nep_adam_step).  Then a short fit with the
+    paper's protocol (warm-up + cosine learning rate, dynamic loss weights)."""
+    from paper_2607_06969_gb300 import train as T
     s, h = I.workload_train128()
     th = I.init_params(h).astype(np.float32)
     teacher = nb.Model(h, I.init_params(h, seed=I.SEED_TEACHER).astype(np.float32))
@@ -328,23 +331,40 @@ def train_leg(nb, torch, I, local) -> dict:
     if nb.check_list(nl) != nb.NEP_OK:
         raise RuntimeError(nb.last_error())
     _, F, E, V = nb.energy_forces_virial(teacher, dsys, nl, ws)
+    F = F.contiguous()
     grad = torch.empty(model.n_params, dtype=torch.float32, device="cuda")
     loss = torch.empty(1, dtype=torch.float64, device="cuda")
+    m1 = torch.zeros_like(grad)
+    m2 = torch.zeros_like(grad)
+    t = 0
     for _ in range(3):
-        nb.param_grad(model, dsys, nl, ws, E, F.contiguous(), V, (1.0, 1.0, 0.1), 0, grad, loss)
+        nb.param_grad(model, dsys, nl, ws, E, F, V, (1.0, 1.0, 0.1), 0, grad, loss)
+        t += 1
+        nb.adam_step(model, grad, m1, m2, t, 1e-4)
     torch.cuda.synchronize()
     K = 20
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0.record()
     for _ in range(K):
-        nb.param_grad(model, dsys, nl, ws, E, F.contiguous(), V, (1.0, 1.0, 0.1), 0, grad, loss)
+        nb.param_grad(model, dsys, nl, ws, E, F, V, (1.0, 1.0, 0.1), 0, grad, loss)
+        t += 1
+        nb.adam_step(model, grad, m1, m2, t, 1e-4)
     t1.record()
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1) / K
+
+    # fit from the initial student weights with the training protocol
+    student = nb.Model(h, th)
+    batch = T.Batch(dsys, nl, ws, E, F, V)
+    cfg = T.TrainConfig(lr_start=3e-3, lr_end=3e-5, epochs=300)
+    tr = T.Trainer(student, [batch], cfg)
+    losses = [tr.step(batch) for _ in range(cfg.epochs)]
     return {"workload": "train128: 128 random packings, N ~ U{24..512} (%d atoms), loss+grad of %d "
-                        "parameters, FP32" % (s.n_atoms, model.n_params),
-            "configs_per_s": s.n_cfg / (ms * 1e-3), "ms_per_step": ms, "loss": float(loss.item()),
-            "steps": K}
+                        "parameters and an Adam step, FP32" % (s.n_atoms, model.n_params),
+            "configs_per_s": s.n_cfg / (ms * 1e-3), "ms_per_step": ms, "steps": K,
+            "fit": {"steps": cfg.epochs, "lr_start": cfg.lr_start, "lr_end": cfg.lr_end,
+                    "loss_first": losses[0], "loss_last": losses[-1],
+                    "loss_at": {str(k): losses[k] for k in (0, 10, 30, 100, 299)}}}
 
 
 def mixed_leg(nb, torch, I) -> dict:

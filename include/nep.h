@@ -94,6 +94,10 @@ int nep_supported(const nep_hparams* hp);
  * (for optimiser steps that stay on the device). */
 nep_status nep_set_params(nep_model* m, const float* params_dev, void* stream);
 
+/* Copy the current parameters (P floats) into a DEVICE buffer, stream-ordered
+ * (checkpoints of a training run that updates them with nep_adam_step). */
+nep_status nep_get_params(const nep_model* m, float* params_dev, void* stream);
+
 /* A batch of B periodic orthorhombic configurations with atoms concatenated.
  * pos    [3][N] float, each atom of config b inside [0, box[b][a]) for
  *        nep_neighbors (nep_energy_forces_virial accepts atoms that drifted
@@ -223,6 +227,17 @@ nep_status nep_param_grad(nep_model* m, const nep_system* sys, const nep_nlist* 
 nep_status nep_param_grad_adjoint(nep_model* m, const nep_system* sys, const nep_nlist* nl,
                                   const double* a_e, const float* lam, const double* mu,
                                   float* grad, void* work, size_t work_bytes, void* stream);
+
+/* One Adam step on the model's own parameters (the optimiser of the
+ * training protocol, Section 3.3.1; Kingma and Ba's update with PyTorch's
+ * arrangement of the bias corrections):
+ *   m = beta1 m + (1 - beta1) g,   v = beta2 v + (1 - beta2) g^2,
+ *   theta -= lr / (1 - beta1^t) * m / (sqrt(v) / sqrt(1 - beta2^t) + eps)
+ * grad [P] float (e.g. from nep_param_grad), m1 [P] and m2 [P] float are the
+ * caller's moment buffers (zero before step t = 1), t >= 1 the step number.
+ * No weight decay.  A hot call: one kernel on `stream`, no allocation. */
+nep_status nep_adam_step(nep_model* m, const float* grad, float* m1, float* m2, int t, float lr,
+                         float beta1, float beta2, float eps, void* stream);
 
 /* One velocity-Verlet step (dt in fs, masses_host[n_types] in u):
  *   v += dt/2 F/m; x += dt v; [wrap + rebuild list if rebuild != 0];

@@ -25,6 +25,9 @@ What it computes, in the paper's order and notation (AI2Pot, Section 2):
 * Eqs. 18-21  loss (mode 1), and the per-atom-normalised batch loss (mode 0):
           L = 1/B sum_b [wE (dE_b/N_b)^2 + wF/(3 N_b) sum |dF|^2
                          + wV/9 sum (dV_b/N_b)^2].
+* Section 3.3.1  the optimiser: Adam with beta1 = 0.9, beta2 = 0.999,
+          eps = 1e-8 and no weight decay (Kingma and Ba's update with bias
+          corrections).
 
 Readings where the paper is silent: n runs 0..n_max-1 and l runs 1..l_max
 (no l = 0); k runs 0..N_basis-1; c is indexed by the ordered species pair;
@@ -455,3 +458,20 @@ def complex_step_grad(fun, theta, indices, h_step=1e-30):
         th[k] += 1j * h_step
         g[a] = np.imag(fun(th)) / h_step
     return g
+
+
+# ---------------------------------------------------------------------------
+# optimiser (Section 3.3.1)
+# ---------------------------------------------------------------------------
+def adam_step(theta, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam step (Section 3.3.1, no weight decay), in FP64: the moving
+    averages m and v of g and g^2, their bias-corrected values m/(1-beta1^t)
+    and v/(1-beta2^t), and the step lr * mhat / (sqrt(vhat) + eps).
+    Returns (theta, m, v) after step t (t = 1 for the first step)."""
+    theta = np.asarray(theta, np.float64)
+    g = np.asarray(g, np.float64)
+    m = beta1 * np.asarray(m, np.float64) + (1.0 - beta1) * g
+    v = beta2 * np.asarray(v, np.float64) + (1.0 - beta2) * g * g
+    mhat = m / (1.0 - beta1 ** t)
+    vhat = v / (1.0 - beta2 ** t)
+    return theta - lr * mhat / (np.sqrt(vhat) + eps), m, v

@@ -19,10 +19,11 @@ NEP_OK, NEP_ERR_ARG, NEP_ERR_CUDA, NEP_ERR_NOMEM, NEP_ERR_CAPACITY, NEP_ERR_TIME
 
 # names of every entry point declared in include/nep.h
 ENTRY_POINTS = (
-    "nep_num_params", "nep_create", "nep_destroy", "nep_supported", "nep_set_params",
+    "nep_num_params", "nep_create", "nep_destroy", "nep_supported", "nep_set_params", "nep_get_params",
     "nep_workspace_bytes", "nep_train_workspace_bytes", "nep_neighbors", "nep_energy_forces_virial",
     "nep_energy_forces_virial_noalloc", "nep_param_grad",
-    "nep_param_grad_adjoint", "nep_md_step", "nep_autotune", "nep_set_variant", "nep_set_timing_events",
+    "nep_param_grad_adjoint", "nep_adam_step", "nep_md_step", "nep_autotune", "nep_set_variant",
+    "nep_set_timing_events",
     "nep_check",
     "nep_last_error", "nep_version",
 )
@@ -71,6 +72,8 @@ def lib() -> ctypes.CDLL:
     L.nep_create.argtypes = [P(Hparams), vp, sz, P(vp)]
     L.nep_destroy.argtypes = [vp]
     L.nep_set_params.argtypes = [vp, vp, vp]
+    L.nep_get_params.argtypes = [vp, vp, vp]
+    L.nep_adam_step.argtypes = [vp, vp, vp, vp, i, f, f, f, f, vp]
     L.nep_workspace_bytes.argtypes = [vp, i, i, i, i]
     L.nep_workspace_bytes.restype = sz
     L.nep_train_workspace_bytes.argtypes = [vp, i, i, i, i]
@@ -89,7 +92,8 @@ def lib() -> ctypes.CDLL:
     L.nep_set_variant.restype = i
     L.nep_last_error.restype = ctypes.c_char_p
     L.nep_version.restype = ctypes.c_char_p
-    for name in ("nep_create", "nep_destroy", "nep_set_params", "nep_neighbors",
+    for name in ("nep_create", "nep_destroy", "nep_set_params", "nep_get_params", "nep_adam_step",
+                 "nep_neighbors",
                  "nep_energy_forces_virial", "nep_energy_forces_virial_noalloc",
                  "nep_param_grad", "nep_param_grad_adjoint",
                  "nep_md_step", "nep_check", "nep_set_timing_events"):
@@ -145,6 +149,14 @@ class Model:
     def set_params(self, params_dev, stream=None):
         assert params_dev.is_cuda and params_dev.dtype.is_floating_point
         check(lib().nep_set_params(self.handle, _ptr(params_dev), _stream(stream)), "nep_set_params")
+
+    def get_params(self, out=None, stream=None):
+        """nep_get_params: the current parameters as a device tensor [P] f32."""
+        import torch
+        if out is None:
+            out = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
+        check(lib().nep_get_params(self.handle, _ptr(out), _stream(stream)), "nep_get_params")
+        return out
 
     def close(self):
         if getattr(self, "handle", None):
@@ -291,6 +303,14 @@ def param_grad_adjoint(model: Model, dsys: DeviceSystem, nl: NeighborList, ws: W
                                        _ptr(a_e), _ptr(lam), _ptr(mu), _ptr(grad), ws.ptr, ws.bytes,
                                        _stream(stream)), "nep_param_grad_adjoint")
     return grad
+
+
+def adam_step(model: Model, grad, m1, m2, t: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+              eps: float = 1e-8, stream=None) -> None:
+    """nep_adam_step: one Adam update of the model's parameters in place.
+    grad, m1, m2: device tensors [P] f32 (m1, m2 zero before t = 1)."""
+    check(lib().nep_adam_step(model.handle, _ptr(grad), _ptr(m1), _ptr(m2), int(t), float(lr), float(beta1),
+                              float(beta2), float(eps), _stream(stream)), "nep_adam_step")
 
 
 NOALLOC_SCRATCH_BYTES = 32 << 20

@@ -501,6 +501,15 @@ nep_status nep_destroy(nep_model* m) {
     return NEP_OK;
 }
 
+nep_status nep_get_params(const nep_model* m, float* params_dev, void* stream) {
+    if (!m) return fail(NEP_ERR_ARG, "model is NULL");
+    if (!params_dev) return fail(NEP_ERR_ARG, "params_dev is NULL");
+    NEP_CUDA(cudaMemcpyAsync(params_dev, m->params, sizeof(float) * nep_num_params(&m->hp),
+                             cudaMemcpyDeviceToDevice, (cudaStream_t)stream),
+             "copy parameters");
+    return NEP_OK;
+}
+
 nep_status nep_set_params(nep_model* m, const float* params_dev, void* stream) {
     if (!m || !params_dev) return fail(NEP_ERR_ARG, "model or params is NULL");
     NEP_CUDA(cudaMemcpyAsync(m->params, params_dev, sizeof(float) * (size_t)m->lay.P,
@@ -662,6 +671,24 @@ nep_status nep_param_grad_adjoint(nep_model* m, const nep_system* sys, const nep
     if ((s = check_train_work(m, sys, nl, work, work_bytes, &tl)) != NEP_OK) return s;
     return train_impl(m, sys, nl, nullptr, nullptr, nullptr, nullptr, 0, a_e, lam, mu, grad, nullptr,
                       work, tl, (cudaStream_t)stream);
+}
+
+nep_status nep_adam_step(nep_model* m, const float* grad, float* m1, float* m2, int t, float lr,
+                         float beta1, float beta2, float eps, void* stream) {
+    if (!m) return fail(NEP_ERR_ARG, "model is NULL");
+    if (!grad || !m1 || !m2) return fail(NEP_ERR_ARG, "grad, m1 or m2 is NULL");
+    if (t < 1) return fail(NEP_ERR_ARG, "step t must be >= 1");
+    if (!(lr >= 0.0f) || !std::isfinite(lr)) return fail(NEP_ERR_ARG, "lr must be finite and >= 0");
+    if (!(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f))
+        return fail(NEP_ERR_ARG, "beta1 and beta2 must lie in [0, 1)");
+    if (!(eps > 0.0f) || !std::isfinite(eps)) return fail(NEP_ERR_ARG, "eps must be finite and > 0");
+    const int P = (int)nep_num_params(&m->hp);
+    const double bc1 = 1.0 - std::pow((double)beta1, (double)t);
+    const double bc2 = 1.0 - std::pow((double)beta2, (double)t);
+    const float c1 = (float)((double)lr / bc1), c2 = (float)(1.0 / std::sqrt(bc2));
+    NEP_CUDA(nep::launch_adam(m->params, grad, m1, m2, P, beta1, beta2, eps, c1, c2, (cudaStream_t)stream),
+             "adam");
+    return NEP_OK;
 }
 
 nep_status nep_set_variant(nep_model* m, int size_class, int variant) {

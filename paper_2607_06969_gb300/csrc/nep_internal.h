@@ -157,6 +157,8 @@ cudaError_t launch_neighbors(const float* pos, const float4* pos4, const int* at
                              const int* cfg, int N, int B, float rc_list, float rc_list_ang, float rc_phys,
                              int min_image, nep_nlist* nl, const NbrWork& w, cudaStream_t st);
 
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int n, float beta1, float beta2,
+                        float eps, float c1, float c2, cudaStream_t st);
 cudaError_t launch_kick(float* vel, const float* force, const int* type, const float* inv_mass,
                         int N, float half_dt, float* pos, float dt, cudaStream_t st);
 cudaError_t launch_wrap(float* pos, const int* cfg, const float* box, int N, cudaStream_t st);

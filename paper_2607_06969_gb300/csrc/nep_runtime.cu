@@ -471,6 +471,20 @@ __global__ void k_rev(int N, nep_nlist nl) {
     }
 }
 
+// ------------------------------------------------------------ optimiser
+// one Adam step per parameter; c1 = lr / (1 - beta1^t), c2 = 1 / sqrt(1 - beta2^t)
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, int n, float beta1, float beta2, float eps, float c1, float c2) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const float gk = g[k];
+    const float mk = beta1 * m[k] + (1.0f - beta1) * gk;
+    const float vk = beta2 * v[k] + (1.0f - beta2) * gk * gk;
+    m[k] = mk;
+    v[k] = vk;
+    p[k] -= c1 * mk / (sqrtf(vk) * c2 + eps);
+}
+
 // ------------------------------------------------------------ integrator
 struct InvMass {
     float v[kMaxTypes];
@@ -647,6 +661,12 @@ cudaError_t launch_neighbors(const float* pos, const float4* pos4, const int* at
     k_build<<<blocks(N, 128), 128, 0, st>>>(pos4, cfg, box, w.plan, w.cell_of, w.cell_start,
                                             w.cell_atoms, N, rr, ra, rp, w.shell, *nl);
     k_rev<<<blocks(N, 128), 128, 0, st>>>(N, *nl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int n, float beta1, float beta2,
+                        float eps, float c1, float c2, cudaStream_t st) {
+    if (n > 0) k_adam<<<blocks(n, 256), 256, 0, st>>>(p, g, m, v, n, beta1, beta2, eps, c1, c2);
     return cudaGetLastError();
 }
 
