@@ -66,7 +66,7 @@ size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 struct WsLayout {
     size_t pos4, cfg, e_atom, fb, S, Pr, comp, cnt_comp, fin, fpart, wat, chunk_start, partial;
     size_t rin, rin_sh, cnt_rin;
-    size_t plan, cell_of, rank, cell_cnt, cell_start, cell_atoms, scan_tmp, shell;
+    size_t plan, cell_of, rank, cell_cnt, cell_start, cell_atoms, scan_tmp, shell, row_start, slot_row;
     size_t total;
     int max_chunks, cmax;
 };
@@ -110,6 +110,8 @@ WsLayout ws_layout(const nep_model* m, int N, int B, int cap, int cap_ang) {
     const size_t ntiles = ((size_t)w.cmax + 1 + 2047) / 2048;
     w.scan_tmp = take(4 * (ntiles + 1));
     w.shell = take(8 * n * (size_t)cap);
+    w.row_start = take(32 * n);
+    w.slot_row = take(n * (size_t)cap_ang);
     w.total = o;
     return w;
 }
@@ -415,6 +417,8 @@ nep_status neighbors_impl(nep_model* m, const nep_system* s, float skin, nep_nli
     nw.cell_atoms = at<int>(work, w.cell_atoms);
     nw.scan_tmp = at<int>(work, w.scan_tmp);
     nw.shell = at<int2>(work, w.shell);
+    nw.row_start = at<unsigned char>(work, w.row_start);
+    nw.slot_row = at<unsigned char>(work, w.slot_row);
     nw.cmax = w.cmax;
     nep_nlist copy = *nl;
     if (mi) copy.shift = nullptr;

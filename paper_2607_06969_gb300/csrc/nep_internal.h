@@ -150,6 +150,8 @@ struct NbrWork {
     int* cell_atoms;       // [N]
     int* scan_tmp;         // [ceil(Cmax/2048)+1]
     int2* shell;           // [cap][N] scratch for the list entries beyond rc_rad
+    unsigned char* row_start;   // [N][32] where each stencil row's angular entries start
+    unsigned char* slot_row;    // [cap_ang][N] stencil row of each angular entry
     int cmax;
 };
 size_t nbr_cell_capacity(int N, int B);

@@ -151,13 +151,19 @@ __global__ void __launch_bounds__(kRedThreads) k_final_reduce(int B, const int* 
 }
 
 // ------------------------------------------------------- neighbour build
-// Cells per edge: floor(L / (rc + 1e-3)) (at least 1), reduced while the cell
-// count of a configuration exceeds 2 N_b + 27.  The stencil half-width is the
-// number of cells needed to reach rc + 1e-3 (1 unless a cell is shorter than
-// the cutoff).  An atom in cell c sees cells c + d, d in [-half, half], with
+// Cells per edge: floor(L / ((rc + 1e-3) / kCellDiv)) (at least 1), reduced
+// while the cell count of a configuration exceeds 2 N_b + 27.  The stencil
+// half-width is the number of cells needed to reach rc + 1e-3 (kCellDiv for
+// large boxes).  Cells of half the cutoff offer (5/2)^3 = 15.6 cutoff-sized
+// cells' worth of candidates instead of 27.  An atom in cell c sees cells c + d, d in [-half, half], with
 // image shift floor((c + d) / nc): every (j, image) within the cutoff is
 // visited exactly once.
 constexpr float kCellMargin = 1e-3f;
+constexpr int kCellDiv = 2;
+// per-atom row starts of the angular prefix, for the reverse-slot search:
+// stencils of up to kMaxRows (x, y) rows, angular capacity below 256
+constexpr int kMaxRows = 25;
+constexpr int kRowStride = 32;
 
 __global__ void k_cell_plan(const float* __restrict__ box, const int* __restrict__ atom_off, int B,
                             float rc, CellPlan* plan, int* status) {
@@ -171,7 +177,7 @@ __global__ void k_cell_plan(const float* __restrict__ box, const int* __restrict
             set_flag(status, 3);
             L[d] = 1.0f;
         }
-        const float r = floorf(L[d] / (rc + kCellMargin));
+        const float r = floorf(L[d] / ((rc + kCellMargin) / (float)kCellDiv));
         nc[d] = r < 1.0f ? 1 : (r > 1024.0f ? 1024 : (int)r);
     }
     const long long cap = 2LL * nb + 27;
@@ -333,6 +339,13 @@ __device__ __forceinline__ int floor_div(int a, int b) {
 // the prefix and the shell appended, all in visit order.  With the pairs
 // inside the cutoff first, a warp's late iterations are mostly outside the
 // cutoff for all of its lanes and skip the pair work together.
+//
+// The stencil is visited row by row: for each (ox, oy) the cells oz =
+// -half..half are consecutive cell ids (one range of the sorted atom array)
+// except where they wrap around the box, which splits the row in two ranges
+// with different z images.  The visit order is that of the cell triple loop.
+// For the reverse-slot search the kernel also records, per atom, where each
+// row's angular entries start (row_start) and, per angular slot, its row.
 __global__ void __launch_bounds__(128) k_build(const float4* __restrict__ pos4,
                                                const int* __restrict__ cfg,
                                                const float* __restrict__ box,
@@ -341,7 +354,8 @@ __global__ void __launch_bounds__(128) k_build(const float4* __restrict__ pos4,
                                                const int* __restrict__ cell_start,
                                                const int* __restrict__ cell_atoms, int N,
                                                float rc2_rad, float rc2_ang, float rc2_phys,
-                                               int2* __restrict__ shell, nep_nlist nl) {
+                                               int2* __restrict__ shell, unsigned char* __restrict__ row_start,
+                                               unsigned char* __restrict__ slot_row, nep_nlist nl) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int b = cfg[i];
@@ -355,28 +369,48 @@ __global__ void __launch_bounds__(128) k_build(const float4* __restrict__ pos4,
     const int cx = c / p.nc[1];
     int n_ang = 0, n_in = 0, n_out = 0, w_ang = 0;
     const int cap = nl.cap, cap_ang = nl.cap_ang;
+    const int rows = (2 * p.half[0] + 1) * (2 * p.half[1] + 1);
+    const bool track = rows <= kMaxRows && cap_ang < 256;
+    unsigned char* rs = row_start + (size_t)i * kRowStride;
+    int row = 0;
     for (int ox = -p.half[0]; ox <= p.half[0]; ++ox) {
         const int ux = cx + ox, sx = floor_div(ux, p.nc[0]), wx = ux - sx * p.nc[0];
-        for (int oy = -p.half[1]; oy <= p.half[1]; ++oy) {
+        for (int oy = -p.half[1]; oy <= p.half[1]; ++oy, ++row) {
             const int uy = cy + oy, sy = floor_div(uy, p.nc[1]), wy = uy - sy * p.nc[1];
-            for (int oz = -p.half[2]; oz <= p.half[2]; ++oz) {
-                const int uz = cz + oz, sz = floor_div(uz, p.nc[2]), wz = uz - sz * p.nc[2];
-                const int cell = p.base + (wx * p.nc[1] + wy) * p.nc[2] + wz;
-                const float fx = mul_rn((float)sx, L[0]);
-                const float fy = mul_rn((float)sy, L[1]);
+            if (track) rs[row] = (unsigned char)(n_ang < 255 ? n_ang : 255);
+            const float fx = mul_rn((float)sx, L[0]);
+            const float fy = mul_rn((float)sy, L[1]);
+            const int rowcell = p.base + (wx * p.nc[1] + wy) * p.nc[2];
+            // z range [cz - half, cz + half], in pieces of one z image each
+            int lo = cz - p.half[2];
+            const int hi = cz + p.half[2];
+            while (lo <= hi) {
+                const int sz = floor_div(lo, p.nc[2]);
+                const int seg_hi = min(hi, (sz + 1) * p.nc[2] - 1);
+                const int wz0 = lo - sz * p.nc[2], wz1 = seg_hi - sz * p.nc[2];
+                lo = seg_hi + 1;
                 const float fz = mul_rn((float)sz, L[2]);
                 const bool zero_img = (sx == 0 && sy == 0 && sz == 0);
-                const int q1 = cell_start[cell + 1];
-                for (int q = cell_start[cell]; q < q1; ++q) {
-                    const int j = cell_atoms[q];
+                const int sh = pack_shift(sx, sy, sz);
+                const int q0 = cell_start[rowcell + wz0], q1 = cell_start[rowcell + wz1 + 1];
+                // candidates' indices two ahead, positions one ahead
+                int j_nx = q0 < q1 ? cell_atoms[q0] : 0;
+                int j_nx2 = q0 + 1 < q1 ? cell_atoms[q0 + 1] : 0;
+                float4 p_nx = pos4[j_nx];
+                for (int q = q0; q < q1; ++q) {
+                    const int j = j_nx;
+                    const float4 pj = p_nx;
+                    if (q + 1 < q1) {
+                        j_nx = j_nx2;
+                        p_nx = pos4[j_nx];
+                        if (q + 2 < q1) j_nx2 = cell_atoms[q + 2];
+                    }
                     if (j == i && zero_img) continue;
-                    const float4 pj = pos4[j];
                     const float dx = add_rn(sub_rn(pj.x, pi.x), fx);
                     const float dy = add_rn(sub_rn(pj.y, pi.y), fy);
                     const float dz = add_rn(sub_rn(pj.z, pi.z), fz);
                     const float d2 = dist2(dx, dy, dz);
                     if (!(d2 < rc2_rad)) continue;
-                    const int sh = pack_shift(sx, sy, sz);
                     if (d2 < rc2_ang) {
                         const int slot = n_ang < cap_ang && n_ang + n_in < cap ? n_ang : -1;
                         ++n_ang;
@@ -384,6 +418,7 @@ __global__ void __launch_bounds__(128) k_build(const float4* __restrict__ pos4,
                         w_ang = n_ang;
                         nl.nbr[(size_t)slot * N + i] = j;
                         if (nl.shift) nl.shift[(size_t)slot * N + i] = sh;
+                        if (track) slot_row[(size_t)slot * N + i] = (unsigned char)row;
                     } else if (d2 < rc2_phys) {
                         const int slot = n_ang + n_in < cap ? cap - 1 - n_in : -1;
                         ++n_in;
@@ -398,6 +433,7 @@ __global__ void __launch_bounds__(128) k_build(const float4* __restrict__ pos4,
             }
         }
     }
+    if (track) rs[rows] = (unsigned char)(n_ang < 255 ? n_ang : 255);
     const int n_rest = n_in + n_out;
     const int n_total = n_ang + n_rest;
     const bool over = n_total > cap || n_ang > cap_ang;
@@ -442,10 +478,19 @@ __global__ void __launch_bounds__(128) k_build(const float4* __restrict__ pos4,
     nl.cnt_ang[i] = n_ang;
 }
 
-__global__ void k_rev(int N, nep_nlist nl) {
+// rev[s][i] = slot of i (with the opposite image) in the angular prefix of
+// j = nbr[s][i].  j visits i in the mirrored stencil row, rows - 1 - row,
+// so only that row's stretch of j's prefix is searched; stencils too large
+// for the row table fall back to scanning j's whole prefix.
+__global__ void k_rev(int N, const int* __restrict__ cfg, const CellPlan* __restrict__ plan,
+                      const unsigned char* __restrict__ row_start, const unsigned char* __restrict__ slot_row,
+                      nep_nlist nl) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int na = nl.cnt_ang[i];
+    const CellPlan p = plan[cfg[i]];
+    const int rows = (2 * p.half[0] + 1) * (2 * p.half[1] + 1);
+    const bool track = rows <= kMaxRows && nl.cap_ang < 256;
     for (int s = 0; s < na; ++s) {
         const int j = nl.nbr[(size_t)s * N + i];
         int want = 0;
@@ -455,10 +500,16 @@ __global__ void k_rev(int N, nep_nlist nl) {
             want = pack_shift(-a, -b, -c);
         }
         const int nj = nl.cnt_ang[j];
+        int t0 = 0, t1 = nj;
+        if (track) {
+            const int mr = rows - 1 - (int)slot_row[(size_t)s * N + i];
+            const unsigned char* rj = row_start + (size_t)j * kRowStride;
+            t0 = rj[mr];
+            t1 = min((int)rj[mr + 1], nj);
+        }
         int found = -1;
-        for (int t = 0; t < nj; ++t) {
-            if (nl.nbr[(size_t)t * N + j] == i &&
-                (!nl.shift || nl.shift[(size_t)t * N + j] == want)) {
+        for (int t = t0; t < t1; ++t) {
+            if (nl.nbr[(size_t)t * N + j] == i && (!nl.shift || nl.shift[(size_t)t * N + j] == want)) {
                 found = t;
                 break;
             }
@@ -659,8 +710,8 @@ cudaError_t launch_neighbors(const float* pos, const float4* pos4, const int* at
     k_sort_cells<<<blocks(cmax, 128), 128, 0, st>>>(w.cell_start, cmax, w.cell_atoms);
     const float rr = rc_list * rc_list, ra = rc_list_ang * rc_list_ang, rp = rc_phys * rc_phys;
     k_build<<<blocks(N, 128), 128, 0, st>>>(pos4, cfg, box, w.plan, w.cell_of, w.cell_start,
-                                            w.cell_atoms, N, rr, ra, rp, w.shell, *nl);
-    k_rev<<<blocks(N, 128), 128, 0, st>>>(N, *nl);
+                                            w.cell_atoms, N, rr, ra, rp, w.shell, w.row_start, w.slot_row, *nl);
+    k_rev<<<blocks(N, 128), 128, 0, st>>>(N, cfg, w.plan, w.row_start, w.slot_row, *nl);
     return cudaGetLastError();
 }
 
