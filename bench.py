@@ -618,7 +618,9 @@ def main():
     dom = max(t_kern, key=t_kern.get)
     t_dom = t_kern[dom]
     achieved = fl[dom] * N / (t_dom * 1e-3) / 1e12
+    fma_peak = nb.fp32_peak()       # measured FMA throughput, right after the timed run
     roofline = {"bound": "alu", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak,
+                "peak_fma_measured": fma_peak, "frac_of_measured_fma": achieved / fma_peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": TRAFFIC_PER_ATOM[dom] * N,
                 "traffic_basis": "ncu dram bytes per atom of the 460,800-atom capture x atoms",

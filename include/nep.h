@@ -276,6 +276,12 @@ nep_status nep_set_variant(nep_model* m, int size_class, int variant);
  * records are ordinary stream work and can be captured into a CUDA graph. */
 nep_status nep_set_timing_events(nep_model* m, void* const* events, int n);
 
+/* Measurement helper, not part of the NEP path: the FP32 FMA throughput of
+ * the device, from a kernel of independent FMA chains on every SM, timed
+ * with CUDA events on `stream` (synchronises).  *tflops receives 2 flops per
+ * FMA per second / 1e12. */
+nep_status nep_fp32_peak(void* stream, double* tflops);
+
 /* Synchronise `stream` and map the list's device flags to a status:
  * NEP_ERR_CAPACITY (status[0]), NEP_ERR_TIMEOUT (status[3] bit 1),
  * NEP_ERR_INPUT (status[3] bit 0) or NEP_OK.

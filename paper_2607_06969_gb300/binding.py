@@ -23,7 +23,7 @@ ENTRY_POINTS = (
     "nep_workspace_bytes", "nep_train_workspace_bytes", "nep_neighbors", "nep_energy_forces_virial",
     "nep_energy_forces_virial_noalloc", "nep_param_grad",
     "nep_param_grad_adjoint", "nep_adam_step", "nep_md_step", "nep_autotune", "nep_set_variant",
-    "nep_set_timing_events",
+    "nep_set_timing_events", "nep_fp32_peak",
     "nep_check",
     "nep_last_error", "nep_version",
 )
@@ -89,6 +89,8 @@ def lib() -> ctypes.CDLL:
     L.nep_autotune.argtypes = [vp, P(System), P(NList), vp, sz, vp, i, P(ctypes.c_int)]
     L.nep_autotune.restype = i
     L.nep_set_variant.argtypes = [vp, i, i]
+    L.nep_fp32_peak.argtypes = [vp, P(ctypes.c_double)]
+    L.nep_fp32_peak.restype = i
     L.nep_set_variant.restype = i
     L.nep_last_error.restype = ctypes.c_char_p
     L.nep_version.restype = ctypes.c_char_p
@@ -371,6 +373,13 @@ def set_variant(model: Model, variant: int, size_class: int = -1) -> None:
     """nep_set_variant: pin the angular kernel variant (-1 = default) for one
     size class or all of them."""
     check(lib().nep_set_variant(model.handle, int(size_class), int(variant)), "nep_set_variant")
+
+
+def fp32_peak(stream=None) -> float:
+    """nep_fp32_peak: measured FP32 FMA throughput of the device, TFLOP/s."""
+    out = ctypes.c_double()
+    check(lib().nep_fp32_peak(_stream(stream), ctypes.byref(out)), "nep_fp32_peak")
+    return float(out.value)
 
 
 def check_list(nl: NeighborList | None, stream=None) -> int:

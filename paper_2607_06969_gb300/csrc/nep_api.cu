@@ -695,6 +695,12 @@ nep_status nep_adam_step(nep_model* m, const float* grad, float* m1, float* m2, 
     return NEP_OK;
 }
 
+nep_status nep_fp32_peak(void* stream, double* tflops) {
+    if (!tflops) return fail(NEP_ERR_ARG, "tflops is NULL");
+    NEP_CUDA(nep::fp32_peak((cudaStream_t)stream, tflops), "FP32 peak kernel");
+    return NEP_OK;
+}
+
 nep_status nep_set_variant(nep_model* m, int size_class, int variant) {
     if (!m) return fail(NEP_ERR_ARG, "model is NULL");
     if (size_class < -1 || size_class >= nep::kSizeBins)

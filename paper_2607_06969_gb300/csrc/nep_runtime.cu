@@ -536,6 +536,25 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
     p[k] -= c1 * mk / (sqrtf(vk) * c2 + eps);
 }
 
+// ------------------------------------------------------------ FP32 peak
+// eight independent FMA chains per thread; a and b come from memory so that
+// nothing folds, the sums are stored so that nothing is dropped
+constexpr int kFmaIters = 4096;
+__global__ void __launch_bounds__(256) k_fma_peak(const float* __restrict__ ab, float* __restrict__ out) {
+    const float a = ab[0], b = ab[1];
+    float x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = (float)(threadIdx.x + k) * 1e-3f;
+    for (int it = 0; it < kFmaIters; ++it) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = fmaf(x[k], a, b);
+    }
+    float sum = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sum += x[k];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = sum;
+}
+
 // ------------------------------------------------------------ integrator
 struct InvMass {
     float v[kMaxTypes];
@@ -718,6 +737,35 @@ cudaError_t launch_neighbors(const float* pos, const float4* pos4, const int* at
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int n, float beta1, float beta2,
                         float eps, float c1, float c2, cudaStream_t st) {
     if (n > 0) k_adam<<<blocks(n, 256), 256, 0, st>>>(p, g, m, v, n, beta1, beta2, eps, c1, c2);
+    return cudaGetLastError();
+}
+
+cudaError_t fp32_peak(cudaStream_t st, double* tflops) {
+    int dev = 0, nsm = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev))) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev))) return e;
+    const int blocks_n = nsm * 8, threads = 256;
+    float* buf = nullptr;
+    if ((e = cudaMalloc(&buf, sizeof(float) * ((size_t)blocks_n * threads + 2)))) return e;
+    const float ab[2] = {0.999f, 1e-3f};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float ms = 0.0f, best = 1e30f;
+    if (!(e = cudaMemcpyAsync(buf, ab, sizeof ab, cudaMemcpyHostToDevice, st)) && !(e = cudaEventCreate(&e0)) &&
+        !(e = cudaEventCreate(&e1))) {
+        for (int r = 0; r < 4 && !e; ++r) {
+            cudaEventRecord(e0, st);
+            k_fma_peak<<<blocks_n, threads, 0, st>>>(buf, buf + 2);
+            cudaEventRecord(e1, st);
+            if (!(e = cudaEventSynchronize(e1)) && !(e = cudaEventElapsedTime(&ms, e0, e1)) && r > 0 && ms < best)
+                best = ms;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(buf);
+    if (e) return e;
+    *tflops = 2.0 * 8.0 * kFmaIters * (double)blocks_n * threads / (best * 1e-3) / 1e12;
     return cudaGetLastError();
 }
 
