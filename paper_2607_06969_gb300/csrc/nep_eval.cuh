@@ -629,16 +629,30 @@ __device__ void angular_atom_tm(const EvalArgs& a, const float* sm, uint32_t tS,
 // from P of atom i (neighbour species row) and P of atom j (row Zi); returns
 // F_i's radial part and the symmetric radial virial (xx yy zz xy xz yz)
 // ---------------------------------------------------------------------------
+// stage (optional): this thread's slot of a [T*KR/4][nthr] float4 array in
+// shared memory; the atom's own adjoint rows are kept there instead of in
+// T*KR registers and read per pair for the neighbour's species
 template <class C, bool MINIMG>
-NEP_HD void radial_force_atom(const EvalArgs& a, int i, float& Fx, float& Fy, float& Fz, float* Wr) {
+NEP_HD void radial_force_atom(const EvalArgs& a, int i, float& Fx, float& Fy, float& Fz, float* Wr,
+                              float4* stage = nullptr, int nthr = 0) {
     constexpr int KR = C::KR, T = C::T;
     const int N = a.N;
     const AtomFrame fr = atom_frame(a, i);
     const int ti = fr.ti;
     const float rcR2 = a.rc_rad * a.rc_rad;
     const float irR = 1.0f / a.rc_rad;
+    constexpr bool kStageable = (KR % 4) == 0;
+    const bool staged = kStageable && stage != nullptr;
     float Pi[T][KR];
-    if ((T * KR) % 4 == 0) {
+    if (staged) {
+        const float4* src = reinterpret_cast<const float4*>(a.Pr + i * T * KR);
+#pragma unroll
+        for (int c = 0; c < T * KR / 4; ++c) stage[c * nthr] = src[c];
+#pragma unroll
+        for (int t = 0; t < T; ++t)
+#pragma unroll
+            for (int k = 0; k < KR; ++k) Pi[t][k] = 0.0f;
+    } else if ((T * KR) % 4 == 0) {
         const float4* src = reinterpret_cast<const float4*>(a.Pr + i * T * KR);
 #pragma unroll
         for (int x = 0; x < T * KR; x += 4) {
@@ -678,13 +692,26 @@ NEP_HD void radial_force_atom(const EvalArgs& a, int i, float& Fx, float& Fy, fl
             for (int k = 0; k < KR; ++k) Pj[k] = a.Pr[(j * T + ti) * KR + k];
         }
         float dEi = 0.0f, dEj = 0.0f;
+        if (kStageable && staged) {
 #pragma unroll
-        for (int k = 0; k < KR; ++k) {
-            float pk = Pi[0][k];
+            for (int c = 0; c < KR / 4; ++c) {
+                const float4 v = stage[(tj * (KR / 4) + c) * nthr];
+                const float pv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-            for (int t = 1; t < T; ++t) pk = (tj == t) ? Pi[t][k] : pk;
-            dEi = fmaf(pk, fp[k], dEi);
-            dEj = fmaf(Pj[k], fp[k], dEj);
+                for (int u = 0; u < 4; ++u) {
+                    dEi = fmaf(pv[u], fp[4 * c + u], dEi);
+                    dEj = fmaf(Pj[4 * c + u], fp[4 * c + u], dEj);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < KR; ++k) {
+                float pk = Pi[0][k];
+#pragma unroll
+                for (int t = 1; t < T; ++t) pk = (tj == t) ? Pi[t][k] : pk;
+                dEi = fmaf(pk, fp[k], dEi);
+                dEj = fmaf(Pj[k], fp[k], dEj);
+            }
         }
         const float tot = (dEi + dEj) * ir;
         Fx = fmaf(tot, dx, Fx); Fy = fmaf(tot, dy, Fy); Fz = fmaf(tot, dz, Fz);
@@ -783,11 +810,12 @@ NEP_HD void radial_force_atom(const EvalArgs& a, int i, float& Fx, float& Fy, fl
 // angular pair forces (subtracted inside radial_force_atom); the per-atom virial (angular owner part minus the
 // radial part) is written back for the FP64 reduction
 template <class C, bool MINIMG>
-NEP_HD void finish_atom(const EvalArgs& a, int i, float* force, float* e_out) {
+NEP_HD void finish_atom(const EvalArgs& a, int i, float* force, float* e_out, float4* stage = nullptr,
+                        int nthr = 0) {
     const int N = a.N;
     float Fx = a.fpart[i], Fy = a.fpart[N + i], Fz = a.fpart[2 * N + i];
     float Wr[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-    radial_force_atom<C, MINIMG>(a, i, Fx, Fy, Fz, Wr);
+    radial_force_atom<C, MINIMG>(a, i, Fx, Fy, Fz, Wr, stage, nthr);
     force[i] = Fx;
     force[N + i] = Fy;
     force[2 * N + i] = Fz;
@@ -814,7 +842,10 @@ constexpr int kFinishThreads = 128;
 #define NEP_RADIAL_MINB 3
 #endif
 #ifndef NEP_FINISH_MINB
-#define NEP_FINISH_MINB 6
+#define NEP_FINISH_MINB 8
+#endif
+#ifndef NEP_FINISH_STAGE
+#define NEP_FINISH_STAGE 1
 #endif
 template <class C, bool MINIMG>
 __global__ void __launch_bounds__(kRadialBlock, NEP_RADIAL_MINB) k_radial(const EvalArgs a) {
@@ -913,7 +944,13 @@ inline int persistent_grid(int ntiles, int per_sm) {
 template <class C, bool MINIMG>
 __global__ void __launch_bounds__(kFinishThreads, NEP_FINISH_MINB) k_finish(const EvalArgs a, float* force, float* e_out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+#if NEP_FINISH_STAGE
+    constexpr int kChunks = (C::KR % 4 == 0) ? C::T * C::KR / 4 : 1;
+    __shared__ float4 stage[kChunks * kFinishThreads];
+    if (i < a.N) finish_atom<C, MINIMG>(a, i, force, e_out, stage + threadIdx.x, kFinishThreads);
+#else
     if (i < a.N) finish_atom<C, MINIMG>(a, i, force, e_out);
+#endif
 }
 
 template <class C>
