@@ -35,28 +35,6 @@ NEP_HD float sub_rn(float a, float b) {
     return r;
 #endif
 }
-NEP_HD float cospi_f(float x) {
-#if defined(__CUDA_ARCH__)
-    return cospif(x);
-#else
-    return (float)std::cos(3.14159265358979323846 * (double)x);
-#endif
-}
-NEP_HD float sinpi_f(float x) {
-#if defined(__CUDA_ARCH__)
-    return sinpif(x);
-#else
-    return (float)std::sin(3.14159265358979323846 * (double)x);
-#endif
-}
-NEP_HD void sincospi_f(float x, float* s, float* c) {
-#if defined(__CUDA_ARCH__)
-    sincospif(x, s, c);
-#else
-    *s = (float)std::sin(3.14159265358979323846 * (double)x);
-    *c = (float)std::cos(3.14159265358979323846 * (double)x);
-#endif
-}
 // correctly rounded reciprocal
 NEP_HD float rcp_f(float x) {
 #if defined(__CUDA_ARCH__)
@@ -156,10 +134,40 @@ NEP_HD float dist2(float dx, float dy, float dz) {
     return add_rn(add_rn(mul_rn(dx, dx), mul_rn(dy, dy)), mul_rn(dz, dz));
 }
 
+// cos(pi z) and sin(pi z) for z = r/rc in [0, 1): with w = z - 1/2,
+// cos(pi z) = -sin(pi w) and sin(pi z) = cos(pi w), |pi w| <= pi/2, summed
+// as their Taylor series in y = (pi w)^2 (Horner), through y^6: the first
+// omitted terms are below (pi/2)^15/15! = 6.7e-10 and (pi/2)^14/14! = 6.9e-9,
+// under the FP32 rounding of the result.
+NEP_HD void cutoff_trig(float z, float& c, float& s) {
+    // pi w with pi split in two floats, so that the product keeps ~45 bits
+    const float w = z - 0.5f;
+    const float t = fmaf(3.14159274101257324f, w, -8.74227766e-8f * w);
+    const float y = t * t;
+    float ps = 1.0f / 6227020800.0f;                 // 1/13!
+    ps = fmaf(ps, y, -1.0f / 39916800.0f);            // 1/11!
+    ps = fmaf(ps, y, 1.0f / 362880.0f);               // 1/9!
+    ps = fmaf(ps, y, -1.0f / 5040.0f);                // 1/7!
+    ps = fmaf(ps, y, 1.0f / 120.0f);
+    ps = fmaf(ps, y, -1.0f / 6.0f);
+    ps = fmaf(ps, y, 1.0f);
+    float pc = 1.0f / 479001600.0f;                  // 1/12!
+    pc = fmaf(pc, y, -1.0f / 3628800.0f);             // 1/10!
+    pc = fmaf(pc, y, 1.0f / 40320.0f);                // 1/8!
+    pc = fmaf(pc, y, -1.0f / 720.0f);
+    pc = fmaf(pc, y, 1.0f / 24.0f);
+    pc = fmaf(pc, y, -0.5f);
+    pc = fmaf(pc, y, 1.0f);
+    c = -t * ps;
+    s = pc;
+}
+
 // Q_k(r) = (T_k(x)+1)/2 f_c(r), x = 2(r/rc-1)^2-1, f_c = (1+cos(pi r/rc))/2.
 template <int K>
 NEP_HD void basis(float r, float inv_rc, float* f) {
-    float fc2 = 0.25f * (1.0f + cospi_f(r * inv_rc));     // f_c / 2
+    float cz, sz;
+    cutoff_trig(r * inv_rc, cz, sz);
+    float fc2 = 0.25f * (1.0f + cz);                       // f_c / 2
     float t = r * inv_rc - 1.0f;
     float x = 2.0f * t * t - 1.0f;
     float Tm = 1.0f, Tk = x;
@@ -178,7 +186,7 @@ NEP_HD void basis(float r, float inv_rc, float* f) {
 template <int K>
 NEP_HD void basis_d(float r, float inv_rc, float* f, float* fp) {
     float sp, cp;
-    sincospi_f(r * inv_rc, &sp, &cp);
+    cutoff_trig(r * inv_rc, cp, sp);
     float fc2 = 0.25f * (1.0f + cp);
     float dfc2 = (-0.25f * 3.14159265358979f) * inv_rc * sp;
     float t = r * inv_rc - 1.0f;
