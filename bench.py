@@ -312,14 +312,21 @@ def run_md(args, nb, torch, dist, world, local, s, h, model, theta, vel0, masses
             force, e_tot, vir, stream, vel)
 
 
-def train_leg(nb, torch, I, local) -> dict:
+def train_leg(nb, torch, I, local, dist=None, world: int = 1, rank: int = 0) -> dict:
     """Secondary leg: batched training steps on the 128-configuration batch
     (N ~ U{24..512}); labels from a teacher NEP evaluated by the same library
     (seed 2 weights).  One step = loss and gradient (nep_param_grad) plus the
-    Adam update of all parameters (nep_adam_step).  Then a short fit with the
-    paper's protocol (warm-up + cosine learning rate, dynamic loss weights)."""
+    Adam update of all parameters (nep_adam_step).  With several ranks the
+    configurations are sharded by atom count and the gradient and loss are
+    combined by one weighted all-reduce per step (data parallelism).  Then a
+    short fit with the paper's protocol (warm-up + cosine learning rate,
+    dynamic loss weights)."""
+    from paper_2607_06969_gb300 import dp
     from paper_2607_06969_gb300 import train as T
-    s, h = I.workload_train128()
+    s_all, h = I.workload_train128()
+    B_all = s_all.n_cfg
+    b0, b1 = dp.shard_bounds(s_all.atom_off, world)[rank]
+    s = dp.shard_system(s_all, b0, b1) if world > 1 else s_all
     th = I.init_params(h).astype(np.float32)
     teacher = nb.Model(h, I.init_params(h, seed=I.SEED_TEACHER).astype(np.float32))
     model = nb.Model(h, th)
@@ -336,32 +343,47 @@ def train_leg(nb, torch, I, local) -> dict:
     loss = torch.empty(1, dtype=torch.float64, device="cuda")
     m1 = torch.zeros_like(grad)
     m2 = torch.zeros_like(grad)
+    reduce = (lambda g, l: dp.allreduce_mean(dist, g, l, b1 - b0, B_all)) if world > 1 else None
     t = 0
-    for _ in range(3):
+
+    def step():
+        nonlocal t
         nb.param_grad(model, dsys, nl, ws, E, F, V, (1.0, 1.0, 0.1), 0, grad, loss)
+        if reduce is not None:
+            reduce(grad, loss)
         t += 1
         nb.adam_step(model, grad, m1, m2, t, 1e-4)
+
+    for _ in range(3):
+        step()
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     K = 20
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0.record()
     for _ in range(K):
-        nb.param_grad(model, dsys, nl, ws, E, F, V, (1.0, 1.0, 0.1), 0, grad, loss)
-        t += 1
-        nb.adam_step(model, grad, m1, m2, t, 1e-4)
+        step()
     t1.record()
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     ms = t0.elapsed_time(t1) / K
+    if world > 1:
+        tm = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        ms = float(tm.item())
 
     # fit from the initial student weights with the training protocol
     student = nb.Model(h, th)
     batch = T.Batch(dsys, nl, ws, E, F, V)
     cfg = T.TrainConfig(lr_start=3e-3, lr_end=3e-5, epochs=300)
-    tr = T.Trainer(student, [batch], cfg)
+    tr = T.Trainer(student, [batch], cfg, allreduce=reduce)
     losses = [tr.step(batch) for _ in range(cfg.epochs)]
     return {"workload": "train128: 128 random packings, N ~ U{24..512} (%d atoms), loss+grad of %d "
-                        "parameters and an Adam step, FP32" % (s.n_atoms, model.n_params),
-            "configs_per_s": s.n_cfg / (ms * 1e-3), "ms_per_step": ms, "steps": K,
+                        "parameters and an Adam step, FP32" % (s_all.n_atoms, model.n_params),
+            "parallelism": f"dp{world}" if world > 1 else "single",
+            "configs_per_s": B_all / (ms * 1e-3), "ms_per_step": ms, "steps": K,
             "fit": {"steps": cfg.epochs, "lr_start": cfg.lr_start, "lr_end": cfg.lr_end,
                     "loss_first": losses[0], "loss_last": losses[-1],
                     "loss_at": {str(k): losses[k] for k in (0, 10, 30, 100, 299)}}}
@@ -661,7 +683,7 @@ def main():
     e2e_ms = e0.elapsed_time(e1)
     e2e_val = world * N * KE / (e2e_ms * 1e-3)
 
-    train = None if args.no_train else train_leg(nb, torch, I, local)
+    train = None if args.no_train else train_leg(nb, torch, I, local, dist, world, rank)
     mixed = None if args.no_mixed else mixed_leg(nb, torch, I)
     replicas = None if args.no_replicas else replicas_leg(nb, torch, I)
     table2 = None if args.no_table2 else table2_leg(nb, torch, I)

@@ -80,8 +80,12 @@ class TrainConfig:
 class Trainer:
     """Adam over a fixed list of batches, one optimiser step per batch."""
 
-    def __init__(self, model: nb.Model, batches, cfg: TrainConfig | None = None):
+    def __init__(self, model: nb.Model, batches, cfg: TrainConfig | None = None, allreduce=None):
+        """allreduce(grad, loss), if given, combines the ranks' gradients and
+        losses in place between nep_param_grad and the Adam step (data
+        parallelism, see dp.allreduce_mean)."""
         import torch
+        self.allreduce = allreduce
         self.model = model
         self.batches = list(batches)
         self.cfg = cfg or TrainConfig()
@@ -102,6 +106,8 @@ class Trainer:
         w = loss_weights(lr, c.lr_start, c.w_start, c.w_end, c.weight_factor)
         nb.param_grad(self.model, batch.dsys, batch.nl, batch.ws, batch.e_lbl, batch.f_lbl, batch.v_lbl,
                       w, c.loss_mode, grad=self.grad, loss=self.loss, stream=stream)
+        if self.allreduce is not None:
+            self.allreduce(self.grad, self.loss)
         self.t += 1
         nb.adam_step(self.model, self.grad, self.m1, self.m2, self.t, lr, c.beta1, c.beta2, c.eps,
                      stream=stream)
