@@ -130,9 +130,9 @@ def algorithmic_flops(h, nbar_rad: float, nbar_ang: float) -> dict:
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the 460,800-atom
 # case of this workload (40^3 cells), divided by its atom count; traffic grows
 # in proportion to the atoms.  Valid only for the kernels as captured.
-TRAFFIC_PER_ATOM = {"radial": (223.652096e6 + 139.176960e6) / 460800,
-                    "angular": (293.204992e6 + 218.010880e6) / 460800,
-                    "finish": (423.694080e6 + 29.356800e6) / 460800}
+TRAFFIC_PER_ATOM = {"radial": (238.608640e6 + 188.353792e6) / 460800,
+                    "angular": (287.219968e6 + 214.080000e6) / 460800,
+                    "finish": (387.855616e6 + 21.186816e6) / 460800}
 
 
 def launches_per_step(rebuild: bool) -> int:
