@@ -14,7 +14,8 @@
 //   k_finish   radial pair forces of both directions of every pair from the
 //              species-projected adjoints, plus the scattered angular forces,
 //              give F_i (Eq. 3); per-atom virials (Eq. 4) and energies are
-//              summed in FP64 per chunk of atoms in a fixed order.
+//              summed per chunk of atoms in a fixed order (two-sum FP32 pairs
+//              inside a warp, FP64 across warps and chunks).
 // In mixed precision k_angular_tc (nep_mlp_tc.cuh) takes k_angular's place
 // with the network on the tensor cores.
 #pragma once

@@ -83,9 +83,21 @@ __global__ void k_chunk_plan(const int* __restrict__ atom_off, int B, int* chunk
 
 constexpr int kRedThreads = 256;
 
-// one CTA per reduction chunk (atoms of one configuration): FP64 sums of the
-// energies and per-atom virials, each thread over a fixed atom subset, then a
-// fixed tree
+// (hi, lo) += x without rounding loss: Knuth's two-sum, in FP32.  The pair
+// carries about 48 significant bits, so the per-thread and per-warp stages
+// below are as exact as FP64 while running on the FP32 pipes (GB300 issues
+// FP64 at a small fraction of the FP32 rate).
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float x) {
+    const float s = __fadd_rn(hi, x);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+    hi = s;
+    lo = __fadd_rn(lo, err);
+}
+
+// one CTA per reduction chunk (atoms of one configuration): sums of the
+// energies and per-atom virials, each thread over a fixed atom subset in
+// two-sum pairs, a fixed warp tree of pairs, then FP64 across the warps
 __global__ void __launch_bounds__(kRedThreads) k_chunk_reduce(const EvalArgs a, FinishArgs f) {
     const int k = blockIdx.x;
     const int B = a.B, N = a.N;
@@ -94,14 +106,49 @@ __global__ void __launch_bounds__(kRedThreads) k_chunk_reduce(const EvalArgs a, 
     const int b = find_segment(f.chunk_start, B, k);
     const int a0 = f.atom_off[b] + (k - f.chunk_start[b]) * kChunk;
     const int a1 = min(f.atom_off[b + 1], a0 + kChunk);
+    float hi[10], lo[10];
+#pragma unroll
+    for (int c = 0; c < 10; ++c) hi[c] = lo[c] = 0.0f;
+    for (int i = a0 + threadIdx.x; i < a1; i += kRedThreads) {
+        two_sum_add(hi[0], lo[0], a.e_atom[i]);
+#pragma unroll
+        for (int c = 0; c < 9; ++c) two_sum_add(hi[1 + c], lo[1 + c], a.wat[(size_t)c * N + i]);
+    }
+    __shared__ double red[10][kRedThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < 10; ++c) {
+        float h = hi[c], l = lo[c];
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_down_sync(0xffffffffu, h, o);
+            const float ol = __shfl_down_sync(0xffffffffu, l, o);
+            two_sum_add(h, l, oh);
+            l = __fadd_rn(l, ol);
+        }
+        if (lane == 0) red[c][w] = (double)h + (double)l;
+    }
+    __syncthreads();
+    if (threadIdx.x < 10) {
+        double v = 0.0;
+        for (int q = 0; q < kRedThreads / 32; ++q) v += red[threadIdx.x][q];
+        f.partial[(size_t)k * 10 + threadIdx.x] = v;
+    }
+}
+
+// one block per configuration: threads take chunk partials k = t, t+256, ...
+// and a fixed tree (warp shuffles, then the 8 warp sums in order) combines
+// them, so the sum order never changes
+__global__ void __launch_bounds__(kRedThreads) k_final_reduce(int B, const int* __restrict__ chunk_start,
+                                                              const double* __restrict__ partial,
+                                                              double* e_tot, double* virial) {
+    const int b = blockIdx.x;
+    if (b >= B) return;
     double acc[10];
 #pragma unroll
     for (int c = 0; c < 10; ++c) acc[c] = 0.0;
-    for (int i = a0 + threadIdx.x; i < a1; i += kRedThreads) {
-        acc[0] += (double)a.e_atom[i];
+    for (int k = chunk_start[b] + threadIdx.x; k < chunk_start[b + 1]; k += kRedThreads)
 #pragma unroll
-        for (int c = 0; c < 9; ++c) acc[1 + c] += (double)a.wat[(size_t)c * N + i];
-    }
+        for (int c = 0; c < 10; ++c) acc[c] += partial[(size_t)k * 10 + c];
     __shared__ double red[10][kRedThreads / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
@@ -114,39 +161,11 @@ __global__ void __launch_bounds__(kRedThreads) k_chunk_reduce(const EvalArgs a, 
     if (threadIdx.x < 10) {
         double v = 0.0;
         for (int q = 0; q < kRedThreads / 32; ++q) v += red[threadIdx.x][q];
-        f.partial[(size_t)k * 10 + threadIdx.x] = v;
-    }
-}
-
-// one block per configuration: threads take chunk partials k = t, t+256, ...
-// and a fixed tree combines them, so the sum order never changes
-__global__ void __launch_bounds__(kRedThreads) k_final_reduce(int B, const int* __restrict__ chunk_start,
-                                                              const double* __restrict__ partial,
-                                                              double* e_tot, double* virial) {
-    const int b = blockIdx.x;
-    if (b >= B) return;
-    double acc[10];
-#pragma unroll
-    for (int c = 0; c < 10; ++c) acc[c] = 0.0;
-    for (int k = chunk_start[b] + threadIdx.x; k < chunk_start[b + 1]; k += kRedThreads)
-#pragma unroll
-        for (int c = 0; c < 10; ++c) acc[c] += partial[(size_t)k * 10 + c];
-    __shared__ double red[kRedThreads];
-    for (int c = 0; c < 10; ++c) {
-        red[threadIdx.x] = acc[c];
-        __syncthreads();
-        for (int o = kRedThreads / 2; o > 0; o >>= 1) {
-            if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-            __syncthreads();
-        }
         if (threadIdx.x == 0) {
-            if (c == 0) {
-                if (e_tot) e_tot[b] = red[0];
-            } else if (virial) {
-                virial[(size_t)b * 9 + c - 1] = red[0];
-            }
+            if (e_tot) e_tot[b] = v;
+        } else if (virial) {
+            virial[(size_t)b * 9 + threadIdx.x - 1] = v;
         }
-        __syncthreads();
     }
 }
 
