@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision leg")
     ap.add_argument("--no-replicas", action="store_true", help="skip the batched-replica leg")
     ap.add_argument("--no-table2", action="store_true", help="skip the paper-model size sweep")
+    ap.add_argument("--no-fig3", action="store_true", help="skip the training-operator size sweep")
     ap.add_argument("--ncell", type=int, default=50,
                     help="rock-salt cells per edge (50 = the 900k-atom workload; smaller for profiling)")
     return ap.parse_args()
@@ -173,13 +174,61 @@ def run_oracle_sample(ncell: int, nsteps: int) -> dict:
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
+# the Fig. 3 size sweep: one random-occupation rock-salt GST cell of n^3
+# conventional cells (Te anions, cations Ge:Sb:vacancy 2:2:1) per size
+FIG3_NCELL = (2, 3, 4, 5)
+
+
 def cpu_baseline() -> dict:
     d = run_oracle_sample(5, 10)
     v = d["atoms"] * d["steps"] / d["seconds"]
+    # oracle E+F+V per configuration at the Fig. 3 sizes (the CPU side of that
+    # sweep; the oracle has no analytic gradient, so this is its forward pass)
+    fig3 = {}
+    for n in FIG3_NCELL:
+        f = run_oracle_sample(n, 3)
+        fig3[str(f["atoms"])] = 1e3 * f["seconds"] / f["steps"]
     return {"value": v, "unit": "atom-steps/s", "cores": 1, "kind": "oracle",
             "sample": f"FP64 numpy oracle, one thread: 10 MD-step force evaluations (list rebuilt "
                       f"once) of a {d['atoms']}-atom 5^3-cell periodic sample of the same rock-salt "
-                      f"structure and model, {d['seconds']:.1f} s"}
+                      f"structure and model, {d['seconds']:.1f} s",
+            "fig3_forward_ms_per_config": fig3}
+
+
+def fig3_leg(nb, torch, I) -> dict:
+    """The training-operator size sweep of the paper's Fig. 3 on the GPU: one
+    random-occupation GST cell per size, loss and gradient of all parameters
+    (nep_param_grad), labels from the seed-2 teacher."""
+    h = I.HYPER_SMALL
+    model = nb.Model(h, I.init_params(h).astype(np.float32))
+    teacher = nb.Model(h, I.init_params(h, seed=I.SEED_TEACHER).astype(np.float32))
+    out = {}
+    for n in FIG3_NCELL:
+        s = I.rocksalt(n, vacancy=0.2, tag=1)
+        d = nb.DeviceSystem.from_inputs(s)
+        nl = nb.NeighborList(s.n_atoms, 160, 80)
+        ws = nb.Workspace(model, s.n_atoms, 1, 160, 80, train=True)
+        nb.neighbors(model, d, nl, 0.0, ws)
+        _, F, E, V = nb.energy_forces_virial(teacher, d, nl, ws)
+        F = F.contiguous()
+        grad = torch.empty(model.n_params, dtype=torch.float32, device="cuda")
+        loss = torch.empty(1, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            nb.param_grad(model, d, nl, ws, E, F, V, (1.0, 1.0, 0.1), 0, grad, loss)
+        torch.cuda.synchronize()
+        K = 50
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(K):
+            nb.param_grad(model, d, nl, ws, E, F, V, (1.0, 1.0, 0.1), 0, grad, loss)
+        t1.record()
+        torch.cuda.synchronize()
+        if nb.check_list(nl) != nb.NEP_OK:
+            raise RuntimeError(nb.last_error())
+        out[str(s.n_atoms)] = t0.elapsed_time(t1) / K
+    return {"workload": "fig3: one random-occupation rock-salt GST cell (2^3..5^3 conventional cells), "
+                        "loss + gradient of 4,611 parameters per call, FP32",
+            "gpu_ms_per_config": out}
 
 
 def reference_arm(args, rank: int) -> None:
@@ -687,10 +736,17 @@ def main():
     mixed = None if args.no_mixed else mixed_leg(nb, torch, I)
     replicas = None if args.no_replicas else replicas_leg(nb, torch, I)
     table2 = None if args.no_table2 else table2_leg(nb, torch, I)
+    fig3 = None if args.no_fig3 else fig3_leg(nb, torch, I)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
+        if fig3 is not None:
+            # GPU training operator against the oracle's forward pass, per size
+            fig3["oracle_forward_ms_per_config"] = cpu["fig3_forward_ms_per_config"]
+            fig3["ratio_oracle_forward_to_gpu_train_op"] = {
+                k: cpu["fig3_forward_ms_per_config"][k] / v for k, v in fig3["gpu_ms_per_config"].items()
+                if k in cpu["fig3_forward_ms_per_config"]}
 
     launches = sum(launches_per_step(k % REBUILD == 0) for k in range(K))
     if rank == 0:
@@ -705,7 +761,7 @@ def main():
                 "e2e": {"value": e2e_val, "unit": "atom-steps/s", "steps": KE,
                         "h2d_bytes_per_step": 24 * N, "d2h_bytes_per_step": 36 * N + 8 + 72},
                 "gpu_launches": launches, "clocks": clk, "train": train, "mixed": mixed, "replicas": replicas,
-                "table2": table2,
+                "table2": table2, "fig3": fig3,
                 "energy": {"e_tot_final": float(e_tot.item())}}
         print(json.dumps(line), flush=True)
     if world > 1:
