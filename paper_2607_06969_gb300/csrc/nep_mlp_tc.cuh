@@ -10,7 +10,9 @@
 //      budgets, whose CTAs cannot all hold it in TMEM);
 //   2. the 128 q rows are written to shared memory in species order, one
 //      16-bit row each, as the A operand (M = 128, K = D padded to 16);
-//   3. GEMM1, once per species s present in the tile:
+//   3. GEMM1, one MMA over the stacked species Z[128 x T Hp] = Q W^T when its
+//      accumulator fits beside S in tensor memory, else once per species s
+//      present in the tile:
 //        Z_s[128 x Hp] = Q[128 x Kp] W0_s^T      (accumulator in TMEM)
 //      the threads whose row has species s read their row of Z_s (their own
 //      TMEM lane), form tanh, the energy and g = w1 (1 - t^2) (registers);
@@ -39,6 +41,7 @@ struct Tc5Dims {
 
 struct Tc5Layout {
     int Hp, NTp, accC, sCol, cols;                  // TMEM: accumulators at 0, S at sCol
+    int single;                                     // GEMM1 for all species at once
     int coef, B1, B2, b0, w1, b1, U, wcnt, rowA, rowS, bar, slot;   // byte offsets
     int total;
 };
@@ -52,9 +55,15 @@ NEP_HD Tc5Layout tc5_layout(int H, bool s_in_tmem) {
     Tc5Layout L;
     L.Hp = (H + 15) / 16 * 16;
     L.NTp = C::T * L.Hp;
-    L.accC = L.Hp > Kp ? L.Hp : Kp;
+    // one GEMM1 over the stacked species when its NTp accumulator columns fit
+    // beside S in the 256 columns a CTA may hold (two CTAs per SM), else one
+    // GEMM1 of Hp columns per species
+    const int sCols = s_in_tmem ? C::NA * kLM : 0;
+    const int accAll = L.NTp > Kp ? L.NTp : Kp;
+    L.single = (L.NTp <= 256 && accAll + sCols <= 256) ? 1 : 0;
+    L.accC = L.single ? accAll : (L.Hp > Kp ? L.Hp : Kp);
     L.sCol = L.accC;
-    L.cols = (int)tc5::tmem_cols(s_in_tmem ? L.accC + C::NA * kLM : L.accC);
+    L.cols = (int)tc5::tmem_cols(L.accC + sCols);
     auto al = [](int x) { return (x + 127) / 128 * 128; };
     int o = 0;
     L.coef = o; o = al(o + 4 * smem_layout<C>(H).W0);     // cA and cR blocks of the FP32 image
@@ -167,7 +176,8 @@ __global__ void __launch_bounds__(kBlock, MINB) k_angular_tc(const EvalArgs a) {
     const uint32_t tbase = *slot;
     const uint32_t tlane = tc5::lane_addr(tbase, warp, 0);       // this thread's lane, column 0
     const uint32_t uA = tc5::smem_addr(U), uB1 = tc5::smem_addr(B1), uB2 = tc5::smem_addr(B2);
-    const uint32_t id1 = tc5::idesc_f16(128, Hp, BF), id2 = tc5::idesc_f16(128, Kp, BF);
+    const bool single = L.single != 0;
+    const uint32_t id1 = tc5::idesc_f16(128, single ? NTp : Hp, BF), id2 = tc5::idesc_f16(128, Kp, BF);
     uint32_t phase = 0;
     bool ok = true;
 
@@ -256,27 +266,33 @@ __global__ void __launch_bounds__(kBlock, MINB) k_angular_tc(const EvalArgs a) {
         unsigned g2[kTcMaxH / 2];      // packed g of the own species (Hp <= kTcMaxH)
 #pragma unroll
         for (int c = 0; c < kTcMaxH / 2; ++c) g2[c] = 0u;
+        bool issued = false;
         for (int s = 0; s < T; ++s) {
             if (tot[s] == 0) continue;
-            if (tid == 0) {
-                for (int ks = 0; ks < Kp / 16; ++ks)
-                    tc5::mma_f16(tbase, tc5::smem_desc(uA + ks * 256, 128, Kp * 16),
-                                 tc5::smem_desc(uB1 + (uint32_t)(s * Hp * Kp * 2) + ks * 256, 128, Kp * 16), id1,
-                                 ks > 0);
-                tc5::commit(bar);
+            if (!single || !issued) {
+                issued = true;
+                // single: B = all T Hp rows of W0, once per tile; else species s's Hp rows
+                if (tid == 0) {
+                    const uint32_t b0 = single ? 0u : (uint32_t)(s * Hp * Kp * 2);
+                    for (int ks = 0; ks < Kp / 16; ++ks)
+                        tc5::mma_f16(tbase, tc5::smem_desc(uA + ks * 256, 128, Kp * 16),
+                                     tc5::smem_desc(uB1 + b0 + ks * 256, 128, Kp * 16), id1, ks > 0);
+                    tc5::commit(bar);
+                }
+                const bool got = tc5::mbar_wait(bar, phase, kMbarPolls);
+                phase ^= 1u;
+                if (!__syncthreads_and(got)) {
+                    ok = false;
+                    break;
+                }
+                tc5::fence_after();
             }
-            const bool got = tc5::mbar_wait(bar, phase, kMbarPolls);
-            phase ^= 1u;
-            if (!__syncthreads_and(got)) {
-                ok = false;
-                break;
-            }
-            tc5::fence_after();
+            const int zc = single ? s * Hp : 0;          // species s's first accumulator column
             if (__ballot_sync(0xffffffffu, rs == s) != 0u) {
                 for (int c = 0; c < Hp; c += 16) {
                     float z[16];
                     __syncwarp();
-                    tc5::ld16(tlane + c, z);
+                    tc5::ld16(tlane + zc + c, z);
                     tc5::wait_ld();
                     if (rs == s) {
 #pragma unroll
@@ -292,11 +308,18 @@ __global__ void __launch_bounds__(kBlock, MINB) k_angular_tc(const EvalArgs a) {
                     }
                 }
             }
-            tc5::fence_before();
-            __syncthreads();             // every read of this species' Z is done before the next GEMM1
-            tc5::fence_after();
+            if (!single) {
+                tc5::fence_before();
+                __syncthreads();         // every read of this species' Z is done before the next GEMM1
+                tc5::fence_after();
+            }
         }
         if (!ok) break;
+        if (single) {
+            tc5::fence_before();
+            __syncthreads();             // every read of Z is done before GEMM2 reuses the columns
+            tc5::fence_after();
+        }
         if (rs < T) a.e_atom[tile * kBlock + rowA[tid]] = E + b1s[rs];
 
         // 4. stacked G rows (Q is no longer read), then GEMM2
