@@ -118,6 +118,32 @@ class Trainer:
     def epoch(self, stream=None) -> float:
         return float(np.mean([self.step(b, stream) for b in self.batches]))
 
+    # --- checkpoint / resume --------------------------------------------------
+    def state_dict(self) -> dict:
+        """Everything a resumed run needs: parameters, Adam moments, the step
+        counter (which also fixes the learning rate and loss weights)."""
+        return {"params": self.model.get_params().cpu().numpy().copy(),
+                "m1": self.m1.cpu().numpy().copy(), "m2": self.m2.cpu().numpy().copy(),
+                "t": self.t, "total": self.total, "warmup": self.warmup}
+
+    def load_state_dict(self, st: dict) -> None:
+        import torch
+        if st["params"].size != self.model.n_params:
+            raise ValueError("checkpoint has %d parameters, the model %d" % (st["params"].size,
+                                                                               self.model.n_params))
+        self.model.set_params(torch.tensor(np.asarray(st["params"], np.float32), device="cuda"))
+        self.m1.copy_(torch.tensor(np.asarray(st["m1"], np.float32)))
+        self.m2.copy_(torch.tensor(np.asarray(st["m2"], np.float32)))
+        self.t, self.total, self.warmup = int(st["t"]), int(st["total"]), int(st["warmup"])
+        torch.cuda.synchronize()
+
+    def save(self, path: str) -> None:
+        np.savez(path, **{k: np.asarray(v) for k, v in self.state_dict().items()})
+
+    def load(self, path: str) -> None:
+        with np.load(path) as z:
+            self.load_state_dict({k: z[k] for k in z.files})
+
 
 def make_batch(model: nb.Model, s, e_lbl, f_lbl, v_lbl, cap: int = 112, cap_ang: int = 56) -> Batch:
     """Device batch for the System `s` with host labels (E [B], F [N,3], V [B,9])."""

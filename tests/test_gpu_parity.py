@@ -253,3 +253,42 @@ def test_autotune_variants_agree(nb):
     assert np.abs(f.cpu().numpy().T - g["F"]).max() <= 1e-5
     assert_parity(dict(E=e.cpu().numpy(), F=f.cpu().numpy().T, Etot=et.cpu().numpy(),
                        V=v.cpu().numpy().reshape(-1, 3, 3), status=0), oracle_eval(h, th, s), s)
+
+
+def test_graph_captured_md_matches_eager(nb):
+    """Velocity-Verlet steps (with a rebuild) captured in one CUDA graph give
+    the same bits as the same calls launched one by one."""
+    import torch
+    h = I.HYPER_SMALL
+    s = I.packing_batch([57, 100, 250], tag=69)
+    th = I.init_params(h).astype(np.float32)
+    masses = I.MASSES.astype(np.float32)
+    vel0 = np.ascontiguousarray(I.maxwell_boltzmann(s.types, 900.0, atom_off=s.atom_off).astype(np.float32).T)
+
+    def run(graph):
+        model = nb.Model(h, th)
+        dsys = nb.DeviceSystem.from_inputs(s)
+        nl = nb.NeighborList(s.n_atoms, 160, 64)
+        ws = nb.Workspace(model, s.n_atoms, s.n_cfg, 160, 64)
+        nb.neighbors(model, dsys, nl, 1.0, ws)
+        e, f, et, v = nb.energy_forces_virial(model, dsys, nl, ws)
+        vel = torch.from_numpy(vel0.copy()).cuda()
+        st = torch.cuda.Stream()
+        torch.cuda.synchronize()
+        steps = lambda: [nb.md_step(model, dsys, nl, vel, f, et, v, masses, 2.0, 1.0, k % 10 == 0, ws, stream=st)
+                         for k in range(12)]
+        if graph:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=st):
+                steps()
+            g.replay()
+        else:
+            with torch.cuda.stream(st):
+                steps()
+        torch.cuda.synchronize()
+        assert nb.check_list(nl) == nb.NEP_OK
+        return dsys.pos.cpu(), vel.cpu(), f.cpu(), et.cpu(), v.cpu()
+
+    a, b = run(False), run(True)
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)

@@ -152,3 +152,37 @@ def test_fit_student_to_teacher(nb):
     assert lrs[0] == pytest.approx(3e-3 * 1e-4)
     assert lrs[1] == pytest.approx(3e-3)
     assert lrs[-1] == pytest.approx(T.lr_at(149, 3e-3, 3e-5, 1, 150))
+
+
+@pytest.mark.gpu
+def test_checkpoint_resume_is_bit_identical(nb, tmp_path):
+    """20 steps straight, or 10 steps, a checkpoint on disk, a fresh model and
+    trainer restored from it, and 10 more steps: the same parameters."""
+    h = I.HYPER_SMALL
+    s = I.packing_batch([24, 40, 33], tag=97)
+    p32 = s.pos32()
+    pairs = O.neighbor_pairs(p32, s.box, s.atom_off, h.rc_rad)
+    teacher = I.init_params(h, seed=I.SEED_TEACHER).astype(np.float32).astype(np.float64)
+    lab = O.energy_forces_virial(h, teacher, p32.astype(np.float64), s.types,
+                                 s.box.astype(np.float32).astype(np.float64), s.atom_off, pairs)
+    th = I.init_params(h).astype(np.float32)
+
+    def trainer():
+        model = nb.Model(h, th)
+        batch = T.make_batch(model, s, lab["Etot"], lab["F"], lab["V"].reshape(-1, 9))
+        return T.Trainer(model, [batch], T.TrainConfig(lr_start=3e-3, lr_end=3e-5, epochs=20)), batch
+
+    a, ba = trainer()
+    for _ in range(20):
+        a.step(ba)
+    b, bb = trainer()
+    for _ in range(10):
+        b.step(bb)
+    path = str(tmp_path / "ckpt.npz")
+    b.save(path)
+    c, bc = trainer()
+    c.load(path)
+    for _ in range(10):
+        c.step(bc)
+    assert np.array_equal(a.model.get_params().cpu().numpy(), c.model.get_params().cpu().numpy())
+    assert c.t == 20
