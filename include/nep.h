@@ -268,12 +268,13 @@ nep_status nep_autotune(nep_model* m, const nep_system* sys, const nep_nlist* nl
 nep_status nep_set_variant(nep_model* m, int size_class, int variant);
 
 /* Profiling hook: the next nep_energy_forces_virial / nep_md_step call of
- * this model records events[0] before the radial-descriptor kernel,
- * events[1] after it, events[2] after the angular kernel(s) (descriptor,
- * network and angular pair forces) and events[3] after the kernel that
- * completes the forces, on the call's stream (events are caller-created
- * cudaEvent_t, n = 4; n = 0 clears).  One-shot: the events are forgotten after that call.  The
- * records are ordinary stream work and can be captured into a CUDA graph. */
+ * this model records events[0] before the radial kernel (radial sums,
+ * angular pair compaction), events[1] after it, events[2] after the angular
+ * kernel (angular descriptors, network, angular pair forces) and events[3]
+ * after the kernel that completes the forces, on the call's stream (events
+ * are caller-created cudaEvent_t, n = 4; n = 0 clears).  One-shot: the
+ * events are forgotten after that call.  The records are ordinary stream work
+ * and can be captured into a CUDA graph. */
 nep_status nep_set_timing_events(nep_model* m, void* const* events, int n);
 
 /* Measurement helper, not part of the NEP path: the FP32 FMA throughput of

@@ -23,8 +23,7 @@ struct nep_model {
     cudaEvent_t timing[4];
     int n_timing;
     // autotuned kernel variants per size class (-1: default)
-    int tune_desc[nep::kSizeBins];
-    int tune_force[nep::kSizeBins];
+    int tune_angular[nep::kSizeBins];   // angular kernel variant per size class, -1 = default
 };
 
 namespace {
@@ -214,10 +213,9 @@ int size_bin(const nep_system* s) {
     return b;
 }
 
-void variants_for(const nep_model* m, const nep_system* s, int* vd, int* vf) {
+int angular_variant(const nep_model* m, const nep_system* s) {
     const int b = size_bin(s);
-    *vd = m->tune_desc[b] >= 0 ? m->tune_desc[b] : nep::kDefaultDescVariant;
-    *vf = m->tune_force[b] >= 0 ? m->tune_force[b] : nep::kDefaultForceVariant;
+    return m->tune_angular[b] >= 0 ? m->tune_angular[b] : nep::kDefaultAngularVariant;
 }
 
 nep::EvalArgs make_args(const nep_model* m, const nep_system* s, const nep_nlist* nl, void* work,
@@ -286,8 +284,7 @@ nep_status efv_impl(nep_model* m, const nep_system* s, const nep_nlist* nl, floa
              "pack");
     NEP_CUDA(nep::launch_chunk_plan(s->atom_off, B, at<int>(work, w.chunk_start), st), "chunk plan");
     const nep::EvalArgs a = make_args(m, s, nl, work, w);
-    int vd, vf;
-    variants_for(m, s, &vd, &vf);
+    const int vd = angular_variant(m, s);
     const int nt = m->n_timing;
     m->n_timing = 0;
     // inside stream capture an event record must be marked external to become
@@ -335,8 +332,7 @@ nep_status train_impl(nep_model* m, const nep_system* s, const nep_nlist* nl, co
     a.q_out = at<float>(work, tl.q);
     a.p_out = at<float>(work, tl.p);
     a.fb_out = a.fb;
-    int vd, vf;
-    variants_for(m, s, &vd, &vf);
+    const int vd = angular_variant(m, s);
     if (N > 0) NEP_CUDA(m->ks->radial(a, st), "radial kernel");
     if (N > 0) NEP_CUDA(m->ks->angular(a, st, vd), "angular kernel");
     if (e_lbl) {
@@ -475,7 +471,7 @@ nep_status nep_create(const nep_hparams* hp, const float* params_host, size_t n_
                                hp->has_4body, hp->n_hidden);
     cudaGetDevice(&m->device);
     m->n_timing = 0;
-    for (int b = 0; b < nep::kSizeBins; ++b) m->tune_desc[b] = m->tune_force[b] = -1;
+    for (int b = 0; b < nep::kSizeBins; ++b) m->tune_angular[b] = -1;
     cudaError_t e = ks->init(hp->n_hidden);
     if (e == cudaSuccess) e = ks->train_init(hp->n_hidden);
     if (e != cudaSuccess) {
@@ -708,7 +704,7 @@ nep_status nep_set_variant(nep_model* m, int size_class, int variant) {
     if (variant < -1 || variant >= nep::kVariants)
         return fail(NEP_ERR_ARG, "variant must be -1 or 0..%d", nep::kVariants - 1);
     for (int b = 0; b < nep::kSizeBins; ++b)
-        if (size_class < 0 || b == size_class) m->tune_desc[b] = variant;
+        if (size_class < 0 || b == size_class) m->tune_angular[b] = variant;
     return NEP_OK;
 }
 
@@ -730,8 +726,8 @@ nep_status nep_autotune(nep_model* m, const nep_system* sys, const nep_nlist* nl
     cudaEvent_t e0, e1;
     NEP_CUDA(cudaEventCreate(&e0), "event");
     NEP_CUDA(cudaEventCreate(&e1), "event");
-    float best_d = 1e30f, best_f = 1e30f;
-    int vd = nep::kDefaultDescVariant, vf = nep::kDefaultForceVariant;
+    float best_d = 1e30f;
+    int vd = nep::kDefaultAngularVariant;
     // time the angular kernel variants (the one register-heavy kernel)
     NEP_CUDA(m->ks->radial(a, st), "radial kernel");
     for (int v = 0; v < nep::kVariants && N > 0; ++v) {
@@ -753,15 +749,13 @@ nep_status nep_autotune(nep_model* m, const nep_system* sys, const nep_nlist* nl
         }
         if (tmin < best_d) best_d = tmin, vd = v;
     }
-    (void)best_f;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     const int b = size_bin(sys);
-    m->tune_desc[b] = vd;
-    m->tune_force[b] = vf;
+    m->tune_angular[b] = vd;
     if (chosen) {
         chosen[0] = vd;
-        chosen[1] = vf;
+        chosen[1] = 0;   // reserved
     }
     return NEP_OK;
 }

@@ -722,7 +722,7 @@ NEP_HD void radial_force_atom(const EvalArgs& a, int i, float& Fx, float& Fy, fl
         Wr[3] = fmaf(wx, dy, Wr[3]); Wr[4] = fmaf(wx, dz, Wr[4]); Wr[5] = fmaf(wy, dz, Wr[5]);
     };
     if (a.compr) {
-        // pairs inside rc_rad, compacted by the radial-descriptor kernel
+        // pairs inside rc_rad, compacted by the radial kernel
         const int ncr = a.cnt_compr[i];
         float4 q_nx = ncr > 0 ? a.compr[i] : make_float4(1.0f, 0.0f, 0.0f, 0.0f);
         for (int s = 0; s < ncr; ++s) {
@@ -808,8 +808,9 @@ NEP_HD void radial_force_atom(const EvalArgs& a, int i, float& Fx, float& Fy, fl
 }
 
 // F_i = radial part + angular owner part - sum of the scattered incoming
-// angular pair forces (subtracted inside radial_force_atom); the per-atom virial (angular owner part minus the
-// radial part) is written back for the FP64 reduction
+// angular pair forces (subtracted inside radial_force_atom); the per-atom
+// virial (angular owner part minus the radial part) is written back for the
+// per-configuration reduction
 template <class C, bool MINIMG>
 NEP_HD void finish_atom(const EvalArgs& a, int i, float* force, float* e_out, float4* stage = nullptr,
                         int nthr = 0) {

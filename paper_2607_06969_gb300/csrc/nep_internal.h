@@ -20,9 +20,8 @@ constexpr int kMaxTypes = 4;
 constexpr int kLM = 24;          // real solid harmonics for l = 1..4: 3+5+7+9
 constexpr int kChunk = 1024;     // atoms per reduction chunk (one CTA)
 constexpr int kBlock = 128;      // threads per block of the per-atom kernels
-constexpr int kVariants = 3;              // register budgets for 2, 3, 4 blocks per SM
-constexpr int kDefaultDescVariant = 0;    // fused angular kernel: 2 blocks per SM
-constexpr int kDefaultForceVariant = 0;   // reserved
+constexpr int kVariants = 3;              // angular kernel register budgets: 2, 3, 4 blocks per SM
+constexpr int kDefaultAngularVariant = 0; // 2 blocks per SM, S_nlm in tensor memory
 constexpr int kSizeBins = 32;             // tuning table: log2 of mean atoms per configuration
 
 // Stencil/cell plan of one configuration for the neighbour build.
@@ -67,7 +66,7 @@ struct EvalArgs {
     int* status;                   // [4] flags (may be null)
     // network precision: 0 FP32 (CUDA cores), 1 FP16, 2 BF16 (tensor cores)
     int q16_kind;
-    // training outputs of the descriptor kernel (null when not training)
+    // training outputs of the angular kernel (null when not training)
     float* q_out;                  // [D][N]          descriptors
     float* p_out;                  // [D][N]          dE/dq
     float* fb_out;                 // [T*KR][N]       species-resolved radial basis sums
