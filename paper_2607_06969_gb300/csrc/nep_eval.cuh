@@ -166,7 +166,7 @@ struct NbrStream {
 };
 
 #ifndef NEP_RADIAL_DEPTH
-#define NEP_RADIAL_DEPTH 2
+#define NEP_RADIAL_DEPTH 1
 #endif
 #ifndef NEP_FINISH_DEPTH
 #define NEP_FINISH_DEPTH 1
@@ -841,7 +841,7 @@ constexpr int kRadialBlock = 256;
 constexpr int kFinishThreads = 128;
 
 #ifndef NEP_RADIAL_MINB
-#define NEP_RADIAL_MINB 3
+#define NEP_RADIAL_MINB 4
 #endif
 #ifndef NEP_FINISH_MINB
 #define NEP_FINISH_MINB 8
