@@ -283,6 +283,14 @@ nep_status nep_set_timing_events(nep_model* m, void* const* events, int n);
  * FMA per second / 1e12. */
 nep_status nep_fp32_peak(void* stream, double* tflops);
 
+/* Self-test of the bounded tensor-core completion wait, not part of the NEP
+ * path: one CTA allocates tensor memory, waits on an mbarrier that nothing
+ * arrives at with a short poll limit, records the timeout in a device flag,
+ * frees its columns and returns; the host reads the flag.  Returns
+ * NEP_ERR_TIMEOUT when the wait ran out as designed (the CUDA context stays
+ * usable), NEP_OK if the wait completed, or a CUDA error.  Synchronises. */
+nep_status nep_selftest_wait_timeout(void* stream);
+
 /* Synchronise `stream` and map the list's device flags to a status:
  * NEP_ERR_CAPACITY (status[0]), NEP_ERR_TIMEOUT (status[3] bit 1),
  * NEP_ERR_INPUT (status[3] bit 0) or NEP_OK.

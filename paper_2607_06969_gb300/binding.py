@@ -23,7 +23,7 @@ ENTRY_POINTS = (
     "nep_workspace_bytes", "nep_train_workspace_bytes", "nep_neighbors", "nep_energy_forces_virial",
     "nep_energy_forces_virial_noalloc", "nep_param_grad",
     "nep_param_grad_adjoint", "nep_adam_step", "nep_md_step", "nep_autotune", "nep_set_variant",
-    "nep_set_timing_events", "nep_fp32_peak",
+    "nep_set_timing_events", "nep_fp32_peak", "nep_selftest_wait_timeout",
     "nep_check",
     "nep_last_error", "nep_version",
 )
@@ -91,6 +91,8 @@ def lib() -> ctypes.CDLL:
     L.nep_set_variant.argtypes = [vp, i, i]
     L.nep_fp32_peak.argtypes = [vp, P(ctypes.c_double)]
     L.nep_fp32_peak.restype = i
+    L.nep_selftest_wait_timeout.argtypes = [vp]
+    L.nep_selftest_wait_timeout.restype = i
     L.nep_set_variant.restype = i
     L.nep_last_error.restype = ctypes.c_char_p
     L.nep_version.restype = ctypes.c_char_p
@@ -380,6 +382,12 @@ def fp32_peak(stream=None) -> float:
     out = ctypes.c_double()
     check(lib().nep_fp32_peak(_stream(stream), ctypes.byref(out)), "nep_fp32_peak")
     return float(out.value)
+
+
+def selftest_wait_timeout(stream=None) -> int:
+    """nep_selftest_wait_timeout: the status of a bounded tensor-core wait
+    that is made to run out (NEP_ERR_TIMEOUT when it works as designed)."""
+    return int(lib().nep_selftest_wait_timeout(_stream(stream)))
 
 
 def check_list(nl: NeighborList | None, stream=None) -> int:

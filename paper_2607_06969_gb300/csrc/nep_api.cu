@@ -691,6 +691,13 @@ nep_status nep_adam_step(nep_model* m, const float* grad, float* m1, float* m2, 
     return NEP_OK;
 }
 
+nep_status nep_selftest_wait_timeout(void* stream) {
+    int outcome = 0;
+    NEP_CUDA(nep::wait_selftest((cudaStream_t)stream, &outcome), "wait self-test");
+    if (outcome & 2) return fail(NEP_ERR_TIMEOUT, "the self-test wait ran out of its poll limit, as designed");
+    return NEP_OK;
+}
+
 nep_status nep_fp32_peak(void* stream, double* tflops) {
     if (!tflops) return fail(NEP_ERR_ARG, "tflops is NULL");
     NEP_CUDA(nep::fp32_peak((cudaStream_t)stream, tflops), "FP32 peak kernel");

@@ -161,6 +161,7 @@ cudaError_t launch_neighbors(const float* pos, const float4* pos4, const int* at
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int n, float beta1, float beta2,
                         float eps, float c1, float c2, cudaStream_t st);
 cudaError_t fp32_peak(cudaStream_t st, double* tflops);
+cudaError_t wait_selftest(cudaStream_t st, int* outcome);
 cudaError_t launch_kick(float* vel, const float* force, const int* type, const float* inv_mass,
                         int N, float half_dt, float* pos, float dt, cudaStream_t st);
 cudaError_t launch_wrap(float* pos, const int* cfg, const float* box, int N, cudaStream_t st);

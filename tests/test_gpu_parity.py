@@ -292,3 +292,15 @@ def test_graph_captured_md_matches_eager(nb):
     a, b = run(False), run(True)
     for x, y in zip(a, b):
         assert torch.equal(x, y)
+
+
+def test_bounded_wait_times_out_and_context_survives(nb):
+    """A tensor-core completion wait made to run out (an mbarrier that nothing
+    arrives at) reports NEP_ERR_TIMEOUT through a device flag; the context
+    keeps working afterwards."""
+    assert nb.selftest_wait_timeout() == nb.NEP_ERR_TIMEOUT
+    assert "ran out" in nb.last_error()
+    h = TINY
+    s = I.rocksalt(3, vacancy=0.0, tag=0)
+    th = I.init_params(h).astype(np.float32)
+    assert_parity(gpu_eval(nb, h, th, s), oracle_eval(h, th, s), s)
