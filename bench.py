@@ -566,8 +566,11 @@ def replicas_leg(nb, torch, I, K: int = 20) -> dict:
     l1.record()
     torch.cuda.synchronize()
     ms_loop = l0.elapsed_time(l1) / KL
+    # the same replicas with the FP32 network, for comparison
+    ms32 = md_graph_ms(nb, torch, I, s, nb.Model(h, th, precision=0), K, cap, cap_ang, shifts=True)
     return {"workload": "replicas1024: 1,024 packings, N log-uniform [64, 4096] (%d atoms), FP16 "
                         "tensor-core network, 900 K velocity Verlet" % N,
+            "fp32_network": {"ms_per_step": ms32, "replica_steps_per_s": B / (ms32 * 1e-3)},
             "replica_steps_per_s": B / (ms * 1e-3), "atom_steps_per_s": N / (ms * 1e-3),
             "ms_per_step": ms, "steps": K,
             "per_replica_loop": {"ms_per_step": ms_loop, "replica_steps_per_s": B / (ms_loop * 1e-3),
@@ -575,14 +578,14 @@ def replicas_leg(nb, torch, I, K: int = 20) -> dict:
             "speedup_vs_loop": ms_loop / ms, "autotuned_angular_variant": chosen[0]}
 
 
-def md_graph_ms(nb, torch, I, s, model, K: int, cap: int = 160, cap_ang: int = 80) -> float:
+def md_graph_ms(nb, torch, I, s, model, K: int, cap: int = 160, cap_ang: int = 80, shifts: bool = False) -> float:
     """ms per velocity-Verlet step (dt 2 fs, 900 K start, rebuild every 10
     steps, skin 1 A) of one system, K steps captured in one CUDA graph."""
     masses = I.MASSES.astype(np.float32)
     N = s.n_atoms
     for _ in range(3):
         dsys = nb.DeviceSystem.from_inputs(s)
-        nl = nb.NeighborList(N, cap, cap_ang, shifts=False)
+        nl = nb.NeighborList(N, cap, cap_ang, shifts=shifts)
         ws = nb.Workspace(model, N, s.n_cfg, cap, cap_ang)
         nb.neighbors(model, dsys, nl, SKIN, ws)
         e_atom, force, e_tot, vir = nb.energy_forces_virial(model, dsys, nl, ws)
