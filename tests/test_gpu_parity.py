@@ -122,12 +122,13 @@ def test_efv_cell(nb, hname):
     assert_parity(gpu_eval(nb, h, th, s), oracle_eval(h, th, s), s)
 
 
-@pytest.mark.parametrize("skin", [0.0, 1.0])
-def test_efv_batch_small_boxes(nb, skin):
+@pytest.mark.parametrize("skin,cap,cap_ang", [(0.0, 160, 64), (1.0, 160, 64), (1.0, 300, 260)])
+def test_efv_batch_small_boxes(nb, skin, cap, cap_ang):
+    # cap_ang >= 256: no per-row table, the reverse-slot search scans the prefix
     h = I.HYPER_SMALL
     s = I.packing_batch([24, 31, 57, 100, 250, 512], tag=64)
     th = I.init_params(h).astype(np.float32)
-    assert_parity(gpu_eval(nb, h, th, s, skin=skin, cap=160, cap_ang=64), oracle_eval(h, th, s), s)
+    assert_parity(gpu_eval(nb, h, th, s, skin=skin, cap=cap, cap_ang=cap_ang), oracle_eval(h, th, s), s)
 
 
 def test_efv_more_than_64_angular_slots(nb):
