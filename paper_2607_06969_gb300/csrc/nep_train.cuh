@@ -15,15 +15,18 @@
 //   xzP/xzR : per angular pair X_n = sum_m P_nm Y_m + sum_m R_nm dY_m . dr and
 //             Z_n = (rhat . dr) sum_m R_nm Y_m, where P = dPhi/dS, R = dPhi/d(dS).
 //   cbins   : per-atom angular c-gradient sum_j Q_k X_n + Q'_k Z_n by species.
-//   grad    : per-chunk sums over atoms of every parameter's contributions,
-//             then an FP64 sum over chunks in fixed order.
+//   grad    : per-chunk sums over atoms of every parameter's contributions
+//             (tiles of atoms staged in shared memory in species order,
+//             accumulators in shared memory), then an FP64 sum over chunks
+//             in fixed order.
 #pragma once
 #include "nep_eval.cuh"
 #include "nep_mlp_tc.cuh"
 
 namespace nep {
 
-constexpr int kGradChunk = 32;   // atoms per gradient-partial CTA
+constexpr int kGradChunk = 32;   // atoms per staged tile
+constexpr int kGradTiles = 8;    // most tiles per gradient chunk (one CTA)
 
 NEP_HD int config_of_comp_j(int addr, int N) { return addr - (addr / N) * N; }
 
@@ -379,8 +382,8 @@ NEP_HD void cbins_atom(const TrainArgs& t, const float* sm, int i) {
 }
 
 // ---------------------------------------------------------------------------
-// Gradient partial of one chunk of kGradChunk atoms: every parameter's
-// contribution summed over the chunk in atom order.
+// Gradient partials: every parameter's contribution summed over a staged
+// tile of kGradChunk atoms whose rows are in species order.
 template <class C>
 struct GradStage {
     static constexpr int NR = C::NR, NA = C::NA, KR = C::KR, KA = C::KA, T = C::T, D = C::D;
@@ -396,33 +399,43 @@ struct GradStage {
     static NEP_HD int o_bins(int H) { return o_df(H) + T * KR; }
 };
 
+// address of field f of atom i's staged row
 template <class C>
-NEP_HD void stage_atom(const TrainArgs& t, float* row, int i) {
+NEP_HD const float* stage_src(const TrainArgs& t, int f, int i) {
     using G = GradStage<C>;
-    constexpr int NR = C::NR, NA = C::NA, KR = C::KR, KA = C::KA, T = C::T, D = C::D;
     const EvalArgs& a = t.e;
-    const int N = a.N, H = a.H;
-    row[0] = i2f(f2i(a.pos4[i].w));
-    row[1] = t.aE[a.cfg[i]];
-    for (int d = 0; d < D; ++d) {
-        row[G::o_q() + d] = a.q_out[d * N + i];
-        row[G::o_dq() + d] = t.dq[d * N + i];
-    }
-    for (int h = 0; h < 3 * H; ++h) row[G::o_coef() + h] = t.coef[h * N + i];
-    for (int n = 0; n < NR; ++n) {
-        row[G::o_rho(H) + n] = t.rho[n * N + i];
-        row[G::o_p(H) + n] = a.p_out[n * N + i];
-    }
-    for (int k = 0; k < T * KR; ++k) {
-        row[G::o_fb(H) + k] = a.fb_out[k * N + i];
-        row[G::o_df(H) + k] = t.df[k * N + i];
-    }
-    for (int k = 0; k < T * NA * KA; ++k) row[G::o_bins(H) + k] = t.bins[k * N + i];
+    const size_t N = a.N;
+    const int H = a.H;
+    if (f == 0) return &a.pos4[i].w;
+    if (f == 1) return t.aE + a.cfg[i];
+    if (f < G::o_dq()) return a.q_out + (f - G::o_q()) * N + i;
+    if (f < G::o_coef()) return t.dq + (f - G::o_dq()) * N + i;
+    if (f < G::o_rho(H)) return t.coef + (f - G::o_coef()) * N + i;
+    if (f < G::o_p(H)) return t.rho + (f - G::o_rho(H)) * N + i;
+    if (f < G::o_fb(H)) return a.p_out + (f - G::o_p(H)) * N + i;
+    if (f < G::o_df(H)) return a.fb_out + (f - G::o_fb(H)) * N + i;
+    if (f < G::o_bins(H)) return t.df + (f - G::o_df(H)) * N + i;
+    return t.bins + (f - G::o_bins(H)) * N + i;
 }
 
-// sum over the staged atoms of parameter p's contribution
+// tiles of kGradChunk atoms per gradient chunk: enough chunks to fill the
+// GPU (about 512), at most kGradTiles; a function of N alone, so that the
+// summation order does not depend on the device
+NEP_HD int grad_tiles_per_chunk(int N) {
+    const int tiles = (N + kGradChunk - 1) / kGradChunk;
+    const int k = (tiles + 511) / 512;
+    return k < 1 ? 1 : (k > kGradTiles ? kGradTiles : k);
+}
+NEP_HD int grad_chunks_of(int N) {
+    const int per = kGradChunk * grad_tiles_per_chunk(N);
+    return (N + per - 1) / per;
+}
+
+// sum over the staged atoms of parameter p's contribution; the rows of
+// species t are [toff[t], toff[t + 1]) (every parameter belongs to one
+// species: the network's, or the centre species of a c coefficient)
 template <class C>
-NEP_HD float param_partial(const float* stage, int natoms, int H, int p) {
+NEP_HD float param_partial(const float* stage, const int* toff, int H, int p) {
     using G = GradStage<C>;
     constexpr int NR = C::NR, NA = C::NA, KR = C::KR, KA = C::KA, T = C::T, D = C::D;
     const int W = G::width(H);
@@ -431,38 +444,29 @@ NEP_HD float param_partial(const float* stage, int natoms, int H, int p) {
     if (p < L.off_cR) {
         const int sp = p / L.mlp_stride, r = p % L.mlp_stride;
         const int HD = H * D;
-        for (int a = 0; a < natoms; ++a) {
-            const float* row = stage + a * W;
-            if (f2i(row[0]) != sp) continue;
-            if (r < HD) {
-                const int h = r / D, d = r % D;
+        if (r < HD) {
+            const int h = r / D, d = r % D;
+            for (int a = toff[sp]; a < toff[sp + 1]; ++a) {
+                const float* row = stage + a * W;
                 acc = fmaf(row[G::o_coef() + h], row[G::o_q() + d], acc);
                 acc = fmaf(row[G::o_coef() + H + h], row[G::o_dq() + d], acc);
-            } else if (r < HD + H) {
-                acc += row[G::o_coef() + (r - HD)];
-            } else if (r < HD + 2 * H) {
-                acc += row[G::o_coef() + 2 * H + (r - HD - H)];
-            } else {
-                acc += row[1];
             }
+        } else {
+            const int o = r < HD + H ? G::o_coef() + (r - HD) : (r < HD + 2 * H ? G::o_coef() + 2 * H + (r - HD - H) : 1);
+            for (int a = toff[sp]; a < toff[sp + 1]; ++a) acc += stage[a * W + o];
         }
     } else if (p < L.off_cA) {
         const int x = p - L.off_cR;
         const int t1 = x / (T * NR * KR), t2 = (x / (NR * KR)) % T, n = (x / KR) % NR, k = x % KR;
-        for (int a = 0; a < natoms; ++a) {
+        for (int a = toff[t1]; a < toff[t1 + 1]; ++a) {
             const float* row = stage + a * W;
-            if (f2i(row[0]) != t1) continue;
             acc = fmaf(row[G::o_rho(H) + n], row[G::o_fb(H) + t2 * KR + k], acc);
             acc = fmaf(row[G::o_p(H) + n], row[G::o_df(H) + t2 * KR + k], acc);
         }
     } else {
         const int x = p - L.off_cA;
         const int t1 = x / (T * NA * KA), rest = x % (T * NA * KA);
-        for (int a = 0; a < natoms; ++a) {
-            const float* row = stage + a * W;
-            if (f2i(row[0]) != t1) continue;
-            acc += row[G::o_bins(H) + rest];
-        }
+        for (int a = toff[t1]; a < toff[t1 + 1]; ++a) acc += stage[a * W + G::o_bins(H) + rest];
     }
     return acc;
 }
@@ -500,31 +504,97 @@ __global__ void __launch_bounds__(kBlock, 2) k_cbins(const TrainArgs t) {
     if (i < t.e.N) cbins_atom<C>(t, nullptr, i);
 }
 constexpr int kGradThreads = 256;
+constexpr int kStageUnroll = 8;
+// one chunk of grad_tiles_per_chunk(N) tiles of kGradChunk atoms per CTA: each tile is staged in
+// shared memory with its rows in species order (stable), every thread adds
+// its parameters' sums over the tile to shared accumulators, and the chunk's
+// partials go out once
 template <class C>
 __global__ void __launch_bounds__(kGradThreads) k_grad_partial(const TrainArgs t) {
-    extern __shared__ float stage[];
-    const int H = t.e.H, N = t.e.N;
-    const int W = GradStage<C>::width(H);
-    const int a0 = blockIdx.x * kGradChunk;
-    const int na = min(kGradChunk, N - a0);
-    for (int a = threadIdx.x; a < na; a += blockDim.x) stage_atom<C>(t, stage + a * W, a0 + a);
-    __syncthreads();
-    const ParamLayout L = param_layout(C::T, C::NR, C::NA, C::KR, C::KA, C::H4, H);
-    for (int p = threadIdx.x; p < L.P; p += blockDim.x)
-        t.gpart[(size_t)blockIdx.x * L.P + p] = param_partial<C>(stage, na, H, p);
+    using G = GradStage<C>;
+    constexpr int NR = C::NR, NA = C::NA, KR = C::KR, KA = C::KA, T = C::T, D = C::D;
+    extern __shared__ float smem[];
+    __shared__ int toff[T + 1];
+    __shared__ int rowpos[kGradChunk];
+    const EvalArgs& a = t.e;
+    const int H = a.H, N = a.N;
+    const int W = G::width(H);
+    const ParamLayout L = param_layout(T, NR, NA, KR, KA, C::H4, H);
+    float* stage = smem;                          // [kGradChunk][W]
+    float* acc = smem + kGradChunk * W;           // [P]
+    for (int p = threadIdx.x; p < L.P; p += blockDim.x) acc[p] = 0.0f;
+    const int tpc = grad_tiles_per_chunk(N);
+    const int c0 = blockIdx.x * tpc * kGradChunk;
+    for (int tile = 0; tile < tpc; ++tile) {
+        const int a0 = c0 + tile * kGradChunk;
+        if (a0 >= N) break;
+        const int na = min(kGradChunk, N - a0);
+        // rows in species order: warp 0, one lane per atom
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            const int sp = lane < na ? f2i(a.pos4[a0 + lane].w) : T;
+            int base = 0, pos = 0;
+            for (int s2 = 0; s2 <= T; ++s2) {
+                const unsigned m = __ballot_sync(0xffffffffu, sp == s2);
+                if (s2 < T && lane == 0) toff[s2] = base;
+                if (sp == s2) pos = base + __popc(m & ((1u << lane) - 1u));
+                base += __popc(m);
+            }
+            if (lane == 0) toff[T] = na;
+            if (lane < na) rowpos[lane] = pos;
+        }
+        __syncthreads();
+        // coalesced staging: a warp takes the tile's atoms of one field; the
+        // addresses first, then kStageUnroll loads in flight per thread
+        const int total = W * kGradChunk;
+        for (int x0 = threadIdx.x; x0 < total; x0 += kStageUnroll * kGradThreads) {
+            float v[kStageUnroll];
+#pragma unroll
+            for (int u = 0; u < kStageUnroll; ++u) {
+                const int x = x0 + u * kGradThreads;
+                const int f = x / kGradChunk, r = x % kGradChunk;
+                const float* src = stage_src<C>(t, x < total ? f : 0, r < na ? a0 + r : a0);
+                v[u] = __ldg(src);
+            }
+#pragma unroll
+            for (int u = 0; u < kStageUnroll; ++u) {
+                const int x = x0 + u * kGradThreads;
+                const int f = x / kGradChunk, r = x % kGradChunk;
+                if (x < total && r < na) stage[rowpos[r] * W + f] = v[u];
+            }
+        }
+        __syncthreads();
+        for (int p = threadIdx.x; p < L.P; p += blockDim.x) acc[p] += param_partial<C>(stage, toff, H, p);
+        __syncthreads();
+    }
+    for (int p = threadIdx.x; p < L.P; p += blockDim.x) t.gpart[(size_t)blockIdx.x * L.P + p] = acc[p];
 }
+// FP64 sum over chunks: 32 parameters per CTA, 8 groups of chunks
+// (k = g mod 8) summed in order, then the 8 group sums in order
+constexpr int kFinalGroups = 8;
 template <class C>
-__global__ void k_grad_final(const TrainArgs t, int nchunk) {
+__global__ void __launch_bounds__(32 * kFinalGroups) k_grad_final(const TrainArgs t, int nchunk) {
+    __shared__ double part[kFinalGroups][32];
     const ParamLayout L = param_layout(C::T, C::NR, C::NA, C::KR, C::KA, C::H4, t.e.H);
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= L.P) return;
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int p = blockIdx.x * 32 + lane;
     double acc = 0.0;
-    for (int k = 0; k < nchunk; ++k) acc += (double)t.gpart[(size_t)k * L.P + p];
-    t.grad[p] = (float)acc;
+    if (p < L.P)
+        for (int k = g; k < nchunk; k += kFinalGroups) acc += (double)t.gpart[(size_t)k * L.P + p];
+    part[g][lane] = acc;
+    __syncthreads();
+    if (g == 0 && p < L.P) {
+        double s = 0.0;
+        for (int q = 0; q < kFinalGroups; ++q) s += part[q][lane];
+        t.grad[p] = (float)s;
+    }
 }
 
 template <class C>
-size_t grad_stage_bytes(int H) { return sizeof(float) * (size_t)kGradChunk * GradStage<C>::width(H); }
+size_t grad_stage_bytes(int H) {
+    const ParamLayout L = param_layout(C::T, C::NR, C::NA, C::KR, C::KA, C::H4, H);
+    return sizeof(float) * ((size_t)kGradChunk * GradStage<C>::width(H) + (size_t)L.P);
+}
 
 // attributes of the training kernels and of the tensor-core network
 template <class C>
@@ -539,7 +609,7 @@ cudaError_t train_init_t(int H) {
 }
 
 template <class C>
-int grad_chunks_t(int N) { return (N + kGradChunk - 1) / kGradChunk; }
+int grad_chunks_t(int N) { return grad_chunks_of(N); }
 
 template <class C>
 cudaError_t train_t(const TrainArgs& t, cudaStream_t st) {
@@ -555,7 +625,7 @@ cudaError_t train_t(const TrainArgs& t, cudaStream_t st) {
         k_grad_partial<C><<<grad_chunks_t<C>(N), kGradThreads, grad_stage_bytes<C>(t.e.H), st>>>(t);
     }
     const ParamLayout L = param_layout(C::T, C::NR, C::NA, C::KR, C::KA, C::H4, t.e.H);
-    k_grad_final<C><<<(L.P + 255) / 256, 256, 0, st>>>(t, grad_chunks_t<C>(N));
+    k_grad_final<C><<<(L.P + 31) / 32, 32 * kFinalGroups, 0, st>>>(t, grad_chunks_t<C>(N));
     return cudaGetLastError();
 }
 #endif
