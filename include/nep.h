@@ -170,6 +170,27 @@ nep_status nep_energy_forces_virial(nep_model* m, const nep_system* sys, const n
                                     float* e_atom, float* force, double* e_tot, double* virial,
                                     void* work, size_t work_bytes, void* stream);
 
+/* FP64 evaluation (Section 3.2: the operators run in float64 as well as
+ * float32).  The same quantities as nep_energy_forces_virial with every
+ * intermediate in double: positions (the FP32 inputs) are promoted, pairs
+ * are kept by r < rc in double, and per-atom E and W_i = -sum_j
+ * dE_i/dr_ij (x) r_ij are summed in FP64 in a fixed order.  The list is an
+ * nep_neighbors list (cnt, nbr, shift or minimum image); pairs that the FP32
+ * list predicate left out are not seen.
+ *   params : [P] double DEVICE parameters in the layout of nep_create, or
+ *            NULL for the model's FP32 parameters promoted to double
+ *   e_atom [N] double (may be NULL), force [3][N] double,
+ *   e_tot [B] double, virial [B][9] double (row-major V_ab, Eq. 4)
+ *   work   : >= nep_workspace_bytes_fp64(m, N, B) bytes, 256-byte aligned
+ * One thread per atom; every pair term is evaluated by both of its atoms, so
+ * the call is deterministic and allocation-free.  Needs n_rad, n_ang <= 16 and
+ * k_rad, k_ang <= 16 (else NEP_ERR_UNSUPPORTED); any precision setting. */
+size_t nep_workspace_bytes_fp64(const nep_model* m, int n_atoms, int n_cfg);
+nep_status nep_energy_forces_virial_fp64(nep_model* m, const nep_system* sys, const nep_nlist* nl,
+                                         const double* params, double* e_atom, double* force,
+                                         double* e_tot, double* virial, void* work, size_t work_bytes,
+                                         void* stream);
+
 /* nep_energy_forces_virial without a caller workspace.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate
  * device memory at all -- for example a force plugin inside a host MD code

@@ -21,7 +21,8 @@ NEP_OK, NEP_ERR_ARG, NEP_ERR_CUDA, NEP_ERR_NOMEM, NEP_ERR_CAPACITY, NEP_ERR_TIME
 ENTRY_POINTS = (
     "nep_num_params", "nep_create", "nep_destroy", "nep_supported", "nep_set_params", "nep_get_params",
     "nep_workspace_bytes", "nep_train_workspace_bytes", "nep_neighbors", "nep_energy_forces_virial",
-    "nep_energy_forces_virial_noalloc", "nep_param_grad",
+    "nep_energy_forces_virial_noalloc", "nep_workspace_bytes_fp64", "nep_energy_forces_virial_fp64",
+    "nep_param_grad",
     "nep_param_grad_adjoint", "nep_adam_step", "nep_md_step", "nep_autotune", "nep_set_variant",
     "nep_set_timing_events", "nep_fp32_peak", "nep_selftest_wait_timeout",
     "nep_check",
@@ -81,6 +82,9 @@ def lib() -> ctypes.CDLL:
     L.nep_neighbors.argtypes = [vp, P(System), f, P(NList), vp, sz, vp]
     L.nep_energy_forces_virial.argtypes = [vp, P(System), P(NList), vp, vp, vp, vp, vp, sz, vp]
     L.nep_energy_forces_virial_noalloc.argtypes = [vp, P(System), P(NList), vp, vp, vp, vp, vp]
+    L.nep_workspace_bytes_fp64.argtypes = [vp, i, i]
+    L.nep_workspace_bytes_fp64.restype = sz
+    L.nep_energy_forces_virial_fp64.argtypes = [vp, P(System), P(NList), vp, vp, vp, vp, vp, vp, sz, vp]
     L.nep_param_grad.argtypes = [vp, P(System), P(NList), vp, vp, vp, vp, i, vp, vp, vp, sz, vp]
     L.nep_param_grad_adjoint.argtypes = [vp, P(System), P(NList), vp, vp, vp, vp, vp, sz, vp]
     L.nep_md_step.argtypes = [vp, P(System), P(NList), vp, vp, vp, vp, vp, f, f, i, vp, sz, vp]
@@ -99,6 +103,7 @@ def lib() -> ctypes.CDLL:
     for name in ("nep_create", "nep_destroy", "nep_set_params", "nep_get_params", "nep_adam_step",
                  "nep_neighbors",
                  "nep_energy_forces_virial", "nep_energy_forces_virial_noalloc",
+                 "nep_energy_forces_virial_fp64",
                  "nep_param_grad", "nep_param_grad_adjoint",
                  "nep_md_step", "nep_check", "nep_set_timing_events"):
         getattr(L, name).restype = i
@@ -274,6 +279,41 @@ def energy_forces_virial(model: Model, dsys: DeviceSystem, nl: NeighborList, ws:
                                          _ptr(e_atom), _ptr(force), _ptr(e_tot), _ptr(vir),
                                          ws.ptr, ws.bytes, _stream(stream)),
           "nep_energy_forces_virial")
+    return out
+
+
+class Workspace64:
+    """Device scratch of the FP64 evaluation (nep_workspace_bytes_fp64)."""
+
+    def __init__(self, model: Model, n_atoms: int, n_cfg: int, device="cuda"):
+        import torch
+        self.bytes = int(lib().nep_workspace_bytes_fp64(model.handle, n_atoms, n_cfg))
+        if self.bytes == 0:
+            raise NepError(NEP_ERR_ARG, "nep_workspace_bytes_fp64", "invalid sizes")
+        self.buf = torch.empty(self.bytes + 256, dtype=torch.uint8, device=device)
+        off = (-self.buf.data_ptr()) % 256
+        self.ptr = ctypes.c_void_p(self.buf.data_ptr() + off)
+
+
+def energy_forces_virial_fp64(model: Model, dsys: DeviceSystem, nl: NeighborList, ws: Workspace64,
+                              params=None, out=None, stream=None):
+    """nep_energy_forces_virial_fp64: (e_atom [N], force [3,N], e_tot [B],
+    virial [B,9]), all f64.  params: optional device tensor [P] f64 (default:
+    the model's FP32 parameters promoted)."""
+    import torch
+    dev = dsys.pos.device
+    if params is not None:
+        assert params.is_cuda and params.dtype == torch.float64 and params.numel() == model.n_params
+    if out is None:
+        out = (torch.empty(dsys.n_atoms, dtype=torch.float64, device=dev),
+               torch.empty(3, dsys.n_atoms, dtype=torch.float64, device=dev),
+               torch.empty(dsys.n_cfg, dtype=torch.float64, device=dev),
+               torch.empty(dsys.n_cfg, 9, dtype=torch.float64, device=dev))
+    e_atom, force, e_tot, vir = out
+    check(lib().nep_energy_forces_virial_fp64(model.handle, ctypes.byref(dsys.c), ctypes.byref(nl.c),
+                                              _ptr(params), _ptr(e_atom), _ptr(force), _ptr(e_tot),
+                                              _ptr(vir), ws.ptr, ws.bytes, _stream(stream)),
+          "nep_energy_forces_virial_fp64")
     return out
 
 

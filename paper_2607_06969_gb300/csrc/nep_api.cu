@@ -275,6 +275,39 @@ nep_status check_work(const nep_model* m, const nep_system* s, const nep_nlist* 
     return NEP_OK;
 }
 
+// Scratch of the FP64 evaluation
+struct Ws64Layout {
+    size_t pos4, cfg, chunk_start, partial, prm, e, p, R, w;
+    size_t total;
+    int max_chunks;
+};
+Ws64Layout ws64_layout(const nep_model* m, int N, int B) {
+    Ws64Layout w;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = align_up(o + bytes);
+        return at;
+    };
+    const size_t n = (size_t)N;
+    w.pos4 = take(16 * n);
+    w.cfg = take(4 * n);
+    w.chunk_start = take(4 * ((size_t)B + 1));
+    w.max_chunks = (int)((n + nep::kChunk - 1) / nep::kChunk) + B;
+    w.partial = take(80 * (size_t)w.max_chunks);
+    w.prm = take(8 * (size_t)m->lay.P);
+    w.e = take(8 * n);
+    w.p = take(8 * n * m->hp.n_rad);
+    w.R = take(8 * n * m->hp.n_ang * nep::kLM);
+    w.w = take(72 * n);
+    w.total = o;
+    return w;
+}
+bool fp64_supported(const nep_hparams& hp) {
+    return hp.n_rad <= nep::kF64MaxN && hp.n_ang <= nep::kF64MaxN && hp.k_rad <= nep::kF64MaxK &&
+           hp.k_ang <= nep::kF64MaxK;
+}
+
 nep_status efv_impl(nep_model* m, const nep_system* s, const nep_nlist* nl, float* e_atom,
                     float* force, double* e_tot, double* virial, void* work, const WsLayout& w,
                     cudaStream_t st) {
@@ -545,6 +578,73 @@ nep_status nep_energy_forces_virial(nep_model* m, const nep_system* sys, const n
     WsLayout w;
     if ((s = check_work(m, sys, nl, work, work_bytes, &w)) != NEP_OK) return s;
     return efv_impl(m, sys, nl, e_atom, force, e_tot, virial, work, w, (cudaStream_t)stream);
+}
+
+size_t nep_workspace_bytes_fp64(const nep_model* m, int n_atoms, int n_cfg) {
+    if (!m || n_atoms < 0 || n_cfg < 1) return 0;
+    return ws64_layout(m, n_atoms, n_cfg).total;
+}
+
+nep_status nep_energy_forces_virial_fp64(nep_model* m, const nep_system* sys, const nep_nlist* nl,
+                                         const double* params, double* e_atom, double* force,
+                                         double* e_tot, double* virial, void* work, size_t work_bytes,
+                                         void* stream) {
+    nep_status s;
+    if ((s = check_system(m, sys)) != NEP_OK) return s;
+    if ((s = check_nlist(nl, sys->n_atoms)) != NEP_OK) return s;
+    if (!fp64_supported(m->hp))
+        return fail(NEP_ERR_UNSUPPORTED, "the FP64 path supports n_rad, n_ang <= %d and k_rad, k_ang <= %d",
+                    nep::kF64MaxN, nep::kF64MaxK);
+    if (sys->n_atoms > 0 && !force) return fail(NEP_ERR_ARG, "force is NULL");
+    if (!nl->min_image && !nl->shift) return fail(NEP_ERR_STATE, "list was not built (no shifts, not min-image)");
+    const Ws64Layout w = ws64_layout(m, sys->n_atoms, sys->n_cfg);
+    if (work_bytes < w.total)
+        return fail(NEP_ERR_ARG, "workspace too small: %zu bytes given, %zu needed", work_bytes, w.total);
+    if (!work && w.total) return fail(NEP_ERR_ARG, "workspace is NULL");
+    if ((reinterpret_cast<uintptr_t>(work) & 255) != 0)
+        return fail(NEP_ERR_ARG, "workspace must be 256-byte aligned");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int N = sys->n_atoms, B = sys->n_cfg;
+    NEP_CUDA(nep::launch_pack(sys->pos, sys->type, sys->atom_off, N, B, m->hp.n_types, at<float4>(work, w.pos4),
+                              at<int>(work, w.cfg), nl->status, st),
+             "pack");
+    NEP_CUDA(nep::launch_chunk_plan(sys->atom_off, B, at<int>(work, w.chunk_start), st), "chunk plan");
+    if (!params) {
+        NEP_CUDA(nep::launch_promote(m->params, at<double>(work, w.prm), m->lay.P, st), "promote parameters");
+        params = at<double>(work, w.prm);
+    }
+    nep::F64Args a;
+    a.N = N;
+    a.B = B;
+    a.T = m->hp.n_types;
+    a.NR = m->hp.n_rad;
+    a.NA = m->hp.n_ang;
+    a.KR = m->hp.k_rad;
+    a.KA = m->hp.k_ang;
+    a.H = m->hp.n_hidden;
+    a.H4 = m->hp.has_4body;
+    a.D = m->lay.D;
+    a.L = m->lay;
+    a.rc_rad = (double)m->hp.rc_rad;
+    a.rc_ang = (double)m->hp.rc_ang;
+    a.pos = sys->pos;
+    a.type = sys->type;
+    a.cfg = at<int>(work, w.cfg);
+    a.box = sys->box;
+    a.cnt = nl->cnt;
+    a.nbr = nl->nbr;
+    a.shift = nl->min_image ? nullptr : nl->shift;
+    a.prm = params;
+    a.e = e_atom ? e_atom : at<double>(work, w.e);
+    a.p = at<double>(work, w.p);
+    a.R = at<double>(work, w.R);
+    a.w = at<double>(work, w.w);
+    a.force = force;
+    a.atom_off = sys->atom_off;
+    a.chunk_start = at<int>(work, w.chunk_start);
+    a.partial = at<double>(work, w.partial);
+    NEP_CUDA(nep::launch_efv_fp64(a, w.max_chunks, e_tot, virial, st), "FP64 kernels");
+    return NEP_OK;
 }
 
 nep_status nep_md_step(nep_model* m, const nep_system* sys, nep_nlist* nl, float* vel, float* force,

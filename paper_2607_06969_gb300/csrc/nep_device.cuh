@@ -263,44 +263,48 @@ NEP_HD void harmonics(float x, float y, float z, float* Y) {
 // Component m of the real solid harmonics: value P_m(u) on the unit sphere
 // and the gradient of the homogeneous polynomial at u.  With m a
 // compile-time constant the switch folds away.
-struct HarmTerms {
-    float x, y, z, xx, yy, zz, xy, xz, yz;
+template <class R>
+struct HarmTermsT {
+    R x, y, z, xx, yy, zz, xy, xz, yz;
 };
-NEP_HD HarmTerms harm_terms(float x, float y, float z) {
-    HarmTerms t;
+using HarmTerms = HarmTermsT<float>;
+template <class R>
+NEP_HD HarmTermsT<R> harm_terms(R x, R y, R z) {
+    HarmTermsT<R> t;
     t.x = x; t.y = y; t.z = z;
     t.xx = x * x; t.yy = y * y; t.zz = z * z;
     t.xy = x * y; t.xz = x * z; t.yz = y * z;
     return t;
 }
-NEP_HD void harm_m(int m, const HarmTerms& t, float& Y, float& gx, float& gy, float& gz) {
-    const float x = t.x, y = t.y, z = t.z, xx = t.xx, yy = t.yy, zz = t.zz;
-    const float xy = t.xy, xz = t.xz, yz = t.yz;
+template <class R>
+NEP_HD void harm_m(int m, const HarmTermsT<R>& t, R& Y, R& gx, R& gy, R& gz) {
+    const R x = t.x, y = t.y, z = t.z, xx = t.xx, yy = t.yy, zz = t.zz;
+    const R xy = t.xy, xz = t.xz, yz = t.yz;
     switch (m) {
-        case 0: Y = y; gx = 0.0f; gy = 1.0f; gz = 0.0f; break;
-        case 1: Y = z; gx = 0.0f; gy = 0.0f; gz = 1.0f; break;
-        case 2: Y = x; gx = 1.0f; gy = 0.0f; gz = 0.0f; break;
-        case 3: Y = xy; gx = y; gy = x; gz = 0.0f; break;
-        case 4: Y = yz; gx = 0.0f; gy = z; gz = y; break;
-        case 5: Y = 3.0f * zz - 1.0f; gx = -2.0f * x; gy = -2.0f * y; gz = 4.0f * z; break;
-        case 6: Y = xz; gx = z; gy = 0.0f; gz = x; break;
-        case 7: Y = xx - yy; gx = 2.0f * x; gy = -2.0f * y; gz = 0.0f; break;
-        case 8: Y = y * (3.0f * xx - yy); gx = 6.0f * xy; gy = 3.0f * (xx - yy); gz = 0.0f; break;
+        case 0: Y = y; gx = R(0.0); gy = R(1.0); gz = R(0.0); break;
+        case 1: Y = z; gx = R(0.0); gy = R(0.0); gz = R(1.0); break;
+        case 2: Y = x; gx = R(1.0); gy = R(0.0); gz = R(0.0); break;
+        case 3: Y = xy; gx = y; gy = x; gz = R(0.0); break;
+        case 4: Y = yz; gx = R(0.0); gy = z; gz = y; break;
+        case 5: Y = R(3.0) * zz - R(1.0); gx = -R(2.0) * x; gy = -R(2.0) * y; gz = R(4.0) * z; break;
+        case 6: Y = xz; gx = z; gy = R(0.0); gz = x; break;
+        case 7: Y = xx - yy; gx = R(2.0) * x; gy = -R(2.0) * y; gz = R(0.0); break;
+        case 8: Y = y * (R(3.0) * xx - yy); gx = R(6.0) * xy; gy = R(3.0) * (xx - yy); gz = R(0.0); break;
         case 9: Y = xy * z; gx = yz; gy = xz; gz = xy; break;
-        case 10: Y = y * (5.0f * zz - 1.0f); gx = -2.0f * xy; gy = 4.0f * zz - xx - 3.0f * yy; gz = 8.0f * yz; break;
-        case 11: Y = z * (5.0f * zz - 3.0f); gx = -6.0f * xz; gy = -6.0f * yz; gz = 6.0f * zz - 3.0f * xx - 3.0f * yy; break;
-        case 12: Y = x * (5.0f * zz - 1.0f); gx = 4.0f * zz - 3.0f * xx - yy; gy = -2.0f * xy; gz = 8.0f * xz; break;
-        case 13: Y = z * (xx - yy); gx = 2.0f * xz; gy = -2.0f * yz; gz = xx - yy; break;
-        case 14: Y = x * (xx - 3.0f * yy); gx = 3.0f * (xx - yy); gy = -6.0f * xy; gz = 0.0f; break;
-        case 15: Y = xy * (xx - yy); gx = y * (3.0f * xx - yy); gy = x * (xx - 3.0f * yy); gz = 0.0f; break;
-        case 16: Y = yz * (3.0f * xx - yy); gx = 6.0f * xy * z; gy = 3.0f * z * (xx - yy); gz = y * (3.0f * xx - yy); break;
-        case 17: Y = xy * (7.0f * zz - 1.0f); gx = -y * (3.0f * xx + yy - 6.0f * zz); gy = -x * (xx + 3.0f * yy - 6.0f * zz); gz = 12.0f * xy * z; break;
-        case 18: Y = yz * (7.0f * zz - 3.0f); gx = -6.0f * xy * z; gy = -z * (3.0f * xx + 9.0f * yy - 4.0f * zz); gz = -3.0f * y * (xx + yy - 4.0f * zz); break;
-        case 19: Y = (35.0f * zz - 30.0f) * zz + 3.0f; gx = 12.0f * x * (xx + yy - 4.0f * zz); gy = 12.0f * y * (xx + yy - 4.0f * zz); gz = -16.0f * z * (3.0f * xx + 3.0f * yy - 2.0f * zz); break;
-        case 20: Y = xz * (7.0f * zz - 3.0f); gx = -z * (9.0f * xx + 3.0f * yy - 4.0f * zz); gy = -6.0f * xy * z; gz = -3.0f * x * (xx + yy - 4.0f * zz); break;
-        case 21: Y = (xx - yy) * (7.0f * zz - 1.0f); gx = -4.0f * x * (xx - 3.0f * zz); gy = 4.0f * y * (yy - 3.0f * zz); gz = 12.0f * z * (xx - yy); break;
-        case 22: Y = xz * (xx - 3.0f * yy); gx = 3.0f * z * (xx - yy); gy = -6.0f * xy * z; gz = x * (xx - 3.0f * yy); break;
-        default: Y = xx * (xx - 3.0f * yy) - yy * (3.0f * xx - yy); gx = 4.0f * x * (xx - 3.0f * yy); gy = -4.0f * y * (3.0f * xx - yy); gz = 0.0f; break;
+        case 10: Y = y * (R(5.0) * zz - R(1.0)); gx = -R(2.0) * xy; gy = R(4.0) * zz - xx - R(3.0) * yy; gz = R(8.0) * yz; break;
+        case 11: Y = z * (R(5.0) * zz - R(3.0)); gx = -R(6.0) * xz; gy = -R(6.0) * yz; gz = R(6.0) * zz - R(3.0) * xx - R(3.0) * yy; break;
+        case 12: Y = x * (R(5.0) * zz - R(1.0)); gx = R(4.0) * zz - R(3.0) * xx - yy; gy = -R(2.0) * xy; gz = R(8.0) * xz; break;
+        case 13: Y = z * (xx - yy); gx = R(2.0) * xz; gy = -R(2.0) * yz; gz = xx - yy; break;
+        case 14: Y = x * (xx - R(3.0) * yy); gx = R(3.0) * (xx - yy); gy = -R(6.0) * xy; gz = R(0.0); break;
+        case 15: Y = xy * (xx - yy); gx = y * (R(3.0) * xx - yy); gy = x * (xx - R(3.0) * yy); gz = R(0.0); break;
+        case 16: Y = yz * (R(3.0) * xx - yy); gx = R(6.0) * xy * z; gy = R(3.0) * z * (xx - yy); gz = y * (R(3.0) * xx - yy); break;
+        case 17: Y = xy * (R(7.0) * zz - R(1.0)); gx = -y * (R(3.0) * xx + yy - R(6.0) * zz); gy = -x * (xx + R(3.0) * yy - R(6.0) * zz); gz = R(12.0) * xy * z; break;
+        case 18: Y = yz * (R(7.0) * zz - R(3.0)); gx = -R(6.0) * xy * z; gy = -z * (R(3.0) * xx + R(9.0) * yy - R(4.0) * zz); gz = -R(3.0) * y * (xx + yy - R(4.0) * zz); break;
+        case 19: Y = (R(35.0) * zz - R(30.0)) * zz + R(3.0); gx = R(12.0) * x * (xx + yy - R(4.0) * zz); gy = R(12.0) * y * (xx + yy - R(4.0) * zz); gz = -R(16.0) * z * (R(3.0) * xx + R(3.0) * yy - R(2.0) * zz); break;
+        case 20: Y = xz * (R(7.0) * zz - R(3.0)); gx = -z * (R(9.0) * xx + R(3.0) * yy - R(4.0) * zz); gy = -R(6.0) * xy * z; gz = -R(3.0) * x * (xx + yy - R(4.0) * zz); break;
+        case 21: Y = (xx - yy) * (R(7.0) * zz - R(1.0)); gx = -R(4.0) * x * (xx - R(3.0) * zz); gy = R(4.0) * y * (yy - R(3.0) * zz); gz = R(12.0) * z * (xx - yy); break;
+        case 22: Y = xz * (xx - R(3.0) * yy); gx = R(3.0) * z * (xx - yy); gy = -R(6.0) * xy * z; gz = x * (xx - R(3.0) * yy); break;
+        default: Y = xx * (xx - R(3.0) * yy) - yy * (R(3.0) * xx - yy); gx = R(4.0) * x * (xx - R(3.0) * yy); gy = -R(4.0) * y * (R(3.0) * xx - yy); gz = R(0.0); break;
     }
 }
 
@@ -343,23 +347,24 @@ NEP_HD void harmonics_grad_contract(float x, float y, float z, const float* a, f
 // sums: A = sum_j g (u u^T - I/3) is traceless symmetric with
 // A_xy = s0, A_yz = s1, A_zz = s2/3, A_xz = s3, A_xx - A_yy = s4.
 // q4 = tr(A^3); dq4/ds returned in ds.
-NEP_HD float fourbody(const float* s, float* ds) {
-    float axy = s[0], ayz = s[1], azz = s[2] * (1.0f / 3.0f), axz = s[3];
-    float axx = 0.5f * (s[4] - azz), ayy = -0.5f * (s[4] + azz);
+template <class R>
+NEP_HD R fourbody(const R* s, R* ds) {
+    R axy = s[0], ayz = s[1], azz = s[2] * (R(1.0) / R(3.0)), axz = s[3];
+    R axx = R(0.5) * (s[4] - azz), ayy = -R(0.5) * (s[4] + azz);
     // B = A^2 (symmetric)
-    float bxx = axx * axx + axy * axy + axz * axz;
-    float byy = axy * axy + ayy * ayy + ayz * ayz;
-    float bzz = axz * axz + ayz * ayz + azz * azz;
-    float bxy = axx * axy + axy * ayy + axz * ayz;
-    float bxz = axx * axz + axy * ayz + axz * azz;
-    float byz = axy * axz + ayy * ayz + ayz * azz;
-    float q4 = axx * bxx + ayy * byy + azz * bzz + 2.0f * (axy * bxy + axz * bxz + ayz * byz);
+    R bxx = axx * axx + axy * axy + axz * axz;
+    R byy = axy * axy + ayy * ayy + ayz * ayz;
+    R bzz = axz * axz + ayz * ayz + azz * azz;
+    R bxy = axx * axy + axy * ayy + axz * ayz;
+    R bxz = axx * axz + axy * ayz + axz * azz;
+    R byz = axy * axz + ayy * ayz + ayz * azz;
+    R q4 = axx * bxx + ayy * byy + azz * bzz + R(2.0) * (axy * bxy + axz * bxz + ayz * byz);
     if (ds) {
-        ds[0] = 6.0f * bxy;
-        ds[1] = 6.0f * byz;
-        ds[2] = bzz - 0.5f * (bxx + byy);
-        ds[3] = 6.0f * bxz;
-        ds[4] = 1.5f * (bxx - byy);
+        ds[0] = R(6.0) * bxy;
+        ds[1] = R(6.0) * byz;
+        ds[2] = bzz - R(0.5) * (bxx + byy);
+        ds[3] = R(6.0) * bxz;
+        ds[4] = R(1.5) * (bxx - byy);
     }
     return q4;
 }

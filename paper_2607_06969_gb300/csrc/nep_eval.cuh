@@ -347,7 +347,7 @@ NEP_HD void angular_q(const float (&S)[C::NA][kLM], float* q) {
         for (int l = 0; l < 4; ++l) q[NR + n * 4 + l] = ql[l];
         if (C::H4) {
             const float s2[5] = {S[n][3], S[n][4], S[n][5], S[n][6], S[n][7]};
-            q[NR + NA * 4 + n] = fourbody(s2, nullptr);
+            q[NR + NA * 4 + n] = fourbody<float>(s2, nullptr);
         }
     }
 }

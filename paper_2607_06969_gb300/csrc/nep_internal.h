@@ -158,6 +158,35 @@ cudaError_t launch_neighbors(const float* pos, const float4* pos4, const int* at
                              const int* cfg, int N, int B, float rc_list, float rc_list_ang, float rc_phys,
                              int min_image, nep_nlist* nl, const NbrWork& w, cudaStream_t st);
 
+// FP64 evaluation (nep_fp64.cu): runtime hyper-parameters, every quantity in
+// double.  Bounds of the per-thread arrays:
+constexpr int kF64MaxN = 16;     // n_rad, n_ang
+constexpr int kF64MaxK = 16;     // k_rad, k_ang
+struct F64Args {
+    int N, B, T, NR, NA, KR, KA, H, H4, D;
+    ParamLayout L;
+    double rc_rad, rc_ang;
+    const float* pos;              // [3][N]
+    const int* type;               // [N]
+    const int* cfg;                // [N]
+    const float* box;              // [B][3]
+    const int* cnt;                // [N]
+    const int* nbr;                // [cap][N]
+    const int* shift;              // [cap][N] packed images, or null (minimum image)
+    const double* prm;             // [P]
+    double* e;                     // [N]     E_i
+    double* p;                     // [NR][N] dE_i/dq_n, radial n
+    double* R;                     // [NA*24][N] dE_i/dS_nlm
+    double* w;                     // [9][N]  per-atom virial
+    double* force;                 // [3][N]
+    const int* atom_off;           // [B+1]
+    const int* chunk_start;        // [B+1]
+    double* partial;               // [chunks][10]
+};
+cudaError_t launch_promote(const float* src, double* dst, int n, cudaStream_t st);
+cudaError_t launch_efv_fp64(const F64Args& a, int max_chunks, double* e_tot, double* virial,
+                            cudaStream_t st);
+
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int n, float beta1, float beta2,
                         float eps, float c1, float c2, cudaStream_t st);
 cudaError_t fp32_peak(cudaStream_t st, double* tflops);
