@@ -3,16 +3,20 @@
 // The operators of Section 3.2 run in float64 as well as float32.  This path
 // computes Eqs. 1-4 and 11-17 with every intermediate in double: positions
 // (FP32 inputs) are promoted, the parameters are FP64, and pairs are kept by
-// r < rc in double.  Hyper-parameters are runtime values; one thread per
-// atom, two passes over the neighbour list:
+// r < rc in double.  Hyper-parameters are runtime values.  G lanes per atom
+// split its neighbour list: G = 1 once N fills the GPU, up to a warp for a
+// few hundred atoms, so that small systems still reach every SM.  Two
+// passes over the list:
 //   k64_atom  : q_n (Eq. 11), S_nlm and q_nl (Eqs. 16-17), q4_n, the network
 //               (Eq. 2), E_i, dE_i/dq_n (radial) and R_nlm = dE_i/dS_nlm
 //   k64_force : F_i = sum_j [dE_i/dr_ij - dE_j/dr_ji] (Eq. 3), each pair
 //               derivative recomputed from its owner's dE/dq and R; per-atom
 //               virial W_i = -sum_j dE_i/dr_ij (x) r_ij (Eq. 4)
 // then FP64 sums per 1,024-atom chunk and per configuration in a fixed order.
-// Every pair term is evaluated by both of its atoms, so nothing is scattered
-// and the result is deterministic.
+// Lane partials are combined by an xor butterfly, whose fixed tree leaves
+// the same bits in every lane of the group; every pair term is evaluated by
+// both of its atoms, so nothing is scattered, and for a given N (which fixes
+// G) the result is deterministic.
 #include <cuda_runtime.h>
 
 #include "nep_device.cuh"
@@ -72,8 +76,22 @@ __device__ int pair64(const F64Args& a, int i, int s, double xi, double yi, doub
     return j;
 }
 
+// sum over the G aligned lanes of an atom; every lane receives the same bits.
+// The shuffles name only the group's lanes: a group whose atom index is past
+// N leaves as a whole, while the other groups of its warp go on.
+template <int G>
+__device__ __forceinline__ double group_sum(double v) {
+    const unsigned mask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+    return v;
+}
+
+// G divides 32 and kF64Block, so no group straddles a warp
+template <int G>
 __global__ void __launch_bounds__(kF64Block) k64_atom(const F64Args a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const int lane = threadIdx.x % G;
     if (i >= a.N) return;
     const int N = a.N, T = a.T, NR = a.NR, NA = a.NA, KR = a.KR, KA = a.KA, H = a.H, D = a.D;
     const int ti = a.type[i], b = a.cfg[i];
@@ -82,8 +100,9 @@ __global__ void __launch_bounds__(kF64Block) k64_atom(const F64Args a) {
     double q[kF64MaxD], S[kF64MaxN * kLM], f[kF64MaxK], fp[kF64MaxK];
     for (int d = 0; d < D; ++d) q[d] = 0.0;
     for (int x = 0; x < NA * kLM; ++x) S[x] = 0.0;
+    // this lane's pairs: list slots lane, lane + G, ...
     const int nc = a.cnt[i];
-    for (int s = 0; s < nc; ++s) {
+    for (int s = lane; s < nc; s += G) {
         double dx, dy, dz;
         const int j = pair64(a, i, s, xi, yi, zi, L, dx, dy, dz);
         const double r = sqrt(dx * dx + dy * dy + dz * dz);
@@ -112,7 +131,9 @@ __global__ void __launch_bounds__(kF64Block) k64_atom(const F64Args a) {
             for (int m = 0; m < kLM; ++m) S[n * kLM + m] += g * Y[m];
         }
     }
-    // q_nl = sum_m C_lm S_nlm^2 and q4_n = tr(A_n^3)
+    for (int n = 0; n < NR; ++n) q[n] = group_sum<G>(q[n]);
+    for (int x = 0; x < NA * kLM; ++x) S[x] = group_sum<G>(S[x]);
+    // q_nl = sum_m C_lm S_nlm^2 and q4_n = tr(A_n^3) (every lane of the group)
     for (int n = 0; n < NA; ++n) {
         for (int m = 0; m < kLM; ++m) {
             const double v = S[n * kLM + m];
@@ -120,14 +141,15 @@ __global__ void __launch_bounds__(kF64Block) k64_atom(const F64Args a) {
         }
         if (a.H4) q[NR + NA * 4 + n] = fourbody<double>(S + n * kLM + 3, nullptr);
     }
-    // network: E_i = w1 . tanh(W0 q + b0) + b1, dE/dq = W0^T (w1 (1 - t^2))
+    // network: E_i = w1 . tanh(W0 q + b0) + b1, dE/dq = W0^T (w1 (1 - t^2));
+    // lane takes hidden units h = lane, lane + G, ...
     const double* W0 = a.prm + (size_t)ti * a.L.mlp_stride;
     const double* b0 = W0 + (size_t)H * D;
     const double* w1 = b0 + H;
-    double E = w1[H];
+    double E = 0.0;
     double pq[kF64MaxD];
     for (int d = 0; d < D; ++d) pq[d] = 0.0;
-    for (int h = 0; h < H; ++h) {
+    for (int h = lane; h < H; h += G) {
         const double* w = W0 + (size_t)h * D;
         double z = b0[h];
         for (int d = 0; d < D; ++d) z += w[d] * q[d];
@@ -136,18 +158,20 @@ __global__ void __launch_bounds__(kF64Block) k64_atom(const F64Args a) {
         const double c = w1[h] * (1.0 - th * th);
         for (int d = 0; d < D; ++d) pq[d] += c * w[d];
     }
-    a.e[i] = E;
-    for (int n = 0; n < NR; ++n) a.p[(size_t)n * N + i] = pq[n];
-    // R_nlm = dE/dq_nl 2 C_lm S_nlm (+ dE/dq4_n dq4_n/dS_n2m)
-    for (int n = 0; n < NA; ++n) {
-        double J[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-        if (a.H4) fourbody<double>(S + n * kLM + 3, J);
-        const double p4 = a.H4 ? pq[NR + NA * 4 + n] : 0.0;
-        for (int m = 0; m < kLM; ++m) {
-            double v = 2.0 * (double)clm(m) * pq[NR + n * 4 + lm_l(m) - 1] * S[n * kLM + m];
-            if (m >= 3 && m < 8) v += p4 * J[m - 3];
-            a.R[(size_t)(n * kLM + m) * N + i] = v;
+    E = group_sum<G>(E) + w1[H];
+    for (int d = 0; d < D; ++d) pq[d] = group_sum<G>(pq[d]);
+    if (lane == 0) a.e[i] = E;
+    for (int n = lane; n < NR; n += G) a.p[(size_t)n * N + i] = pq[n];
+    // R_nlm = dE/dq_nl 2 C_lm S_nlm (+ dE/dq4_n dq4_n/dS_n2m), entries split over lanes
+    for (int x = lane; x < NA * kLM; x += G) {
+        const int n = x / kLM, m = x % kLM;
+        double v = 2.0 * (double)clm(m) * pq[NR + n * 4 + lm_l(m) - 1] * S[x];
+        if (a.H4 && m >= 3 && m < 8) {
+            double J[5];
+            fourbody<double>(S + n * kLM + 3, J);
+            v += pq[NR + NA * 4 + n] * J[m - 3];
         }
+        a.R[(size_t)x * N + i] = v;
     }
 }
 
@@ -194,8 +218,10 @@ __device__ void pair_deriv(const F64Args& a, int o, int to, int tn, double r, co
     }
 }
 
+template <int G>
 __global__ void __launch_bounds__(kF64Block) k64_force(const F64Args a) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const int lane = threadIdx.x % G;
     if (i >= a.N) return;
     const int N = a.N;
     const int ti = a.type[i], b = a.cfg[i];
@@ -204,7 +230,7 @@ __global__ void __launch_bounds__(kF64Block) k64_force(const F64Args a) {
     double F[3] = {0.0, 0.0, 0.0}, W[9];
     for (int c = 0; c < 9; ++c) W[c] = 0.0;
     const int nc = a.cnt[i];
-    for (int s = 0; s < nc; ++s) {
+    for (int s = lane; s < nc; s += G) {
         double d[3];
         const int j = pair64(a, i, s, xi, yi, zi, L, d[0], d[1], d[2]);
         const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
@@ -219,8 +245,10 @@ __global__ void __launch_bounds__(kF64Block) k64_force(const F64Args a) {
         for (int x = 0; x < 3; ++x)
             for (int y = 0; y < 3; ++y) W[3 * x + y] -= fij[x] * d[y];
     }
-    for (int c = 0; c < 3; ++c) a.force[(size_t)c * N + i] = F[c];
-    for (int c = 0; c < 9; ++c) a.w[(size_t)c * N + i] = W[c];
+    for (int c = 0; c < 3; ++c) F[c] = group_sum<G>(F[c]);
+    for (int c = 0; c < 9; ++c) W[c] = group_sum<G>(W[c]);
+    for (int c = lane; c < 3; c += G) a.force[(size_t)c * N + i] = F[c];
+    for (int c = lane; c < 9; c += G) a.w[(size_t)c * N + i] = W[c];
 }
 
 __device__ int segment_of(const int* off, int B, int x) {
@@ -269,6 +297,14 @@ __global__ void k_promote(const float* src, double* dst, int n) {
 
 }  // namespace
 
+// lanes per atom: enough threads to fill the GPU (N G >= 2^17, about 1,024 per
+// SM), with G in {1, 8, 32}; a function of N alone
+int fp64_lanes_per_atom(int N) {
+    if (N >= (1 << 17)) return 1;
+    if (N >= (1 << 14)) return 8;
+    return 32;
+}
+
 cudaError_t launch_promote(const float* src, double* dst, int n, cudaStream_t st) {
     if (n > 0) k_promote<<<(n + 255) / 256, 256, 0, st>>>(src, dst, n);
     return cudaGetLastError();
@@ -277,9 +313,18 @@ cudaError_t launch_promote(const float* src, double* dst, int n, cudaStream_t st
 cudaError_t launch_efv_fp64(const F64Args& a, int max_chunks, double* e_tot, double* virial,
                             cudaStream_t st) {
     if (a.N > 0) {
-        const int grid = (a.N + kF64Block - 1) / kF64Block;
-        k64_atom<<<grid, kF64Block, 0, st>>>(a);
-        k64_force<<<grid, kF64Block, 0, st>>>(a);
+        const int G = fp64_lanes_per_atom(a.N);
+        const int grid = (int)(((long long)a.N * G + kF64Block - 1) / kF64Block);
+        if (G == 1) {
+            k64_atom<1><<<grid, kF64Block, 0, st>>>(a);
+            k64_force<1><<<grid, kF64Block, 0, st>>>(a);
+        } else if (G == 8) {
+            k64_atom<8><<<grid, kF64Block, 0, st>>>(a);
+            k64_force<8><<<grid, kF64Block, 0, st>>>(a);
+        } else {
+            k64_atom<32><<<grid, kF64Block, 0, st>>>(a);
+            k64_force<32><<<grid, kF64Block, 0, st>>>(a);
+        }
     }
     if (max_chunks > 0) k64_chunk_reduce<<<max_chunks, kF64Red, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();

@@ -184,6 +184,7 @@ struct F64Args {
     double* partial;               // [chunks][10]
 };
 cudaError_t launch_promote(const float* src, double* dst, int n, cudaStream_t st);
+int fp64_lanes_per_atom(int N);
 cudaError_t launch_efv_fp64(const F64Args& a, int max_chunks, double* e_tot, double* virial,
                             cudaStream_t st);
 

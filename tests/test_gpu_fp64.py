@@ -159,6 +159,27 @@ def test_fp64_workspace_too_small(nb):
     assert st == nb.NEP_ERR_ARG
 
 
+@pytest.mark.parametrize("ncell", [6, 14])
+def test_fp64_lane_groups_sampled(nb, ncell):
+    """Systems on the 32- and 8-lanes-per-atom paths (N = 1,555 and 19,757;
+    19,757 leaves the last warp with one atom group): sampled atoms, the last
+    atoms among them, against the oracle's neighbourhood evaluation, and a
+    zero net force."""
+    s = I.rocksalt(ncell, vacancy=0.2, tag=6)
+    h = I.HYPER_SMALL
+    N = s.n_atoms
+    th = I.init_params(h).astype(np.float32)
+    g = run64(nb, h, th, s)
+    centers = np.concatenate([np.random.default_rng(15).choice(N - 4, 20, replace=False), np.arange(N - 4, N)])
+    p32 = s.pos32()
+    ref = O.evaluate_centers(h, th.astype(np.float64), p32, p32.astype(np.float64), s.types,
+                             s.box.astype(np.float32).astype(np.float64), s.atom_off, centers)
+    assert np.abs(g["E"][ref["centers"]] - ref["E"]).max() <= TOL
+    assert np.abs(g["F"][ref["centers"]] - ref["F"]).max() <= TOL
+    assert np.abs(g["F"].sum(0)).max() <= TOL
+    assert abs(g["Etot"][0] - g["E"].sum()) <= TOL * N
+
+
 def test_fp64_md900k_sampled(nb):
     """Full 900,000-atom workload: 24 sampled atoms against the oracle's
     neighbourhood evaluation, and the FP64 properties at any size."""
