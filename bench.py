@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-replicas", action="store_true", help="skip the batched-replica leg")
     ap.add_argument("--no-table2", action="store_true", help="skip the paper-model size sweep")
     ap.add_argument("--no-fig3", action="store_true", help="skip the training-operator size sweep")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-mode leg")
     ap.add_argument("--ncell", type=int, default=50,
                     help="rock-salt cells per edge (50 = the 900k-atom workload; smaller for profiling)")
     return ap.parse_args()
@@ -229,6 +230,43 @@ def fig3_leg(nb, torch, I) -> dict:
     return {"workload": "fig3: one random-occupation rock-salt GST cell (2^3..5^3 conventional cells), "
                         "loss + gradient of 4,611 parameters per call, FP32",
             "gpu_ms_per_config": out}
+
+
+def fp64_leg(nb, torch, I) -> dict:
+    """E+F+V in the FP64 mode (nep_energy_forces_virial_fp64) against the
+    FP32 evaluation on the same list: the 216-atom cell and the 900k MD
+    system (18 A box with image shifts; minimum image for 900k)."""
+    out = {}
+    for name, (s, h) in (("cell216", I.workload_cell216()), ("md900k", I.workload_md900k())):
+        model = nb.Model(h, I.init_params(h).astype(np.float32))
+        d = nb.DeviceSystem.from_inputs(s)
+        nl = nb.NeighborList(s.n_atoms, 96, 40, shifts=s.n_atoms < 1000)
+        ws = nb.Workspace(model, s.n_atoms, s.n_cfg, 96, 40)
+        nb.neighbors(model, d, nl, 0.0, ws)
+        _raise_if_overflow(nb, nl)
+        ws64 = nb.Workspace64(model, s.n_atoms, s.n_cfg)
+        o64 = nb.energy_forces_virial_fp64(model, d, nl, ws64)
+        o32 = nb.energy_forces_virial(model, d, nl, ws)
+        K = 20 if s.n_atoms < 1000 else 5
+        ms = {}
+        for tag, fn in (("fp64", lambda: nb.energy_forces_virial_fp64(model, d, nl, ws64, out=o64)),
+                        ("fp32", lambda: nb.energy_forces_virial(model, d, nl, ws, out=o32))):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record()
+            for _ in range(K):
+                fn()
+            t1.record()
+            torch.cuda.synchronize()
+            ms[tag] = t0.elapsed_time(t1) / K
+        out[name] = {"n_atoms": s.n_atoms, "fp64_ms": ms["fp64"], "fp32_ms": ms["fp32"],
+                     "fp64_atoms_per_s": s.n_atoms / (ms["fp64"] * 1e-3),
+                     "max_abs_force_diff_fp32_vs_fp64": float((o32[1].double() - o64[1]).abs().max().item())}
+        del ws64, ws, nl, d, model
+    return {"workload": "one E+F+V evaluation, every intermediate in double (FP32 positions promoted)",
+            "cases": out}
 
 
 def reference_arm(args, rank: int) -> None:
@@ -740,6 +778,7 @@ def main():
     replicas = None if args.no_replicas else replicas_leg(nb, torch, I)
     table2 = None if args.no_table2 else table2_leg(nb, torch, I)
     fig3 = None if args.no_fig3 else fig3_leg(nb, torch, I)
+    fp64 = None if args.no_fp64 else fp64_leg(nb, torch, I)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -764,7 +803,7 @@ def main():
                 "e2e": {"value": e2e_val, "unit": "atom-steps/s", "steps": KE,
                         "h2d_bytes_per_step": 24 * N, "d2h_bytes_per_step": 36 * N + 8 + 72},
                 "gpu_launches": launches, "clocks": clk, "train": train, "mixed": mixed, "replicas": replicas,
-                "table2": table2, "fig3": fig3,
+                "table2": table2, "fig3": fig3, "fp64": fp64,
                 "energy": {"e_tot_final": float(e_tot.item())}}
         print(json.dumps(line), flush=True)
     if world > 1:
