@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-table2", action="store_true", help="skip the paper-model size sweep")
     ap.add_argument("--no-fig3", action="store_true", help="skip the training-operator size sweep")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-mode leg")
+    ap.add_argument("--train-only", action="store_true",
+                    help="run the training leg alone and print its JSON object (for profiling it)")
     ap.add_argument("--ncell", type=int, default=50,
                     help="rock-salt cells per edge (50 = the 900k-atom workload; smaller for profiling)")
     return ap.parse_args()
@@ -696,6 +698,13 @@ def main():
         dist.init_process_group("nccl")
     from paper_2607_06969_gb300 import binding as nb
     from paper_2607_06969_gb300 import inputs as I
+    if args.train_only:
+        train = train_leg(nb, torch, I, local, dist, world, rank)
+        if rank == 0:
+            print(json.dumps({"train": train}), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return
 
     if args.ncell == 50:
         s, h = I.workload_md900k()

@@ -151,7 +151,7 @@ TrainLayout train_layout(const nep_model* m, int N, int B, int cap, int cap_ang)
     t.df = take(4 * n * T * KR);
     t.coef = take(4 * n * 3 * H);
     t.rho = take(4 * n * D);
-    t.xz = take(4 * n * 2 * NA * (size_t)cap_ang);
+    t.xz = take(4 * n * 3 * NA * (size_t)cap_ang);
     t.bins = take(4 * n * T * NA * KA);
     t.gpart = take(4 * (size_t)m->ks->grad_chunks(N) * m->lay.P);
     t.loss = take(8);

@@ -83,7 +83,7 @@ struct TrainArgs {
     float* df;                     // [T*KR][N]
     float* coef;                   // [3H][N]  alpha, beta, gamma of the network gradient
     float* rho;                    // [D][N]   a dE/dq + d(dE/dq . dq)/dq
-    float* xz;                     // [2*NA][cap_ang][N] per angular pair X_n, Z_n
+    float* xz;                     // [3*NA][cap_ang][N] per angular pair: X_n from P, Z_n, X_n from R
     float* bins;                   // [T*NA*KA][N] per-atom angular c-gradient
     float* gpart;                  // [chunks][P] per-chunk gradient partials
     float* grad;                   // [P] output

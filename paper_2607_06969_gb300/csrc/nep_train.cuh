@@ -14,7 +14,8 @@
 //             gradient coefficients) and rho = aE p + d(p . dq)/dq.
 //   xzP/xzR : per angular pair X_n = sum_m P_nm Y_m + sum_m R_nm dY_m . dr and
 //             Z_n = (rhat . dr) sum_m R_nm Y_m, where P = dPhi/dS, R = dPhi/d(dS).
-//   cbins   : per-atom angular c-gradient sum_j Q_k X_n + Q'_k Z_n by species.
+//   cbins   : per-atom angular c-gradient sum_j Q_k X_n + Q'_k Z_n by species
+//             (X_n = the sum of its P and R planes).
 //   grad    : per-chunk sums over atoms of every parameter's contributions
 //             (tiles of atoms staged in shared memory in species order,
 //             accumulators in shared memory), then an FP64 sum over chunks
@@ -24,6 +25,24 @@
 #include "nep_mlp_tc.cuh"
 
 namespace nep {
+
+// resident 128-thread blocks per SM asked of each per-atom training kernel
+// (their register budget: 65,536 / (128 x blocks))
+#ifndef NEP_MINB_TANGENT
+#define NEP_MINB_TANGENT 2
+#endif
+#ifndef NEP_MINB_MLP2
+#define NEP_MINB_MLP2 2
+#endif
+#ifndef NEP_MINB_XZP
+#define NEP_MINB_XZP 2
+#endif
+#ifndef NEP_MINB_XZR
+#define NEP_MINB_XZR 2
+#endif
+#ifndef NEP_MINB_CBINS
+#define NEP_MINB_CBINS 2
+#endif
 
 constexpr int kGradChunk = 32;   // atoms per staged tile
 constexpr int kGradTiles = 8;    // most tiles per gradient chunk (one CTA)
@@ -36,6 +55,42 @@ NEP_HD void adjoint_frame(const TrainArgs& t, int i, float4& li, float* mu) {
 #pragma unroll
     for (int k = 0; k < 9; ++k) mu[k] = t.mu[9 * b + k];
 }
+
+// Pair records of a compacted list read ahead: the record two pairs ahead
+// and the neighbour's adjoint one pair ahead, so that the two dependent
+// global loads of a pair overlap the work on the pairs before it.  J(e)
+// decodes the neighbour index of a record.
+template <class J>
+struct AdjointStream {
+    const float4* rec;     // [slot][N] records of atom i
+    const float4* lam4;
+    int N, i, n;
+    float4 e1, e2, l1;
+    J j_of;
+    NEP_HD AdjointStream(const float4* rec_, const float4* lam4_, int N_, int i_, int n_, J j)
+        : rec(rec_), lam4(lam4_), N(N_), i(i_), n(n_), j_of(j) {
+        const float4 z = {0.0f, 0.0f, 0.0f, 0.0f};
+        e1 = n > 0 ? rec[i] : z;
+        e2 = n > 1 ? rec[N + i] : z;
+        l1 = n > 0 ? lam4[j_of(e1)] : z;
+    }
+    // record and neighbour adjoint of pair c, then the loads for c + 1, c + 2
+    NEP_HD void next(int c, float4& e, float4& lj) {
+        const float4 z = {0.0f, 0.0f, 0.0f, 0.0f};
+        e = e1;
+        lj = l1;
+        e1 = e2;
+        l1 = c + 1 < n ? lam4[j_of(e1)] : z;
+        e2 = c + 2 < n ? rec[(size_t)(c + 2) * N + i] : z;
+    }
+};
+struct RadialJ {
+    NEP_HD int operator()(float4 e) const { return (int)((unsigned)f2i(e.w) >> 2); }
+};
+struct AngularJ {
+    int N;
+    NEP_HD int operator()(float4 e) const { return config_of_comp_j((int)((unsigned)f2i(e.w) >> 2), N); }
+};
 
 // dr_ij = -(lam_j - lam_i) - mu r_ij
 NEP_HD void pair_tangent(const float* mu, float4 li, float4 lj, float rx, float ry, float rz,
@@ -65,13 +120,13 @@ NEP_HD void tangent_atom(const TrainArgs& t, const float* sm, int i) {
 #pragma unroll
         for (int k = 0; k < KR; ++k) df[s][k] = 0.0f;
     const int ncr = a.cnt_compr[i];
+    AdjointStream<RadialJ> rs(a.compr, t.lam4, N, i, ncr, RadialJ{});
     for (int s = 0; s < ncr; ++s) {
-        const float4 e = a.compr[s * N + i];
-        const int bits = f2i(e.w);
-        const int tj = bits & 3;
-        const int j = (int)((unsigned)bits >> 2);
+        float4 e, lj;
+        rs.next(s, e, lj);
+        const int tj = f2i(e.w) & 3;
         float drx, dry, drz;
-        pair_tangent(mu, li, t.lam4[j], e.x, e.y, e.z, drx, dry, drz);
+        pair_tangent(mu, li, lj, e.x, e.y, e.z, drx, dry, drz);
         const float r = sqrt_f(dist2(e.x, e.y, e.z));
         const float ir = rcp_f(r);
         const float udr = (e.x * drx + e.y * dry + e.z * drz) * ir;
@@ -108,13 +163,13 @@ NEP_HD void tangent_atom(const TrainArgs& t, const float* sm, int i) {
 #pragma unroll
         for (int m = 0; m < kLM; ++m) dS[n][m] = 0.0f;
     const int nc = a.cnt_comp[i];
+    AdjointStream<AngularJ> as(a.comp, t.lam4, N, i, nc, AngularJ{N});
     for (int c = 0; c < nc; ++c) {
-        const float4 e = a.comp[c * N + i];
-        const int bits = f2i(e.w);
-        const int tj = bits & 3;
-        const int j = config_of_comp_j((int)((unsigned)bits >> 2), N);
+        float4 e, lj;
+        as.next(c, e, lj);
+        const int tj = f2i(e.w) & 3;
         float drx, dry, drz;
-        pair_tangent(mu, li, t.lam4[j], e.x, e.y, e.z, drx, dry, drz);
+        pair_tangent(mu, li, lj, e.x, e.y, e.z, drx, dry, drz);
         const float r = sqrt_f(dist2(e.x, e.y, e.z));
         const float ir = rcp_f(r);
         const HarmTerms ht = harm_terms(e.x * ir, e.y * ir, e.z * ir);
@@ -268,7 +323,9 @@ NEP_HD void xzp_atom(const TrainArgs& t, const float* sm, int i) {
     }
 }
 
-// X_n += sum_m R dY_m . dr, Z_n = (rhat.dr) sum_m R Y_m with R = dPhi/d(dS) (pass 2)
+// X_n's second part sum_m R dY_m . dr and Z_n = (rhat.dr) sum_m R Y_m with
+// R = dPhi/d(dS) (pass 2); the two parts of X_n sit in separate planes, so
+// this pass only writes
 template <class C>
 NEP_HD void xzr_atom(const TrainArgs& t, const float* sm, int i) {
     constexpr int NR = C::NR, NA = C::NA;
@@ -300,12 +357,12 @@ NEP_HD void xzr_atom(const TrainArgs& t, const float* sm, int i) {
     float mu[9];
     adjoint_frame(t, i, li, mu);
     const int nc = a.cnt_comp[i];
+    AdjointStream<AngularJ> as(a.comp, t.lam4, N, i, nc, AngularJ{N});
     for (int c = 0; c < nc; ++c) {
-        const float4 e = a.comp[c * N + i];
-        const int bits = f2i(e.w);
-        const int j = config_of_comp_j((int)((unsigned)bits >> 2), N);
+        float4 e, lj;
+        as.next(c, e, lj);
         float drx, dry, drz;
-        pair_tangent(mu, li, t.lam4[j], e.x, e.y, e.z, drx, dry, drz);
+        pair_tangent(mu, li, lj, e.x, e.y, e.z, drx, dry, drz);
         const float ir = rcp_f(sqrt_f(dist2(e.x, e.y, e.z)));
         const HarmTerms ht = harm_terms(e.x * ir, e.y * ir, e.z * ir);
         const float udr = ht.x * drx + ht.y * dry + ht.z * drz;
@@ -328,8 +385,7 @@ NEP_HD void xzr_atom(const TrainArgs& t, const float* sm, int i) {
         }
 #pragma unroll
         for (int n = 0; n < NA; ++n) {
-            const size_t xi = ((size_t)n * capA + c) * N + i;
-            t.xz[xi] += X[n];
+            t.xz[((size_t)(2 * NA + n) * capA + c) * N + i] = X[n];
             t.xz[((size_t)(NA + n) * capA + c) * N + i] = udr * Z[n];
         }
     }
@@ -360,7 +416,7 @@ NEP_HD void cbins_atom(const TrainArgs& t, const float* sm, int i) {
         float X[NA], Z[NA];
 #pragma unroll
         for (int n = 0; n < NA; ++n) {
-            X[n] = t.xz[((size_t)n * capA + c) * N + i];
+            X[n] = t.xz[((size_t)n * capA + c) * N + i] + t.xz[((size_t)(2 * NA + n) * capA + c) * N + i];
             Z[n] = t.xz[((size_t)(NA + n) * capA + c) * N + i];
         }
 #pragma unroll
@@ -473,7 +529,7 @@ NEP_HD float param_partial(const float* stage, const int* toff, int H, int p) {
 
 #if defined(__CUDACC__)
 template <class C>
-__global__ void __launch_bounds__(kBlock, 2) k_tangent(const TrainArgs t) {
+__global__ void __launch_bounds__(kBlock, NEP_MINB_TANGENT) k_tangent(const TrainArgs t) {
     extern __shared__ float sm[];
     load_model<C>(sm, t.e.params, t.e.H, threadIdx.x, blockDim.x);
     __syncthreads();
@@ -481,7 +537,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_tangent(const TrainArgs t) {
     if (i < t.e.N) tangent_atom<C>(t, sm, i);
 }
 template <class C>
-__global__ void __launch_bounds__(kBlock, 2) k_mlp2(const TrainArgs t) {
+__global__ void __launch_bounds__(kBlock, NEP_MINB_MLP2) k_mlp2(const TrainArgs t) {
     extern __shared__ float sm[];
     load_model<C>(sm, t.e.params, t.e.H, threadIdx.x, blockDim.x);
     __syncthreads();
@@ -489,17 +545,17 @@ __global__ void __launch_bounds__(kBlock, 2) k_mlp2(const TrainArgs t) {
     if (i < t.e.N) mlp2_atom<C>(t, sm, i);
 }
 template <class C>
-__global__ void __launch_bounds__(kBlock, 2) k_xzp(const TrainArgs t) {
+__global__ void __launch_bounds__(kBlock, NEP_MINB_XZP) k_xzp(const TrainArgs t) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < t.e.N) xzp_atom<C>(t, nullptr, i);
 }
 template <class C>
-__global__ void __launch_bounds__(kBlock, 2) k_xzr(const TrainArgs t) {
+__global__ void __launch_bounds__(kBlock, NEP_MINB_XZR) k_xzr(const TrainArgs t) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < t.e.N) xzr_atom<C>(t, nullptr, i);
 }
 template <class C>
-__global__ void __launch_bounds__(kBlock, 2) k_cbins(const TrainArgs t) {
+__global__ void __launch_bounds__(kBlock, NEP_MINB_CBINS) k_cbins(const TrainArgs t) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < t.e.N) cbins_atom<C>(t, nullptr, i);
 }
