@@ -440,38 +440,111 @@ NEP_HD void cbins_atom(const TrainArgs& t, const float* sm, int i) {
 // ---------------------------------------------------------------------------
 // Gradient partials: every parameter's contribution summed over a staged
 // tile of kGradChunk atoms whose rows are in species order.
+//
+// A staged row holds, per atom (floats): the species bits and dE_b/dE of its
+// configuration, then q and dq (each padded to a multiple of 4 and 16-byte
+// aligned, so that four columns are one vector load), alpha/beta/gamma,
+// rho and p (radial n), the species-resolved basis sums F and DF, and the
+// angular c-gradient bins.  The logical field order (the staging sources)
+// is the same without the padding.
 template <class C>
 struct GradStage {
     static constexpr int NR = C::NR, NA = C::NA, KR = C::KR, KA = C::KA, T = C::T, D = C::D;
-    // per-atom layout in shared memory (floats)
-    static NEP_HD int width(int H) { return 2 + 2 * D + 3 * H + 2 * NR + 2 * T * KR + T * NA * KA; }
-    static NEP_HD int o_q() { return 2; }
-    static NEP_HD int o_dq() { return 2 + D; }
-    static NEP_HD int o_coef() { return 2 + 2 * D; }
-    static NEP_HD int o_rho(int H) { return 2 + 2 * D + 3 * H; }
+    static constexpr int Dp = (D + 3) & ~3;
+    static NEP_HD int o_q() { return 4; }
+    static NEP_HD int o_dq() { return 4 + Dp; }
+    static NEP_HD int o_coef() { return 4 + 2 * Dp; }
+    static NEP_HD int o_rho(int H) { return o_coef() + 3 * H; }
     static NEP_HD int o_p(int H) { return o_rho(H) + NR; }
     static NEP_HD int o_fb(int H) { return o_p(H) + NR; }
     static NEP_HD int o_df(int H) { return o_fb(H) + T * KR; }
     static NEP_HD int o_bins(int H) { return o_df(H) + T * KR; }
+    // row stride: a multiple of 4 (16-byte rows) with W/4 odd, so that 8
+    // consecutive rows start in 8 distinct groups of 4 banks
+    static NEP_HD int width(int H) {
+        const int w = (o_bins(H) + T * NA * KA + 3) & ~3;
+        return (w & 4) ? w : w + 4;
+    }
+    // logical fields: 2 + 2D + 3H + 2 NR + 2 T KR + T NA KA
+    static NEP_HD int fields(int H) { return 2 + 2 * D + 3 * H + 2 * NR + 2 * T * KR + T * NA * KA; }
+    // column of logical field f in the padded row
+    static NEP_HD int column(int f) {
+        return f < 2 ? f : (f < 2 + D ? f + 2 : (f < 2 + 2 * D ? f + 2 + (Dp - D) : f + 2 + 2 * (Dp - D)));
+    }
 };
 
-// address of field f of atom i's staged row
+// address of logical field f of atom i
 template <class C>
 NEP_HD const float* stage_src(const TrainArgs& t, int f, int i) {
-    using G = GradStage<C>;
+    constexpr int NR = C::NR, KR = C::KR, T = C::T, D = C::D;
     const EvalArgs& a = t.e;
     const size_t N = a.N;
     const int H = a.H;
     if (f == 0) return &a.pos4[i].w;
     if (f == 1) return t.aE + a.cfg[i];
-    if (f < G::o_dq()) return a.q_out + (f - G::o_q()) * N + i;
-    if (f < G::o_coef()) return t.dq + (f - G::o_dq()) * N + i;
-    if (f < G::o_rho(H)) return t.coef + (f - G::o_coef()) * N + i;
-    if (f < G::o_p(H)) return t.rho + (f - G::o_rho(H)) * N + i;
-    if (f < G::o_fb(H)) return a.p_out + (f - G::o_p(H)) * N + i;
-    if (f < G::o_df(H)) return a.fb_out + (f - G::o_fb(H)) * N + i;
-    if (f < G::o_bins(H)) return t.df + (f - G::o_df(H)) * N + i;
-    return t.bins + (f - G::o_bins(H)) * N + i;
+    f -= 2;
+    if (f < D) return a.q_out + f * N + i;
+    f -= D;
+    if (f < D) return t.dq + f * N + i;
+    f -= D;
+    if (f < 3 * H) return t.coef + f * N + i;
+    f -= 3 * H;
+    if (f < NR) return t.rho + f * N + i;
+    f -= NR;
+    if (f < NR) return a.p_out + f * N + i;
+    f -= NR;
+    if (f < T * KR) return a.fb_out + f * N + i;
+    f -= T * KR;
+    if (f < T * KR) return t.df + f * N + i;
+    f -= T * KR;
+    return t.bins + f * N + i;
+}
+
+// Work items of a tile.  Items [0, NW) are blocks of the W0 gradient,
+// (species, h, four columns d0..d0+3); the rest are the other parameters,
+// one each: b0, w1, b1 of every species, then cR and cA.
+template <class C>
+NEP_HD int grad_w0_items(int H) { return C::T * H * (GradStage<C>::Dp / 4); }
+template <class C>
+NEP_HD int grad_items(int H) {
+    const ParamLayout L = param_layout(C::T, C::NR, C::NA, C::KR, C::KA, C::H4, H);
+    return grad_w0_items<C>(H) + C::T * (2 * H + 1) + (L.P - L.off_cR);
+}
+
+// W0 block: dPhi/dW0[sp][h][d] = sum over the species' atoms of
+// alpha_h q_d + beta_h dq_d, for four columns at once
+template <class C>
+NEP_HD void grad_w0_item(const float* stage, const int* toff, int H, int it, float* acc) {
+    using G = GradStage<C>;
+    constexpr int D = C::D, NB = G::Dp / 4;
+    const int W = G::width(H);
+    const ParamLayout L = param_layout(C::T, C::NR, C::NA, C::KR, C::KA, C::H4, H);
+    const int sp = it / (H * NB), rem = it % (H * NB), h = rem / NB, d0 = 4 * (rem % NB);
+    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+    for (int a = toff[sp]; a < toff[sp + 1]; ++a) {
+        const float* row = stage + a * W;
+        const float al = row[G::o_coef() + h], be = row[G::o_coef() + H + h];
+        const float4 q = *reinterpret_cast<const float4*>(row + G::o_q() + d0);
+        const float4 dq = *reinterpret_cast<const float4*>(row + G::o_dq() + d0);
+        s0 = fmaf(be, dq.x, fmaf(al, q.x, s0));
+        s1 = fmaf(be, dq.y, fmaf(al, q.y, s1));
+        s2 = fmaf(be, dq.z, fmaf(al, q.z, s2));
+        s3 = fmaf(be, dq.w, fmaf(al, q.w, s3));
+    }
+    float* out = acc + sp * L.mlp_stride + h * D + d0;
+    out[0] += s0;
+    if (d0 + 1 < D) out[1] += s1;
+    if (d0 + 2 < D) out[2] += s2;
+    if (d0 + 3 < D) out[3] += s3;
+}
+
+// parameter of item o >= NW
+template <class C>
+NEP_HD int grad_other_param(int H, int o) {
+    const ParamLayout L = param_layout(C::T, C::NR, C::NA, C::KR, C::KA, C::H4, H);
+    const int per = 2 * H + 1;
+    if (o < C::T * per) return (o / per) * L.mlp_stride + H * C::D + o % per;
+    return L.off_cR + (o - C::T * per);
 }
 
 // tiles of kGradChunk atoms per gradient chunk: enough chunks to fill the
@@ -487,9 +560,10 @@ NEP_HD int grad_chunks_of(int N) {
     return (N + per - 1) / per;
 }
 
-// sum over the staged atoms of parameter p's contribution; the rows of
-// species t are [toff[t], toff[t + 1]) (every parameter belongs to one
-// species: the network's, or the centre species of a c coefficient)
+// sum over the staged atoms of the contribution to parameter p (not a W0
+// entry); the rows of species t are [toff[t], toff[t + 1]) (every parameter
+// belongs to one species: the network's, or the centre species of a c
+// coefficient)
 template <class C>
 NEP_HD float param_partial(const float* stage, const int* toff, int H, int p) {
     using G = GradStage<C>;
@@ -498,19 +572,10 @@ NEP_HD float param_partial(const float* stage, const int* toff, int H, int p) {
     const ParamLayout L = param_layout(T, NR, NA, KR, KA, C::H4, H);
     float acc = 0.0f;
     if (p < L.off_cR) {
-        const int sp = p / L.mlp_stride, r = p % L.mlp_stride;
-        const int HD = H * D;
-        if (r < HD) {
-            const int h = r / D, d = r % D;
-            for (int a = toff[sp]; a < toff[sp + 1]; ++a) {
-                const float* row = stage + a * W;
-                acc = fmaf(row[G::o_coef() + h], row[G::o_q() + d], acc);
-                acc = fmaf(row[G::o_coef() + H + h], row[G::o_dq() + d], acc);
-            }
-        } else {
-            const int o = r < HD + H ? G::o_coef() + (r - HD) : (r < HD + 2 * H ? G::o_coef() + 2 * H + (r - HD - H) : 1);
-            for (int a = toff[sp]; a < toff[sp + 1]; ++a) acc += stage[a * W + o];
-        }
+        // b0 (alpha), w1 (gamma) or b1 (dPhi/dE); W0 goes through grad_w0_item
+        const int sp = p / L.mlp_stride, r = p % L.mlp_stride - H * D;
+        const int o = r < H ? G::o_coef() + r : (r < 2 * H ? G::o_coef() + 2 * H + (r - H) : 1);
+        for (int a = toff[sp]; a < toff[sp + 1]; ++a) acc += stage[a * W + o];
     } else if (p < L.off_cA) {
         const int x = p - L.off_cR;
         const int t1 = x / (T * NR * KR), t2 = (x / (NR * KR)) % T, n = (x / KR) % NR, k = x % KR;
@@ -561,24 +626,52 @@ __global__ void __launch_bounds__(kBlock, NEP_MINB_CBINS) k_cbins(const TrainArg
 }
 constexpr int kGradThreads = 256;
 constexpr int kStageUnroll = 8;
-// one chunk of grad_tiles_per_chunk(N) tiles of kGradChunk atoms per CTA: each tile is staged in
-// shared memory with its rows in species order (stable), every thread adds
-// its parameters' sums over the tile to shared accumulators, and the chunk's
-// partials go out once
+// shared memory of k_grad_partial: the staged tile, the field tables, the
+// chunk's accumulators
+template <class C>
+struct GradSmem {
+    size_t stage, src, col, acc, total;   // byte offsets
+};
+template <class C>
+NEP_HD GradSmem<C> grad_smem(int H) {
+    using G = GradStage<C>;
+    const ParamLayout L = param_layout(C::T, C::NR, C::NA, C::KR, C::KA, C::H4, H);
+    GradSmem<C> m;
+    m.stage = 0;
+    m.src = m.stage + sizeof(float) * (size_t)kGradChunk * G::width(H);        // 16-byte multiple
+    m.col = m.src + sizeof(const float*) * (size_t)G::fields(H);
+    m.acc = m.col + sizeof(int) * (size_t)G::fields(H);
+    m.total = m.acc + sizeof(float) * (size_t)L.P;
+    return m;
+}
+
+// one chunk of grad_tiles_per_chunk(N) tiles of kGradChunk atoms per CTA:
+// each tile is staged in shared memory with its rows in species order
+// (stable), every thread adds its work items' sums over the tile to shared
+// accumulators, and the chunk's partials go out once
 template <class C>
 __global__ void __launch_bounds__(kGradThreads) k_grad_partial(const TrainArgs t) {
     using G = GradStage<C>;
-    constexpr int NR = C::NR, NA = C::NA, KR = C::KR, KA = C::KA, T = C::T, D = C::D;
-    extern __shared__ float smem[];
+    constexpr int NR = C::NR, NA = C::NA, KR = C::KR, KA = C::KA, T = C::T;
+    extern __shared__ float4 smem4[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(smem4);
     __shared__ int toff[T + 1];
-    __shared__ int rowpos[kGradChunk];
+    __shared__ int rowatom[kGradChunk];
     const EvalArgs& a = t.e;
     const int H = a.H, N = a.N;
-    const int W = G::width(H);
+    const int W = G::width(H), WF = G::fields(H);
     const ParamLayout L = param_layout(T, NR, NA, KR, KA, C::H4, H);
-    float* stage = smem;                          // [kGradChunk][W]
-    float* acc = smem + kGradChunk * W;           // [P]
+    const GradSmem<C> sm = grad_smem<C>(H);
+    float* stage = reinterpret_cast<float*>(smem + sm.stage);        // [kGradChunk][W]
+    const float** src = reinterpret_cast<const float**>(smem + sm.src);  // [WF] field bases
+    int* col = reinterpret_cast<int*>(smem + sm.col);                // [WF] field columns
+    float* acc = reinterpret_cast<float*>(smem + sm.acc);            // [P]
     for (int p = threadIdx.x; p < L.P; p += blockDim.x) acc[p] = 0.0f;
+    for (int f = threadIdx.x; f < WF; f += blockDim.x) {
+        src[f] = f >= 2 ? stage_src<C>(t, f, 0) : nullptr;
+        col[f] = G::column(f);
+    }
+    const int NW = grad_w0_items<C>(H), NI = grad_items<C>(H);
     const int tpc = grad_tiles_per_chunk(N);
     const int c0 = blockIdx.x * tpc * kGradChunk;
     for (int tile = 0; tile < tpc; ++tile) {
@@ -597,30 +690,44 @@ __global__ void __launch_bounds__(kGradThreads) k_grad_partial(const TrainArgs t
                 base += __popc(m);
             }
             if (lane == 0) toff[T] = na;
-            if (lane < na) rowpos[lane] = pos;
+            if (lane < na) rowatom[pos] = lane;
         }
         __syncthreads();
-        // coalesced staging: a warp takes the tile's atoms of one field; the
-        // addresses first, then kStageUnroll loads in flight per thread
-        const int total = W * kGradChunk;
+        // staging in patches of 8 rows x 4 fields per warp: the 8 rows' atoms
+        // lie in the tile's 128-byte window of each field, and the stores of
+        // a patch fall in 32 distinct banks; kStageUnroll loads in flight per
+        // thread before the stores
+        const int total = (kGradChunk / 8) * ((WF + 3) / 4) * 32;
         for (int x0 = threadIdx.x; x0 < total; x0 += kStageUnroll * kGradThreads) {
             float v[kStageUnroll];
 #pragma unroll
             for (int u = 0; u < kStageUnroll; ++u) {
                 const int x = x0 + u * kGradThreads;
-                const int f = x / kGradChunk, r = x % kGradChunk;
-                const float* src = stage_src<C>(t, x < total ? f : 0, r < na ? a0 + r : a0);
-                v[u] = __ldg(src);
+                const int w = x >> 5, l = x & 31;
+                const int k = (w % (kGradChunk / 8)) * 8 + (l & 7), f = (w / (kGradChunk / 8)) * 4 + (l >> 3);
+                const bool ok = x < total && f < WF && k < na;
+                const int fv = ok ? f : 2;
+                const int i = a0 + (ok ? rowatom[k] : 0);
+                const float* p = fv >= 2 ? src[fv] + i : (fv == 0 ? &a.pos4[i].w : t.aE + a.cfg[i]);
+                v[u] = __ldg(p);
             }
 #pragma unroll
             for (int u = 0; u < kStageUnroll; ++u) {
                 const int x = x0 + u * kGradThreads;
-                const int f = x / kGradChunk, r = x % kGradChunk;
-                if (x < total && r < na) stage[rowpos[r] * W + f] = v[u];
+                const int w = x >> 5, l = x & 31;
+                const int k = (w % (kGradChunk / 8)) * 8 + (l & 7), f = (w / (kGradChunk / 8)) * 4 + (l >> 3);
+                if (x < total && f < WF && k < na) stage[k * W + col[f]] = v[u];
             }
         }
         __syncthreads();
-        for (int p = threadIdx.x; p < L.P; p += blockDim.x) acc[p] += param_partial<C>(stage, toff, H, p);
+        for (int it = threadIdx.x; it < NI; it += blockDim.x) {
+            if (it < NW) {
+                grad_w0_item<C>(stage, toff, H, it, acc);
+            } else {
+                const int p = grad_other_param<C>(H, it - NW);
+                acc[p] += param_partial<C>(stage, toff, H, p);
+            }
+        }
         __syncthreads();
     }
     for (int p = threadIdx.x; p < L.P; p += blockDim.x) t.gpart[(size_t)blockIdx.x * L.P + p] = acc[p];
@@ -647,10 +754,7 @@ __global__ void __launch_bounds__(32 * kFinalGroups) k_grad_final(const TrainArg
 }
 
 template <class C>
-size_t grad_stage_bytes(int H) {
-    const ParamLayout L = param_layout(C::T, C::NR, C::NA, C::KR, C::KA, C::H4, H);
-    return sizeof(float) * ((size_t)kGradChunk * GradStage<C>::width(H) + (size_t)L.P);
-}
+size_t grad_stage_bytes(int H) { return grad_smem<C>(H).total; }
 
 // attributes of the training kernels and of the tensor-core network
 template <class C>
