@@ -191,6 +191,35 @@ nep_status nep_energy_forces_virial_fp64(nep_model* m, const nep_system* sys, co
                                          double* e_tot, double* virial, void* work, size_t work_bytes,
                                          void* stream);
 
+/* FP64 loss and gradient (the training operator of Sections 3.2-3.3 in
+ * float64): the quantities of nep_param_grad / nep_param_grad_adjoint with
+ * every intermediate in double, on the FP64 evaluation above.
+ *   params : [P] double DEVICE parameters, or NULL for the model's FP32
+ *            parameters promoted to double
+ *   e_lbl [B] double, f_lbl [3][N] double, v_lbl [B][9] double,
+ *   w_host[3] = (wE, wF, wV), loss_mode 0 or 1 (as nep_param_grad)
+ *   grad [P] double (overwritten), loss [1] double (may be NULL)
+ *   work   : >= nep_train_workspace_bytes_fp64(m, N, B) bytes, 256-byte aligned
+ * Per atom: descriptors, network, the tangent of q along
+ * dr_ij = -(lam_j - lam_i) - mu r_ij, the network's second-order terms and
+ * the per-pair angular coefficients, recomputed (nothing cached across
+ * calls); the parameter sums run per 1,024-atom chunk and then over chunks,
+ * in a fixed order.  Needs, besides the FP64 evaluation's limits,
+ * n_types * n_ang * k_ang <= 256 (else NEP_ERR_UNSUPPORTED). */
+size_t nep_train_workspace_bytes_fp64(const nep_model* m, int n_atoms, int n_cfg);
+nep_status nep_param_grad_fp64(nep_model* m, const nep_system* sys, const nep_nlist* nl, const double* params,
+                               const double* e_lbl, const double* f_lbl, const double* v_lbl,
+                               const float* w_host, int loss_mode, double* grad, double* loss, void* work,
+                               size_t work_bytes, void* stream);
+/* The gradient of Phi = sum_b a_e[b] E_b + sum_i lam[:,i] . F_i
+ * + sum_b mu[b] : V_b at fixed adjoints, in FP64: a_e [B], lam [3][N],
+ * mu [B][9] double; grad [P] double.  The vector-Jacobian product of an
+ * FP64 autograd backward. */
+nep_status nep_param_grad_adjoint_fp64(nep_model* m, const nep_system* sys, const nep_nlist* nl,
+                                       const double* params, const double* a_e, const double* lam,
+                                       const double* mu, double* grad, void* work, size_t work_bytes,
+                                       void* stream);
+
 /* nep_energy_forces_virial without a caller workspace.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate
  * device memory at all -- for example a force plugin inside a host MD code

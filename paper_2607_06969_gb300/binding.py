@@ -22,6 +22,7 @@ ENTRY_POINTS = (
     "nep_num_params", "nep_create", "nep_destroy", "nep_supported", "nep_set_params", "nep_get_params",
     "nep_workspace_bytes", "nep_train_workspace_bytes", "nep_neighbors", "nep_energy_forces_virial",
     "nep_energy_forces_virial_noalloc", "nep_workspace_bytes_fp64", "nep_energy_forces_virial_fp64",
+    "nep_train_workspace_bytes_fp64", "nep_param_grad_fp64", "nep_param_grad_adjoint_fp64",
     "nep_param_grad",
     "nep_param_grad_adjoint", "nep_adam_step", "nep_md_step", "nep_autotune", "nep_set_variant",
     "nep_set_timing_events", "nep_fp32_peak", "nep_selftest_wait_timeout",
@@ -85,6 +86,10 @@ def lib() -> ctypes.CDLL:
     L.nep_workspace_bytes_fp64.argtypes = [vp, i, i]
     L.nep_workspace_bytes_fp64.restype = sz
     L.nep_energy_forces_virial_fp64.argtypes = [vp, P(System), P(NList), vp, vp, vp, vp, vp, vp, sz, vp]
+    L.nep_train_workspace_bytes_fp64.argtypes = [vp, i, i]
+    L.nep_train_workspace_bytes_fp64.restype = sz
+    L.nep_param_grad_fp64.argtypes = [vp, P(System), P(NList), vp, vp, vp, vp, vp, i, vp, vp, vp, sz, vp]
+    L.nep_param_grad_adjoint_fp64.argtypes = [vp, P(System), P(NList), vp, vp, vp, vp, vp, vp, sz, vp]
     L.nep_param_grad.argtypes = [vp, P(System), P(NList), vp, vp, vp, vp, i, vp, vp, vp, sz, vp]
     L.nep_param_grad_adjoint.argtypes = [vp, P(System), P(NList), vp, vp, vp, vp, vp, sz, vp]
     L.nep_md_step.argtypes = [vp, P(System), P(NList), vp, vp, vp, vp, vp, f, f, i, vp, sz, vp]
@@ -103,7 +108,7 @@ def lib() -> ctypes.CDLL:
     for name in ("nep_create", "nep_destroy", "nep_set_params", "nep_get_params", "nep_adam_step",
                  "nep_neighbors",
                  "nep_energy_forces_virial", "nep_energy_forces_virial_noalloc",
-                 "nep_energy_forces_virial_fp64",
+                 "nep_energy_forces_virial_fp64", "nep_param_grad_fp64", "nep_param_grad_adjoint_fp64",
                  "nep_param_grad", "nep_param_grad_adjoint",
                  "nep_md_step", "nep_check", "nep_set_timing_events"):
         getattr(L, name).restype = i
@@ -283,11 +288,13 @@ def energy_forces_virial(model: Model, dsys: DeviceSystem, nl: NeighborList, ws:
 
 
 class Workspace64:
-    """Device scratch of the FP64 evaluation (nep_workspace_bytes_fp64)."""
+    """Device scratch of the FP64 calls (nep_workspace_bytes_fp64, or
+    nep_train_workspace_bytes_fp64 with train=True)."""
 
-    def __init__(self, model: Model, n_atoms: int, n_cfg: int, device="cuda"):
+    def __init__(self, model: Model, n_atoms: int, n_cfg: int, device="cuda", train: bool = False):
         import torch
-        self.bytes = int(lib().nep_workspace_bytes_fp64(model.handle, n_atoms, n_cfg))
+        fn = lib().nep_train_workspace_bytes_fp64 if train else lib().nep_workspace_bytes_fp64
+        self.bytes = int(fn(model.handle, n_atoms, n_cfg))
         if self.bytes == 0:
             raise NepError(NEP_ERR_ARG, "nep_workspace_bytes_fp64", "invalid sizes")
         self.buf = torch.empty(self.bytes + 256, dtype=torch.uint8, device=device)
@@ -315,6 +322,44 @@ def energy_forces_virial_fp64(model: Model, dsys: DeviceSystem, nl: NeighborList
                                               _ptr(vir), ws.ptr, ws.bytes, _stream(stream)),
           "nep_energy_forces_virial_fp64")
     return out
+
+
+def param_grad_fp64(model: Model, dsys: DeviceSystem, nl: NeighborList, ws: Workspace64, e_lbl, f_lbl,
+                    v_lbl, w=(1.0, 1.0, 0.1), loss_mode: int = 0, params=None, grad=None, loss=None,
+                    stream=None):
+    """nep_param_grad_fp64: (grad [P] f64, loss [1] f64); labels e_lbl [B],
+    f_lbl [3,N], v_lbl [B,9] f64 on the device; ws a training Workspace64."""
+    import torch
+    dev = dsys.pos.device
+    for t in (e_lbl, f_lbl, v_lbl) + (() if params is None else (params,)):
+        assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+    if grad is None:
+        grad = torch.empty(model.n_params, dtype=torch.float64, device=dev)
+    if loss is None:
+        loss = torch.empty(1, dtype=torch.float64, device=dev)
+    wh = np.ascontiguousarray(np.asarray(w, np.float32))
+    check(lib().nep_param_grad_fp64(model.handle, ctypes.byref(dsys.c), ctypes.byref(nl.c), _ptr(params),
+                                    _ptr(e_lbl), _ptr(f_lbl), _ptr(v_lbl), wh.ctypes.data_as(ctypes.c_void_p),
+                                    int(loss_mode), _ptr(grad), _ptr(loss), ws.ptr, ws.bytes, _stream(stream)),
+          "nep_param_grad_fp64")
+    return grad, loss
+
+
+def param_grad_adjoint_fp64(model: Model, dsys: DeviceSystem, nl: NeighborList, ws: Workspace64, a_e, lam,
+                            mu, params=None, grad=None, stream=None):
+    """nep_param_grad_adjoint_fp64: grad [P] f64 of sum a_e E + lam . F +
+    mu : V (a_e [B], lam [3,N], mu [B,9] f64 on the device)."""
+    import torch
+    dev = dsys.pos.device
+    for t in (a_e, lam, mu) + (() if params is None else (params,)):
+        assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+    if grad is None:
+        grad = torch.empty(model.n_params, dtype=torch.float64, device=dev)
+    check(lib().nep_param_grad_adjoint_fp64(model.handle, ctypes.byref(dsys.c), ctypes.byref(nl.c),
+                                            _ptr(params), _ptr(a_e), _ptr(lam), _ptr(mu), _ptr(grad), ws.ptr,
+                                            ws.bytes, _stream(stream)),
+          "nep_param_grad_adjoint_fp64")
+    return grad
 
 
 def param_grad(model: Model, dsys: DeviceSystem, nl: NeighborList, ws: Workspace, e_lbl, f_lbl,

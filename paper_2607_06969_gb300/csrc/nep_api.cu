@@ -278,6 +278,8 @@ nep_status check_work(const nep_model* m, const nep_system* s, const nep_nlist* 
 // Scratch of the FP64 evaluation
 struct Ws64Layout {
     size_t pos4, cfg, chunk_start, partial, prm, e, p, R, w;
+    // training: FP64 forces, totals, adjoints, staged factors, gradient partials
+    size_t force, etot, vir, lam, aE, mu, st, gpart;
     size_t total;
     int max_chunks;
 };
@@ -301,7 +303,44 @@ Ws64Layout ws64_layout(const nep_model* m, int N, int B) {
     w.R = take(8 * n * m->hp.n_ang * nep::kLM);
     w.w = take(72 * n);
     w.total = o;
+    w.force = w.etot = w.vir = w.lam = w.aE = w.mu = w.st = w.gpart = 0;
     return w;
+}
+// the evaluation scratch followed by the training gradient's
+Ws64Layout ws64_train_layout(const nep_model* m, int N, int B, int n_fields) {
+    Ws64Layout w = ws64_layout(m, N, B);
+    size_t o = w.total;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o = align_up(o + bytes);
+        return at;
+    };
+    const size_t n = (size_t)N;
+    w.force = take(24 * n);
+    w.etot = take(8 * (size_t)B);
+    w.vir = take(72 * (size_t)B);
+    w.lam = take(24 * n);
+    w.aE = take(8 * (size_t)B);
+    w.mu = take(72 * (size_t)B);
+    w.st = take(8 * n * (size_t)n_fields);
+    w.gpart = take(8 * (size_t)nep::fp64_grad_chunks(N) * (size_t)m->lay.P);
+    w.total = o;
+    return w;
+}
+// staged factors per atom of the FP64 gradient (the layout of nep_fp64.cu)
+int fp64_fields_of(const nep_model* m) {
+    nep::F64Args a{};
+    a.D = m->lay.D;
+    a.H = m->hp.n_hidden;
+    a.NR = m->hp.n_rad;
+    a.T = m->hp.n_types;
+    a.KR = m->hp.k_rad;
+    a.NA = m->hp.n_ang;
+    a.KA = m->hp.k_ang;
+    return nep::fp64_grad_fields(a);
+}
+bool fp64_grad_supported(const nep_hparams& hp) {
+    return hp.n_types * hp.n_ang * hp.k_ang <= nep::kF64MaxBins;
 }
 bool fp64_supported(const nep_hparams& hp) {
     return hp.n_rad <= nep::kF64MaxN && hp.n_ang <= nep::kF64MaxN && hp.k_rad <= nep::kF64MaxK &&
@@ -585,25 +624,29 @@ size_t nep_workspace_bytes_fp64(const nep_model* m, int n_atoms, int n_cfg) {
     return ws64_layout(m, n_atoms, n_cfg).total;
 }
 
-nep_status nep_energy_forces_virial_fp64(nep_model* m, const nep_system* sys, const nep_nlist* nl,
-                                         const double* params, double* e_atom, double* force,
-                                         double* e_tot, double* virial, void* work, size_t work_bytes,
-                                         void* stream) {
+size_t nep_train_workspace_bytes_fp64(const nep_model* m, int n_atoms, int n_cfg) {
+    if (!m || n_atoms < 0 || n_cfg < 1) return 0;
+    return ws64_train_layout(m, n_atoms, n_cfg, fp64_fields_of(m)).total;
+}
+
+}  // extern "C"
+
+namespace {
+// checks shared by the FP64 calls, then the packed positions, the chunk plan
+// and (params == NULL) the promoted parameters
+nep_status fp64_begin(nep_model* m, const nep_system* sys, const nep_nlist* nl, const double* params,
+                      void* work, size_t work_bytes, const Ws64Layout& w, cudaStream_t st, nep::F64Args* out) {
     nep_status s;
-    if ((s = check_system(m, sys)) != NEP_OK) return s;
     if ((s = check_nlist(nl, sys->n_atoms)) != NEP_OK) return s;
     if (!fp64_supported(m->hp))
         return fail(NEP_ERR_UNSUPPORTED, "the FP64 path supports n_rad, n_ang <= %d and k_rad, k_ang <= %d",
                     nep::kF64MaxN, nep::kF64MaxK);
-    if (sys->n_atoms > 0 && !force) return fail(NEP_ERR_ARG, "force is NULL");
     if (!nl->min_image && !nl->shift) return fail(NEP_ERR_STATE, "list was not built (no shifts, not min-image)");
-    const Ws64Layout w = ws64_layout(m, sys->n_atoms, sys->n_cfg);
     if (work_bytes < w.total)
         return fail(NEP_ERR_ARG, "workspace too small: %zu bytes given, %zu needed", work_bytes, w.total);
     if (!work && w.total) return fail(NEP_ERR_ARG, "workspace is NULL");
     if ((reinterpret_cast<uintptr_t>(work) & 255) != 0)
         return fail(NEP_ERR_ARG, "workspace must be 256-byte aligned");
-    cudaStream_t st = (cudaStream_t)stream;
     const int N = sys->n_atoms, B = sys->n_cfg;
     NEP_CUDA(nep::launch_pack(sys->pos, sys->type, sys->atom_off, N, B, m->hp.n_types, at<float4>(work, w.pos4),
                               at<int>(work, w.cfg), nl->status, st),
@@ -613,7 +656,7 @@ nep_status nep_energy_forces_virial_fp64(nep_model* m, const nep_system* sys, co
         NEP_CUDA(nep::launch_promote(m->params, at<double>(work, w.prm), m->lay.P, st), "promote parameters");
         params = at<double>(work, w.prm);
     }
-    nep::F64Args a;
+    nep::F64Args a{};
     a.N = N;
     a.B = B;
     a.T = m->hp.n_types;
@@ -635,15 +678,96 @@ nep_status nep_energy_forces_virial_fp64(nep_model* m, const nep_system* sys, co
     a.nbr = nl->nbr;
     a.shift = nl->min_image ? nullptr : nl->shift;
     a.prm = params;
-    a.e = e_atom ? e_atom : at<double>(work, w.e);
+    a.e = at<double>(work, w.e);
     a.p = at<double>(work, w.p);
     a.R = at<double>(work, w.R);
     a.w = at<double>(work, w.w);
-    a.force = force;
     a.atom_off = sys->atom_off;
     a.chunk_start = at<int>(work, w.chunk_start);
     a.partial = at<double>(work, w.partial);
+    *out = a;
+    return NEP_OK;
+}
+}  // namespace
+
+extern "C" {
+
+nep_status nep_energy_forces_virial_fp64(nep_model* m, const nep_system* sys, const nep_nlist* nl,
+                                         const double* params, double* e_atom, double* force,
+                                         double* e_tot, double* virial, void* work, size_t work_bytes,
+                                         void* stream) {
+    nep_status s;
+    if ((s = check_system(m, sys)) != NEP_OK) return s;
+    if (sys->n_atoms > 0 && !force) return fail(NEP_ERR_ARG, "force is NULL");
+    const Ws64Layout w = ws64_layout(m, sys->n_atoms, sys->n_cfg);
+    nep::F64Args a;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((s = fp64_begin(m, sys, nl, params, work, work_bytes, w, st, &a)) != NEP_OK) return s;
+    if (e_atom) a.e = e_atom;
+    a.force = force;
     NEP_CUDA(nep::launch_efv_fp64(a, w.max_chunks, e_tot, virial, st), "FP64 kernels");
+    return NEP_OK;
+}
+
+nep_status nep_param_grad_fp64(nep_model* m, const nep_system* sys, const nep_nlist* nl, const double* params,
+                               const double* e_lbl, const double* f_lbl, const double* v_lbl,
+                               const float* w_host, int loss_mode, double* grad, double* loss, void* work,
+                               size_t work_bytes, void* stream) {
+    nep_status s;
+    if ((s = check_system(m, sys)) != NEP_OK) return s;
+    if (!fp64_grad_supported(m->hp))
+        return fail(NEP_ERR_UNSUPPORTED, "the FP64 gradient supports n_types * n_ang * k_ang <= %d",
+                    nep::kF64MaxBins);
+    if (!grad) return fail(NEP_ERR_ARG, "grad is NULL");
+    if (!e_lbl || !v_lbl || (sys->n_atoms > 0 && !f_lbl)) return fail(NEP_ERR_ARG, "labels are NULL");
+    if (!w_host) return fail(NEP_ERR_ARG, "w_host is NULL");
+    if (loss_mode != 0 && loss_mode != 1) return fail(NEP_ERR_ARG, "loss_mode must be 0 or 1");
+    const Ws64Layout w = ws64_train_layout(m, sys->n_atoms, sys->n_cfg, fp64_fields_of(m));
+    nep::F64Args a;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((s = fp64_begin(m, sys, nl, params, work, work_bytes, w, st, &a)) != NEP_OK) return s;
+    a.force = at<double>(work, w.force);
+    double* etot = at<double>(work, w.etot);
+    double* vir = at<double>(work, w.vir);
+    NEP_CUDA(nep::launch_efv_fp64(a, w.max_chunks, etot, vir, st), "FP64 kernels");
+    double* lam = at<double>(work, w.lam);
+    double* aE = at<double>(work, w.aE);
+    double* mu = at<double>(work, w.mu);
+    NEP_CUDA(nep::launch_loss_fp64(a, w.max_chunks, etot, vir, e_lbl, f_lbl, v_lbl, w_host, loss_mode, lam, aE,
+                                   mu, loss, st),
+             "FP64 loss");
+    a.lam = lam;
+    a.aE = aE;
+    a.mu = mu;
+    a.st = at<double>(work, w.st);
+    a.gpart = at<double>(work, w.gpart);
+    a.grad = grad;
+    NEP_CUDA(nep::launch_grad_fp64(a, st), "FP64 gradient");
+    return NEP_OK;
+}
+
+nep_status nep_param_grad_adjoint_fp64(nep_model* m, const nep_system* sys, const nep_nlist* nl,
+                                       const double* params, const double* a_e, const double* lam,
+                                       const double* mu, double* grad, void* work, size_t work_bytes,
+                                       void* stream) {
+    nep_status s;
+    if ((s = check_system(m, sys)) != NEP_OK) return s;
+    if (!fp64_grad_supported(m->hp))
+        return fail(NEP_ERR_UNSUPPORTED, "the FP64 gradient supports n_types * n_ang * k_ang <= %d",
+                    nep::kF64MaxBins);
+    if (!grad) return fail(NEP_ERR_ARG, "grad is NULL");
+    if (!a_e || !mu || (sys->n_atoms > 0 && !lam)) return fail(NEP_ERR_ARG, "adjoints are NULL");
+    const Ws64Layout w = ws64_train_layout(m, sys->n_atoms, sys->n_cfg, fp64_fields_of(m));
+    nep::F64Args a;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((s = fp64_begin(m, sys, nl, params, work, work_bytes, w, st, &a)) != NEP_OK) return s;
+    a.lam = lam;
+    a.aE = a_e;
+    a.mu = mu;
+    a.st = at<double>(work, w.st);
+    a.gpart = at<double>(work, w.gpart);
+    a.grad = grad;
+    NEP_CUDA(nep::launch_grad_fp64(a, st), "FP64 gradient");
     return NEP_OK;
 }
 

@@ -369,49 +369,53 @@ NEP_HD R fourbody(const R* s, R* ds) {
     return q4;
 }
 
+NEP_HD float fma_r(float a, float b, float c) { return fmaf(a, b, c); }
+NEP_HD double fma_r(double a, double b, double c) { return fma(a, b, c); }
+
 // Directional derivative of the 4-body gradient: J = dq4/ds (as fourbody)
 // and dJ = d/de J(s + e ds) at e = 0.  With A(s) linear, d(A^2) = A dA + dA A
 // and J is the same linear map of A^2 as dJ is of A dA + dA A.
-NEP_HD void fourbody_jvp(const float* s, const float* ds, float* J, float* dJ) {
-    float a[3][3], d[3][3];
+template <class R>
+NEP_HD void fourbody_jvp(const R* s, const R* ds, R* J, R* dJ) {
+    R a[3][3], d[3][3];
     {
-        const float azz = s[2] * (1.0f / 3.0f);
+        const R azz = s[2] * (R(1.0) / R(3.0));
         a[0][1] = a[1][0] = s[0];
         a[1][2] = a[2][1] = s[1];
         a[0][2] = a[2][0] = s[3];
         a[2][2] = azz;
-        a[0][0] = 0.5f * (s[4] - azz);
-        a[1][1] = -0.5f * (s[4] + azz);
-        const float dzz = ds[2] * (1.0f / 3.0f);
+        a[0][0] = R(0.5) * (s[4] - azz);
+        a[1][1] = -R(0.5) * (s[4] + azz);
+        const R dzz = ds[2] * (R(1.0) / R(3.0));
         d[0][1] = d[1][0] = ds[0];
         d[1][2] = d[2][1] = ds[1];
         d[0][2] = d[2][0] = ds[3];
         d[2][2] = dzz;
-        d[0][0] = 0.5f * (ds[4] - dzz);
-        d[1][1] = -0.5f * (ds[4] + dzz);
+        d[0][0] = R(0.5) * (ds[4] - dzz);
+        d[1][1] = -R(0.5) * (ds[4] + dzz);
     }
-    float B[3][3], C[3][3];
+    R B[3][3], C[3][3];
     for (int r = 0; r < 3; ++r)
         for (int c = 0; c < 3; ++c) {
-            float b = 0.0f, x = 0.0f, y = 0.0f;
+            R b = R(0.0), x = R(0.0), y = R(0.0);
             for (int k = 0; k < 3; ++k) {
-                b = fmaf(a[r][k], a[k][c], b);
-                x = fmaf(a[r][k], d[k][c], x);
-                y = fmaf(d[r][k], a[k][c], y);
+                b = fma_r(a[r][k], a[k][c], b);
+                x = fma_r(a[r][k], d[k][c], x);
+                y = fma_r(d[r][k], a[k][c], y);
             }
             B[r][c] = b;
             C[r][c] = x + y;
         }
-    J[0] = 6.0f * B[0][1];
-    J[1] = 6.0f * B[1][2];
-    J[2] = B[2][2] - 0.5f * (B[0][0] + B[1][1]);
-    J[3] = 6.0f * B[0][2];
-    J[4] = 1.5f * (B[0][0] - B[1][1]);
-    dJ[0] = 6.0f * C[0][1];
-    dJ[1] = 6.0f * C[1][2];
-    dJ[2] = C[2][2] - 0.5f * (C[0][0] + C[1][1]);
-    dJ[3] = 6.0f * C[0][2];
-    dJ[4] = 1.5f * (C[0][0] - C[1][1]);
+    J[0] = R(6.0) * B[0][1];
+    J[1] = R(6.0) * B[1][2];
+    J[2] = B[2][2] - R(0.5) * (B[0][0] + B[1][1]);
+    J[3] = R(6.0) * B[0][2];
+    J[4] = R(1.5) * (B[0][0] - B[1][1]);
+    dJ[0] = R(6.0) * C[0][1];
+    dJ[1] = R(6.0) * C[1][2];
+    dJ[2] = C[2][2] - R(0.5) * (C[0][0] + C[1][1]);
+    dJ[3] = R(6.0) * C[0][2];
+    dJ[4] = R(1.5) * (C[0][0] - C[1][1]);
 }
 
 }  // namespace nep

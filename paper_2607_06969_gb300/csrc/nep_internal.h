@@ -158,10 +158,12 @@ cudaError_t launch_neighbors(const float* pos, const float4* pos4, const int* at
                              const int* cfg, int N, int B, float rc_list, float rc_list_ang, float rc_phys,
                              int min_image, nep_nlist* nl, const NbrWork& w, cudaStream_t st);
 
-// FP64 evaluation (nep_fp64.cu): runtime hyper-parameters, every quantity in
-// double.  Bounds of the per-thread arrays:
-constexpr int kF64MaxN = 16;     // n_rad, n_ang
-constexpr int kF64MaxK = 16;     // k_rad, k_ang
+// FP64 evaluation and training gradient (nep_fp64.cu): runtime
+// hyper-parameters, every quantity in double.  Bounds of the per-thread
+// arrays:
+constexpr int kF64MaxN = 16;      // n_rad, n_ang
+constexpr int kF64MaxK = 16;      // k_rad, k_ang
+constexpr int kF64MaxBins = 256;  // n_types * n_ang * k_ang (training gradient)
 struct F64Args {
     int N, B, T, NR, NA, KR, KA, H, H4, D;
     ParamLayout L;
@@ -182,11 +184,26 @@ struct F64Args {
     const int* atom_off;           // [B+1]
     const int* chunk_start;        // [B+1]
     double* partial;               // [chunks][10]
+    // training gradient
+    const double* lam;             // [3][N] dL/dF
+    const double* aE;              // [B]    dL/dE
+    const double* mu;              // [B][9] dL/dV
+    double* st;                    // [fields][N] per-atom gradient factors
+    double* gpart;                 // [gradient chunks][P]
+    double* grad;                  // [P]
 };
 cudaError_t launch_promote(const float* src, double* dst, int n, cudaStream_t st);
 int fp64_lanes_per_atom(int N);
+int fp64_grad_fields(const F64Args& a);
+int fp64_grad_chunks(int N);
 cudaError_t launch_efv_fp64(const F64Args& a, int max_chunks, double* e_tot, double* virial,
                             cudaStream_t st);
+// loss (Eqs. 18-21, modes as nep_param_grad) and its adjoints from the FP64
+// forces, energies and virials
+cudaError_t launch_loss_fp64(const F64Args& a, int max_chunks, const double* e_tot, const double* vir,
+                             const double* e_lbl, const double* f_lbl, const double* v_lbl, const float* w,
+                             int mode, double* lam, double* aE, double* mu, double* loss, cudaStream_t st);
+cudaError_t launch_grad_fp64(const F64Args& a, cudaStream_t st);
 
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int n, float beta1, float beta2,
                         float eps, float c1, float c2, cudaStream_t st);
