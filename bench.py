@@ -235,9 +235,10 @@ def fig3_leg(nb, torch, I) -> dict:
 
 
 def fp64_leg(nb, torch, I) -> dict:
-    """E+F+V in the FP64 mode (nep_energy_forces_virial_fp64) against the
-    FP32 evaluation on the same list: the 216-atom cell and the 900k MD
-    system (18 A box with image shifts; minimum image for 900k)."""
+    """The FP64 mode against FP32 on the same lists: E+F+V
+    (nep_energy_forces_virial_fp64) on the 216-atom cell and the 900k MD
+    system (18 A box with image shifts; minimum image for 900k), and the
+    loss + gradient (nep_param_grad_fp64) on the 128-configuration batch."""
     out = {}
     for name, (s, h) in (("cell216", I.workload_cell216()), ("md900k", I.workload_md900k())):
         model = nb.Model(h, I.init_params(h).astype(np.float32))
@@ -267,8 +268,39 @@ def fp64_leg(nb, torch, I) -> dict:
                      "fp64_atoms_per_s": s.n_atoms / (ms["fp64"] * 1e-3),
                      "max_abs_force_diff_fp32_vs_fp64": float((o32[1].double() - o64[1]).abs().max().item())}
         del ws64, ws, nl, d, model
-    return {"workload": "one E+F+V evaluation, every intermediate in double (FP32 positions promoted)",
-            "cases": out}
+    # the training operator on the 128-configuration batch, FP64 against FP32
+    s, h = I.workload_train128()
+    model = nb.Model(h, I.init_params(h).astype(np.float32))
+    teacher = nb.Model(h, I.init_params(h, seed=I.SEED_TEACHER).astype(np.float32))
+    d = nb.DeviceSystem.from_inputs(s)
+    nl = nb.NeighborList(s.n_atoms, 112, 56)
+    ws = nb.Workspace(model, s.n_atoms, s.n_cfg, 112, 56, train=True)
+    nb.neighbors(model, d, nl, 0.0, ws)
+    _raise_if_overflow(nb, nl)
+    _, F, E, V = nb.energy_forces_virial(teacher, d, nl, ws)
+    F = F.contiguous()
+    F64 = F.double().contiguous()
+    ws64 = nb.Workspace64(model, s.n_atoms, s.n_cfg, train=True)
+    w = (1.0, 1.0, 0.1)
+    g32, _ = nb.param_grad(model, d, nl, ws, E, F, V, w, 0)
+    g64, _ = nb.param_grad_fp64(model, d, nl, ws64, E, F64, V, w, 0)
+    ms = {}
+    for tag, fn in (("fp64", lambda: nb.param_grad_fp64(model, d, nl, ws64, E, F64, V, w, 0, grad=g64)),
+                    ("fp32", lambda: nb.param_grad(model, d, nl, ws, E, F, V, w, 0, g32))):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(10):
+            fn()
+        t1.record()
+        torch.cuda.synchronize()
+        ms[tag] = t0.elapsed_time(t1) / 10
+    out["train128_loss_grad"] = {"n_atoms": s.n_atoms, "fp64_ms": ms["fp64"], "fp32_ms": ms["fp32"],
+                                 "rel_l2_fp32_vs_fp64": float((g32.double() - g64).norm() / g64.norm())}
+    return {"workload": "E+F+V evaluations and the loss + gradient, every intermediate in double "
+                        "(FP32 positions promoted)", "cases": out}
 
 
 def reference_arm(args, rank: int) -> None:
