@@ -76,6 +76,15 @@ class TrainConfig:
     eps: float = 1e-8
     history: list = field(default_factory=list)
 
+    @classmethod
+    def table2(cls, **kw) -> "TrainConfig":
+        """The training settings of Table 2: lr 1e-3 -> 1e-6 over 200 epochs,
+        loss weights (E, F, V) from (0.1, 10, 0.1) to (2, 1, 1).  The table
+        prints w_v^end twice; the first of the two rows is read as w_f^end."""
+        base = dict(lr_start=1e-3, lr_end=1e-6, epochs=200, w_start=(0.1, 10.0, 0.1), w_end=(2.0, 1.0, 1.0))
+        base.update(kw)
+        return cls(**base)
+
 
 class Trainer:
     """Adam over a fixed list of batches, one optimiser step per batch."""
