@@ -220,6 +220,55 @@ nep_status nep_param_grad_adjoint_fp64(nep_model* m, const nep_system* sys, cons
                                        const double* mu, double* grad, void* work, size_t work_bytes,
                                        void* stream);
 
+/* nep_energy_forces_virial with the per-configuration sums restricted to
+ * the atoms [0, n_owned): forces (and e_atom) are computed for every atom,
+ * e_tot and virial sum only the first n_owned.  The evaluation of one rank's
+ * local system in a spatial decomposition, whose owned atoms come first and
+ * whose ghost atoms follow (nep_domain_select). */
+nep_status nep_energy_forces_virial_owned(nep_model* m, const nep_system* sys, const nep_nlist* nl, int n_owned,
+                                          float* e_atom, float* force, double* e_tot, double* virial, void* work,
+                                          size_t work_bytes, void* stream);
+
+/* The velocity-Verlet pieces of nep_md_step, for callers that evaluate the
+ * forces themselves (a spatial decomposition): per atom v += half_dt F/m
+ * (masses_host[n_types] in u, F in eV/A, v in A/fs), then, if drift_dt > 0,
+ * x += drift_dt v.  nep_md_wrap wraps every atom into its configuration's
+ * box, as nep_md_step does at a rebuild.  sys->pos is written. */
+nep_status nep_md_kick(nep_model* m, const nep_system* sys, float* vel, const float* force, const float* masses_host,
+                       float half_dt, float drift_dt, void* stream);
+nep_status nep_md_wrap(nep_model* m, const nep_system* sys, void* stream);
+
+/* Spatial decomposition of one periodic configuration into slabs along x,
+ * for a multi-GPU run of one large system.  A rank owns the atoms with
+ * x in [x_lo, x_hi) and evaluates them with the ghost atoms within `halo` of
+ * its slab (for each ghost, the image in [x_lo - halo, x_hi + halo)).  With
+ * halo >= 2 (rc_rad + skin), the owned atoms' energies, forces and per-atom
+ * virials equal those of the whole-system evaluation; the ranks then combine
+ * their owned rows (one all-reduce of the forces, energies and virials).
+ *
+ * nep_domain_select: pos [3][N] device (x wrapped into [0, box_host[0])),
+ *   idx [cap], img [cap] device outputs: owned atoms, then ghosts, each in
+ *   atom order; img = the ghost's image in units of box x (0 for owned);
+ *   counts [2] device: owned, owned + ghosts (entries beyond cap are not
+ *   written: the caller compares counts[1] with cap and selects again).
+ *   Needs 0 <= x_lo < x_hi <= box x and slab + 2 halo <= box x.  work:
+ *   nep_domain_workspace_bytes(N) bytes.  Deterministic.
+ * nep_domain_gather: the n_local selected atoms into the local frame,
+ *   pos_local [3][n_local] = (x + img box_x - x_origin, y, z) and
+ *   type_local [n_local].
+ * nep_domain_scatter: dst[c][idx[l]] = src[c][l] for the owned rows
+ *   l < n_owned, c < ncomp (src [ncomp][n_local], dst [ncomp][N]); the
+ *   other entries of dst are left as they are. */
+size_t nep_domain_workspace_bytes(int n_atoms);
+nep_status nep_domain_select(const float* pos, int n_atoms, const float* box_host, float x_lo, float x_hi,
+                             float halo, int* idx, int* img, int cap, int* counts, void* work, size_t work_bytes,
+                             void* stream);
+nep_status nep_domain_gather(const float* pos, const int* type, int n_atoms, const int* idx, const int* img,
+                             int n_local, const float* box_host, float x_origin, float* pos_local, int* type_local,
+                             void* stream);
+nep_status nep_domain_scatter(const float* src, int n_local, int ncomp, const int* idx, int n_owned, float* dst,
+                              int n_atoms, void* stream);
+
 /* nep_energy_forces_virial without a caller workspace.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate
  * device memory at all -- for example a force plugin inside a host MD code

@@ -349,7 +349,7 @@ bool fp64_supported(const nep_hparams& hp) {
 
 nep_status efv_impl(nep_model* m, const nep_system* s, const nep_nlist* nl, float* e_atom,
                     float* force, double* e_tot, double* virial, void* work, const WsLayout& w,
-                    cudaStream_t st) {
+                    cudaStream_t st, int n_owned = -1) {
     const int N = s->n_atoms, B = s->n_cfg;
     NEP_CUDA(nep::launch_pack(s->pos, s->type, s->atom_off, N, B, m->hp.n_types, at<float4>(work, w.pos4),
                               at<int>(work, w.cfg), nl->status, st),
@@ -378,6 +378,7 @@ nep_status efv_impl(nep_model* m, const nep_system* s, const nep_nlist* nl, floa
     f.partial = at<double>(work, w.partial);
     f.force = force;
     f.e_out = e_atom;
+    f.n_owned = n_owned < 0 ? N : n_owned;
     NEP_CUDA(m->ks->finish(a, f, w.max_chunks, st), "finish kernel");
     NEP_CUDA(mark(3), "timing event");
     NEP_CUDA(nep::launch_final_reduce(B, at<int>(work, w.chunk_start), at<double>(work, w.partial), e_tot,
@@ -415,6 +416,7 @@ nep_status train_impl(nep_model* m, const nep_system* s, const nep_nlist* nl, co
         f.partial = at<double>(work, w.partial);
         f.force = at<float>(work, tl.force);
         f.e_out = nullptr;
+        f.n_owned = N;
         NEP_CUDA(m->ks->finish(a, f, w.max_chunks, st), "finish kernel");
         NEP_CUDA(nep::launch_final_reduce(B, at<int>(work, w.chunk_start), at<double>(work, w.partial),
                                           at<double>(work, tl.etot), at<double>(work, tl.vir), st),
@@ -768,6 +770,95 @@ nep_status nep_param_grad_adjoint_fp64(nep_model* m, const nep_system* sys, cons
     a.gpart = at<double>(work, w.gpart);
     a.grad = grad;
     NEP_CUDA(nep::launch_grad_fp64(a, st), "FP64 gradient");
+    return NEP_OK;
+}
+
+nep_status nep_energy_forces_virial_owned(nep_model* m, const nep_system* sys, const nep_nlist* nl, int n_owned,
+                                          float* e_atom, float* force, double* e_tot, double* virial, void* work,
+                                          size_t work_bytes, void* stream) {
+    nep_status s;
+    if ((s = check_system(m, sys)) != NEP_OK) return s;
+    if ((s = check_nlist(nl, sys->n_atoms)) != NEP_OK) return s;
+    if (n_owned < 0 || n_owned > sys->n_atoms) return fail(NEP_ERR_ARG, "need 0 <= n_owned <= n_atoms");
+    if (sys->n_atoms > 0 && !force) return fail(NEP_ERR_ARG, "force is NULL");
+    if (!nl->min_image && !nl->shift) return fail(NEP_ERR_STATE, "list was not built (no shifts, not min-image)");
+    WsLayout w;
+    if ((s = check_work(m, sys, nl, work, work_bytes, &w)) != NEP_OK) return s;
+    return efv_impl(m, sys, nl, e_atom, force, e_tot, virial, work, w, (cudaStream_t)stream, n_owned);
+}
+
+size_t nep_domain_workspace_bytes(int n_atoms) {
+    return n_atoms < 0 ? 0 : nep::domain_scratch_bytes(n_atoms);
+}
+
+nep_status nep_domain_select(const float* pos, int n_atoms, const float* box_host, float x_lo, float x_hi,
+                             float halo, int* idx, int* img, int cap, int* counts, void* work, size_t work_bytes,
+                             void* stream) {
+    if (n_atoms < 0 || cap < 0) return fail(NEP_ERR_ARG, "n_atoms and cap must be >= 0");
+    if (!box_host || !counts || (n_atoms > 0 && !pos) || (cap > 0 && (!idx || !img)))
+        return fail(NEP_ERR_ARG, "a pointer argument is NULL");
+    const float Lx = box_host[0];
+    if (!(Lx > 0.0f) || !std::isfinite(Lx)) return fail(NEP_ERR_ARG, "box x must be positive and finite");
+    if (!(x_lo >= 0.0f && x_lo < x_hi && x_hi <= Lx)) return fail(NEP_ERR_ARG, "need 0 <= x_lo < x_hi <= box x");
+    if (!(halo >= 0.0f) || !(x_hi - x_lo + 2.0f * halo <= Lx))
+        return fail(NEP_ERR_ARG, "need halo >= 0 and slab + 2 halo <= box x (one image per atom)");
+    if (work_bytes < nep::domain_scratch_bytes(n_atoms) || !work)
+        return fail(NEP_ERR_ARG, "workspace too small: %zu bytes given, %zu needed", work_bytes,
+                    nep::domain_scratch_bytes(n_atoms));
+    NEP_CUDA(nep::launch_domain_select(pos, n_atoms, Lx, x_lo, x_hi, halo, idx, img, cap, counts, work,
+                                       (cudaStream_t)stream),
+             "domain select");
+    return NEP_OK;
+}
+
+nep_status nep_domain_gather(const float* pos, const int* type, int n_atoms, const int* idx, const int* img,
+                             int n_local, const float* box_host, float x_origin, float* pos_local, int* type_local,
+                             void* stream) {
+    if (n_atoms < 0 || n_local < 0) return fail(NEP_ERR_ARG, "sizes must be >= 0");
+    if (!box_host || (n_local > 0 && (!pos || !type || !idx || !img || !pos_local || !type_local)))
+        return fail(NEP_ERR_ARG, "a pointer argument is NULL");
+    NEP_CUDA(nep::launch_domain_gather(pos, type, n_atoms, idx, img, n_local, box_host[0], x_origin, pos_local,
+                                       type_local, (cudaStream_t)stream),
+             "domain gather");
+    return NEP_OK;
+}
+
+nep_status nep_domain_scatter(const float* src, int n_local, int ncomp, const int* idx, int n_owned, float* dst,
+                              int n_atoms, void* stream) {
+    if (n_local < 0 || n_owned < 0 || n_owned > n_local || ncomp < 1 || n_atoms < 0)
+        return fail(NEP_ERR_ARG, "need 0 <= n_owned <= n_local and ncomp >= 1");
+    if (n_owned > 0 && (!src || !idx || !dst)) return fail(NEP_ERR_ARG, "a pointer argument is NULL");
+    NEP_CUDA(nep::launch_domain_scatter(src, n_local, ncomp, idx, n_owned, dst, n_atoms, (cudaStream_t)stream),
+             "domain scatter");
+    return NEP_OK;
+}
+
+nep_status nep_md_kick(nep_model* m, const nep_system* sys, float* vel, const float* force, const float* masses_host,
+                       float half_dt, float drift_dt, void* stream) {
+    nep_status s;
+    if ((s = check_system(m, sys)) != NEP_OK) return s;
+    if (!masses_host) return fail(NEP_ERR_ARG, "masses_host is NULL");
+    if (sys->n_atoms > 0 && (!vel || !force)) return fail(NEP_ERR_ARG, "vel or force is NULL");
+    if (!std::isfinite(half_dt) || !(drift_dt >= 0.0f) || !std::isfinite(drift_dt))
+        return fail(NEP_ERR_ARG, "half_dt must be finite and drift_dt finite and >= 0");
+    float inv_m[nep::kMaxTypes] = {0, 0, 0, 0};
+    for (int t = 0; t < m->hp.n_types; ++t) {
+        if (!(masses_host[t] > 0.0f)) return fail(NEP_ERR_ARG, "mass of species %d must be positive", t);
+        inv_m[t] = 1.0f / (masses_host[t] * 103.6427f);
+    }
+    float* pos = drift_dt > 0.0f ? const_cast<float*>(sys->pos) : nullptr;
+    NEP_CUDA(nep::launch_kick(vel, force, sys->type, inv_m, sys->n_atoms, half_dt, pos, drift_dt,
+                              (cudaStream_t)stream),
+             "kick");
+    return NEP_OK;
+}
+
+nep_status nep_md_wrap(nep_model* m, const nep_system* sys, void* stream) {
+    nep_status s;
+    if ((s = check_system(m, sys)) != NEP_OK) return s;
+    NEP_CUDA(nep::launch_wrap_segments(const_cast<float*>(sys->pos), sys->atom_off, sys->n_cfg, sys->box,
+                                       sys->n_atoms, (cudaStream_t)stream),
+             "wrap");
     return NEP_OK;
 }
 

@@ -96,6 +96,7 @@ struct FinishArgs {
     double* partial;               // [chunks][10] FP64 E and virial per chunk
     float* force;                  // [3][N]
     float* e_out;                  // [N] or null
+    int n_owned;                   // atoms [0, n_owned) enter the E and virial sums
 };
 
 // Offsets of the parameter blocks in the flat vector.
@@ -205,6 +206,16 @@ cudaError_t launch_loss_fp64(const F64Args& a, int max_chunks, const double* e_t
                              int mode, double* lam, double* aE, double* mu, double* loss, cudaStream_t st);
 cudaError_t launch_grad_fp64(const F64Args& a, cudaStream_t st);
 
+// slab decomposition along x (nep_domain.cu)
+size_t domain_scratch_bytes(int N);
+cudaError_t launch_domain_select(const float* pos, int N, float Lx, float lo, float hi, float halo, int* idx,
+                                 int* img, int cap, int* counts, void* scratch, cudaStream_t st);
+cudaError_t launch_domain_gather(const float* pos, const int* type, int N, const int* idx, const int* img,
+                                 int n_local, float Lx, float x_origin, float* pos_local, int* type_local,
+                                 cudaStream_t st);
+cudaError_t launch_domain_scatter(const float* src, int n_local, int ncomp, const int* idx, int n_owned,
+                                  float* dst, int N, cudaStream_t st);
+
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int n, float beta1, float beta2,
                         float eps, float c1, float c2, cudaStream_t st);
 cudaError_t fp32_peak(cudaStream_t st, double* tflops);
@@ -212,6 +223,7 @@ cudaError_t wait_selftest(cudaStream_t st, int* outcome);
 cudaError_t launch_kick(float* vel, const float* force, const int* type, const float* inv_mass,
                         int N, float half_dt, float* pos, float dt, cudaStream_t st);
 cudaError_t launch_wrap(float* pos, const int* cfg, const float* box, int N, cudaStream_t st);
+cudaError_t launch_wrap_segments(float* pos, const int* atom_off, int B, const float* box, int N, cudaStream_t st);
 cudaError_t launch_loss(int N, int B, const int* atom_off, const int* chunk_start, int max_chunks,
                         const float* force, const float* f_lbl, const double* e_tot,
                         const double* vir, const double* e_lbl, const double* v_lbl,

@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(kRedThreads) k_chunk_reduce(const EvalArgs a, 
     if (k >= total) return;
     const int b = find_segment(f.chunk_start, B, k);
     const int a0 = f.atom_off[b] + (k - f.chunk_start[b]) * kChunk;
-    const int a1 = min(f.atom_off[b + 1], a0 + kChunk);
+    const int a1 = min(min(f.atom_off[b + 1], a0 + kChunk), f.n_owned);
     float hi[10], lo[10];
 #pragma unroll
     for (int c = 0; c < 10; ++c) hi[c] = lo[c] = 0.0f;
@@ -592,20 +592,28 @@ __global__ void k_kick(float* __restrict__ vel, const float* __restrict__ force,
     }
 }
 
+// x wrapped into [0, L)
+__device__ __forceinline__ float wrap_coord(float x, float L) {
+    x = x - L * floorf(x / L);
+    if (x >= L) x -= L;
+    if (x < 0.0f) x += L;
+    if (!(x < L)) x = 0.0f;
+    return x;
+}
 __global__ void k_wrap(float* pos, const int* __restrict__ cfg, const float* __restrict__ box,
                        int N) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int b = cfg[i];
-    for (int d = 0; d < 3; ++d) {
-        const float L = box[3 * b + d];
-        float x = pos[(size_t)d * N + i];
-        x = x - L * floorf(x / L);
-        if (x >= L) x -= L;
-        if (x < 0.0f) x += L;
-        if (!(x < L)) x = 0.0f;
-        pos[(size_t)d * N + i] = x;
-    }
+    for (int d = 0; d < 3; ++d) pos[(size_t)d * N + i] = wrap_coord(pos[(size_t)d * N + i], box[3 * b + d]);
+}
+// the same, with each atom's configuration found from the CSR offsets
+__global__ void k_wrap_seg(float* pos, const int* __restrict__ atom_off, int B, const float* __restrict__ box,
+                           int N) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const int b = find_segment(atom_off, B, i);
+    for (int d = 0; d < 3; ++d) pos[(size_t)d * N + i] = wrap_coord(pos[(size_t)d * N + i], box[3 * b + d]);
 }
 
 // ------------------------------------------------------------- loss adjoints
@@ -818,6 +826,11 @@ cudaError_t launch_pack_adjoint(int N, int B, const float* lam, const double* a_
 
 cudaError_t launch_wrap(float* pos, const int* cfg, const float* box, int N, cudaStream_t st) {
     if (N > 0) k_wrap<<<blocks(N, 256), 256, 0, st>>>(pos, cfg, box, N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wrap_segments(float* pos, const int* atom_off, int B, const float* box, int N, cudaStream_t st) {
+    if (N > 0) k_wrap_seg<<<blocks(N, 256), 256, 0, st>>>(pos, atom_off, B, box, N);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,211 @@
+"""Spatial decomposition of one large periodic system over GPUs (one process
+per GPU): slabs along x with a two-layer ghost halo, replicated positions
+and velocities, and one all-reduce per step.
+
+Each rank holds the whole system's positions, velocities and forces.  At a
+list rebuild (every few steps, after the positions are wrapped) it selects
+its owned atoms (x in its slab) and the ghosts within halo = 2 (rc + skin)
+of the slab (nep_domain_select).  It gathers them into a local system whose
+x runs over [0, slab + 2 halo + pad), with pad > rc + skin so that the local
+periodic image in x never comes within the list cutoff, and builds the local
+list there.  Every step it then:
+  * gathers the current positions of its local atoms (nep_domain_gather);
+  * evaluates them, summing energy and virial over the owned atoms only
+    (nep_energy_forces_virial_owned);
+  * scatters the owned rows of the forces into a zeroed whole-system array
+    (nep_domain_scatter).
+One all-reduce (sum) over the ranks combines the forces, the energy and the
+virial.  Every rank then integrates all atoms identically (nep_md_kick),
+which keeps the positions replicated without a position exchange.
+
+With halo = 2 (rc + skin), each owned atom's neighbours (the first ghost
+layer) see their whole neighbourhood (the second layer).  So the owned atoms'
+forces, energies and per-atom virials are those of the whole-system
+evaluation, up to the order of FP32 sums.  Ownership and the ghost set are
+fixed between rebuilds, as the Verlet list is.
+
+The exchange is an all-reduce of 3N floats and 10 doubles per step, which
+suits a few GPUs of one NVLink domain.  The slab plus two halos must fit in
+the box: slab + 2 halo <= L_x.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import binding as nb
+
+
+def plan_slabs(Lx: float, world: int, rc: float, skin: float) -> tuple[list[tuple[float, float]], float]:
+    """Equal slabs [lo, hi) of [0, Lx) per rank and the halo 2 (rc + skin);
+    raises if a slab and its two halos do not fit in the box."""
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    halo = 2.0 * (rc + skin)
+    w = Lx / world
+    if world > 1 and w + 2.0 * halo > Lx:
+        raise ValueError(f"{world} slabs of {w:.2f} A with halos of {halo:.2f} A do not fit in {Lx:.2f} A")
+    edges = [Lx * r / world for r in range(world + 1)]
+    return [(float(edges[r]), float(edges[r + 1])) for r in range(world)], halo
+
+
+class LocalSystem:
+    """A device-resident single-configuration system built on device tensors
+    (the local system of one slab)."""
+
+    def __init__(self, n: int, box, device="cuda"):
+        import torch
+        self.n_atoms, self.n_cfg = n, 1
+        self.pos = torch.zeros(3, max(n, 1), dtype=torch.float32, device=device)
+        self.type = torch.zeros(max(n, 1), dtype=torch.int32, device=device)
+        self.atom_off_host = np.array([0, n], np.int32)
+        self.box_host = np.ascontiguousarray(np.asarray(box, np.float32).reshape(1, 3))
+        self.atom_off = torch.from_numpy(self.atom_off_host).to(device)
+        self.box = torch.from_numpy(self.box_host).to(device)
+        self.c = nb.System(n, 1, self.pos.data_ptr(), self.type.data_ptr(), self.atom_off.data_ptr(),
+                           self.box.data_ptr(), self.atom_off_host.ctypes.data, self.box_host.ctypes.data)
+
+
+class SlabDomain:
+    """One rank's slab of a single-configuration system `gsys`
+    (binding.DeviceSystem with n_cfg == 1)."""
+
+    def __init__(self, model: nb.Model, gsys: nb.DeviceSystem, lo: float, hi: float, halo: float, skin: float,
+                 cap: int, cap_ang: int, local_cap: int | None = None):
+        import torch
+        if gsys.n_cfg != 1:
+            raise ValueError("the spatial decomposition takes one configuration")
+        self.model, self.g = model, gsys
+        self.lo, self.hi, self.halo, self.skin = lo, hi, halo, skin
+        self.cap, self.cap_ang = cap, cap_ang
+        L = gsys.box_host[0]
+        h = model.h
+        self.origin = lo - halo
+        pad = h.rc_rad + skin + 1.0
+        self.box_local = np.array([hi - lo + 2.0 * halo + pad, L[1], L[2]], np.float32)
+        N = gsys.n_atoms
+        if local_cap is None:
+            local_cap = int(1.2 * N * min(1.0, (hi - lo + 2.0 * halo) / L[0])) + 64
+        self.local_cap = local_cap
+        dev = gsys.pos.device
+        self.idx = torch.zeros(local_cap, dtype=torch.int32, device=dev)
+        self.img = torch.zeros(local_cap, dtype=torch.int32, device=dev)
+        self.counts = torch.zeros(2, dtype=torch.int32, device=dev)
+        self.sel_bytes = int(nb.lib().nep_domain_workspace_bytes(N))
+        self.sel_work = torch.empty(self.sel_bytes + 256, dtype=torch.uint8, device=dev)
+        self.n_owned = self.n_local = 0
+        self.loc = None
+
+    def _select(self, stream=None) -> tuple[int, int]:
+        w = ctypes.c_void_p(self.sel_work.data_ptr() + (-self.sel_work.data_ptr()) % 256)
+        nb.check(nb.lib().nep_domain_select(
+            nb._ptr(self.g.pos), self.g.n_atoms, self.g.box_host.ctypes.data_as(ctypes.c_void_p),
+            ctypes.c_float(self.lo), ctypes.c_float(self.hi), ctypes.c_float(self.halo), nb._ptr(self.idx),
+            nb._ptr(self.img), self.local_cap, nb._ptr(self.counts), w, self.sel_bytes, nb._stream(stream)),
+            "nep_domain_select")
+        c = self.counts.cpu().numpy()
+        return int(c[0]), int(c[1])
+
+    def rebuild(self, stream=None) -> None:
+        """Select the owned atoms and the ghosts (positions wrapped into the
+        box), gather them and build the local list."""
+        import torch
+        n_owned, n_local = self._select(stream)
+        if n_local > self.local_cap:
+            self.local_cap = int(1.2 * n_local) + 64
+            dev = self.g.pos.device
+            self.idx = torch.zeros(self.local_cap, dtype=torch.int32, device=dev)
+            self.img = torch.zeros(self.local_cap, dtype=torch.int32, device=dev)
+            n_owned, n_local = self._select(stream)
+        if self.loc is None or self.loc.n_atoms != n_local:
+            self.loc = LocalSystem(n_local, self.box_local, self.g.pos.device)
+            self.nl = nb.NeighborList(n_local, self.cap, self.cap_ang, shifts=False)
+            self.ws = nb.Workspace(self.model, n_local, 1, self.cap, self.cap_ang)
+            self.force = torch.zeros(3, max(n_local, 1), dtype=torch.float32, device=self.g.pos.device)
+            self.e_tot = torch.zeros(1, dtype=torch.float64, device=self.g.pos.device)
+            self.vir = torch.zeros(1, 9, dtype=torch.float64, device=self.g.pos.device)
+        self.n_owned, self.n_local = n_owned, n_local
+        self.gather(stream)
+        nb.neighbors(self.model, self.loc, self.nl, self.skin, self.ws, stream)
+
+    def gather(self, stream=None) -> None:
+        nb.check(nb.lib().nep_domain_gather(
+            nb._ptr(self.g.pos), nb._ptr(self.g.type), self.g.n_atoms, nb._ptr(self.idx), nb._ptr(self.img),
+            self.n_local, self.g.box_host.ctypes.data_as(ctypes.c_void_p), ctypes.c_float(self.origin),
+            nb._ptr(self.loc.pos), nb._ptr(self.loc.type), nb._stream(stream)), "nep_domain_gather")
+
+    def evaluate(self, force_global, stream=None):
+        """Forces of the owned atoms into force_global [3][N] (other entries
+        untouched), and the owned energy [1] and virial [1, 9] sums."""
+        self.gather(stream)
+        nb.check(nb.lib().nep_energy_forces_virial_owned(
+            self.model.handle, ctypes.byref(self.loc.c), ctypes.byref(self.nl.c), self.n_owned, None,
+            nb._ptr(self.force), nb._ptr(self.e_tot), nb._ptr(self.vir), self.ws.ptr, self.ws.bytes,
+            nb._stream(stream)), "nep_energy_forces_virial_owned")
+        nb.check(nb.lib().nep_domain_scatter(
+            nb._ptr(self.force), self.n_local, 3, nb._ptr(self.idx), self.n_owned, nb._ptr(force_global),
+            self.g.n_atoms, nb._stream(stream)), "nep_domain_scatter")
+        return self.e_tot, self.vir
+
+
+def combine_owned(dist, force_global, e_tot, virial) -> None:
+    """In place over the process group: every rank's owned rows of the
+    forces (zeros elsewhere) and its owned energy and virial sums become the
+    whole system's (one all-reduce each)."""
+    dist.all_reduce(force_global)
+    dist.all_reduce(e_tot)
+    dist.all_reduce(virial)
+
+
+class SpatialMD:
+    """Velocity Verlet for one rank of a slab decomposition (dt in fs,
+    masses in u, rebuild every `rebuild_every` steps), with the whole
+    system's state replicated on every rank.  `reduce(force, e, v)` combines
+    the ranks' owned results in place (combine_owned with a process group,
+    or a sum over emulated ranks)."""
+
+    def __init__(self, model: nb.Model, gsys: nb.DeviceSystem, vel, masses, domains, reduce, dt: float = 2.0,
+                 skin: float = 1.0, rebuild_every: int = 10):
+        import torch
+        self.model, self.g, self.vel = model, gsys, vel
+        self.masses = np.ascontiguousarray(np.asarray(masses, np.float32))
+        self.domains, self.reduce = list(domains), reduce
+        self.dt, self.skin, self.every = dt, skin, rebuild_every
+        dev = gsys.pos.device
+        self.force = torch.zeros(3, gsys.n_atoms, dtype=torch.float32, device=dev)
+        self.e_tot = torch.zeros(1, dtype=torch.float64, device=dev)
+        self.vir = torch.zeros(1, 9, dtype=torch.float64, device=dev)
+        self.k = 0
+
+    def _forces(self) -> None:
+        self.force.zero_()
+        self.e_tot.zero_()
+        self.vir.zero_()
+        for d in self.domains:
+            e, v = d.evaluate(self.force)
+            self.e_tot += e
+            self.vir += v
+        self.reduce(self.force, self.e_tot, self.vir)
+
+    def start(self) -> None:
+        """Wrap, select, build the lists and evaluate the initial forces."""
+        nb.check(nb.lib().nep_md_wrap(self.model.handle, ctypes.byref(self.g.c), nb._stream()), "nep_md_wrap")
+        for d in self.domains:
+            d.rebuild()
+        self._forces()
+
+    def step(self) -> None:
+        lib, mp = nb.lib(), self.masses.ctypes.data_as(ctypes.c_void_p)
+        nb.check(lib.nep_md_kick(self.model.handle, ctypes.byref(self.g.c), nb._ptr(self.vel), nb._ptr(self.force),
+                                 mp, ctypes.c_float(0.5 * self.dt), ctypes.c_float(self.dt), nb._stream()),
+                 "nep_md_kick")
+        self.k += 1
+        if self.k % self.every == 0:
+            nb.check(lib.nep_md_wrap(self.model.handle, ctypes.byref(self.g.c), nb._stream()), "nep_md_wrap")
+            for d in self.domains:
+                d.rebuild()
+        self._forces()
+        nb.check(lib.nep_md_kick(self.model.handle, ctypes.byref(self.g.c), nb._ptr(self.vel), nb._ptr(self.force),
+                                 mp, ctypes.c_float(0.5 * self.dt), ctypes.c_float(0.0), nb._stream()),
+                 "nep_md_kick")

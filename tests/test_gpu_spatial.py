@@ -1,0 +1,130 @@
+"""Spatial decomposition (slabs along x with a two-layer halo) against the
+whole-system evaluation, with the ranks emulated one after another on one
+GPU: the owned atoms' forces, the energy and the virial; the selection
+against a host recomputation; and a short decomposed MD run against
+nep_md_step.
+
+The owned atoms see the same neighbours as in the whole system, in another
+list order.  FP32 sums in another order differ by a few ulp of the terms, so
+forces agree to 1e-5 eV/A (terms are below ~1 eV/A).  The FP64 totals sum
+FP32 per-atom values: 1e-6 eV per atom."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2607_06969_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+SKIN = 1.0
+
+
+@pytest.fixture(scope="module")
+def nb():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2607_06969_gb300 import build as B
+    B.build()
+    from paper_2607_06969_gb300 import binding
+    binding.lib()
+    return binding
+
+
+def whole(nb, model, s, cap=112, cap_ang=56):
+    dsys = nb.DeviceSystem.from_inputs(s)
+    nl = nb.NeighborList(s.n_atoms, cap, cap_ang, shifts=False)
+    ws = nb.Workspace(model, s.n_atoms, 1, cap, cap_ang)
+    nb.neighbors(model, dsys, nl, SKIN, ws)
+    assert nb.check_list(nl) == nb.NEP_OK
+    return dsys, nl, ws, nb.energy_forces_virial(model, dsys, nl, ws)
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_slab_evaluation_matches_whole_system(nb, world):
+    import torch
+    from paper_2607_06969_gb300 import spatial as SP
+    h = I.HYPER_SMALL
+    s = I.rocksalt(14, vacancy=0.2, tag=6)
+    model = nb.Model(h, I.init_params(h).astype(np.float32))
+    dsys, _, _, (e_ref, f_ref, et_ref, v_ref) = whole(nb, model, s)
+    slabs, halo = SP.plan_slabs(float(s.box[0, 0]), world, h.rc_rad, SKIN)
+    doms = [SP.SlabDomain(model, dsys, lo, hi, halo, SKIN, 112, 56) for lo, hi in slabs]
+    F = torch.zeros_like(f_ref)
+    E = torch.zeros(1, dtype=torch.float64, device="cuda")
+    V = torch.zeros(1, 9, dtype=torch.float64, device="cuda")
+    owned = []
+    for d in doms:
+        d.rebuild()
+        assert nb.check_list(d.nl) == nb.NEP_OK
+        e, v = d.evaluate(F)
+        E += e
+        V += v
+        owned.append(d.idx[:d.n_owned].cpu().numpy())
+    owned = np.concatenate(owned)
+    assert owned.size == s.n_atoms and np.array_equal(np.sort(owned), np.arange(s.n_atoms))
+    assert (F - f_ref).abs().max().item() <= 1e-5
+    assert abs(E.item() - et_ref.item()) <= 1e-6 * s.n_atoms
+    assert (V - v_ref).abs().max().item() <= 1e-6 * s.n_atoms
+
+
+def test_domain_select_against_host(nb):
+    """Owned atoms and ghosts with their images, in atom order, against the
+    same classification done on the host in FP32."""
+    from paper_2607_06969_gb300 import spatial as SP
+    h = I.HYPER_SMALL
+    s = I.rocksalt(14, vacancy=0.2, tag=6)
+    model = nb.Model(h, I.init_params(h).astype(np.float32))
+    dsys = nb.DeviceSystem.from_inputs(s)
+    Lx = np.float32(s.box[0, 0])
+    slabs, halo = SP.plan_slabs(float(Lx), 3, h.rc_rad, SKIN)
+    x = s.pos32()[:, 0].astype(np.float32)
+    for lo, hi in slabs:
+        d = SP.SlabDomain(model, dsys, lo, hi, halo, SKIN, 112, 56)
+        n_owned, n_local = d._select()
+        lo32, hi32, ha32 = np.float32(lo), np.float32(hi), np.float32(halo)
+        own = np.nonzero((x >= lo32) & (x < hi32))[0]
+        gh, im = [], []
+        for i in np.setdiff1d(np.arange(x.size), own):
+            for k in (-1, 0, 1):
+                xs = np.float32(x[i] + np.float32(k) * Lx)
+                if (lo32 - ha32 <= xs < lo32) or (hi32 <= xs < hi32 + ha32):
+                    gh.append(i)
+                    im.append(k)
+                    break
+        assert n_owned == own.size and n_local == own.size + len(gh)
+        assert np.array_equal(d.idx[:n_local].cpu().numpy(), np.concatenate([own, gh]).astype(np.int32))
+        assert np.array_equal(d.img[:n_local].cpu().numpy(), np.concatenate([np.zeros(own.size), im]).astype(np.int32))
+
+
+def test_spatial_md_tracks_whole_system_md(nb):
+    """Twelve velocity-Verlet steps (a rebuild at step 10) of two emulated
+    ranks against nep_md_step on the whole system."""
+    import torch
+    from paper_2607_06969_gb300 import spatial as SP
+    h = I.HYPER_SMALL
+    s = I.rocksalt(14, vacancy=0.2, tag=6)
+    model = nb.Model(h, I.init_params(h).astype(np.float32))
+    masses = I.MASSES.astype(np.float32)
+    v0 = np.ascontiguousarray(I.maxwell_boltzmann(s.types, 900.0).astype(np.float32).T)
+    # whole system
+    dsys, nl, ws, (_, force, et, vir) = whole(nb, model, s)
+    vel = torch.from_numpy(v0.copy()).cuda()
+    for k in range(1, 13):
+        nb.md_step(model, dsys, nl, vel, force, et, vir, masses, 2.0, SKIN, k % 10 == 0, ws)
+    # two slabs, state replicated in one set of arrays
+    gsys = nb.DeviceSystem.from_inputs(s)
+    vel2 = torch.from_numpy(v0.copy()).cuda()
+    slabs, halo = SP.plan_slabs(float(s.box[0, 0]), 2, h.rc_rad, SKIN)
+    doms = [SP.SlabDomain(model, gsys, lo, hi, halo, SKIN, 112, 56) for lo, hi in slabs]
+    md = SP.SpatialMD(model, gsys, vel2, masses, doms, reduce=lambda f, e, v: None, dt=2.0, skin=SKIN,
+                      rebuild_every=10)
+    md.start()
+    for _ in range(12):
+        md.step()
+    torch.cuda.synchronize()
+    for d in doms:
+        assert nb.check_list(d.nl) == nb.NEP_OK
+    assert (gsys.pos - dsys.pos).abs().max().item() <= 1e-4
+    assert (vel2 - vel).abs().max().item() <= 1e-5
+    assert abs(md.e_tot.item() - et.item()) <= 1e-5 * s.n_atoms
