@@ -51,20 +51,56 @@ def plan_slabs(Lx: float, world: int, rc: float, skin: float) -> tuple[list[tupl
 
 
 class LocalSystem:
-    """A device-resident single-configuration system built on device tensors
-    (the local system of one slab)."""
+    """A device-resident single-configuration system of up to `cap` atoms
+    (the local system of one slab).  Its arrays are allocated once; resize(n)
+    re-points the nep_system at the first n atoms ([3][n] is the contiguous
+    head of the [3 cap] buffer)."""
 
-    def __init__(self, n: int, box, device="cuda"):
+    def __init__(self, cap: int, box, device="cuda"):
         import torch
-        self.n_atoms, self.n_cfg = n, 1
-        self.pos = torch.zeros(3, max(n, 1), dtype=torch.float32, device=device)
-        self.type = torch.zeros(max(n, 1), dtype=torch.int32, device=device)
-        self.atom_off_host = np.array([0, n], np.int32)
+        self.cap = max(cap, 1)
+        self.pos_buf = torch.zeros(3 * self.cap, dtype=torch.float32, device=device)
+        self.type = torch.zeros(self.cap, dtype=torch.int32, device=device)
         self.box_host = np.ascontiguousarray(np.asarray(box, np.float32).reshape(1, 3))
-        self.atom_off = torch.from_numpy(self.atom_off_host).to(device)
         self.box = torch.from_numpy(self.box_host).to(device)
+        self.atom_off_host = np.zeros(2, np.int32)
+        self.atom_off = torch.zeros(2, dtype=torch.int32, device=device)
+        self.resize(0)
+
+    def resize(self, n: int) -> None:
+        import torch
+        if n > self.cap:
+            raise ValueError(f"{n} atoms exceed the local capacity {self.cap}")
+        self.n_atoms, self.n_cfg = n, 1
+        self.pos = self.pos_buf[:3 * max(n, 1)].view(3, max(n, 1))
+        self.atom_off_host[1] = n
+        self.atom_off.copy_(torch.from_numpy(self.atom_off_host))
         self.c = nb.System(n, 1, self.pos.data_ptr(), self.type.data_ptr(), self.atom_off.data_ptr(),
                            self.box.data_ptr(), self.atom_off_host.ctypes.data, self.box_host.ctypes.data)
+
+
+class LocalList:
+    """A minimum-image Verlet list for up to `cap_atoms` atoms, allocated
+    once; resize(n) re-points the nep_nlist at n atoms (slot-major arrays
+    [cap][n] are the contiguous head of each buffer)."""
+
+    def __init__(self, cap_atoms: int, cap: int, cap_ang: int, device="cuda"):
+        import torch
+        self.cap_atoms, self.cap, self.cap_ang = max(cap_atoms, 1), cap, cap_ang
+        z = dict(dtype=torch.int32, device=device)
+        self.cnt_buf = torch.zeros(self.cap_atoms, **z)
+        self.cnt_ang_buf = torch.zeros(self.cap_atoms, **z)
+        self.nbr_buf = torch.zeros(cap * self.cap_atoms, **z)
+        self.rev_buf = torch.zeros(cap_ang * self.cap_atoms, **z)
+        self.status = torch.zeros(4, **z)
+        self.resize(0)
+
+    def resize(self, n: int) -> None:
+        if n > self.cap_atoms:
+            raise ValueError(f"{n} atoms exceed the list capacity {self.cap_atoms}")
+        self.n_atoms = n
+        self.c = nb.NList(self.cap, self.cap_ang, self.cnt_buf.data_ptr(), self.cnt_ang_buf.data_ptr(),
+                          self.nbr_buf.data_ptr(), 0, self.rev_buf.data_ptr(), self.status.data_ptr(), 0.0, 0)
 
 
 class SlabDomain:
@@ -109,7 +145,9 @@ class SlabDomain:
 
     def rebuild(self, stream=None) -> None:
         """Select the owned atoms and the ghosts (positions wrapped into the
-        box), gather them and build the local list."""
+        box), gather them and build the local list.  The local arrays are
+        allocated at the first call and grown only when the selection
+        outgrows them."""
         import torch
         n_owned, n_local = self._select(stream)
         if n_local > self.local_cap:
@@ -118,14 +156,18 @@ class SlabDomain:
             self.idx = torch.zeros(self.local_cap, dtype=torch.int32, device=dev)
             self.img = torch.zeros(self.local_cap, dtype=torch.int32, device=dev)
             n_owned, n_local = self._select(stream)
-        if self.loc is None or self.loc.n_atoms != n_local:
-            self.loc = LocalSystem(n_local, self.box_local, self.g.pos.device)
-            self.nl = nb.NeighborList(n_local, self.cap, self.cap_ang, shifts=False)
-            self.ws = nb.Workspace(self.model, n_local, 1, self.cap, self.cap_ang)
-            self.force = torch.zeros(3, max(n_local, 1), dtype=torch.float32, device=self.g.pos.device)
-            self.e_tot = torch.zeros(1, dtype=torch.float64, device=self.g.pos.device)
-            self.vir = torch.zeros(1, 9, dtype=torch.float64, device=self.g.pos.device)
+        if self.loc is None or n_local > self.loc.cap:
+            dev = self.g.pos.device
+            self.loc = LocalSystem(self.local_cap, self.box_local, dev)
+            self.nl = LocalList(self.local_cap, self.cap, self.cap_ang, dev)
+            self.ws = nb.Workspace(self.model, self.local_cap, 1, self.cap, self.cap_ang)
+            self.force_buf = torch.zeros(3 * self.local_cap, dtype=torch.float32, device=dev)
+            self.e_tot = torch.zeros(1, dtype=torch.float64, device=dev)
+            self.vir = torch.zeros(1, 9, dtype=torch.float64, device=dev)
         self.n_owned, self.n_local = n_owned, n_local
+        self.loc.resize(n_local)
+        self.nl.resize(n_local)
+        self.force = self.force_buf[:3 * max(n_local, 1)].view(3, max(n_local, 1))
         self.gather(stream)
         nb.neighbors(self.model, self.loc, self.nl, self.skin, self.ws, stream)
 
