@@ -149,12 +149,22 @@ __device__ void angular_g(const F64Args& a, int ti, int tj, const double* f, con
     }
 }
 
+// g_n only (the descriptors need no derivative)
+__device__ void angular_g_value(const F64Args& a, int ti, int tj, const double* f, double* g) {
+    const double* cA = a.prm + a.L.off_cA + (size_t)(ti * a.T + tj) * a.NA * a.KA;
+    for (int n = 0; n < a.NA; ++n) {
+        double u = 0.0;
+        for (int k = 0; k < a.KA; ++k) u += cA[n * a.KA + k] * f[k];
+        g[n] = u;
+    }
+}
+
 // q [D], S [NA*24] and the species-resolved radial basis sums F [T*KR] of
 // atom fr.i (the same values in every lane of its group)
 template <int G>
 __device__ void descriptors64(const F64Args& a, const Frame64& fr, int lane, double* q, double* S, double* F) {
     const int T = a.T, NR = a.NR, NA = a.NA, KR = a.KR, KA = a.KA;
-    double f[kF64MaxK], fp[kF64MaxK], g[kF64MaxN], gp[kF64MaxN];
+    double f[kF64MaxK], fp[kF64MaxK], g[kF64MaxN];
     for (int x = 0; x < T * KR; ++x) F[x] = 0.0;
     for (int x = 0; x < NA * kLM; ++x) S[x] = 0.0;
     const int nc = a.cnt[fr.i];
@@ -165,7 +175,7 @@ __device__ void descriptors64(const F64Args& a, const Frame64& fr, int lane, dou
         for (int k = 0; k < KR; ++k) F[p.tj * KR + k] += f[k];
         if (!(p.r < a.rc_ang)) continue;
         basis64(p.r, a.rc_ang, KA, f, fp);
-        angular_g(a, fr.ti, p.tj, f, fp, g, gp);
+        angular_g_value(a, fr.ti, p.tj, f, g);
         const HarmTermsT<double> ht = harm_terms(p.u[0], p.u[1], p.u[2]);
         for (int m = 0; m < kLM; ++m) {
             double Y, gx, gy, gz;
