@@ -57,3 +57,27 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu(L):
     ok = nb.hparams_of(I.HYPER_SMALL)
     assert L.nep_create(ctypes.byref(ok), None, 3, ctypes.byref(out)) == nb.NEP_ERR_ARG
     assert L.nep_num_params(ctypes.byref(bad)) == 0
+
+
+def test_domain_calls_reject_bad_arguments_before_touching_the_gpu(L):
+    """The slab-decomposition calls check their host arguments first."""
+    box = (ctypes.c_float * 3)(30.0, 30.0, 30.0)
+    counts = ctypes.c_void_p(16)            # never dereferenced: the checks fail first
+    f = ctypes.c_float
+    assert L.nep_domain_workspace_bytes(-1) == 0
+    ws = L.nep_domain_workspace_bytes(1000)
+    assert ws > 0
+    # slab outside the box, and a slab whose halos overlap it
+    assert L.nep_domain_select(ctypes.c_void_p(16), 1000, box, f(10.0), f(40.0), f(2.0), ctypes.c_void_p(16),
+                               ctypes.c_void_p(16), 10, counts, ctypes.c_void_p(256), ws, None) == nb.NEP_ERR_ARG
+    assert L.nep_domain_select(ctypes.c_void_p(16), 1000, box, f(0.0), f(20.0), f(6.0), ctypes.c_void_p(16),
+                               ctypes.c_void_p(16), 10, counts, ctypes.c_void_p(256), ws, None) == nb.NEP_ERR_ARG
+    assert "halo" in nb.last_error()
+    # workspace too small
+    assert L.nep_domain_select(ctypes.c_void_p(16), 1000, box, f(0.0), f(10.0), f(2.0), ctypes.c_void_p(16),
+                               ctypes.c_void_p(16), 10, counts, ctypes.c_void_p(256), ws - 1, None) == nb.NEP_ERR_ARG
+    # scatter: more owned rows than local rows
+    assert L.nep_domain_scatter(ctypes.c_void_p(16), 5, 3, ctypes.c_void_p(16), 6, ctypes.c_void_p(16), 10,
+                                None) == nb.NEP_ERR_ARG
+    # gather: missing pointers
+    assert L.nep_domain_gather(None, None, 10, None, None, 4, box, f(0.0), None, None, None) == nb.NEP_ERR_ARG
