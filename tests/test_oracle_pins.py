@@ -412,3 +412,28 @@ def test_generators_composition():
         d, _ = cKDTree(P, boxsize=b.box[k, 0]).query(P, k=2)
         assert d[:, 1].min() >= 2.4
     assert np.isclose(b.box[1, 0], (100 / 0.0325) ** (1 / 3))
+
+
+def test_evaluate_centers_equals_whole_system():
+    """The neighbourhood evaluation of sampled atoms (used at the full
+    workload sizes) against the whole-system evaluation (pinned above by
+    finite differences and invariances): the same E_i and F_i, and per-atom
+    virials that sum to each configuration's virial."""
+    s = I.packing_batch([24, 40], tag=77)
+    h = tiny_hyper()
+    th = I.init_params(h)
+    p32 = s.pos32()
+    box64 = s.box.astype(np.float32).astype(np.float64)
+    pairs = O.neighbor_pairs(p32, s.box, s.atom_off, h.rc_rad)
+    whole = O.energy_forces_virial(h, th, p32.astype(np.float64), s.types, box64, s.atom_off, pairs)
+    centers = np.arange(s.n_atoms)
+    part = O.evaluate_centers(h, th, p32, p32.astype(np.float64), s.types, box64, s.atom_off, centers)
+    assert np.allclose(part["E"], whole["E"], rtol=0, atol=1e-12)
+    assert np.allclose(part["F"], whole["F"], rtol=0, atol=1e-12)
+    for b in range(s.n_cfg):
+        a0, a1 = s.atom_off[b], s.atom_off[b + 1]
+        assert np.allclose(part["W"][a0:a1].sum(0), whole["V"][b], rtol=0, atol=1e-11)
+    # a sample of centres gives the same rows as the full evaluation
+    sub = O.evaluate_centers(h, th, p32, p32.astype(np.float64), s.types, box64, s.atom_off,
+                             np.array([3, 30, 50]))
+    assert np.allclose(sub["F"], whole["F"][[3, 30, 50]], rtol=0, atol=1e-12)
