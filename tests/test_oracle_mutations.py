@@ -1,0 +1,130 @@
+"""The pins bind: each test plants one plausible mistake in the oracle (on
+the CPU, by replacing one of its functions for the duration of the test)
+and checks that a pin in tests/test_oracle_pins.py or tests/test_train_loop.py
+then fails."""
+import importlib.util
+import os
+
+import numpy as np
+import pytest
+
+from oracle import nep_oracle as O
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _load(name):
+    spec = importlib.util.spec_from_file_location("_mut_" + name, os.path.join(HERE, name + ".py"))
+    m = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(m)
+    return m
+
+
+P = _load("test_oracle_pins")
+TL = _load("test_train_loop")
+
+
+def _fails(fn, *args):
+    with pytest.raises(AssertionError):
+        fn(*args)
+
+
+def test_cutoff_with_the_wrong_sign_is_caught(monkeypatch):
+    """f_c = (1 - cos(pi r/rc))/2 instead of (1 + cos)/2 (Eq. 14)."""
+    def wrong(r, rc):
+        inside = r < rc
+        fc = np.where(inside, 0.5 * (1.0 - np.cos(np.pi * r / rc)), 0.0)
+        dfc = np.where(inside, 0.5 * np.pi / rc * np.sin(np.pi * r / rc), 0.0)
+        return fc, dfc
+    monkeypatch.setattr(O, "cutoff_fn", wrong)
+    _fails(P.test_cutoff_values)
+    _fails(P.test_dimer_closed_form, 0, 2)
+
+
+def test_chebyshev_index_shift_is_caught(monkeypatch):
+    """Q_k built from T_{k+1} instead of T_k (Eq. 12)."""
+    real = O.chebyshev_basis
+
+    def wrong(r, rc, K):
+        Q, dQ = real(r, rc, K + 1)
+        return Q[..., 1:], dQ[..., 1:]
+    monkeypatch.setattr(O, "chebyshev_basis", wrong)
+    _fails(P.test_chebyshev_basis_against_library_and_cosines)
+    _fails(P.test_dimer_closed_form, 1, 1)
+
+
+def test_legendre_recursion_error_is_caught(monkeypatch):
+    """Bonnet's recursion with (2l+1) in place of (2l-1)."""
+    def wrong(c, L):
+        Pl = [np.ones_like(c), c]
+        dP = [np.zeros_like(c), np.ones_like(c)]
+        for l in range(2, L + 1):
+            Pl.append(((2 * l + 1) * c * Pl[l - 1] - (l - 1) * Pl[l - 2]) / l)
+            dP.append(dP[l - 2] + (2 * l - 1) * Pl[l - 1])
+        return Pl, dP
+    monkeypatch.setattr(O, "legendre", wrong)
+    _fails(P.test_legendre_against_scipy)
+    _fails(P.test_legendre_form_equals_sform_addition_theorem)
+
+
+def test_swapped_species_pair_is_caught(monkeypatch):
+    """c indexed by (Zj, Zi) instead of (Zi, Zj)."""
+    real = O._type_pair_apply
+    monkeypatch.setattr(O, "_type_pair_apply", lambda coef, ti, tj, X: real(coef, tj, ti, X))
+    _fails(P.test_dimer_closed_form, 0, 2)
+
+
+def test_force_sign_flip_is_caught(monkeypatch):
+    """F_i = +dE/dr_i instead of -dE/dr_i (Eq. 3)."""
+    real = O.energy_forces_virial
+
+    def wrong(*a, **k):
+        out = dict(real(*a, **k))
+        out["F"] = -out["F"]
+        return out
+    monkeypatch.setattr(O, "energy_forces_virial", wrong)
+    _fails(P.test_forces_central_difference, "tiny")
+
+
+def test_transposed_virial_sign_is_caught(monkeypatch):
+    """V = +sum f (x) r instead of -sum f (x) r (Eq. 4)."""
+    real = O.energy_forces_virial
+
+    def wrong(*a, **k):
+        out = dict(real(*a, **k))
+        out["V"] = -out["V"]
+        return out
+    monkeypatch.setattr(O, "energy_forces_virial", wrong)
+    _fails(P.test_virial_finite_strain)
+
+
+def test_dropped_images_are_caught(monkeypatch):
+    """Pairs through periodic images dropped (only the zero image kept)."""
+    real = O.neighbor_pairs
+
+    def wrong(*a, **k):
+        i, j, s = real(*a, **k)
+        keep = np.all(s == 0, axis=1)
+        return i[keep], j[keep], s[keep]
+    monkeypatch.setattr(O, "neighbor_pairs", wrong)
+    _fails(P.test_neighbors_small_box_counts_images)
+
+
+def test_loss_without_the_batch_mean_is_caught(monkeypatch):
+    """The batch sum in place of the batch mean (Eqs. 18-21)."""
+    real = O.loss_value
+
+    def wrong(h, theta, pos, types, box, atom_off, *rest, **k):
+        return real(h, theta, pos, types, box, atom_off, *rest, **k) * (len(atom_off) - 1)
+    monkeypatch.setattr(O, "loss_value", wrong)
+    _fails(P.test_loss_closed_form)
+
+
+def test_adam_without_bias_correction_is_caught(monkeypatch):
+    """Adam's first and second moments used without the 1 - beta^t corrections."""
+    def wrong(theta, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        m = beta1 * m + (1 - beta1) * g
+        v = beta2 * v + (1 - beta2) * g * g
+        return theta - lr * m / (np.sqrt(v) + eps), m, v
+    monkeypatch.setattr(O, "adam_step", wrong)
+    _fails(TL.test_oracle_adam_first_step_and_constant_gradient)
