@@ -242,7 +242,6 @@ def test_every_angular_variant(nb, variant):
 def test_autotune_variants_agree(nb):
     """Every compiled register-budget variant computes the same E, F, V; the
     autotuner picks valid indices and later calls use them."""
-    import ctypes
     h = I.HYPER_SMALL
     s = I.packing_batch([57, 100, 250], tag=67)
     th = I.init_params(h).astype(np.float32)

@@ -8,8 +8,6 @@ The owned atoms see the same neighbours as in the whole system, in another
 list order.  FP32 sums in another order differ by a few ulp of the terms, so
 forces agree to 1e-5 eV/A (terms are below ~1 eV/A).  The FP64 totals sum
 FP32 per-atom values: 1e-6 eV per atom."""
-import ctypes
-
 import numpy as np
 import pytest
 
