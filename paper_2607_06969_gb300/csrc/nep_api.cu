@@ -80,7 +80,6 @@ WsLayout ws_layout(const nep_model* m, int N, int B, int cap, int cap_ang) {
     };
     const size_t n = (size_t)N;
     const int NA = m->hp.n_ang, T = m->hp.n_types, KR = m->hp.k_rad;
-    const int NP = NA * (4 + m->hp.has_4body);
     w.pos4 = take(16 * n);
     w.cfg = take(4 * n);
     w.e_atom = take(4 * n);
