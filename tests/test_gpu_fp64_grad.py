@@ -99,10 +99,12 @@ def test_fp64_full_gradient_tiny_model(nb, tiny64, mode):
     assert abs(loss - c.oracle_loss(c.theta, mode)) <= TOL64 * abs(loss)
 
 
-def test_fp64_sampled_gradient_38_30_1_model(nb):
-    """The 38-30-1 model with 4-body terms: parameters sampled from every
-    block (W0, b0, w1, b1, cR, cA) of every species."""
-    h = I.HYPER_SMALL
+@pytest.mark.parametrize("hname", ["HYPER_SMALL", "HYPER_TABLE2", "HYPER_LARGE"])
+def test_fp64_sampled_gradient(nb, hname):
+    """The 38-30-1 model with 4-body terms, the Table 2 model (2+3-body,
+    n_A = 8) and the 52-64-1 model (n_R = 12, n_A = 8): parameters sampled
+    from every block (W0, b0, w1, b1, cR, cA) of every species."""
+    h = getattr(I, hname)
     c = Case64(h, I.packing_batch([24, 57, 100], tag=92))
     g = c.gpu(nb)
     grad, _ = c.gpu_grad(nb, g)

@@ -105,6 +105,39 @@ def test_sampled_gradient_216_atom_model(nb, small_case):
     assert rel_l2(grad[idx], want) <= TOL_G
 
 
+def block_sample(h, rng, per=6):
+    """Parameter indices from every block (W0, b0, w1, b1 of each species,
+    then cR and cA)."""
+    D = O.descriptor_dim(h)
+    H, T = h.n_hidden, h.n_types
+    stride = H * D + 2 * H + 1
+    idx = []
+    for t in range(T):
+        base = t * stride
+        idx += list(base + rng.choice(H * D, per, replace=False))
+        idx += [base + H * D + int(rng.integers(H)), base + H * D + H + int(rng.integers(H)), base + stride - 1]
+    off_cR = T * stride
+    nR = T * T * h.n_rad * h.k_rad
+    idx += list(off_cR + rng.choice(nR, 2 * per, replace=False))
+    idx += list(off_cR + nR + rng.choice(h.n_params - off_cR - nR, 2 * per, replace=False))
+    return sorted(set(int(i) for i in idx))
+
+
+@pytest.mark.parametrize("hname", ["HYPER_TABLE2", "HYPER_LARGE"])
+def test_sampled_gradient_other_compiled_models(nb, hname):
+    """The Table 2 model (2+3-body, n_A = 8) and the 52-64-1 model
+    (n_R = 12, n_A = 8, 4-body): the training kernels of their compiled sets."""
+    h = getattr(I, hname)
+    c = Case(h, I.packing_batch([24, 57], tag=96))
+    th32 = I.init_params(h).astype(np.float32)
+    th = th32.astype(np.float64)
+    grad, loss = c.gpu_grad(nb, c.gpu(nb, th32))
+    idx = block_sample(h, np.random.default_rng(30))
+    want = c.oracle_grad(th, idx)
+    assert rel_l2(grad[idx], want) <= TOL_G
+    assert abs(loss - c.oracle_loss(th)) <= 1e-5 * abs(c.oracle_loss(th))
+
+
 def test_gradient_against_central_differences(nb, small_case):
     c = small_case
     th32 = I.init_params(c.h).astype(np.float32)
