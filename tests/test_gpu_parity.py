@@ -304,3 +304,31 @@ def test_bounded_wait_times_out_and_context_survives(nb):
     s = I.rocksalt(3, vacancy=0.0, tag=0)
     th = I.init_params(h).astype(np.float32)
     assert_parity(gpu_eval(nb, h, th, s), oracle_eval(h, th, s), s)
+
+
+def test_zero_atom_batch(nb):
+    """Two configurations holding no atoms at all: the list, E/F/V, the
+    training gradient, the FP64 evaluation and an MD step all return OK with
+    zero totals."""
+    import torch
+    h = I.HYPER_SMALL
+    s = I.System(pos=np.zeros((0, 3)), types=np.zeros(0, np.int32), box=np.array([[20.0] * 3, [25.0] * 3]),
+                 atom_off=np.array([0, 0, 0]))
+    model = nb.Model(h, I.init_params(h).astype(np.float32))
+    dsys = nb.DeviceSystem.from_inputs(s)
+    nl = nb.NeighborList(0, 64, 32)
+    ws = nb.Workspace(model, 0, 2, 64, 32, train=True)
+    nb.neighbors(model, dsys, nl, 0.0, ws)
+    assert nb.check_list(nl) == nb.NEP_OK
+    e, f, et, v = nb.energy_forces_virial(model, dsys, nl, ws)
+    assert torch.count_nonzero(et).item() == 0 and torch.count_nonzero(v).item() == 0
+    z = dict(device="cuda")
+    grad, loss = nb.param_grad(model, dsys, nl, ws, torch.zeros(2, dtype=torch.float64, **z),
+                               torch.zeros(3, 0, dtype=torch.float32, **z), torch.zeros(2, 9, dtype=torch.float64, **z))
+    assert torch.count_nonzero(grad).item() == 0 and loss.item() == 0.0
+    ws64 = nb.Workspace64(model, 0, 2)
+    _, _, et64, v64 = nb.energy_forces_virial_fp64(model, dsys, nl, ws64)
+    assert torch.count_nonzero(et64).item() == 0 and torch.count_nonzero(v64).item() == 0
+    vel = torch.zeros(3, 0, **z)
+    nb.md_step(model, dsys, nl, vel, f, et, v, I.MASSES.astype(np.float32), 2.0, 0.0, True, ws)
+    assert nb.check_list(nl) == nb.NEP_OK
