@@ -442,34 +442,55 @@ NEP_HD void cbins_atom(const TrainArgs& t, const float* sm, int i) {
 // tile of kGradChunk atoms whose rows are in species order.
 //
 // A staged row holds, per atom (floats): the species bits and dE_b/dE of its
-// configuration, then q and dq (each padded to a multiple of 4 and 16-byte
-// aligned, so that four columns are one vector load), alpha/beta/gamma,
-// rho and p (radial n), the species-resolved basis sums F and DF, and the
-// angular c-gradient bins.  The logical field order (the staging sources)
-// is the same without the padding.
+// configuration, then q and dq, alpha, beta and gamma, rho and p (radial n),
+// the species-resolved basis sums F and DF (one block of K_R per species),
+// and the angular c-gradient bins.  Every block starts on a multiple of 4
+// (16 bytes) and is padded to a multiple of 4, so that four consecutive
+// entries are one vector load.  The logical field order (the staging
+// sources) is the same without the padding.
 template <class C>
 struct GradStage {
     static constexpr int NR = C::NR, NA = C::NA, KR = C::KR, KA = C::KA, T = C::T, D = C::D;
-    static constexpr int Dp = (D + 3) & ~3;
+    static constexpr int Dp = (D + 3) & ~3, NRp = (NR + 3) & ~3, KRp = (KR + 3) & ~3;
+    static constexpr int NBINS = T * NA * KA, NBp = (NBINS + 3) & ~3;
+    static NEP_HD int Hp(int H) { return (H + 3) & ~3; }
     static NEP_HD int o_q() { return 4; }
     static NEP_HD int o_dq() { return 4 + Dp; }
-    static NEP_HD int o_coef() { return 4 + 2 * Dp; }
-    static NEP_HD int o_rho(int H) { return o_coef() + 3 * H; }
-    static NEP_HD int o_p(int H) { return o_rho(H) + NR; }
-    static NEP_HD int o_fb(int H) { return o_p(H) + NR; }
-    static NEP_HD int o_df(int H) { return o_fb(H) + T * KR; }
-    static NEP_HD int o_bins(int H) { return o_df(H) + T * KR; }
+    static NEP_HD int o_al() { return 4 + 2 * Dp; }
+    static NEP_HD int o_be(int H) { return o_al() + Hp(H); }
+    static NEP_HD int o_ga(int H) { return o_be(H) + Hp(H); }
+    static NEP_HD int o_rho(int H) { return o_ga(H) + Hp(H); }
+    static NEP_HD int o_p(int H) { return o_rho(H) + NRp; }
+    static NEP_HD int o_fb(int H) { return o_p(H) + NRp; }
+    static NEP_HD int o_df(int H) { return o_fb(H) + T * KRp; }
+    static NEP_HD int o_bins(int H) { return o_df(H) + T * KRp; }
     // row stride: a multiple of 4 (16-byte rows) with W/4 odd, so that 8
     // consecutive rows start in 8 distinct groups of 4 banks
     static NEP_HD int width(int H) {
-        const int w = (o_bins(H) + T * NA * KA + 3) & ~3;
+        const int w = o_bins(H) + NBp;
         return (w & 4) ? w : w + 4;
     }
     // logical fields: 2 + 2D + 3H + 2 NR + 2 T KR + T NA KA
-    static NEP_HD int fields(int H) { return 2 + 2 * D + 3 * H + 2 * NR + 2 * T * KR + T * NA * KA; }
+    static NEP_HD int fields(int H) { return 2 + 2 * D + 3 * H + 2 * NR + 2 * T * KR + NBINS; }
     // column of logical field f in the padded row
-    static NEP_HD int column(int f) {
-        return f < 2 ? f : (f < 2 + D ? f + 2 : (f < 2 + 2 * D ? f + 2 + (Dp - D) : f + 2 + 2 * (Dp - D)));
+    static NEP_HD int column(int f, int H) {
+        if (f < 2) return f;
+        f -= 2;
+        if (f < D) return o_q() + f;
+        f -= D;
+        if (f < D) return o_dq() + f;
+        f -= D;
+        if (f < 3 * H) return o_al() + (f / H) * Hp(H) + f % H;
+        f -= 3 * H;
+        if (f < NR) return o_rho(H) + f;
+        f -= NR;
+        if (f < NR) return o_p(H) + f;
+        f -= NR;
+        if (f < T * KR) return o_fb(H) + (f / KR) * KRp + f % KR;
+        f -= T * KR;
+        if (f < T * KR) return o_df(H) + (f / KR) * KRp + f % KR;
+        f -= T * KR;
+        return o_bins(H) + f;
     }
 };
 
@@ -500,53 +521,6 @@ NEP_HD const float* stage_src(const TrainArgs& t, int f, int i) {
     return t.bins + f * N + i;
 }
 
-// Work items of a tile.  Items [0, NW) are blocks of the W0 gradient,
-// (species, h, four columns d0..d0+3); the rest are the other parameters,
-// one each: b0, w1, b1 of every species, then cR and cA.
-template <class C>
-NEP_HD int grad_w0_items(int H) { return C::T * H * (GradStage<C>::Dp / 4); }
-template <class C>
-NEP_HD int grad_items(int H) {
-    const ParamLayout L = param_layout(C::T, C::NR, C::NA, C::KR, C::KA, C::H4, H);
-    return grad_w0_items<C>(H) + C::T * (2 * H + 1) + (L.P - L.off_cR);
-}
-
-// W0 block: dPhi/dW0[sp][h][d] = sum over the species' atoms of
-// alpha_h q_d + beta_h dq_d, for four columns at once
-template <class C>
-NEP_HD void grad_w0_item(const float* stage, const int* toff, int H, int it, float* acc) {
-    using G = GradStage<C>;
-    constexpr int D = C::D, NB = G::Dp / 4;
-    const int W = G::width(H);
-    const ParamLayout L = param_layout(C::T, C::NR, C::NA, C::KR, C::KA, C::H4, H);
-    const int sp = it / (H * NB), rem = it % (H * NB), h = rem / NB, d0 = 4 * (rem % NB);
-    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
-    for (int a = toff[sp]; a < toff[sp + 1]; ++a) {
-        const float* row = stage + a * W;
-        const float al = row[G::o_coef() + h], be = row[G::o_coef() + H + h];
-        const float4 q = *reinterpret_cast<const float4*>(row + G::o_q() + d0);
-        const float4 dq = *reinterpret_cast<const float4*>(row + G::o_dq() + d0);
-        s0 = fmaf(be, dq.x, fmaf(al, q.x, s0));
-        s1 = fmaf(be, dq.y, fmaf(al, q.y, s1));
-        s2 = fmaf(be, dq.z, fmaf(al, q.z, s2));
-        s3 = fmaf(be, dq.w, fmaf(al, q.w, s3));
-    }
-    float* out = acc + sp * L.mlp_stride + h * D + d0;
-    out[0] += s0;
-    if (d0 + 1 < D) out[1] += s1;
-    if (d0 + 2 < D) out[2] += s2;
-    if (d0 + 3 < D) out[3] += s3;
-}
-
-// parameter of item o >= NW
-template <class C>
-NEP_HD int grad_other_param(int H, int o) {
-    const ParamLayout L = param_layout(C::T, C::NR, C::NA, C::KR, C::KA, C::H4, H);
-    const int per = 2 * H + 1;
-    if (o < C::T * per) return (o / per) * L.mlp_stride + H * C::D + o % per;
-    return L.off_cR + (o - C::T * per);
-}
-
 // tiles of kGradChunk atoms per gradient chunk: enough chunks to fill the
 // GPU (about 512), at most kGradTiles; a function of N alone, so that the
 // summation order does not depend on the device
@@ -560,36 +534,102 @@ NEP_HD int grad_chunks_of(int N) {
     return (N + per - 1) / per;
 }
 
-// sum over the staged atoms of the contribution to parameter p (not a W0
-// entry); the rows of species t are [toff[t], toff[t + 1]) (every parameter
-// belongs to one species: the network's, or the centre species of a c
-// coefficient)
+// Work items of a tile: each sums, over the staged rows of its species,
+// four parameters of one block that read four consecutive columns:
+//   W0  (species, h, d0..d0+3):    alpha_h q_d + beta_h dq_d
+//   b0  (species, h0..h0+3):       alpha_h
+//   w1  (species, h0..h0+3):       gamma_h
+//   b1  (species):                 dPhi/dE of the atom's configuration
+//   cR  (t1, t2, n, k0..k0+3):     rho_n F[t2][k] + p_n DF[t2][k]
+//   cA  (t1, bins b0..b0+3):       bins[b]
 template <class C>
-NEP_HD float param_partial(const float* stage, const int* toff, int H, int p) {
+struct GradItems {
     using G = GradStage<C>;
+    static constexpr int T = C::T;
+    static NEP_HD int nW0(int H) { return T * H * (G::Dp / 4); }
+    static NEP_HD int nB(int H) { return T * (G::Hp(H) / 4); }
+    static constexpr int nCR = T * T * C::NR * (G::KRp / 4);
+    static constexpr int nCA = T * (G::NBp / 4);
+    static NEP_HD int total(int H) { return nW0(H) + 2 * nB(H) + T + nCR + nCA; }
+};
+
+template <class C>
+NEP_HD void grad_item(const float* stage, const int* toff, int H, int it, float* acc) {
+    using G = GradStage<C>;
+    using I = GradItems<C>;
     constexpr int NR = C::NR, NA = C::NA, KR = C::KR, KA = C::KA, T = C::T, D = C::D;
     const int W = G::width(H);
     const ParamLayout L = param_layout(T, NR, NA, KR, KA, C::H4, H);
-    float acc = 0.0f;
-    if (p < L.off_cR) {
-        // b0 (alpha), w1 (gamma) or b1 (dPhi/dE); W0 goes through grad_w0_item
-        const int sp = p / L.mlp_stride, r = p % L.mlp_stride - H * D;
-        const int o = r < H ? G::o_coef() + r : (r < 2 * H ? G::o_coef() + 2 * H + (r - H) : 1);
-        for (int a = toff[sp]; a < toff[sp + 1]; ++a) acc += stage[a * W + o];
-    } else if (p < L.off_cA) {
-        const int x = p - L.off_cR;
-        const int t1 = x / (T * NR * KR), t2 = (x / (NR * KR)) % T, n = (x / KR) % NR, k = x % KR;
-        for (int a = toff[t1]; a < toff[t1 + 1]; ++a) {
+    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+    int sp, pbase, cnt;
+    if (it < I::nW0(H)) {
+        constexpr int NB = G::Dp / 4;
+        sp = it / (H * NB);
+        const int rem = it % (H * NB), h = rem / NB, d0 = 4 * (rem % NB);
+        for (int a = toff[sp]; a < toff[sp + 1]; ++a) {
             const float* row = stage + a * W;
-            acc = fmaf(row[G::o_rho(H) + n], row[G::o_fb(H) + t2 * KR + k], acc);
-            acc = fmaf(row[G::o_p(H) + n], row[G::o_df(H) + t2 * KR + k], acc);
+            const float al = row[G::o_al() + h], be = row[G::o_be(H) + h];
+            const float4 q = *reinterpret_cast<const float4*>(row + G::o_q() + d0);
+            const float4 dq = *reinterpret_cast<const float4*>(row + G::o_dq() + d0);
+            s0 = fmaf(be, dq.x, fmaf(al, q.x, s0));
+            s1 = fmaf(be, dq.y, fmaf(al, q.y, s1));
+            s2 = fmaf(be, dq.z, fmaf(al, q.z, s2));
+            s3 = fmaf(be, dq.w, fmaf(al, q.w, s3));
         }
+        pbase = sp * L.mlp_stride + h * D + d0;
+        cnt = D - d0;
+    } else if ((it -= I::nW0(H)) < 2 * I::nB(H)) {
+        const int which = it / I::nB(H), r = it % I::nB(H), HB = G::Hp(H) / 4;
+        sp = r / HB;
+        const int h0 = 4 * (r % HB);
+        const int col = (which ? G::o_ga(H) : G::o_al()) + h0;
+        for (int a = toff[sp]; a < toff[sp + 1]; ++a) {
+            const float4 v = *reinterpret_cast<const float4*>(stage + a * W + col);
+            s0 += v.x; s1 += v.y; s2 += v.z; s3 += v.w;
+        }
+        pbase = sp * L.mlp_stride + H * D + which * H + h0;
+        cnt = H - h0;
+    } else if ((it -= 2 * I::nB(H)) < T) {
+        sp = it;
+        for (int a = toff[sp]; a < toff[sp + 1]; ++a) s0 += stage[a * W + 1];
+        pbase = sp * L.mlp_stride + H * D + 2 * H;
+        cnt = 1;
+    } else if ((it -= T) < I::nCR) {
+        constexpr int KB = G::KRp / 4;
+        const int k0 = 4 * (it % KB);
+        int x = it / KB;
+        const int n = x % NR;
+        x /= NR;
+        const int t2 = x % T;
+        sp = x / T;
+        for (int a = toff[sp]; a < toff[sp + 1]; ++a) {
+            const float* row = stage + a * W;
+            const float rho = row[G::o_rho(H) + n], pn = row[G::o_p(H) + n];
+            const float4 F = *reinterpret_cast<const float4*>(row + G::o_fb(H) + t2 * G::KRp + k0);
+            const float4 DF = *reinterpret_cast<const float4*>(row + G::o_df(H) + t2 * G::KRp + k0);
+            s0 = fmaf(pn, DF.x, fmaf(rho, F.x, s0));
+            s1 = fmaf(pn, DF.y, fmaf(rho, F.y, s1));
+            s2 = fmaf(pn, DF.z, fmaf(rho, F.z, s2));
+            s3 = fmaf(pn, DF.w, fmaf(rho, F.w, s3));
+        }
+        pbase = L.off_cR + ((sp * T + t2) * NR + n) * KR + k0;
+        cnt = KR - k0;
     } else {
-        const int x = p - L.off_cA;
-        const int t1 = x / (T * NA * KA), rest = x % (T * NA * KA);
-        for (int a = toff[t1]; a < toff[t1 + 1]; ++a) acc += stage[a * W + G::o_bins(H) + rest];
+        it -= I::nCR;
+        constexpr int BB = G::NBp / 4;
+        sp = it / BB;
+        const int b0 = 4 * (it % BB);
+        for (int a = toff[sp]; a < toff[sp + 1]; ++a) {
+            const float4 v = *reinterpret_cast<const float4*>(stage + a * W + G::o_bins(H) + b0);
+            s0 += v.x; s1 += v.y; s2 += v.z; s3 += v.w;
+        }
+        pbase = L.off_cA + sp * G::NBINS + b0;
+        cnt = G::NBINS - b0;
     }
-    return acc;
+    acc[pbase] += s0;
+    if (cnt > 1) acc[pbase + 1] += s1;
+    if (cnt > 2) acc[pbase + 2] += s2;
+    if (cnt > 3) acc[pbase + 3] += s3;
 }
 
 #if defined(__CUDACC__)
@@ -669,9 +709,9 @@ __global__ void __launch_bounds__(kGradThreads) k_grad_partial(const TrainArgs t
     for (int p = threadIdx.x; p < L.P; p += blockDim.x) acc[p] = 0.0f;
     for (int f = threadIdx.x; f < WF; f += blockDim.x) {
         src[f] = f >= 2 ? stage_src<C>(t, f, 0) : nullptr;
-        col[f] = G::column(f);
+        col[f] = G::column(f, H);
     }
-    const int NW = grad_w0_items<C>(H), NI = grad_items<C>(H);
+    const int NI = GradItems<C>::total(H);
     const int tpc = grad_tiles_per_chunk(N);
     const int c0 = blockIdx.x * tpc * kGradChunk;
     for (int tile = 0; tile < tpc; ++tile) {
@@ -720,14 +760,7 @@ __global__ void __launch_bounds__(kGradThreads) k_grad_partial(const TrainArgs t
             }
         }
         __syncthreads();
-        for (int it = threadIdx.x; it < NI; it += blockDim.x) {
-            if (it < NW) {
-                grad_w0_item<C>(stage, toff, H, it, acc);
-            } else {
-                const int p = grad_other_param<C>(H, it - NW);
-                acc[p] += param_partial<C>(stage, toff, H, p);
-            }
-        }
+        for (int it = threadIdx.x; it < NI; it += blockDim.x) grad_item<C>(stage, toff, H, it, acc);
         __syncthreads();
     }
     for (int p = threadIdx.x; p < L.P; p += blockDim.x) t.gpart[(size_t)blockIdx.x * L.P + p] = acc[p];
