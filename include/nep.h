@@ -14,11 +14,13 @@
  *     in _host.  The library never frees caller memory.
  *   - Per-atom arrays are structure-of-arrays: a [3][N] array holds all x,
  *     then all y, then all z.
- *   - Hot calls (nep_neighbors, nep_energy_forces_virial, nep_param_grad*,
- *     nep_md_step) allocate nothing and never synchronise the host; they only
- *     enqueue kernels on `stream` (a cudaStream_t, NULL = legacy default
- *     stream).  Scratch memory is the caller's `work` buffer, sized by
- *     nep_workspace_bytes.
+ *   - Hot calls (nep_neighbors, nep_energy_forces_virial*, nep_param_grad*,
+ *     nep_adam_step, nep_md_step, nep_md_kick, nep_md_wrap, nep_domain_*)
+ *     allocate nothing and never synchronise the host; they only enqueue
+ *     kernels on `stream` (a cudaStream_t, NULL = legacy default stream).
+ *     Scratch memory is the caller's `work` buffer, sized by
+ *     nep_workspace_bytes, or by the sizing call that the entry point names
+ *     (training, FP64, slab selection).
  *   - Host-detectable argument errors return immediately with a status and a
  *     message (nep_last_error).  Device-detected conditions (neighbour list
  *     overflow, non-finite or out-of-box positions, species out of range) set
