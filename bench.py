@@ -511,6 +511,29 @@ def train_leg(nb, torch, I, local, dist=None, world: int = 1, rank: int = 0) -> 
         tm = torch.tensor([ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(tm, op=dist.ReduceOp.MAX)
         ms = float(tm.item())
+    # the same steps with the loss and gradient captured once in a CUDA graph
+    # (the model's parameters are read from device memory, which the Adam
+    # step updates in place, so every replay sees the current parameters)
+    ms_graph = None
+    if world == 1:
+        gst = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=gst):
+            nb.param_grad(model, dsys, nl, ws, E, F, V, (1.0, 1.0, 0.1), 0, grad, loss, stream=gst)
+        for _ in range(3):
+            g.replay()
+            t += 1
+            nb.adam_step(model, grad, m1, m2, t, 1e-4)
+        torch.cuda.synchronize()
+        t0.record()
+        for _ in range(K):
+            g.replay()
+            t += 1
+            nb.adam_step(model, grad, m1, m2, t, 1e-4)
+        t1.record()
+        torch.cuda.synchronize()
+        ms_graph = t0.elapsed_time(t1) / K
+        del g
 
     # fit from the initial student weights with the training protocol
     student = nb.Model(h, th)
@@ -522,6 +545,8 @@ def train_leg(nb, torch, I, local, dist=None, world: int = 1, rank: int = 0) -> 
                         "parameters and an Adam step, FP32" % (s_all.n_atoms, model.n_params),
             "parallelism": f"dp{world}" if world > 1 else "single",
             "configs_per_s": B_all / (ms * 1e-3), "ms_per_step": ms, "steps": K,
+            "ms_per_step_graph": ms_graph,
+            "configs_per_s_graph": None if ms_graph is None else B_all / (ms_graph * 1e-3),
             "fit": {"steps": cfg.epochs, "lr_start": cfg.lr_start, "lr_end": cfg.lr_end,
                     "loss_first": losses[0], "loss_last": losses[-1],
                     "loss_at": {str(k): losses[k] for k in (0, 10, 30, 100, 299)}}}
