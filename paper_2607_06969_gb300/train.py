@@ -89,7 +89,8 @@ class TrainConfig:
 class Trainer:
     """Adam over a fixed list of batches, one optimiser step per batch."""
 
-    def __init__(self, model: nb.Model, batches, cfg: TrainConfig | None = None, allreduce=None):
+    def __init__(self, model: nb.Model, batches, cfg: TrainConfig | None = None, allreduce=None,
+                 device: str = "cuda"):
         """allreduce(grad, loss), if given, combines the ranks' gradients and
         losses in place between nep_param_grad and the Adam step (data
         parallelism, see dp.allreduce_mean)."""
@@ -98,11 +99,12 @@ class Trainer:
         self.model = model
         self.batches = list(batches)
         self.cfg = cfg or TrainConfig()
+        self.device = device
         P = model.n_params
-        self.m1 = torch.zeros(P, dtype=torch.float32, device="cuda")
-        self.m2 = torch.zeros(P, dtype=torch.float32, device="cuda")
-        self.grad = torch.empty(P, dtype=torch.float32, device="cuda")
-        self.loss = torch.empty(1, dtype=torch.float64, device="cuda")
+        self.m1 = torch.zeros(P, dtype=torch.float32, device=device)
+        self.m2 = torch.zeros(P, dtype=torch.float32, device=device)
+        self.grad = torch.empty(P, dtype=torch.float32, device=device)
+        self.loss = torch.empty(1, dtype=torch.float64, device=device)
         self.t = 0
         self.total = self.cfg.epochs * len(self.batches)
         self.warmup = len(self.batches)           # one epoch
@@ -140,11 +142,12 @@ class Trainer:
         if st["params"].size != self.model.n_params:
             raise ValueError("checkpoint has %d parameters, the model %d" % (st["params"].size,
                                                                                self.model.n_params))
-        self.model.set_params(torch.tensor(np.asarray(st["params"], np.float32), device="cuda"))
+        self.model.set_params(torch.tensor(np.asarray(st["params"], np.float32), device=self.device))
         self.m1.copy_(torch.tensor(np.asarray(st["m1"], np.float32)))
         self.m2.copy_(torch.tensor(np.asarray(st["m2"], np.float32)))
         self.t, self.total, self.warmup = int(st["t"]), int(st["total"]), int(st["warmup"])
-        torch.cuda.synchronize()
+        if self.device != "cpu":
+            torch.cuda.synchronize()
 
     def save(self, path: str) -> None:
         np.savez(path, **{k: np.asarray(v) for k, v in self.state_dict().items()})
