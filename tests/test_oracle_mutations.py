@@ -128,3 +128,65 @@ def test_adam_without_bias_correction_is_caught(monkeypatch):
         return theta - lr * m / (np.sqrt(v) + eps), m, v
     monkeypatch.setattr(O, "adam_step", wrong)
     _fails(TL.test_oracle_adam_first_step_and_constant_gradient)
+
+
+def test_pair_vector_sign_flip_is_caught(monkeypatch):
+    """r_ij = r_i - r_j (images likewise) in place of r_j - r_i (Eq. 3)."""
+    real = O.pair_vectors
+    monkeypatch.setattr(O, "pair_vectors", lambda pos, box, i, j, s: -real(pos, box, i, j, s))
+    _fails(P.test_forces_central_difference, "tiny")
+
+
+def test_image_shift_with_the_wrong_sign_is_caught(monkeypatch):
+    """r_ij = r_j - s L - r_i: the periodic image taken on the wrong side."""
+    monkeypatch.setattr(O, "pair_vectors", lambda pos, box, i, j, s: (pos[j] - pos[i]) - s * box[i])
+    _fails(P.test_rotation_translation_permutation_invariance)
+
+
+def test_basis_derivative_without_the_chain_factor_is_caught(monkeypatch):
+    """dQ_k/dr with dT_k/dx not multiplied by dx/dr (Eqs. 12-13)."""
+    def wrong(r, rc, K):
+        r = np.asarray(r, np.float64)
+        fc, dfc = O.cutoff_fn(r, rc)
+        x = 2.0 * (r / rc - 1.0) ** 2 - 1.0
+        T = np.polynomial.chebyshev.chebvander(x, K - 1)
+        dT = np.stack([np.polynomial.chebyshev.chebval(x, np.polynomial.chebyshev.chebder(np.eye(K)[k]))
+                       for k in range(K)], -1)
+        return 0.5 * (T + 1.0) * fc[..., None], 0.5 * dT * fc[..., None] + 0.5 * (T + 1.0) * dfc[..., None]
+    monkeypatch.setattr(O, "chebyshev_basis", wrong)
+    _fails(P.test_forces_central_difference, "tiny")
+
+
+def test_legendre_derivative_error_is_caught(monkeypatch):
+    """P'_l = P'_{l-2} + (2l+1) P_{l-1}: the values right, the derivatives wrong."""
+    def wrong(c, L):
+        Pl = [np.ones_like(c), c]
+        dP = [np.zeros_like(c), np.ones_like(c)]
+        for l in range(2, L + 1):
+            Pl.append(((2 * l - 1) * c * Pl[l - 1] - (l - 1) * Pl[l - 2]) / l)
+            dP.append(dP[l - 2] + (2 * l + 1) * Pl[l - 1])
+        return Pl, dP
+    monkeypatch.setattr(O, "legendre", wrong)
+    _fails(P.test_legendre_against_scipy)
+    _fails(P.test_forces_central_difference, "tiny")
+
+
+def test_adam_with_eps_inside_the_root_is_caught(monkeypatch):
+    """lr mhat / sqrt(vhat + eps) in place of lr mhat / (sqrt(vhat) + eps)."""
+    def wrong(theta, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        m = beta1 * m + (1 - beta1) * g
+        v = beta2 * v + (1 - beta2) * g * g
+        mh, vh = m / (1 - beta1 ** t), v / (1 - beta2 ** t)
+        return theta - lr * mh / np.sqrt(vh + eps), m, v
+    monkeypatch.setattr(O, "adam_step", wrong)
+    _fails(TL.test_oracle_adam_first_step_and_constant_gradient)
+
+
+def test_loss_mode1_with_the_mode0_energy_term_is_caught(monkeypatch):
+    """Mode 1's energy term (dE_b)^2/N_b replaced by mode 0's (dE_b/N_b)^2 (Eq. 19)."""
+    real = O.loss_value
+
+    def wrong(*a, mode=0, **k):
+        return real(*a, mode=0 if mode == 1 else mode, **k)
+    monkeypatch.setattr(O, "loss_value", wrong)
+    _fails(P.test_loss_closed_form)
