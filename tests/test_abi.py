@@ -81,3 +81,48 @@ def test_domain_calls_reject_bad_arguments_before_touching_the_gpu(L):
                                 None) == nb.NEP_ERR_ARG
     # gather: missing pointers
     assert L.nep_domain_gather(None, None, 10, None, None, 4, box, f(0.0), None, None, None) == nb.NEP_ERR_ARG
+
+
+def test_plain_c_client_compiles_links_and_runs(L, tmp_path):
+    """include/nep.h is a C99 header: a C program that takes the address of
+    every declared entry point compiles with warnings as errors, links
+    against libnep.so, and its host-only calls give the oracle's parameter
+    count and the documented argument errors."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    names = sorted(header_functions())
+    h = I.HYPER_TABLE2
+    src = "\n".join([
+        "#include <stdio.h>",
+        "#include <string.h>",
+        '#include "nep.h"',
+        "typedef void (*fn)(void);",
+        "int main(void) {",
+        "    static const fn table[] = {" + ", ".join(f"(fn){n}" for n in names) + "};",
+        "    nep_hparams hp;",
+        "    nep_model* m = NULL;",
+        "    size_t k;",
+        "    for (k = 0; k < sizeof table / sizeof table[0]; ++k) if (!table[k]) return 2;",
+        "    memset(&hp, 0, sizeof hp);",
+        f"    hp.n_types = {h.n_types}; hp.n_rad = {h.n_rad}; hp.n_ang = {h.n_ang};",
+        f"    hp.k_rad = {h.k_rad}; hp.k_ang = {h.k_ang}; hp.l_max = {h.l_max};",
+        f"    hp.has_4body = {h.has_4body}; hp.n_hidden = {h.n_hidden};",
+        f"    hp.rc_rad = {h.rc_rad}f; hp.rc_ang = {h.rc_ang}f; hp.precision = 0;",
+        '    printf("%zu %d ", nep_num_params(&hp), nep_supported(&hp));',
+        '    printf("%d ", (int)nep_create(&hp, NULL, 3, &m));',
+        '    printf("%d %s\\n", m == NULL, strstr(nep_version(), "libnep") == nep_version() ? "ok" : "bad");',
+        "    return 0;",
+        "}",
+    ])
+    (tmp_path / "client.c").write_text(src)
+    libdir = os.path.dirname(L._name)
+    exe = str(tmp_path / "client")
+    subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Wpedantic", "-Werror",
+                    "-I", os.path.join(ROOT, "include"), str(tmp_path / "client.c"), "-o", exe,
+                    "-L", libdir, "-lnep", "-Wl,-rpath," + libdir], check=True, capture_output=True, text=True)
+    out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split()
+    assert int(out[0]) == O.param_count(h) and out[1] == "1"
+    assert int(out[2]) == nb.NEP_ERR_ARG and out[3] == "1" and out[4] == "ok"
