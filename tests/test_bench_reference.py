@@ -21,3 +21,41 @@ def test_reference_arm_json_line():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
+
+
+def test_clock_sampler_summary(tmp_path):
+    """The clocks object of the bench line from nvidia-smi CSV samples: the
+    median SM clock of the loaded three quarters of the samples, the maximum,
+    and every throttle reason seen Active at least once."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("_bench", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+
+    class Done:
+        def terminate(self):
+            pass
+
+        def wait(self):
+            return 0
+
+    rows = ["0, 600, 2070, 120.5, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    rows += [f"0, {1900 + 10 * k}, 2070, 900.0, 0x4, Not Active, Not Active, Not Active, Active" for k in range(7)]
+    rows += ["0, [N/A], 2070, [N/A], 0x0, Not Active, Not Active, Not Active, Not Active", "garbled"]
+    path = tmp_path / "clocks.csv"
+    path.write_text("\n".join(rows) + "\n")
+    cs = bench.ClockSampler(0)
+    cs.proc, cs.path = Done(), str(path)
+    out = cs.stop()
+    assert out["samples"] == 9 and out["sm_max_mhz"] == 2070.0 and out["power_w_max"] == 900.0
+    assert out["sm_mhz"] == 1935.0     # the lowest quarter (600 and 1900 MHz) dropped, median of 1910..1960
+    assert out["reasons"] == ["sw_power_cap"]
+    assert not path.exists()
+
+    rows = ["0, 1500, 2070, 1000, 0x8, Active, Not Active, Active, Not Active"] * 4
+    path.write_text("\n".join(rows) + "\n")
+    cs.proc, cs.path = Done(), str(path)
+    assert cs.stop()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+
+    cs.proc = None
+    assert cs.stop()["reasons"] == ["nvidia-smi unavailable"]
