@@ -147,34 +147,88 @@ def launches_per_step(rebuild: bool) -> int:
 
 # --------------------------------------------------------------- cpu legs
 CPU_SNIPPET = r"""
-import json, sys, time, os
+import json, sys, time
 sys.path.insert(0, {root!r})
 import numpy as np
 from paper_2607_06969_gb300 import inputs as I
 from oracle import nep_oracle as O
-ncell, nsteps = {ncell}, {nsteps}
+ncell, nsteps, warm = {ncell}, {nsteps}, {warmup}
 s = I.rocksalt(ncell, vacancy=0.2, tag=1)
 h = I.HYPER_SMALL
 th = I.init_params(h).astype(np.float32).astype(np.float64)
 p = s.pos32()
-t0 = time.perf_counter()
-pairs = None
-for k in range(nsteps):
-    if k % {rebuild} == 0:
-        pairs = O.neighbor_pairs(p, s.box, s.atom_off, h.rc_rad + {skin})
-    O.energy_forces_virial(h, th, p.astype(np.float64), s.types, s.box, s.atom_off, pairs)
+
+
+def run(n):
+    pairs = None
+    for k in range(n):
+        if k % {rebuild} == 0:
+            pairs = O.neighbor_pairs(p, s.box, s.atom_off, h.rc_rad + {skin})
+        O.energy_forces_virial(h, th, p.astype(np.float64), s.types, s.box, s.atom_off, pairs)
+
+
+run(warm)
+if {barrier}:
+    print("ready", flush=True)
+    sys.stdin.readline()
+w0, t0 = time.time(), time.perf_counter()
+run(nsteps)
 dt = time.perf_counter() - t0
-print(json.dumps(dict(atoms=s.n_atoms, steps=nsteps, seconds=dt)))
+print(json.dumps(dict(atoms=s.n_atoms, steps=nsteps, seconds=dt, t_start=w0, t_end=w0 + dt)), flush=True)
 """
 
 
-def run_oracle_sample(ncell: int, nsteps: int) -> dict:
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_oracle_sample(ncell: int, nsteps: int, procs: int = 1, warmup: int = 0) -> dict:
+    """`procs` single-threaded oracle processes, each running `nsteps` MD-step
+    force evaluations of its own copy of the ncell^3-cell sample after
+    `warmup` untimed ones.  With procs > 1 they are released together once
+    every one has finished its set-up (a barrier on stdin), and `seconds` is
+    the span from the first timed start to the last timed end."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = CPU_SNIPPET.format(root=ROOT, ncell=ncell, nsteps=nsteps, rebuild=REBUILD, skin=SKIN)
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
-    if r.returncode != 0:
-        raise RuntimeError(r.stderr[-2000:])
-    return json.loads(r.stdout.strip().splitlines()[-1])
+    code = CPU_SNIPPET.format(root=ROOT, ncell=ncell, nsteps=nsteps, warmup=warmup, rebuild=REBUILD, skin=SKIN,
+                              barrier=procs > 1)
+    errs = [tempfile.TemporaryFile(mode="w+") for _ in range(procs)]
+    ps = [subprocess.Popen([sys.executable, "-c", code], stdin=subprocess.PIPE if procs > 1 else subprocess.DEVNULL,
+                           stdout=subprocess.PIPE, stderr=e, text=True, env=env) for e in errs]
+
+    def failed(k):
+        for q in ps:
+            if q.poll() is None:
+                q.kill()
+            q.wait()
+        errs[k].seek(0)
+        return RuntimeError(errs[k].read()[-2000:])
+
+    try:
+        if procs > 1:
+            for k, q in enumerate(ps):
+                if q.stdout.readline().strip() != "ready":
+                    raise failed(k)
+            for q in ps:
+                q.stdin.write("go\n")
+                q.stdin.flush()
+        outs = [q.communicate()[0] for q in ps]
+        for k, q in enumerate(ps):
+            if q.returncode != 0:
+                raise failed(k)
+    finally:
+        for q in ps:
+            if q.poll() is None:
+                q.kill()
+                q.wait()
+        for e in errs:
+            e.close()
+    ds = [json.loads(o.strip().splitlines()[-1]) for o in outs]
+    span = max(d["t_end"] for d in ds) - min(d["t_start"] for d in ds)
+    return {"atoms": ds[0]["atoms"], "steps": nsteps * procs, "seconds": span, "procs": procs,
+            "seconds_each": [d["seconds"] for d in ds]}
 
 
 # the Fig. 3 size sweep: one random-occupation rock-salt GST cell of n^3
@@ -183,19 +237,25 @@ FIG3_NCELL = (2, 3, 4, 5)
 
 
 def cpu_baseline() -> dict:
-    # about ten seconds of CPU work: 50 evaluations of the 900-atom sample
-    d = run_oracle_sample(5, 50)
-    v = d["atoms"] * d["steps"] / d["seconds"]
+    # about ten seconds of CPU work per process: 30 evaluations of the
+    # 900-atom sample, on one thread and then on every host core at once
+    n = host_cores()
+    d1 = run_oracle_sample(5, 30, 1, warmup=1)
+    dn = run_oracle_sample(5, 30, n, warmup=1) if n > 1 else d1
+    v1 = d1["atoms"] * d1["steps"] / d1["seconds"]
+    vn = dn["atoms"] * dn["steps"] / dn["seconds"]
     # oracle E+F+V per configuration at the Fig. 3 sizes (the CPU side of that
     # sweep; the oracle has no analytic gradient, so this is its forward pass)
     fig3 = {}
-    for n in FIG3_NCELL:
-        f = run_oracle_sample(n, 3)
+    for c in FIG3_NCELL:
+        f = run_oracle_sample(c, 3, 1, warmup=1)
         fig3[str(f["atoms"])] = 1e3 * f["seconds"] / f["steps"]
-    return {"value": v, "unit": "atom-steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"FP64 numpy oracle, one thread: {d['steps']} MD-step force evaluations (list "
-                      f"rebuilt every {REBUILD}) of a {d['atoms']}-atom 5^3-cell periodic sample of the "
-                      f"same rock-salt structure and model, {d['seconds']:.1f} s",
+    return {"value": vn, "unit": "atom-steps/s", "cores": n, "kind": "oracle",
+            "sample": f"FP64 numpy oracle, {n} single-threaded processes released together, each running "
+                      f"30 MD-step force evaluations (list rebuilt every {REBUILD}) of its own {d1['atoms']}-atom "
+                      f"5^3-cell periodic sample of the same rock-salt structure and model; "
+                      f"{dn['seconds']:.1f} s from the first start to the last end",
+            "one_thread": {"value": v1, "cores": 1, "seconds": d1["seconds"]},
             "fig3_forward_ms_per_config": fig3}
 
 
@@ -323,17 +383,20 @@ def fp64_leg(nb, torch, I) -> dict:
 def reference_arm(args, rank: int) -> None:
     if rank != 0:
         return
-    # each step: one E+F+V of a 3^3-cell (194-atom) periodic sample, list every 10 steps
-    run_oracle_sample(3, max(3, args.warmup))
-    d = run_oracle_sample(3, args.steps)
+    # each step: one E+F+V of a 3^3-cell (194-atom) periodic sample in every
+    # one of the host's cores (one single-threaded oracle process per core),
+    # list every 10 steps
+    n = host_cores()
+    d = run_oracle_sample(3, args.steps, n, warmup=max(1, args.warmup))
     v = d["atoms"] * d["steps"] / d["seconds"]
+    sample = (f"{d['atoms']}-atom 3^3-cell periodic sample, one E+F+V per step in each of {n} "
+              f"single-threaded oracle processes released together")
     line = {"metric": METRIC, "value": v, "unit": "atom-steps/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * d["seconds"] / d["steps"],
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * d["seconds"] / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "sample": "3^3-cell periodic sample per step"},
-            "cpu_baseline": {"value": v, "unit": "atom-steps/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{d['atoms']}-atom 3^3-cell periodic sample, one E+F+V per step"},
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "atom-steps/s", "cores": n, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "atom-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
