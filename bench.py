@@ -185,6 +185,24 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
+def host_cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo) and architecture."""
+    import platform
+    name = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        name = next((l.split(":", 1)[1].strip() for l in out.splitlines() if l.startswith("Model name")), "")
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not name:
+        try:
+            with open("/proc/cpuinfo") as f:
+                name = next((l.split(":", 1)[1].strip() for l in f if l.lower().startswith("model name")), "")
+        except OSError:
+            pass
+    return f"{name or 'unknown'} ({platform.machine()})"
+
+
 def run_oracle_sample(ncell: int, nsteps: int, procs: int = 1, warmup: int = 0) -> dict:
     """`procs` single-threaded oracle processes, each running `nsteps` MD-step
     force evaluations of its own copy of the ncell^3-cell sample after
@@ -250,7 +268,7 @@ def cpu_baseline() -> dict:
     for c in FIG3_NCELL:
         f = run_oracle_sample(c, 3, 1, warmup=1)
         fig3[str(f["atoms"])] = 1e3 * f["seconds"] / f["steps"]
-    return {"value": vn, "unit": "atom-steps/s", "cores": n, "kind": "oracle",
+    return {"value": vn, "unit": "atom-steps/s", "cores": n, "kind": "oracle", "cpu_model": host_cpu_model(),
             "sample": f"FP64 numpy oracle, {n} single-threaded processes released together, each running "
                       f"30 MD-step force evaluations (list rebuilt every {REBUILD}) of its own {d1['atoms']}-atom "
                       f"5^3-cell periodic sample of the same rock-salt structure and model; "
@@ -396,7 +414,8 @@ def reference_arm(args, rank: int) -> None:
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOAD, "sample": sample},
-            "cpu_baseline": {"value": v, "unit": "atom-steps/s", "cores": n, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "atom-steps/s", "cores": n, "kind": "oracle", "sample": sample,
+                             "cpu_model": host_cpu_model()},
             "e2e": {"value": v, "unit": "atom-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
