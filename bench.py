@@ -692,14 +692,19 @@ def mixed_leg(nb, torch, I) -> dict:
     return out
 
 
-def replicas_leg(nb, torch, I, K: int = 20) -> dict:
+def replicas_leg(nb, torch, I, K: int = 20, dist=None, world: int = 1, rank: int = 0) -> dict:
     """Secondary leg: 1,024 independent periodic packings, N log-uniform in
     [64, 4096] (~975k atoms), config-0 NEP with the FP16 tensor-core network,
     900 K velocity Verlet (dt 2 fs, rebuild every 10 steps, skin 1 A).  All
     replicas advance in one launch per kernel, K steps captured in one CUDA
     graph, kernel variants autotuned; compared with a loop that launches each
-    replica separately."""
-    s, h = I.workload_replicas1024()
+    replica separately.  Over several ranks the replicas are split into
+    contiguous shards balanced by atom count, with no collective on the data
+    path (only the max of the ranks' step times)."""
+    from paper_2607_06969_gb300 import dp
+    s_all, h = I.workload_replicas1024()
+    B_all, N_all = s_all.n_cfg, s_all.n_atoms
+    s = dp.shard_system(s_all, *dp.shard_bounds(s_all.atom_off, world)[rank]) if world > 1 else s_all
     N, B = s.n_atoms, s.n_cfg
     th = I.init_params(h).astype(np.float32)
     masses = I.MASSES.astype(np.float32)
@@ -728,12 +733,16 @@ def replicas_leg(nb, torch, I, K: int = 20) -> dict:
                        stream=stream)
     g.replay()
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
         t0.record(stream)
         g.replay()
         t1.record(stream)
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     if nb.check_list(nl, stream) != nb.NEP_OK:
         raise RuntimeError("replica list overflow: " + nb.last_error())
     ms = t0.elapsed_time(t1) / K
@@ -764,12 +773,18 @@ def replicas_leg(nb, torch, I, K: int = 20) -> dict:
     ms_loop = l0.elapsed_time(l1) / KL
     # the same replicas with the FP32 network, for comparison
     ms32 = md_graph_ms(nb, torch, I, s, nb.Model(h, th, precision=0), K, cap, cap_ang, shifts=True)
+    if world > 1:
+        t = torch.tensor([ms, ms_loop, ms32], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, ms_loop, ms32 = (float(x) for x in t.tolist())
     return {"workload": "replicas1024: 1,024 packings, N log-uniform [64, 4096] (%d atoms), FP16 "
-                        "tensor-core network, 900 K velocity Verlet" % N,
-            "fp32_network": {"ms_per_step": ms32, "replica_steps_per_s": B / (ms32 * 1e-3)},
-            "replica_steps_per_s": B / (ms * 1e-3), "atom_steps_per_s": N / (ms * 1e-3),
+                        "tensor-core network, 900 K velocity Verlet" % N_all,
+            "shards": {"ranks": world, "split": "contiguous, balanced by atom count", "collective": None,
+                       "rank0_replicas": B, "rank0_atoms": N},
+            "fp32_network": {"ms_per_step": ms32, "replica_steps_per_s": B_all / (ms32 * 1e-3)},
+            "replica_steps_per_s": B_all / (ms * 1e-3), "atom_steps_per_s": N_all / (ms * 1e-3),
             "ms_per_step": ms, "steps": K,
-            "per_replica_loop": {"ms_per_step": ms_loop, "replica_steps_per_s": B / (ms_loop * 1e-3),
+            "per_replica_loop": {"ms_per_step": ms_loop, "replica_steps_per_s": B_all / (ms_loop * 1e-3),
                                  "steps": KL},
             "speedup_vs_loop": ms_loop / ms, "autotuned_angular_variant": chosen[0]}
 
@@ -940,7 +955,7 @@ def main():
 
     train = None if args.no_train else train_leg(nb, torch, I, local, dist, world, rank)
     mixed = None if args.no_mixed else mixed_leg(nb, torch, I)
-    replicas = None if args.no_replicas else replicas_leg(nb, torch, I)
+    replicas = None if args.no_replicas else replicas_leg(nb, torch, I, dist=dist, world=world, rank=rank)
     table2 = None if args.no_table2 else table2_leg(nb, torch, I)
     fig3 = None if args.no_fig3 else fig3_leg(nb, torch, I)
     fp64 = None if args.no_fp64 else fp64_leg(nb, torch, I)

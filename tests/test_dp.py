@@ -27,6 +27,18 @@ def test_shard_bounds_cover_and_balance():
         dp.shard_bounds(off, 129)
 
 
+def test_replica_batch_shards_by_atoms():
+    """The 1,024-replica batch (N log-uniform in [64, 4096]) split over 2-8
+    ranks: every rank within one replica of an equal share of the atoms."""
+    counts = np.asarray(I.loguniform_counts(1024, 64, 4096, tag=4))
+    off = np.concatenate([[0], np.cumsum(counts)])
+    for world in (2, 4, 8):
+        b = dp.shard_bounds(off, world)
+        atoms = np.array([off[b1] - off[b0] for b0, b1 in b])
+        assert atoms.sum() == off[-1]
+        assert np.all(np.abs(atoms - off[-1] / world) <= counts.max())
+
+
 def test_shard_system_round_trip():
     s = I.packing_batch([24, 31, 57, 100], tag=95)
     sub = dp.shard_system(s, 1, 3)
