@@ -13,7 +13,7 @@ What it computes, in the paper's order and notation (AI2Pot, Section 2):
 * Eq. 4   V_ab = - sum_i sum_j dE_i/dr_ij,a r_ij,b
 * Eq. 11  q_n = sum_j sum_k cR[Zi][Zj][n][k] Q_k(r_ij)
 * Eqs. 12-15  Q_k(r) = (T_k(x)+1)/2 f_c(r),  x = 2(r/rc-1)^2-1,
-              f_c = (1+cos(pi r/rc))/2 for r <= rc, else 0
+              f_c = (1+cos(pi r/rc))/2 for r < rc, else 0 (both give 0 at rc)
 * Eqs. 16-17  q_nl = sum_m C_lm S_nlm^2; written here in its Legendre form
           q_nl = sum_j sum_k g_n(r_ij) g_n(r_ik) P_l(rhat_ij . rhat_ik),
           which equals Eq. 17 by the addition theorem of spherical harmonics
@@ -35,7 +35,8 @@ no descriptor scaling; cutoff is strict (r < rc).  The parameter gradient is
 taken by complex-step differentiation (Squire & Trapp 1998) through the
 analytic force code: every step below is complex-analytic in the parameters.
 
-Parity pins for every function live in tests/test_oracle_*.py.
+Pins for every function live in tests/test_oracle_pins.py, tests/test_train_loop.py
+and tests/test_golden.py; tests/test_oracle_mutations.py shows that they bind.
 """
 from __future__ import annotations
 
