@@ -376,6 +376,32 @@ def test_gradient_complex_step_vs_central_difference():
         assert abs(g[a] - fd) <= 1e-6 * max(abs(fd), 1e-3), (k, g[a], fd)
 
 
+def test_gradient_without_4body_mode1_complex_step_vs_central_difference():
+    """The paper's own 2+3-body form (no 4-body term) under the printed loss
+    (mode 1, Eqs. 19-21): the complex-step gradient against central FD."""
+    h = tiny_hyper(has_4body=0)
+    th = I.init_params(h, seed=26)
+    s, pr = batch_case(h, seed=1)
+    pos = s.pos32().astype(np.float64)
+    lab = O.energy_forces_virial(h, I.init_params(h, seed=27), pos, s.types, s.box, s.atom_off, pr)
+
+    def Lf(t):
+        return O.loss_value(h, t, pos, s.types, s.box, s.atom_off, pr, lab["Etot"], lab["F"], lab["V"],
+                            w=(0.5, 2.0, 0.3), mode=1)
+
+    P = O.param_count(h)
+    assert P == 3 * (h.n_hidden * (h.n_rad + 4 * h.n_ang) + 2 * h.n_hidden + 1) + 9 * (
+        h.n_rad * h.k_rad + h.n_ang * h.k_ang)
+    idx = list(range(0, P, max(1, P // 20))) + [P - 1]
+    g = O.complex_step_grad(Lf, th, idx)
+    for a, k in enumerate(idx):
+        tp, tm = th.copy(), th.copy()
+        tp[k] += 1e-4
+        tm[k] -= 1e-4
+        fd = (Lf(tp) - Lf(tm)) / 2e-4
+        assert abs(g[a] - fd) <= 1e-6 * max(abs(fd), 1e-3), (k, g[a], fd)
+
+
 def test_adjoint_functional_gives_loss_gradient():
     # dL/dtheta = dPhi/dtheta with aE = dL/dE, lam = dL/dF, mu = dL/dV held fixed
     h = tiny_hyper()
