@@ -1,5 +1,8 @@
-"""Host logic of the spatial decomposition: slab planning, and the
-all-reduce that combines the ranks' owned rows (gloo, world size 2, CPU)."""
+"""Host logic of the spatial decomposition: slab planning, the all-reduce
+that combines the ranks' owned rows (gloo, world size 2, CPU), and, with the
+FP64 oracle, the reason for the two-layer halo: a slab's local system of
+owned atoms and ghosts within 2 rc reproduces every owned atom's energy and
+force, and one layer does not."""
 import os
 
 import numpy as np
@@ -52,3 +55,62 @@ def test_combine_owned_gloo_world2():
         assert p.exitcode == 0
     for rank, same, e, v in res:
         assert same and e == 4.0 and v == 0.75
+
+
+def _slab_local(pos, L, lo, hi, halo):
+    """Owned atoms (x in [lo, hi)) then ghosts (the first image k = -1, 0, 1
+    whose x lies within `halo` of the slab), each in atom order, and their
+    positions in the slab's frame (x - (lo - halo))."""
+    owned, ghosts, img = [], [], []
+    for i, x in enumerate(pos[:, 0]):
+        if lo <= x < hi:
+            owned.append(i)
+            continue
+        for k in (-1, 0, 1):
+            xs = x + k * L[0]
+            if lo - halo <= xs < lo or hi <= xs < hi + halo:
+                ghosts.append(i)
+                img.append(k)
+                break
+    idx = np.array(owned + ghosts, dtype=np.int64)
+    lp = pos[idx].copy()
+    lp[:, 0] += np.array([0] * len(owned) + img) * L[0] - (lo - halo)
+    return idx, len(owned), lp
+
+
+def _oracle_efv(h, th, pos, types, box, rc):
+    from oracle import nep_oracle as O
+    off = np.array([0, len(types)])
+    pr = O.neighbor_pairs(pos.astype(np.float32), box, off, rc)
+    return O.energy_forces_virial(h, th, pos, types, box, off, pr)
+
+
+def test_two_layer_halo_reproduces_owned_atoms_in_the_oracle():
+    from paper_2607_06969_gb300 import inputs as I
+    h = I.Hyper(n_types=3, n_rad=3, n_ang=2, k_rad=4, k_ang=3, l_max=4, has_4body=1, n_hidden=4,
+                rc_rad=5.0, rc_ang=4.0)
+    th = I.init_params(h, seed=31)
+    rng = np.random.default_rng(12)
+    g = np.stack(np.meshgrid(np.arange(15), np.arange(4), np.arange(4), indexing="ij"), -1).reshape(-1, 3)
+    pos = 3.0 * g + 1.5 + rng.normal(0.0, 0.2, size=g.shape)
+    types = rng.integers(0, 3, size=len(pos)).astype(np.int32)
+    L = np.array([45.0, 12.0, 12.0])
+    whole = _oracle_efv(h, th, pos, types, L[None, :], h.rc_rad)
+    slabs, _ = SP.plan_slabs(L[0], 2, h.rc_rad, 0.0)
+    e_sum = 0.0
+    for halo, exact in ((2.0 * h.rc_rad, True), (h.rc_rad, False)):
+        worst = 0.0
+        for lo, hi in slabs:
+            idx, n_own, lp = _slab_local(pos, L, lo, hi, halo)
+            box = np.array([[hi - lo + 2.0 * halo + h.rc_rad + 1.0, L[1], L[2]]])
+            loc = _oracle_efv(h, th, lp, types[idx], box, h.rc_rad)
+            own = idx[:n_own]
+            worst = max(worst, np.abs(loc["F"][:n_own] - whole["F"][own]).max())
+            if exact:
+                assert np.allclose(loc["E"][:n_own], whole["E"][own], rtol=0, atol=1e-11)
+                e_sum += loc["E"][:n_own].sum()
+        if exact:
+            assert worst < 1e-10
+            assert abs(e_sum - whole["Etot"][0]) < 1e-10
+        else:
+            assert worst > 1e-6            # ghosts' own neighbourhoods cut short
