@@ -402,6 +402,32 @@ def test_gradient_without_4body_mode1_complex_step_vs_central_difference():
         assert abs(g[a] - fd) <= 1e-6 * max(abs(fd), 1e-3), (k, g[a], fd)
 
 
+def test_force_and_virial_adjoints_are_one_energy_tangent():
+    """lam.F + mu:V (Eqs. 3-4) equals the derivative of the energy along the
+    pair-vector tangent dr_ij = -(lam_j - lam_i) - mu r_ij: the identity the
+    training backward evaluates instead of differentiating F and V."""
+    h = tiny_hyper()
+    th = I.init_params(h, seed=28)
+    s = small_periodic(seed=3)
+    pr = O.neighbor_pairs(s.pos.astype(np.float32), s.box, s.atom_off, h.rc_rad + 1.0)
+    out = O.energy_forces_virial(h, th, s.pos, s.types, s.box, s.atom_off, pr)
+    rng = np.random.default_rng(9)
+    lam = rng.normal(size=(s.n_atoms, 3))
+    mu = rng.normal(size=(3, 3))
+    i, j, sh = pr
+    rij = O.pair_vectors(s.pos, s.box[np.zeros(s.n_atoms, int)], i, j, sh)
+    drij = -(lam[j] - lam[i]) - rij @ mu.T
+    prm = O.unpack(h, th)
+
+    def E(eps):
+        return O.atom_terms(h, prm, s.types, np.arange(s.n_atoms), i, j, rij + eps * drij)[1].sum()
+
+    d = 1e-6
+    fd = (E(d) - E(-d)) / (2 * d)
+    want = (lam * out["F"]).sum() + (mu * out["V"][0]).sum()
+    assert abs(fd - want) < 1e-7 * max(1.0, abs(want)), (fd, want)
+
+
 def test_adjoint_functional_gives_loss_gradient():
     # dL/dtheta = dPhi/dtheta with aE = dL/dE, lam = dL/dF, mu = dL/dV held fixed
     h = tiny_hyper()
