@@ -153,6 +153,57 @@ def _ptr(t) -> ctypes.c_void_p:
     return ctypes.c_void_p(0 if t is None else t.data_ptr())
 
 
+def _dev(t, dtype, numel: int, name: str, where: str, optional: bool = False):
+    """A device argument of a library call: a contiguous CUDA tensor of
+    `dtype` with at least `numel` elements (the count the call reads or
+    writes), or None where the call accepts NULL.  Raises ValueError
+    otherwise, so that a wrong tensor never reaches the device."""
+    if t is None:
+        if optional:
+            return None
+        raise ValueError(f"{where}: {name} is required")
+    if not (t.is_cuda and t.dtype == dtype and t.is_contiguous() and t.numel() >= numel):
+        raise ValueError(f"{where}: {name} must be a contiguous CUDA {dtype} tensor of at least {numel} "
+                         f"elements (got {t.dtype}, shape {tuple(t.shape)}, "
+                         f"{'cuda' if t.is_cuda else 'cpu'}, {'' if t.is_contiguous() else 'not '}contiguous)")
+    return t
+
+
+def _outputs(dsys, out, dtype, where: str):
+    """(e_atom [N] or None, force [3,N], e_tot [B], virial [B,9]) checked."""
+    import torch
+    e_atom, force, e_tot, vir = out
+    _dev(e_atom, dtype, dsys.n_atoms, "e_atom", where, optional=True)
+    _dev(force, dtype, 3 * dsys.n_atoms, "force", where)
+    _dev(e_tot, torch.float64, dsys.n_cfg, "e_tot", where)
+    _dev(vir, torch.float64, 9 * dsys.n_cfg, "virial", where)
+    return out
+
+
+def _labels(dsys, e_lbl, f_lbl, v_lbl, f_dtype, where: str) -> None:
+    """Labels E [B] f64, F [3,N] (f_dtype), V [B,9] f64."""
+    import torch
+    _dev(e_lbl, torch.float64, dsys.n_cfg, "e_lbl", where)
+    _dev(f_lbl, f_dtype, 3 * dsys.n_atoms, "f_lbl", where)
+    _dev(v_lbl, torch.float64, 9 * dsys.n_cfg, "v_lbl", where)
+
+
+def _adjoints(dsys, a_e, lam, mu, lam_dtype, where: str) -> None:
+    """Adjoints a_e [B] f64, lam [3,N] (lam_dtype), mu [B,9] f64."""
+    import torch
+    _dev(a_e, torch.float64, dsys.n_cfg, "a_e", where)
+    _dev(lam, lam_dtype, 3 * dsys.n_atoms, "lam", where)
+    _dev(mu, torch.float64, 9 * dsys.n_cfg, "mu", where)
+
+
+def _weights(w, where: str) -> np.ndarray:
+    """The loss weights (wE, wF, wV) as a host float array."""
+    wh = np.ascontiguousarray(np.asarray(w, np.float32).reshape(-1))
+    if wh.size != 3:
+        raise ValueError(f"{where}: w must hold the three weights (wE, wF, wV)")
+    return wh
+
+
 def _stream(stream=None) -> ctypes.c_void_p:
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
@@ -173,7 +224,8 @@ class Model:
         self.handle = handle
 
     def set_params(self, params_dev, stream=None):
-        assert params_dev.is_cuda and params_dev.dtype.is_floating_point
+        import torch
+        _dev(params_dev, torch.float32, self.n_params, "params", "nep_set_params")
         check(lib().nep_set_params(self.handle, _ptr(params_dev), _stream(stream)), "nep_set_params")
 
     def get_params(self, out=None, stream=None):
@@ -181,6 +233,7 @@ class Model:
         import torch
         if out is None:
             out = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
+        _dev(out, torch.float32, self.n_params, "out", "nep_get_params")
         check(lib().nep_get_params(self.handle, _ptr(out), _stream(stream)), "nep_get_params")
         return out
 
@@ -291,7 +344,7 @@ def energy_forces_virial(model: Model, dsys: DeviceSystem, nl: NeighborList, ws:
                torch.empty(3, dsys.n_atoms, dtype=torch.float32, device=dev),
                torch.empty(dsys.n_cfg, dtype=torch.float64, device=dev),
                torch.empty(dsys.n_cfg, 9, dtype=torch.float64, device=dev))
-    e_atom, force, e_tot, vir = out
+    e_atom, force, e_tot, vir = _outputs(dsys, out, torch.float32, "nep_energy_forces_virial")
     check(lib().nep_energy_forces_virial(model.handle, ctypes.byref(dsys.c), ctypes.byref(nl.c),
                                          _ptr(e_atom), _ptr(force), _ptr(e_tot), _ptr(vir),
                                          ws.ptr, ws.bytes, _stream(stream)),
@@ -321,14 +374,13 @@ def energy_forces_virial_fp64(model: Model, dsys: DeviceSystem, nl: NeighborList
     the model's FP32 parameters promoted)."""
     import torch
     dev = dsys.pos.device
-    if params is not None:
-        assert params.is_cuda and params.dtype == torch.float64 and params.numel() == model.n_params
+    _dev(params, torch.float64, model.n_params, "params", "nep_energy_forces_virial_fp64", optional=True)
     if out is None:
         out = (torch.empty(dsys.n_atoms, dtype=torch.float64, device=dev),
                torch.empty(3, dsys.n_atoms, dtype=torch.float64, device=dev),
                torch.empty(dsys.n_cfg, dtype=torch.float64, device=dev),
                torch.empty(dsys.n_cfg, 9, dtype=torch.float64, device=dev))
-    e_atom, force, e_tot, vir = out
+    e_atom, force, e_tot, vir = _outputs(dsys, out, torch.float64, "nep_energy_forces_virial_fp64")
     check(lib().nep_energy_forces_virial_fp64(model.handle, ctypes.byref(dsys.c), ctypes.byref(nl.c),
                                               _ptr(params), _ptr(e_atom), _ptr(force), _ptr(e_tot),
                                               _ptr(vir), ws.ptr, ws.bytes, _stream(stream)),
@@ -343,13 +395,16 @@ def param_grad_fp64(model: Model, dsys: DeviceSystem, nl: NeighborList, ws: Work
     f_lbl [3,N], v_lbl [B,9] f64 on the device; ws a training Workspace64."""
     import torch
     dev = dsys.pos.device
-    for t in (e_lbl, f_lbl, v_lbl) + (() if params is None else (params,)):
-        assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+    where, f64 = "nep_param_grad_fp64", torch.float64
+    _labels(dsys, e_lbl, f_lbl, v_lbl, f64, where)
+    _dev(params, f64, model.n_params, "params", where, optional=True)
     if grad is None:
-        grad = torch.empty(model.n_params, dtype=torch.float64, device=dev)
+        grad = torch.empty(model.n_params, dtype=f64, device=dev)
     if loss is None:
-        loss = torch.empty(1, dtype=torch.float64, device=dev)
-    wh = np.ascontiguousarray(np.asarray(w, np.float32))
+        loss = torch.empty(1, dtype=f64, device=dev)
+    _dev(grad, f64, model.n_params, "grad", where)
+    _dev(loss, f64, 1, "loss", where)
+    wh = _weights(w, where)
     check(lib().nep_param_grad_fp64(model.handle, ctypes.byref(dsys.c), ctypes.byref(nl.c), _ptr(params),
                                     _ptr(e_lbl), _ptr(f_lbl), _ptr(v_lbl), wh.ctypes.data_as(ctypes.c_void_p),
                                     int(loss_mode), _ptr(grad), _ptr(loss), ws.ptr, ws.bytes, _stream(stream)),
@@ -363,10 +418,12 @@ def param_grad_adjoint_fp64(model: Model, dsys: DeviceSystem, nl: NeighborList, 
     mu : V (a_e [B], lam [3,N], mu [B,9] f64 on the device)."""
     import torch
     dev = dsys.pos.device
-    for t in (a_e, lam, mu) + (() if params is None else (params,)):
-        assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+    where, f64 = "nep_param_grad_adjoint_fp64", torch.float64
+    _adjoints(dsys, a_e, lam, mu, f64, where)
+    _dev(params, f64, model.n_params, "params", where, optional=True)
     if grad is None:
-        grad = torch.empty(model.n_params, dtype=torch.float64, device=dev)
+        grad = torch.empty(model.n_params, dtype=f64, device=dev)
+    _dev(grad, f64, model.n_params, "grad", where)
     check(lib().nep_param_grad_adjoint_fp64(model.handle, ctypes.byref(dsys.c), ctypes.byref(nl.c),
                                             _ptr(params), _ptr(a_e), _ptr(lam), _ptr(mu), _ptr(grad), ws.ptr,
                                             ws.bytes, _stream(stream)),
@@ -381,11 +438,15 @@ def param_grad(model: Model, dsys: DeviceSystem, nl: NeighborList, ws: Workspace
     training workspace.  Returns (grad [P] f32, loss [1] f64)."""
     import torch
     dev = dsys.pos.device
+    where = "nep_param_grad"
+    _labels(dsys, e_lbl, f_lbl, v_lbl, torch.float32, where)
     if grad is None:
         grad = torch.empty(model.n_params, dtype=torch.float32, device=dev)
     if loss is None:
         loss = torch.empty(1, dtype=torch.float64, device=dev)
-    wh = np.ascontiguousarray(np.asarray(w, np.float32))
+    _dev(grad, torch.float32, model.n_params, "grad", where)
+    _dev(loss, torch.float64, 1, "loss", where)
+    wh = _weights(w, where)
     check(lib().nep_param_grad(model.handle, ctypes.byref(dsys.c), ctypes.byref(nl.c), _ptr(e_lbl),
                                _ptr(f_lbl), _ptr(v_lbl), wh.ctypes.data_as(ctypes.c_void_p),
                                int(loss_mode), _ptr(grad), _ptr(loss), ws.ptr, ws.bytes, _stream(stream)),
@@ -398,8 +459,11 @@ def param_grad_adjoint(model: Model, dsys: DeviceSystem, nl: NeighborList, ws: W
     """nep_param_grad_adjoint: d/dtheta of sum a_e E + lam . F + mu : V.
     a_e [B] f64, lam [3,N] f32, mu [B,9] f64.  Returns grad [P] f32."""
     import torch
+    where = "nep_param_grad_adjoint"
+    _adjoints(dsys, a_e, lam, mu, torch.float32, where)
     if grad is None:
         grad = torch.empty(model.n_params, dtype=torch.float32, device=dsys.pos.device)
+    _dev(grad, torch.float32, model.n_params, "grad", where)
     check(lib().nep_param_grad_adjoint(model.handle, ctypes.byref(dsys.c), ctypes.byref(nl.c),
                                        _ptr(a_e), _ptr(lam), _ptr(mu), _ptr(grad), ws.ptr, ws.bytes,
                                        _stream(stream)), "nep_param_grad_adjoint")
@@ -410,6 +474,9 @@ def adam_step(model: Model, grad, m1, m2, t: int, lr: float, beta1: float = 0.9,
               eps: float = 1e-8, stream=None) -> None:
     """nep_adam_step: one Adam update of the model's parameters in place.
     grad, m1, m2: device tensors [P] f32 (m1, m2 zero before t = 1)."""
+    import torch
+    for name, t in (("grad", grad), ("m1", m1), ("m2", m2)):
+        _dev(t, torch.float32, model.n_params, name, "nep_adam_step")
     check(lib().nep_adam_step(model.handle, _ptr(grad), _ptr(m1), _ptr(m2), int(t), float(lr), float(beta1),
                               float(beta2), float(eps), _stream(stream)), "nep_adam_step")
 
@@ -430,7 +497,7 @@ def energy_forces_virial_noalloc(model: Model, dsys: DeviceSystem, nl: NeighborL
                torch.empty(3, dsys.n_atoms, dtype=torch.float32, device=dev),
                torch.empty(dsys.n_cfg, dtype=torch.float64, device=dev),
                torch.empty(dsys.n_cfg, 9, dtype=torch.float64, device=dev))
-    e_atom, force, e_tot, vir = out
+    e_atom, force, e_tot, vir = _outputs(dsys, out, torch.float32, "nep_energy_forces_virial_noalloc")
     check(lib().nep_energy_forces_virial_noalloc(model.handle, ctypes.byref(dsys.c),
                                                  ctypes.byref(nl.c), _ptr(e_atom), _ptr(force),
                                                  _ptr(e_tot), _ptr(vir), _stream(stream)),
@@ -440,7 +507,14 @@ def energy_forces_virial_noalloc(model: Model, dsys: DeviceSystem, nl: NeighborL
 
 def md_step(model: Model, dsys: DeviceSystem, nl: NeighborList, vel, force, e_tot, virial,
             masses, dt: float, skin: float, rebuild: bool, ws: Workspace, stream=None) -> None:
+    """nep_md_step: vel [3,N] f32 (in place), force [3,N] f32, e_tot [B] and
+    virial [B,9] f64 on the device; masses: host, one per species."""
+    import torch
+    _outputs(dsys, (None, force, e_tot, virial), torch.float32, "nep_md_step")
+    _dev(vel, torch.float32, 3 * dsys.n_atoms, "vel", "nep_md_step")
     m = np.ascontiguousarray(np.asarray(masses, np.float32))
+    if m.size < model.hp.n_types:
+        raise ValueError(f"nep_md_step: {m.size} masses for {model.hp.n_types} species")
     check(lib().nep_md_step(model.handle, ctypes.byref(dsys.c), ctypes.byref(nl.c), _ptr(vel),
                             _ptr(force), _ptr(e_tot), _ptr(virial),
                             m.ctypes.data_as(ctypes.c_void_p), float(dt), float(skin),

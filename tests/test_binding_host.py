@@ -1,0 +1,72 @@
+"""The binding's device-argument checks, on the CPU: a tensor handed to a
+library call must be a contiguous CUDA tensor of the call's dtype with at
+least as many elements as the call reads or writes; anything else raises
+ValueError before the library is reached."""
+from types import SimpleNamespace
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2607_06969_gb300 import binding as nb
+
+
+class DeviceLike:
+    """Stands in for a CUDA tensor (no GPU here): the attributes the checks read."""
+
+    def __init__(self, numel, dtype=torch.float32, contiguous=True):
+        self.is_cuda, self.dtype, self._n, self._c = True, dtype, numel, contiguous
+        self.shape = (numel,)
+
+    def numel(self):
+        return self._n
+
+    def is_contiguous(self):
+        return self._c
+
+
+def test_dev_accepts_and_rejects():
+    assert nb._dev(None, torch.float32, 4, "x", "call", optional=True) is None
+    t = DeviceLike(10)
+    assert nb._dev(t, torch.float32, 10, "x", "call") is t
+    for bad in (None, DeviceLike(9), DeviceLike(10, torch.float64), DeviceLike(10, contiguous=False),
+                torch.zeros(10)):
+        with pytest.raises(ValueError, match="call: x"):
+            nb._dev(bad, torch.float32, 10, "x", "call")
+
+
+def test_group_checks_size_by_atoms_and_configurations():
+    dsys = SimpleNamespace(n_atoms=7, n_cfg=2)
+    f32, f64 = torch.float32, torch.float64
+    nb._outputs(dsys, (None, DeviceLike(21), DeviceLike(2, f64), DeviceLike(18, f64)), f32, "efv")
+    with pytest.raises(ValueError, match="virial"):
+        nb._outputs(dsys, (None, DeviceLike(21), DeviceLike(2, f64), DeviceLike(17, f64)), f32, "efv")
+    with pytest.raises(ValueError, match="e_atom"):
+        nb._outputs(dsys, (DeviceLike(6), DeviceLike(21), DeviceLike(2, f64), DeviceLike(18, f64)), f32, "efv")
+    nb._labels(dsys, DeviceLike(2, f64), DeviceLike(21, f64), DeviceLike(18, f64), f64, "grad64")
+    with pytest.raises(ValueError, match="f_lbl"):
+        nb._labels(dsys, DeviceLike(2, f64), DeviceLike(21), DeviceLike(18, f64), f64, "grad64")
+    with pytest.raises(ValueError, match="a_e"):
+        nb._adjoints(dsys, DeviceLike(1, f64), DeviceLike(21), DeviceLike(18, f64), f32, "adj")
+    assert nb._weights((1, 2, 3), "g").dtype == np.float32
+    with pytest.raises(ValueError):
+        nb._weights((1, 2), "g")
+
+
+def test_calls_check_before_reaching_the_library(monkeypatch):
+    def no_library():
+        raise AssertionError("the library was reached")
+    monkeypatch.setattr(nb, "lib", no_library)
+    model = SimpleNamespace(n_params=5, hp=SimpleNamespace(n_types=3), handle=None)
+    dsys = SimpleNamespace(n_atoms=4, n_cfg=1, pos=SimpleNamespace(device="cuda"))
+    f64 = torch.float64
+    with pytest.raises(ValueError, match="m2"):
+        nb.adam_step(model, DeviceLike(5), DeviceLike(5), DeviceLike(4), 1, 1e-3)
+    with pytest.raises(ValueError, match="masses"):
+        nb.md_step(model, dsys, None, DeviceLike(12), DeviceLike(12), DeviceLike(1, f64), DeviceLike(9, f64),
+                   [72.6, 121.8], 2.0, 1.0, False, None)
+    with pytest.raises(ValueError, match="grad"):
+        nb.param_grad(model, dsys, None, None, DeviceLike(1, f64), DeviceLike(12), DeviceLike(9, f64),
+                      grad=DeviceLike(4), loss=DeviceLike(1, f64))
+    with pytest.raises(ValueError, match="params"):
+        nb.Model.set_params(model, DeviceLike(5, f64))
