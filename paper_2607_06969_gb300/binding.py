@@ -253,14 +253,27 @@ class DeviceSystem:
     """A batch of periodic configurations resident on the GPU (nep_system)."""
 
     def __init__(self, pos, types, box, atom_off, device="cuda"):
+        """pos [N,3], types [N], box [B,3] (orthorhombic edges), atom_off [B+1]
+        on the host; the shapes are checked here, the values by the library."""
         import torch
         pos = np.asarray(pos, np.float32)
+        types = np.asarray(types, np.int32)
+        box = np.asarray(box, np.float32)
+        atom_off = np.asarray(atom_off, np.int32)
+        if pos.ndim != 2 or pos.shape[1] != 3:
+            raise ValueError(f"pos must be [N, 3], got {pos.shape}")
+        if types.shape != (pos.shape[0],):
+            raise ValueError(f"types must be [N] = [{pos.shape[0]}], got {types.shape}")
+        if box.ndim != 2 or box.shape[1] != 3:
+            raise ValueError(f"box must be [B, 3], got {box.shape}")
+        if atom_off.shape != (box.shape[0] + 1,):
+            raise ValueError(f"atom_off must be [B + 1] = [{box.shape[0] + 1}], got {atom_off.shape}")
         self.n_atoms = int(pos.shape[0])
-        self.n_cfg = int(np.asarray(box).shape[0])
+        self.n_cfg = int(box.shape[0])
         self.pos = torch.from_numpy(np.ascontiguousarray(pos.T)).to(device)        # [3][N]
-        self.type = torch.from_numpy(np.asarray(types, np.int32)).to(device)
-        self.atom_off_host = np.ascontiguousarray(np.asarray(atom_off, np.int32))
-        self.box_host = np.ascontiguousarray(np.asarray(box, np.float32))
+        self.type = torch.from_numpy(np.ascontiguousarray(types)).to(device)
+        self.atom_off_host = np.ascontiguousarray(atom_off)
+        self.box_host = np.ascontiguousarray(box)
         self.atom_off = torch.from_numpy(self.atom_off_host).to(device)
         self.box = torch.from_numpy(self.box_host).to(device)
         self.refresh()

@@ -70,3 +70,14 @@ def test_calls_check_before_reaching_the_library(monkeypatch):
                       grad=DeviceLike(4), loss=DeviceLike(1, f64))
     with pytest.raises(ValueError, match="params"):
         nb.Model.set_params(model, DeviceLike(5, f64))
+
+
+def test_device_system_checks_shapes():
+    pos, types = np.zeros((5, 3)), np.zeros(5, np.int32)
+    box, off = np.full((2, 3), 10.0), np.array([0, 2, 5])
+    s = nb.DeviceSystem(pos, types, box, off, device="cpu")
+    assert (s.n_atoms, s.n_cfg) == (5, 2) and tuple(s.pos.shape) == (3, 5)
+    for args in ((np.zeros((5, 2)), types, box, off), (pos, types[:4], box, off),
+                 (pos, types, np.full(3, 10.0), off), (pos, types, box, off[:2])):
+        with pytest.raises(ValueError):
+            nb.DeviceSystem(*args, device="cpu")
