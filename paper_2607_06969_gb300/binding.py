@@ -204,6 +204,14 @@ def _weights(w, where: str) -> np.ndarray:
     return wh
 
 
+def _same_atoms(dsys, nl, where: str) -> None:
+    """The list's per-atom arrays must be sized for the system's atoms (the
+    library indexes them by the system's atom count)."""
+    n = getattr(nl, "n_atoms", None)
+    if nl is not None and n != dsys.n_atoms:
+        raise ValueError(f"{where}: the neighbour list holds {n} atoms, the system {dsys.n_atoms}")
+
+
 def _stream(stream=None) -> ctypes.c_void_p:
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
@@ -343,6 +351,7 @@ class Workspace:
 
 def neighbors(model: Model, dsys: DeviceSystem, nl: NeighborList, skin: float, ws: Workspace,
               stream=None) -> None:
+    _same_atoms(dsys, nl, "nep_neighbors")
     check(lib().nep_neighbors(model.handle, ctypes.byref(dsys.c), float(skin), ctypes.byref(nl.c),
                               ws.ptr, ws.bytes, _stream(stream)), "nep_neighbors")
 
@@ -350,6 +359,7 @@ def neighbors(model: Model, dsys: DeviceSystem, nl: NeighborList, skin: float, w
 def energy_forces_virial(model: Model, dsys: DeviceSystem, nl: NeighborList, ws: Workspace,
                          out=None, stream=None):
     """Returns (e_atom [N] f32, force [3,N] f32, e_tot [B] f64, virial [B,9] f64)."""
+    _same_atoms(dsys, nl, "nep_energy_forces_virial")
     import torch
     dev = dsys.pos.device
     if out is None:
@@ -385,6 +395,7 @@ def energy_forces_virial_fp64(model: Model, dsys: DeviceSystem, nl: NeighborList
     """nep_energy_forces_virial_fp64: (e_atom [N], force [3,N], e_tot [B],
     virial [B,9]), all f64.  params: optional device tensor [P] f64 (default:
     the model's FP32 parameters promoted)."""
+    _same_atoms(dsys, nl, "nep_energy_forces_virial_fp64")
     import torch
     dev = dsys.pos.device
     _dev(params, torch.float64, model.n_params, "params", "nep_energy_forces_virial_fp64", optional=True)
@@ -406,6 +417,7 @@ def param_grad_fp64(model: Model, dsys: DeviceSystem, nl: NeighborList, ws: Work
                     stream=None):
     """nep_param_grad_fp64: (grad [P] f64, loss [1] f64); labels e_lbl [B],
     f_lbl [3,N], v_lbl [B,9] f64 on the device; ws a training Workspace64."""
+    _same_atoms(dsys, nl, "nep_param_grad_fp64")
     import torch
     dev = dsys.pos.device
     where, f64 = "nep_param_grad_fp64", torch.float64
@@ -429,6 +441,7 @@ def param_grad_adjoint_fp64(model: Model, dsys: DeviceSystem, nl: NeighborList, 
                             mu, params=None, grad=None, stream=None):
     """nep_param_grad_adjoint_fp64: grad [P] f64 of sum a_e E + lam . F +
     mu : V (a_e [B], lam [3,N], mu [B,9] f64 on the device)."""
+    _same_atoms(dsys, nl, "nep_param_grad_adjoint_fp64")
     import torch
     dev = dsys.pos.device
     where, f64 = "nep_param_grad_adjoint_fp64", torch.float64
@@ -449,6 +462,7 @@ def param_grad(model: Model, dsys: DeviceSystem, nl: NeighborList, ws: Workspace
     """nep_param_grad: loss (Eqs. 18-21) and its gradient over all parameters.
     e_lbl [B] f64, f_lbl [3,N] f32, v_lbl [B,9] f64 on the device; ws must be a
     training workspace.  Returns (grad [P] f32, loss [1] f64)."""
+    _same_atoms(dsys, nl, "nep_param_grad")
     import torch
     dev = dsys.pos.device
     where = "nep_param_grad"
@@ -471,6 +485,7 @@ def param_grad_adjoint(model: Model, dsys: DeviceSystem, nl: NeighborList, ws: W
                        grad=None, stream=None):
     """nep_param_grad_adjoint: d/dtheta of sum a_e E + lam . F + mu : V.
     a_e [B] f64, lam [3,N] f32, mu [B,9] f64.  Returns grad [P] f32."""
+    _same_atoms(dsys, nl, "nep_param_grad_adjoint")
     import torch
     where = "nep_param_grad_adjoint"
     _adjoints(dsys, a_e, lam, mu, torch.float32, where)
@@ -503,6 +518,7 @@ def energy_forces_virial_noalloc(model: Model, dsys: DeviceSystem, nl: NeighborL
     energy_forces_virial, with scratch taken from the library's static
     device array instead of a caller workspace (for callers that cannot
     allocate device memory).  Returns (e_atom, force [3,N], e_tot, virial)."""
+    _same_atoms(dsys, nl, "nep_energy_forces_virial_noalloc")
     import torch
     dev = dsys.pos.device
     if out is None:
@@ -522,6 +538,7 @@ def md_step(model: Model, dsys: DeviceSystem, nl: NeighborList, vel, force, e_to
             masses, dt: float, skin: float, rebuild: bool, ws: Workspace, stream=None) -> None:
     """nep_md_step: vel [3,N] f32 (in place), force [3,N] f32, e_tot [B] and
     virial [B,9] f64 on the device; masses: host, one per species."""
+    _same_atoms(dsys, nl, "nep_md_step")
     import torch
     _outputs(dsys, (None, force, e_tot, virial), torch.float32, "nep_md_step")
     _dev(vel, torch.float32, 3 * dsys.n_atoms, "vel", "nep_md_step")
@@ -549,6 +566,7 @@ def autotune(model: Model, dsys: DeviceSystem, nl: NeighborList, ws: Workspace, 
              stream=None):
     """nep_autotune: pick the angular kernel variant for this system's size
     class; returns (chosen variant, 0)."""
+    _same_atoms(dsys, nl, "nep_autotune")
     chosen = (ctypes.c_int * 2)()
     check(lib().nep_autotune(model.handle, ctypes.byref(dsys.c), ctypes.byref(nl.c), ws.ptr, ws.bytes,
                              _stream(stream), int(reps), chosen), "nep_autotune")

@@ -70,6 +70,10 @@ def test_calls_check_before_reaching_the_library(monkeypatch):
                       grad=DeviceLike(4), loss=DeviceLike(1, f64))
     with pytest.raises(ValueError, match="params"):
         nb.Model.set_params(model, DeviceLike(5, f64))
+    with pytest.raises(ValueError, match="neighbour list holds 3 atoms"):
+        nb.neighbors(model, dsys, SimpleNamespace(n_atoms=3), 0.0, None)
+    with pytest.raises(ValueError, match="neighbour list"):
+        nb.energy_forces_virial(model, dsys, SimpleNamespace(n_atoms=5), None)
 
 
 def test_device_system_checks_shapes():
