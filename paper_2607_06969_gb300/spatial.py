@@ -211,7 +211,10 @@ class SpatialMD:
                  skin: float = 1.0, rebuild_every: int = 10):
         import torch
         self.model, self.g, self.vel = model, gsys, vel
+        nb._dev(vel, torch.float32, 3 * gsys.n_atoms, "vel", "SpatialMD")
         self.masses = np.ascontiguousarray(np.asarray(masses, np.float32))
+        if self.masses.size < model.hp.n_types:
+            raise ValueError(f"SpatialMD: {self.masses.size} masses for {model.hp.n_types} species")
         self.domains, self.reduce = list(domains), reduce
         self.dt, self.skin, self.every = dt, skin, rebuild_every
         dev = gsys.pos.device
