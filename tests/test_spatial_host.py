@@ -1,8 +1,9 @@
 """Host logic of the spatial decomposition: slab planning, the all-reduce
 that combines the ranks' owned rows (gloo, world size 2, CPU), and, with the
 FP64 oracle, the reason for the two-layer halo: a slab's local system of
-owned atoms and ghosts within 2 rc reproduces every owned atom's energy and
-force, and one layer does not."""
+owned atoms and ghosts within 2 rc reproduces every owned atom's energy,
+force and per-atom virial (so the owned sums add up to the whole system's
+E and V), and one layer does not."""
 import os
 
 import numpy as np
@@ -96,8 +97,9 @@ def test_two_layer_halo_reproduces_owned_atoms_in_the_oracle():
     types = rng.integers(0, 3, size=len(pos)).astype(np.int32)
     L = np.array([45.0, 12.0, 12.0])
     whole = _oracle_efv(h, th, pos, types, L[None, :], h.rc_rad)
+    from oracle import nep_oracle as O
     slabs, _ = SP.plan_slabs(L[0], 2, h.rc_rad, 0.0)
-    e_sum = 0.0
+    e_sum, v_sum = 0.0, np.zeros((3, 3))
     for halo, exact in ((2.0 * h.rc_rad, True), (h.rc_rad, False)):
         worst = 0.0
         for lo, hi in slabs:
@@ -109,8 +111,13 @@ def test_two_layer_halo_reproduces_owned_atoms_in_the_oracle():
             if exact:
                 assert np.allclose(loc["E"][:n_own], whole["E"][own], rtol=0, atol=1e-11)
                 e_sum += loc["E"][:n_own].sum()
+                # per-atom virials W_i = -sum_j f_ij (x) r_ij of the owned atoms
+                c = O.evaluate_centers(h, th, lp.astype(np.float32), lp, types[idx], box,
+                                       np.array([0, len(idx)]), np.arange(n_own))
+                v_sum += c["W"].sum(0)
         if exact:
             assert worst < 1e-10
             assert abs(e_sum - whole["Etot"][0]) < 1e-10
+            assert np.allclose(v_sum, whole["V"][0], rtol=0, atol=1e-9)
         else:
             assert worst > 1e-6            # ghosts' own neighbourhoods cut short
