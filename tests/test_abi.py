@@ -126,3 +126,43 @@ def test_plain_c_client_compiles_links_and_runs(L, tmp_path):
     out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split()
     assert int(out[0]) == O.param_count(h) and out[1] == "1"
     assert int(out[2]) == nb.NEP_ERR_ARG and out[3] == "1" and out[4] == "ok"
+
+
+def test_system_and_list_checks_reject_before_touching_the_gpu(L):
+    """The library's host-side checks of a system and a list run before the
+    model or any device pointer is used: offsets that do not end at N, a
+    box that is not positive, cap_ang > cap, and lists whose slot-major
+    arrays would pass 2^31 (cap * N) or 2^30 (cap_ang * N) entries.  A
+    zero-filled host buffer stands in for the model and the device arrays."""
+    import numpy as np
+    N = 216
+    stand_in = ctypes.create_string_buffer(4096)
+    p = ctypes.cast(stand_in, ctypes.c_void_p)
+    off = np.array([0, N], np.int32)
+    box = np.array([18.0, 18.0, 18.0], np.float32)
+
+    def system(off_arr, box_arr):
+        return nb.System(N, 1, p, p, p, p, off_arr.ctypes.data, box_arr.ctypes.data)
+
+    def nlist(cap, cap_ang):
+        return nb.NList(cap, cap_ang, p, p, p, p, p, p, 0.0, 0)
+
+    def status(sysc, nlc):
+        return L.nep_neighbors(p, ctypes.byref(sysc), ctypes.c_float(0.0), ctypes.byref(nlc), p, 1 << 20, None)
+
+    ok_list = nlist(96, 40)
+    cases = [
+        (system(np.array([0, N - 1], np.int32), box), ok_list, "end at n_atoms"),
+        (system(off, np.array([18.0, 0.0, 18.0], np.float32)), ok_list, "positive and finite"),
+        (system(off, box), nlist(40, 96), "cap_ang <= cap"),
+        (system(off, box), nlist((1 << 31) // N + 1, 1), "2^31"),
+        (system(off, box), nlist((1 << 30) // N + 1, (1 << 30) // N + 1), "2^30"),
+    ]
+    for sysc, nlc, msg in cases:
+        assert status(sysc, nlc) == nb.NEP_ERR_ARG, msg
+        assert msg in nb.last_error(), (msg, nb.last_error())
+    sysc = system(off, box)
+    nlc = nlist((1 << 31) // N + 1, 1)
+    assert L.nep_energy_forces_virial(p, ctypes.byref(sysc), ctypes.byref(nlc), p, p, p, p, p, 1 << 20,
+                                      None) == nb.NEP_ERR_ARG
+    assert "2^31" in nb.last_error()
