@@ -166,3 +166,43 @@ def test_system_and_list_checks_reject_before_touching_the_gpu(L):
     assert L.nep_energy_forces_virial(p, ctypes.byref(sysc), ctypes.byref(nlc), p, p, p, p, p, 1 << 20,
                                       None) == nb.NEP_ERR_ARG
     assert "2^31" in nb.last_error()
+
+
+def test_call_argument_checks_reject_before_touching_the_gpu(L):
+    """Per-call argument checks that precede any use of the model or the
+    device: the integrator's time steps and masses, the loss mode and
+    weights, and Adam's step, rate, moments and epsilon."""
+    import numpy as np
+    N = 216
+    stand_in = ctypes.create_string_buffer(4096)
+    p = ctypes.cast(stand_in, ctypes.c_void_p)
+    off = np.array([0, N], np.int32)
+    box = np.array([18.0, 18.0, 18.0], np.float32)
+    sysc = nb.System(N, 1, p, p, p, p, off.ctypes.data, box.ctypes.data)
+    nlc = nb.NList(96, 40, p, p, p, p, p, p, 0.0, 0)
+    masses = np.array([72.63, 121.76, 127.6], np.float32)
+    mp = masses.ctypes.data_as(ctypes.c_void_p)
+    f = ctypes.c_float
+
+    def expect(st, msg):
+        assert st == nb.NEP_ERR_ARG and msg in nb.last_error(), (st, msg, nb.last_error())
+
+    for dt in (0.0, -1.0, float("nan")):
+        expect(L.nep_md_step(p, ctypes.byref(sysc), ctypes.byref(nlc), p, p, p, p, mp, f(dt), f(1.0), 1, p,
+                             1 << 20, None), "dt must be positive")
+    expect(L.nep_md_step(p, ctypes.byref(sysc), ctypes.byref(nlc), p, p, p, p, None, f(2.0), f(1.0), 1, p,
+                         1 << 20, None), "masses_host is NULL")
+    expect(L.nep_md_kick(p, ctypes.byref(sysc), p, p, mp, f(float("inf")), f(2.0), None), "half_dt")
+    expect(L.nep_md_kick(p, ctypes.byref(sysc), p, p, mp, f(1.0), f(-2.0), None), "drift_dt")
+    w = np.array([1.0, 1.0, 0.1], np.float32)
+    wp = w.ctypes.data_as(ctypes.c_void_p)
+    expect(L.nep_param_grad(p, ctypes.byref(sysc), ctypes.byref(nlc), p, p, p, wp, 2, p, p, p, 1 << 20, None),
+           "loss_mode must be 0 or 1")
+    expect(L.nep_param_grad(p, ctypes.byref(sysc), ctypes.byref(nlc), p, p, p, None, 0, p, p, p, 1 << 20, None),
+           "loss weights are NULL")
+    for kw, msg in ((dict(t=0), "t must be >= 1"), (dict(lr=-1.0), "lr must be"), (dict(beta1=1.0), "beta1"),
+                    (dict(beta2=-0.1), "beta1 and beta2"), (dict(eps=0.0), "eps must be")):
+        a = dict(t=1, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8)
+        a.update(kw)
+        expect(L.nep_adam_step(p, p, p, p, a["t"], f(a["lr"]), f(a["beta1"]), f(a["beta2"]), f(a["eps"]), None),
+               msg)
