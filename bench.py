@@ -37,13 +37,16 @@ CAP, CAP_ANG, SKIN, DT, REBUILD = 160, 80, 1.0, 2.0, 10
 
 
 def parse():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
-    ap.add_argument("--warmup", type=int, default=20)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=100)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap = argparse.ArgumentParser(description="NEP benchmark: one JSON line on rank 0")
+    ap.add_argument("--gpus", type=int, default=1,
+                    help="GPUs of the run (one process each, launched by torch.distributed.run for N > 1)")
+    ap.add_argument("--steps", type=int, default=1000, help="timed MD steps (one CUDA graph)")
+    ap.add_argument("--warmup", type=int, default=20, help="untimed MD steps before them")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"],
+                    help="reference: the FP64 oracle on the host cores instead of the GPU path")
+    ap.add_argument("--e2e-steps", type=int, default=100,
+                    help="steps of the end-to-end run from pinned host buffers")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing on the host")
     ap.add_argument("--no-train", action="store_true", help="skip the training-step leg")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision leg")
     ap.add_argument("--no-replicas", action="store_true", help="skip the batched-replica leg")
