@@ -235,7 +235,9 @@ nep_status nep_energy_forces_virial_owned(nep_model* m, const nep_system* sys, c
  * forces themselves (a spatial decomposition): per atom v += half_dt F/m
  * (masses_host[n_types] in u, F in eV/A, v in A/fs), then, if drift_dt > 0,
  * x += drift_dt v.  nep_md_wrap wraps every atom into its configuration's
- * box, as nep_md_step does at a rebuild.  sys->pos is written. */
+ * box, as nep_md_step does at a rebuild.  sys->pos is written.
+ * NEP_ERR_ARG: masses_host NULL or a mass <= 0, vel or force NULL, half_dt
+ * not finite, drift_dt negative or not finite. */
 nep_status nep_md_kick(nep_model* m, const nep_system* sys, float* vel, const float* force, const float* masses_host,
                        float half_dt, float drift_dt, void* stream);
 nep_status nep_md_wrap(nep_model* m, const nep_system* sys, void* stream);
@@ -336,7 +338,9 @@ nep_status nep_param_grad_adjoint(nep_model* m, const nep_system* sys, const nep
  *   theta -= lr / (1 - beta1^t) * m / (sqrt(v) / sqrt(1 - beta2^t) + eps)
  * grad [P] float (e.g. from nep_param_grad), m1 [P] and m2 [P] float are the
  * caller's moment buffers (zero before step t = 1), t >= 1 the step number.
- * No weight decay.  A hot call: one kernel on `stream`, no allocation. */
+ * No weight decay.  A hot call: one kernel on `stream`, no allocation.
+ * NEP_ERR_ARG: a NULL buffer, t < 1, lr negative or not finite, beta1 or
+ * beta2 outside [0, 1), eps <= 0 or not finite. */
 nep_status nep_adam_step(nep_model* m, const float* grad, float* m1, float* m2, int t, float lr,
                          float beta1, float beta2, float eps, void* stream);
 
@@ -346,7 +350,10 @@ nep_status nep_adam_step(nep_model* m, const float* grad, float* m1, float* m2, 
  * pos is updated in place (sys->pos is treated as writable), vel [3][N],
  * force [3][N] must hold the forces of the current positions on entry
  * (call nep_energy_forces_virial once before the first step).
- * e_tot/virial receive the new step's values. */
+ * e_tot/virial receive the new step's values.
+ * NEP_ERR_ARG: the system or list checks of nep_neighbors, masses_host NULL
+ * or a mass <= 0, vel or force NULL, dt <= 0 or not finite, a workspace
+ * smaller than nep_workspace_bytes. */
 nep_status nep_md_step(nep_model* m, const nep_system* sys, nep_nlist* nl, float* vel,
                        float* force, double* e_tot, double* virial, const float* masses_host,
                        float dt, float skin, int rebuild, void* work, size_t work_bytes,
