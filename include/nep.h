@@ -313,6 +313,8 @@ size_t nep_train_workspace_bytes(const nep_model* m, int n_atoms, int n_cfg, int
  *                             + wV/9 sum_ab (dV_b,ab/N_b)^2]
  * loss_mode 1: Eqs. 19-21 per configuration, averaged over the batch:
  *              1/B sum_b [wE dE_b^2/N_b + wF/(3N_b) sum |dF|^2 + wV/(9N_b) sum dV^2]
+ * A configuration with no atoms adds no term (its per-atom normalisation is
+ * undefined) but counts in B.
  * grad [P] float (overwritten), loss [1] double (may be NULL).
  * work: nep_train_workspace_bytes bytes.  The gradient is that of the FP32
  * forward; sums over atoms and chunks are fixed-order (FP64 across chunks),
