@@ -434,13 +434,17 @@ def loss_value(h, theta, pos, types, box, atom_off, pairs, E_lbl, F_lbl, V_lbl,
     dV = (out["V"] - V_lbl.reshape(B, 3, 3)).reshape(B, 9)
     sF = np.zeros(B, dtype=dF.dtype)
     np.add.at(sF, cfg, (dF * dF).sum(1))
+    # a configuration with no atoms has no per-atom normalisation: it adds no
+    # term but still counts in B
+    has = Nb > 0
+    n = np.where(has, Nb, 1.0)
     if mode == 0:
-        Lb = w[0] * (dE / Nb) ** 2 + w[1] * sF / (3 * Nb) + w[2] * ((dV / Nb[:, None]) ** 2).sum(1) / 9.0
+        Lb = w[0] * (dE / n) ** 2 + w[1] * sF / (3 * n) + w[2] * ((dV / n[:, None]) ** 2).sum(1) / 9.0
     elif mode == 1:
-        Lb = w[0] * dE ** 2 / Nb + w[1] * sF / (3 * Nb) + w[2] * (dV ** 2).sum(1) / (9.0 * Nb)
+        Lb = w[0] * dE ** 2 / n + w[1] * sF / (3 * n) + w[2] * (dV ** 2).sum(1) / (9.0 * n)
     else:
         raise ValueError(mode)
-    return Lb.sum() / B
+    return np.where(has, Lb, 0.0).sum() / B
 
 
 def adjoint_functional(h, theta, pos, types, box, atom_off, pairs, aE, lamF, muV):

@@ -354,6 +354,34 @@ def test_loss_closed_form():
     assert abs(zero) < 1e-28
 
 
+def test_loss_with_an_empty_configuration():
+    """An empty configuration adds no loss term, whatever its labels, but
+    counts in the batch size: inserting one into a batch of B scales the
+    loss and its gradient by B / (B + 1), in both modes."""
+    h = tiny_hyper()
+    th = I.init_params(h, seed=29)
+    s, pr = batch_case(h)
+    pos = s.pos32().astype(np.float64)
+    lab = O.energy_forces_virial(h, I.init_params(h, seed=30), pos, s.types, s.box, s.atom_off, pr)
+    off2 = np.insert(s.atom_off, 1, s.atom_off[1])                     # empty configuration 1
+    box2 = np.insert(s.box, 1, [20.0, 20.0, 20.0], axis=0)
+    pr2 = O.neighbor_pairs(s.pos32(), box2, off2, h.rc_rad)
+    E2 = np.insert(lab["Etot"], 1, 3.0)
+    V2 = np.insert(lab["V"].reshape(-1, 9), 1, np.arange(9.0), axis=0)
+    B = s.n_cfg
+    for mode in (0, 1):
+        def L1(t):
+            return O.loss_value(h, t, pos, s.types, s.box, s.atom_off, pr, lab["Etot"], lab["F"], lab["V"],
+                                mode=mode)
+
+        def L2(t):
+            return O.loss_value(h, t, pos, s.types, box2, off2, pr2, E2, lab["F"], V2, mode=mode)
+        assert abs(L2(th) - L1(th) * B / (B + 1)) <= 1e-14 * abs(L1(th))
+        idx = [0, 7, O.param_count(h) - 1]
+        assert np.allclose(O.complex_step_grad(L2, th, idx), O.complex_step_grad(L1, th, idx) * B / (B + 1),
+                           rtol=1e-12, atol=0)
+
+
 def test_gradient_complex_step_vs_central_difference():
     h = tiny_hyper()
     th = I.init_params(h, seed=22)
