@@ -190,3 +190,15 @@ def test_loss_mode1_with_the_mode0_energy_term_is_caught(monkeypatch):
         return real(*a, mode=0 if mode == 1 else mode, **k)
     monkeypatch.setattr(O, "loss_value", wrong)
     _fails(P.test_loss_closed_form)
+
+
+def test_empty_configuration_left_out_of_the_mean_is_caught(monkeypatch):
+    """An empty configuration dropped from B as well as from the sum."""
+    real = O.loss_value
+
+    def wrong(h, theta, pos, types, box, atom_off, *rest, **k):
+        n_cfg = len(atom_off) - 1
+        n_full = int(np.count_nonzero(np.diff(atom_off)))
+        return real(h, theta, pos, types, box, atom_off, *rest, **k) * n_cfg / max(n_full, 1)
+    monkeypatch.setattr(O, "loss_value", wrong)
+    _fails(P.test_loss_with_an_empty_configuration)
