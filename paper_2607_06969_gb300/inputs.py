@@ -241,7 +241,8 @@ def maxwell_boltzmann(types: np.ndarray, temp: float = 900.0, seed: int = SEED_V
     for b in range(len(off) - 1):
         s = slice(off[b], off[b + 1])
         mm = m[s]
-        v[s] -= (mm[:, None] * v[s]).sum(0) / mm.sum()
+        if mm.size:                                # an empty configuration has no centre of mass
+            v[s] -= (mm[:, None] * v[s]).sum(0) / mm.sum()
     return v
 
 

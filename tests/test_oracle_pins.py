@@ -494,6 +494,26 @@ def test_generators_composition():
     assert np.isclose(b.box[1, 0], (100 / 0.0325) ** (1 / 3))
 
 
+def test_velocities_temperature_momentum_and_units():
+    """The MD start: Maxwell-Boltzmann velocities at T with zero momentum per
+    configuration, and the unit constants against CODATA 2018 (1 u A^2/fs^2
+    in eV, and k_B in eV/K)."""
+    assert abs(I.MVV_TO_EV - 1.66053906660e-27 * 1e-20 / 1e-30 / 1.602176634e-19) < 1e-4
+    assert abs(I.KB_EV - 1.380649e-23 / 1.602176634e-19) < 1e-12
+    types = np.repeat(np.array([0, 1, 2], np.int32), 20000)
+    np.random.default_rng(2).shuffle(types)
+    off = np.array([0, 25000, 25000, 60000])                       # one empty configuration
+    v = I.maxwell_boltzmann(types, 900.0, atom_off=off)
+    m = I.MASSES[types]
+    for b in (0, 2):
+        s = slice(off[b], off[b + 1])
+        p = (m[s, None] * v[s]).sum(0)
+        assert np.abs(p).max() < 1e-9 * np.sqrt((m[s, None] * v[s] ** 2).sum())
+        n = off[b + 1] - off[b]
+        T = (m[s, None] * v[s] ** 2).sum() * I.MVV_TO_EV / (3 * (n - 1) * I.KB_EV)
+        assert abs(T - 900.0) < 0.02 * 900.0, T
+
+
 def test_evaluate_centers_equals_whole_system():
     """The neighbourhood evaluation of sampled atoms (used at the full
     workload sizes) against the whole-system evaluation (pinned above by
