@@ -424,7 +424,8 @@ def loss_value(h, theta, pos, types, box, atom_off, pairs, E_lbl, F_lbl, V_lbl,
                w=(1.0, 1.0, 0.1), mode=0):
     """mode 0: L = 1/B sum_b [wE (dE_b/N_b)^2 + wF/(3N_b) sum dF^2 + wV/9 sum (dV_b/N_b)^2]
     mode 1: L = 1/B sum_b [wE/N_b dE_b^2 + wF/(3N_b) sum dF^2 + wV/(9N_b) sum dV_b^2]
-    (Eqs. 19-21 per configuration, averaged over the batch)."""
+    (Eqs. 19-21 per configuration, averaged over the batch).  A configuration
+    with N_b = 0 adds no term but counts in B (the paper is silent there)."""
     out = energy_forces_virial(h, theta, pos, types, box, atom_off, pairs)
     Nb = np.diff(atom_off).astype(np.float64)
     B = Nb.size
