@@ -85,3 +85,14 @@ def test_device_system_checks_shapes():
                  (pos, types, np.full(3, 10.0), off), (pos, types, box, off[:2])):
         with pytest.raises(ValueError):
             nb.DeviceSystem(*args, device="cpu")
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without libnep.so every call raises: there is no fallback path."""
+    monkeypatch.setattr(nb, "_LIB", None)
+    monkeypatch.setattr(nb, "LIB_PATH", str(tmp_path / "libnep.so"))
+    with pytest.raises(RuntimeError, match="is missing"):
+        nb.lib()
+    with pytest.raises(RuntimeError, match="is missing"):
+        nb.num_params(SimpleNamespace(n_types=3, n_rad=8, n_ang=6, k_rad=8, k_ang=8, l_max=4, has_4body=1,
+                                      n_hidden=30, rc_rad=7.0, rc_ang=5.0))
