@@ -121,3 +121,66 @@ def test_two_layer_halo_reproduces_owned_atoms_in_the_oracle():
             assert np.allclose(v_sum, whole["V"][0], rtol=0, atol=1e-9)
         else:
             assert worst > 1e-6            # ghosts' own neighbourhoods cut short
+
+
+def test_spatial_md_step_order(monkeypatch):
+    """SpatialMD's velocity-Verlet order with the library and the slab
+    domains replaced by recorders: kick + drift, a wrap and rebuild every
+    `rebuild_every` steps, the owned forces of every domain combined by one
+    reduce, then the closing half kick."""
+    import ctypes
+    from types import SimpleNamespace
+
+    import torch
+
+    from paper_2607_06969_gb300 import binding as nb
+    log = []
+
+    class Lib:
+        def nep_md_kick(self, m, sysc, vel, force, masses, half_dt, drift_dt, stream):
+            log.append(("kick", round(half_dt.value, 6), round(drift_dt.value, 6)))
+            return 0
+
+        def nep_md_wrap(self, m, sysc, stream):
+            log.append(("wrap",))
+            return 0
+
+    class Dom:
+        def __init__(self, k):
+            self.k = k
+
+        def rebuild(self):
+            log.append(("rebuild", self.k))
+
+        def evaluate(self, force):
+            log.append(("evaluate", self.k))
+            return torch.ones(1, dtype=torch.float64), torch.ones(1, 9, dtype=torch.float64)
+
+    class Vel:
+        is_cuda, dtype, shape = True, torch.float32, (3, 4)
+
+        def numel(self):
+            return 12
+
+        def is_contiguous(self):
+            return True
+
+        def data_ptr(self):
+            return 0
+
+    monkeypatch.setattr(nb, "lib", lambda: Lib())
+    monkeypatch.setattr(nb, "_stream", lambda stream=None: ctypes.c_void_p(0))
+    model = SimpleNamespace(handle=None, hp=SimpleNamespace(n_types=3))
+    gsys = SimpleNamespace(n_atoms=4, pos=torch.zeros(3, 4), c=nb.System())
+    md = SP.SpatialMD(model, gsys, Vel(), [72.6, 121.8, 127.6], [Dom(0), Dom(1)],
+                      reduce=lambda f, e, v: log.append(("reduce", float(e.item()))), dt=2.0, rebuild_every=3)
+    md.start()
+    assert log == [("wrap",), ("rebuild", 0), ("rebuild", 1), ("evaluate", 0), ("evaluate", 1), ("reduce", 2.0)]
+    for _ in range(3):
+        log.clear()
+        md.step()
+        body = [("evaluate", 0), ("evaluate", 1), ("reduce", 2.0), ("kick", 1.0, 0.0)]
+        if md.k % 3 == 0:
+            assert log == [("kick", 1.0, 2.0), ("wrap",), ("rebuild", 0), ("rebuild", 1)] + body
+        else:
+            assert log == [("kick", 1.0, 2.0)] + body
