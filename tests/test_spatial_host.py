@@ -184,3 +184,25 @@ def test_spatial_md_step_order(monkeypatch):
             assert log == [("kick", 1.0, 2.0), ("wrap",), ("rebuild", 0), ("rebuild", 1)] + body
         else:
             assert log == [("kick", 1.0, 2.0)] + body
+
+
+def test_slab_domain_frame_and_capacity():
+    """A slab's local frame: origin lo - halo, a local box whose x exceeds
+    slab + 2 halo by more than rc + skin (no local image in range), and a
+    local capacity that covers the slab's share of the atoms."""
+    from types import SimpleNamespace
+
+    import torch
+    h = SimpleNamespace(rc_rad=7.0)
+    model = SimpleNamespace(h=h)
+    N, L = 900_000, np.array([[300.0, 300.0, 300.0]], np.float32)
+    g = SimpleNamespace(n_cfg=1, n_atoms=N, box_host=L, pos=torch.zeros(3, 1))
+    slabs, halo = SP.plan_slabs(300.0, 4, 7.0, 1.0)
+    lo, hi = slabs[1]
+    d = SP.SlabDomain(model, g, lo, hi, halo, 1.0, 160, 80)
+    assert d.origin == lo - halo
+    assert d.box_local[0] > hi - lo + 2 * halo + h.rc_rad + 1.0 - 1e-3
+    assert tuple(d.box_local[1:]) == (300.0, 300.0)
+    assert d.local_cap >= N * (hi - lo + 2 * halo) / 300.0
+    with pytest.raises(ValueError):
+        SP.SlabDomain(model, SimpleNamespace(n_cfg=2, n_atoms=N, box_host=L, pos=g.pos), lo, hi, halo, 1.0, 160, 80)
