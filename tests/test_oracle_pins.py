@@ -494,6 +494,27 @@ def test_generators_composition():
     assert np.isclose(b.box[1, 0], (100 / 0.0325) ** (1 / 3))
 
 
+def test_workload_sizes():
+    """The synthetic workloads have the sizes the workload definitions state:
+    216 atoms; 900,000 atoms in a 300 A box; 3,686,400 atoms in a 480 A box;
+    128 configurations of 24-512 atoms (mean about 268); 1,024 replicas of
+    64-4096 atoms, log-uniform (about 1.0M atoms)."""
+    s, h = I.workload_cell216()
+    assert s.n_atoms == 216 and np.allclose(s.box, 18.0) and O.descriptor_dim(h) == 38
+    s, _ = I.workload_md900k()
+    assert s.n_atoms == 900_000 and np.allclose(s.box, 300.0)
+    assert np.bincount(s.types).tolist() == [200_000, 200_000, 500_000]     # 20% of 500,000 cation sites vacant
+    del s
+    s, h = I.workload_mixed3m7()
+    assert s.n_atoms == 3_686_400 and np.allclose(s.box, 480.0) and h.n_hidden == 64
+    del s
+    c = np.asarray(I.uniform_counts(128, 24, 512, tag=2))
+    assert c.min() >= 24 and c.max() <= 512 and abs(c.mean() - 268) < 25
+    c = np.asarray(I.loguniform_counts(1024, 64, 4096, tag=4))
+    assert c.min() >= 64 and c.max() <= 4096 and abs(c.sum() - 1.0e6) < 0.1e6
+    assert abs(np.median(np.log(c)) - 0.5 * (np.log(64) + np.log(4096))) < 0.2     # log-uniform
+
+
 def test_velocities_temperature_momentum_and_units():
     """The MD start: Maxwell-Boltzmann velocities at T with zero momentum per
     configuration, and the unit constants against CODATA 2018 (1 u A^2/fs^2
