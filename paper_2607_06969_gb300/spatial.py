@@ -39,7 +39,10 @@ from . import binding as nb
 
 def plan_slabs(Lx: float, world: int, rc: float, skin: float) -> tuple[list[tuple[float, float]], float]:
     """Equal slabs [lo, hi) of [0, Lx) per rank and the halo 2 (rc + skin);
-    raises if a slab and its two halos do not fit in the box."""
+    raises if a slab and its two halos do not fit in the box.  One rank gets
+    the whole box, which needs no decomposition: nep_domain_select rejects
+    it (an atom would be its own ghost), so a single GPU runs the
+    whole-system calls instead."""
     if world < 1:
         raise ValueError("world must be >= 1")
     halo = 2.0 * (rc + skin)
