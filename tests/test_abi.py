@@ -200,6 +200,13 @@ def test_call_argument_checks_reject_before_touching_the_gpu(L):
            "loss_mode must be 0 or 1")
     expect(L.nep_param_grad(p, ctypes.byref(sysc), ctypes.byref(nlc), p, p, p, None, 0, p, p, p, 1 << 20, None),
            "loss weights are NULL")
+    for n_owned in (-1, N + 1):
+        expect(L.nep_energy_forces_virial_owned(p, ctypes.byref(sysc), ctypes.byref(nlc), n_owned, p, p, p, p, p,
+                                                1 << 20, None), "need 0 <= n_owned <= n_atoms")
+    unbuilt = nb.NList(96, 40, p, p, p, None, p, p, 0.0, 0)         # no shifts and not minimum-image
+    assert L.nep_energy_forces_virial(p, ctypes.byref(sysc), ctypes.byref(unbuilt), p, p, p, p, p, 1 << 20,
+                                      None) == nb.NEP_ERR_STATE
+    assert "not built" in nb.last_error()
     for kw, msg in ((dict(t=0), "t must be >= 1"), (dict(lr=-1.0), "lr must be"), (dict(beta1=1.0), "beta1"),
                     (dict(beta2=-0.1), "beta1 and beta2"), (dict(eps=0.0), "eps must be")):
         a = dict(t=1, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8)
