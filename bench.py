@@ -863,6 +863,17 @@ def table2_leg(nb, torch, I) -> dict:
 
 
 # ------------------------------------------------------------------ our arm
+def guarded(leg, *args, **kwargs) -> dict:
+    """Run one secondary bench leg; an exception becomes {"error": ...} in
+    its place, so that it cannot take the measured headline with it."""
+    try:
+        return leg(*args, **kwargs)
+    except Exception as e:  # noqa: BLE001 - any failure of a side leg is recorded, not raised
+        import traceback
+        traceback.print_exc(file=sys.stderr)
+        return {"error": f"{type(e).__name__}: {e}"}
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -962,17 +973,21 @@ def main():
     e2e_ms = e0.elapsed_time(e1)
     e2e_val = world * N * KE / (e2e_ms * 1e-3)
 
-    train = None if args.no_train else train_leg(nb, torch, I, local, dist, world, rank)
-    mixed = None if args.no_mixed else mixed_leg(nb, torch, I)
-    replicas = None if args.no_replicas else replicas_leg(nb, torch, I, dist=dist, world=world, rank=rank)
-    table2 = None if args.no_table2 else table2_leg(nb, torch, I)
-    fig3 = None if args.no_fig3 else fig3_leg(nb, torch, I)
-    fp64 = None if args.no_fp64 else fp64_leg(nb, torch, I)
+    # The secondary legs run after the headline is measured.  A leg that
+    # raises is recorded under its key as {"error": ...}; the line is printed
+    # whatever the legs do.
+    train = None if args.no_train else guarded(train_leg, nb, torch, I, local, dist, world, rank)
+    mixed = None if args.no_mixed else guarded(mixed_leg, nb, torch, I)
+    replicas = None if args.no_replicas else guarded(replicas_leg, nb, torch, I, dist=dist, world=world,
+                                                     rank=rank)
+    table2 = None if args.no_table2 else guarded(table2_leg, nb, torch, I)
+    fig3 = None if args.no_fig3 else guarded(fig3_leg, nb, torch, I)
+    fp64 = None if args.no_fp64 else guarded(fp64_leg, nb, torch, I)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline()
-        if fig3 is not None:
+        cpu = guarded(cpu_baseline)
+        if fig3 is not None and "error" not in fig3 and "error" not in cpu:
             # GPU training operator against the oracle's forward pass, per size
             fig3["oracle_forward_ms_per_config"] = cpu["fig3_forward_ms_per_config"]
             fig3["ratio_oracle_forward_to_gpu_train_op"] = {

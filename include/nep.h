@@ -290,7 +290,11 @@ nep_status nep_domain_scatter(const float* src, int n_local, int ncomp, const in
  *
  * The first call on a device looks up the array's device address for that
  * device (cudaGetSymbolAddress, once per device, with the caller's device
- * current); make that first call before any stream capture.  Every call
+ * current); make that first call before any stream capture.  The address
+ * is cached for the life of the process: it belongs to the device's primary
+ * context, so after cudaDeviceReset (or any other teardown of that context)
+ * it is stale and this entry point must not be called again in that
+ * process.  Every call
  * shares the one array and leaves its contents behind; the computation
  * writes every scratch word it later reads, so nothing needs clearing
  * between calls.  Calls whose GPU work overlaps (different streams, or

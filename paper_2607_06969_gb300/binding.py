@@ -503,8 +503,8 @@ def adam_step(model: Model, grad, m1, m2, t: int, lr: float, beta1: float = 0.9,
     """nep_adam_step: one Adam update of the model's parameters in place.
     grad, m1, m2: device tensors [P] f32 (m1, m2 zero before t = 1)."""
     import torch
-    for name, t in (("grad", grad), ("m1", m1), ("m2", m2)):
-        _dev(t, torch.float32, model.n_params, name, "nep_adam_step")
+    for name, x in (("grad", grad), ("m1", m1), ("m2", m2)):
+        _dev(x, torch.float32, model.n_params, name, "nep_adam_step")
     check(lib().nep_adam_step(model.handle, _ptr(grad), _ptr(m1), _ptr(m2), int(t), float(lr), float(beta1),
                               float(beta2), float(eps), _stream(stream)), "nep_adam_step")
 

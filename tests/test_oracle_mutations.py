@@ -202,3 +202,37 @@ def test_empty_configuration_left_out_of_the_mean_is_caught(monkeypatch):
         return real(h, theta, pos, types, box, atom_off, *rest, **k) * n_cfg / max(n_full, 1)
     monkeypatch.setattr(O, "loss_value", wrong)
     _fails(P.test_loss_with_an_empty_configuration)
+
+
+def test_swapped_network_bias_blocks_are_caught(monkeypatch):
+    """unpack reading w1 where b0 sits and b0 where w1 sits."""
+    real = O.unpack
+
+    def wrong(h, theta):
+        p = real(h, theta)
+        return O.Params(p.W0, p.w1, p.b0, p.b1, p.cR, p.cA)
+    monkeypatch.setattr(O, "unpack", wrong)
+    _fails(P.test_unpack_follows_the_header_block_order)
+
+
+def test_transposed_w0_block_is_caught(monkeypatch):
+    """unpack reading each W0[t] as [D][H] and transposing it."""
+    real = O.unpack
+
+    def wrong(h, theta):
+        p = real(h, theta)
+        T, H, D = p.W0.shape
+        return O.Params(p.W0.reshape(T, D, H).transpose(0, 2, 1).copy(), p.b0, p.w1, p.b1, p.cR, p.cA)
+    monkeypatch.setattr(O, "unpack", wrong)
+    _fails(P.test_unpack_follows_the_header_block_order)
+
+
+def test_swapped_c_blocks_are_caught(monkeypatch):
+    """unpack taking cR's species pair as (Zj, Zi)."""
+    real = O.unpack
+
+    def wrong(h, theta):
+        p = real(h, theta)
+        return O.Params(p.W0, p.b0, p.w1, p.b1, p.cR.transpose(1, 0, 2, 3).copy(), p.cA)
+    monkeypatch.setattr(O, "unpack", wrong)
+    _fails(P.test_unpack_follows_the_header_block_order)

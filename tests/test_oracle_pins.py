@@ -96,6 +96,57 @@ def g_closed(coef, r, rc):
     return coef @ Q
 
 
+def named_blocks(h, seed=11):
+    """Random named parameter blocks, and theta assembled from them in the
+    flat order that include/nep.h states: for t in types W0[t][H][D], b0[t][H],
+    w1[t][H], b1[t]; then cR[Zi][Zj][n_rad][k_rad]; then cA[Zi][Zj][n_ang][k_ang]."""
+    rng = np.random.default_rng(seed)
+    T, H, D = h.n_types, h.n_hidden, O.descriptor_dim(h)
+    blk = dict(W0=rng.normal(size=(T, H, D)), b0=rng.normal(size=(T, H)), w1=rng.normal(size=(T, H)),
+               b1=rng.normal(size=T), cR=0.3 * rng.normal(size=(T, T, h.n_rad, h.k_rad)),
+               cA=0.3 * rng.normal(size=(T, T, h.n_ang, h.k_ang)))
+    parts = []
+    for t in range(T):
+        for r in range(H):                      # W0[t] row by row: hidden unit outer, descriptor inner
+            parts += [blk["W0"][t, r, d] for d in range(D)]
+        parts += list(blk["b0"][t]) + list(blk["w1"][t]) + [blk["b1"][t]]
+    for a in range(T):
+        for b in range(T):
+            for n in range(h.n_rad):
+                parts += list(blk["cR"][a, b, n])
+    for a in range(T):
+        for b in range(T):
+            for n in range(h.n_ang):
+                parts += list(blk["cA"][a, b, n])
+    return blk, np.array(parts, np.float64)
+
+
+def test_unpack_follows_the_header_block_order():
+    """unpack maps the flat vector onto the named blocks in nep.h's order
+    (H != D, so a transposed W0 cannot pass), and the energy computed from
+    the named blocks by hand equals the oracle's: an isolated atom has q = 0
+    and E = w1 . tanh(b0) + b1 (a swapped b0/w1 fails); a dimer's E uses W0
+    and the ordered-pair radial and angular blocks."""
+    h = tiny_hyper()
+    blk, th = named_blocks(h)
+    assert th.size == O.param_count(h)
+    prm = O.unpack(h, th)
+    for k in ("W0", "b0", "w1", "b1", "cR", "cA"):
+        assert np.array_equal(getattr(prm, k), blk[k]), k
+    for t in range(h.n_types):
+        out, _ = efv(h, th, iso_system([[0, 0, 0]], [t]))
+        assert abs(out["Etot"][0] - (blk["w1"][t] @ np.tanh(blk["b0"][t]) + blk["b1"][t])) < 1e-13
+    r, ta, tb = 2.7, 0, 2
+    out, _ = efv(h, th, iso_system([[0, 0, 0], [0, 0, r]], [ta, tb]))
+    e = 0.0
+    for a, b in ((ta, tb), (tb, ta)):
+        gR = g_closed(blk["cR"][a, b], r, h.rc_rad)
+        gA = g_closed(blk["cA"][a, b], r, h.rc_ang)
+        qq = np.concatenate([gR, np.repeat(gA ** 2, h.l_max), 2.0 / 9.0 * gA ** 3])
+        e += blk["w1"][a] @ np.tanh(blk["W0"][a] @ qq + blk["b0"][a]) + blk["b1"][a]
+    assert abs(out["Etot"][0] - e) < 1e-12
+
+
 @pytest.mark.parametrize("ta,tb", [(0, 2), (1, 1), (2, 0)])
 def test_dimer_closed_form(ta, tb):
     h = H0

@@ -50,6 +50,9 @@ def test_noalloc_matches_workspace_call_twice(nb, case):
         assert np.abs(got[1] - ref[1]).max() <= TOL_F
         assert np.all(np.abs(got[2] - ref[2]) <= TOL_ET * Nb)
         assert np.all(np.abs(got[3] - ref[3]).max(1) <= TOL_V * Nb)
+        # the same kernels on the same inputs, scratch elsewhere: bit for bit
+        for g, r in zip(got, ref):
+            assert np.array_equal(g, r)
 
 
 def test_noalloc_rejects_systems_beyond_the_static_array(nb):
