@@ -467,6 +467,66 @@ def complex_step_grad(fun, theta, indices, h_step=1e-30):
 
 
 # ---------------------------------------------------------------------------
+# molecular dynamics: velocity Verlet around the forces of Eq. 3
+# ---------------------------------------------------------------------------
+# 1 u A^2 / fs^2 expressed in eV, from the CODATA atomic mass constant and the
+# elementary charge: a = F / (m * MVV_EV) in A/fs^2 for F in eV/A and m in u.
+ATOMIC_MASS_KG = 1.66053906660e-27
+ELEMENTARY_CHARGE_C = 1.602176634e-19
+MVV_EV = ATOMIC_MASS_KG * 1e-20 / 1e-30 / ELEMENTARY_CHARGE_C
+
+
+def wrap_positions(pos, box, atom_off):
+    """Each atom's coordinates mapped into [0, L) of its configuration's box."""
+    cfg = np.repeat(np.arange(box.shape[0]), np.diff(atom_off))
+    L = box[cfg]
+    return pos - L * np.floor(pos / L)
+
+
+def kinetic_energy(vel, types, masses, atom_off):
+    """Per-configuration sum of m v^2 / 2 in eV (v in A/fs, m in u)."""
+    B = len(atom_off) - 1
+    cfg = np.repeat(np.arange(B), np.diff(atom_off))
+    ke = 0.5 * MVV_EV * np.asarray(masses, np.float64)[types] * (vel * vel).sum(1)
+    out = np.zeros(B)
+    np.add.at(out, cfg, ke)
+    return out
+
+
+def velocity_verlet(h, theta, pos, vel, types, box, atom_off, masses, dt, n_steps, rebuild_every=10,
+                    force=None):
+    """n_steps of velocity Verlet in FP64, each step in this order:
+    v += dt/2 F/(m MVV_EV); x += dt v; at every rebuild_every-th step
+    (counting from step 0) x is wrapped into the box; F = F(x) by Eq. 3 over
+    every pair inside rc_rad at the new positions; v += dt/2 F/(m MVV_EV).
+    force: F at the starting positions (evaluated here when None).
+    Returns the final pos, vel and F, and per step the potential and
+    kinetic energy of every configuration."""
+    pos = np.array(pos, np.float64)
+    vel = np.array(vel, np.float64)
+    types = np.asarray(types)
+    inv_m = 1.0 / (np.asarray(masses, np.float64)[types] * MVV_EV)
+
+    def forces(x):
+        pairs = neighbor_pairs(x.astype(np.float32), box, atom_off, h.rc_rad)
+        out = energy_forces_virial(h, theta, x, types, box, atom_off, pairs)
+        return out["F"], out["Etot"]
+
+    F = np.array(force, np.float64) if force is not None else forces(pos)[0]
+    epot, ekin = [], []
+    for k in range(n_steps):
+        vel = vel + 0.5 * dt * F * inv_m[:, None]
+        pos = pos + dt * vel
+        if k % rebuild_every == 0:
+            pos = wrap_positions(pos, box, atom_off)
+        F, E = forces(pos)
+        vel = vel + 0.5 * dt * F * inv_m[:, None]
+        epot.append(E)
+        ekin.append(kinetic_energy(vel, types, masses, atom_off))
+    return dict(pos=pos, vel=vel, F=F, epot=np.array(epot), ekin=np.array(ekin))
+
+
+# ---------------------------------------------------------------------------
 # optimiser (Section 3.3.1)
 # ---------------------------------------------------------------------------
 def adam_step(theta, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):

@@ -236,3 +236,50 @@ def test_swapped_c_blocks_are_caught(monkeypatch):
         return O.Params(p.W0, p.b0, p.w1, p.b1, p.cR.transpose(1, 0, 2, 3).copy(), p.cA)
     monkeypatch.setattr(O, "unpack", wrong)
     _fails(P.test_unpack_follows_the_header_block_order)
+
+
+MD = _load("test_oracle_md")
+
+
+def test_wrong_unit_factor_is_caught(monkeypatch):
+    """a = F m 103.6427 / 1e4 instead of F / (m 103.6427)."""
+    monkeypatch.setattr(O, "MVV_EV", 1e4 / 103.6427)
+    _fails(MD.test_unit_factor_against_codata)
+    _fails(MD.test_one_dimer_step_by_hand)
+
+
+def test_wrong_mass_index_is_caught(monkeypatch):
+    """Each species integrated with the next species' mass."""
+    real = O.velocity_verlet
+
+    def wrong(h, theta, pos, vel, types, box, atom_off, masses, *a, **k):
+        return real(h, theta, pos, vel, types, box, atom_off, np.roll(np.asarray(masses), 1), *a, **k)
+    monkeypatch.setattr(O, "velocity_verlet", wrong)
+    _fails(MD.test_one_dimer_step_by_hand)
+
+
+def test_full_kick_before_drift_is_caught(monkeypatch):
+    """Symplectic Euler (a full kick, then the drift) in place of velocity
+    Verlet's two half kicks."""
+    def wrong(h, theta, pos, vel, types, box, atom_off, masses, dt, n_steps, rebuild_every=10, force=None):
+        pos, vel = np.array(pos, np.float64), np.array(vel, np.float64)
+        inv_m = 1.0 / (np.asarray(masses, np.float64)[types] * O.MVV_EV)
+
+        def forces(x):
+            pr = O.neighbor_pairs(x.astype(np.float32), box, atom_off, h.rc_rad)
+            out = O.energy_forces_virial(h, theta, x, types, box, atom_off, pr)
+            return out["F"], out["Etot"]
+        F = np.array(force, np.float64) if force is not None else forces(pos)[0]
+        epot, ekin = [], []
+        for k in range(n_steps):
+            vel = vel + dt * F * inv_m[:, None]
+            pos = pos + dt * vel
+            if k % rebuild_every == 0:
+                pos = O.wrap_positions(pos, box, atom_off)
+            F, E = forces(pos)
+            epot.append(E)
+            ekin.append(O.kinetic_energy(vel, types, masses, atom_off))
+        return dict(pos=pos, vel=vel, F=F, epot=np.array(epot), ekin=np.array(ekin))
+    monkeypatch.setattr(O, "velocity_verlet", wrong)
+    _fails(MD.test_one_dimer_step_by_hand)
+    _fails(MD.test_time_reversal)
