@@ -95,7 +95,9 @@ def parts(stub):
                            np.array([0, 4, N]), device="cpu")
     nl = SimpleNamespace(n_atoms=N, c=nb.NList(64, 32, 0, 0, 0, 0, 0, 0, 0.0, 0))
     ws = nb.Workspace(model, N, B, 64, 32, device="cpu")
-    return SimpleNamespace(h=h, model=model, dsys=dsys, nl=nl, ws=ws, N=N, B=B, P=model.n_params)
+    yield SimpleNamespace(h=h, model=model, dsys=dsys, nl=nl, ws=ws, N=N, B=B, P=model.n_params)
+    # the handle is the stub's: never let the real library destroy it
+    model.handle = None
 
 
 def test_create_passes_hparams_and_parameter_count(stub, parts):
