@@ -180,17 +180,29 @@ class SlabDomain:
             self.n_local, self.g.box_host.ctypes.data_as(ctypes.c_void_p), ctypes.c_float(self.origin),
             nb._ptr(self.loc.pos), nb._ptr(self.loc.type), nb._stream(stream)), "nep_domain_gather")
 
-    def evaluate(self, force_global, stream=None):
+    def evaluate(self, force_global, stream=None, e_atom_global=None):
         """Forces of the owned atoms into force_global [3][N] (other entries
-        untouched), and the owned energy [1] and virial [1, 9] sums."""
+        untouched), and the owned energy [1] and virial [1, 9] sums.  With
+        e_atom_global [N], the owned atoms' energies E_i go there too."""
+        import torch
         self.gather(stream)
+        e_loc = None
+        if e_atom_global is not None:
+            nb._dev(e_atom_global, torch.float32, self.g.n_atoms, "e_atom_global", "SlabDomain.evaluate")
+            if getattr(self, "e_atom", None) is None or self.e_atom.numel() < self.local_cap:
+                self.e_atom = torch.zeros(self.local_cap, dtype=torch.float32, device=self.g.pos.device)
+            e_loc = self.e_atom
         nb.check(nb.lib().nep_energy_forces_virial_owned(
-            self.model.handle, ctypes.byref(self.loc.c), ctypes.byref(self.nl.c), self.n_owned, None,
+            self.model.handle, ctypes.byref(self.loc.c), ctypes.byref(self.nl.c), self.n_owned, nb._ptr(e_loc),
             nb._ptr(self.force), nb._ptr(self.e_tot), nb._ptr(self.vir), self.ws.ptr, self.ws.bytes,
             nb._stream(stream)), "nep_energy_forces_virial_owned")
         nb.check(nb.lib().nep_domain_scatter(
             nb._ptr(self.force), self.n_local, 3, nb._ptr(self.idx), self.n_owned, nb._ptr(force_global),
             self.g.n_atoms, nb._stream(stream)), "nep_domain_scatter")
+        if e_loc is not None:
+            nb.check(nb.lib().nep_domain_scatter(
+                nb._ptr(e_loc), self.n_local, 1, nb._ptr(self.idx), self.n_owned, nb._ptr(e_atom_global),
+                self.g.n_atoms, nb._stream(stream)), "nep_domain_scatter")
         return self.e_tot, self.vir
 
 
