@@ -65,6 +65,7 @@ size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 struct WsLayout {
     size_t pos4, cfg, e_atom, fb, S, Pr, comp, cnt_comp, fin, fpart, wat, chunk_start, partial;
     size_t rin, rin_sh, cnt_rin;
+    size_t amask;
     size_t plan, cell_of, rank, cell_cnt, cell_start, cell_atoms, scan_tmp, shell, row_start, slot_row;
     size_t total;
     int max_chunks, cmax;
@@ -93,6 +94,7 @@ WsLayout ws_layout(const nep_model* m, int N, int B, int cap, int cap_ang) {
     w.rin = take(4 * n * cap);
     w.rin_sh = take(4 * n * cap);
     w.cnt_rin = take(4 * n);
+    w.amask = take(8 * n);
     w.fpart = take(12 * n);
     w.wat = take(36 * n);
     w.chunk_start = take(4 * ((size_t)B + 1));
@@ -246,6 +248,7 @@ nep::EvalArgs make_args(const nep_model* m, const nep_system* s, const nep_nlist
     a.cnt_comp = at<int>(work, w.cnt_comp);
     a.compr = nullptr;
     a.cnt_compr = nullptr;
+    a.amask = at<unsigned long long>(work, w.amask);
     a.fin = at<float4>(work, w.fin);
     // the compact list of post-prefix entries inside rc_rad pays off only
     // when the list carries a shell beyond rc_rad (a skin)

@@ -190,6 +190,7 @@ NEP_HD void radial_atom(const EvalArgs& a, int i) {
         for (int k = 0; k < KR; ++k) fb[t][k] = 0.0f;
     const int cnt = a.cnt[i], cnt_ang = a.cnt_ang[i];
     int nc = 0, ncr = 0, nr = 0;
+    unsigned long long amask = 0ull;
     NbrStream<MINIMG, NEP_RADIAL_DEPTH> ns(a, a.nbr, a.shift, i, cnt);
     for (int s = 0; s < cnt; ++s) {
         const int j = ns.j[0];
@@ -225,15 +226,18 @@ NEP_HD void radial_atom(const EvalArgs& a, int i) {
                 a.comp[nc * N + i] =
                     make_float4(dx, dy, dz, i2f((int)(((unsigned)addr << 2) | (unsigned)tj)));
                 ++nc;
-            } else if (a.compr) {
-                // the compacted-record force pass reads every angular slot;
-                // the list walk of k_finish reads only the slots inside rc_A
+                if (s < 64) amask |= 1ull << s;
+            } else if (a.compr && (!a.amask || s >= 64)) {
+                // the compacted-record force pass reads every angular slot
+                // not covered by the mask; the list walk of k_finish reads
+                // only the slots inside rc_A
                 a.fin[addr] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             }
         }
     }
     a.cnt_comp[i] = nc;
     if (a.compr) a.cnt_compr[i] = ncr;
+    if (a.compr && a.amask) a.amask[i] = amask;
     if (a.rin) a.cnt_rin[i] = nr;
 #pragma unroll
     for (int t = 0; t < T; ++t)
@@ -731,9 +735,32 @@ NEP_HD void radial_force_atom(const EvalArgs& a, int i, float& Fx, float& Fy, fl
             const int bits = f2i(e.w);
             pair((int)((unsigned)bits >> 2), bits & 3, e.x, e.y, e.z, dist2(e.x, e.y, e.z));
         }
-        // incoming angular pair forces: every slot of the angular prefix
+        // incoming angular pair forces: the prefix slots inside rc_A (the
+        // mask, in batches of four independent loads, ascending) and every
+        // slot from 64 on; without a mask every slot of the prefix
         const int na = a.cnt_ang[i];
-        for (int s = 0; s < na; ++s) {
+        int s0 = 0;
+        if (a.amask) {
+            s0 = na < 64 ? na : 64;
+            unsigned long long m = a.amask[i];
+            while (m) {
+                int sl[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    sl[u] = m ? low_bit(m) : -1;
+                    m &= m - 1ull;
+                }
+                float4 g[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    g[u] = sl[u] >= 0 ? a.fin[(size_t)sl[u] * N + i] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (sl[u] >= 0) { Fx -= g[u].x; Fy -= g[u].y; Fz -= g[u].z; }
+                }
+            }
+        }
+        for (int s = s0; s < na; ++s) {
             const float4 g = a.fin[(size_t)s * N + i];
             Fx -= g.x; Fy -= g.y; Fz -= g.z;
         }

@@ -57,6 +57,7 @@ struct EvalArgs {
     int* cnt_comp;                 // [N]
     float4* compr;                 // [cap][N]        compacted radial pairs (r_ij, j|tj), training only
     int* cnt_compr;                // [N]
+    unsigned long long* amask;     // [N] angular-prefix slots below 64 that lie inside rc_ang (with compr)
     int* rin;                      // [cap][N]        list entries after the angular prefix that lie
     int* rin_sh;                   // [cap][N]        inside rc_rad (j; image shift or null), in
     int* cnt_rin;                  // [N]             list order, written by the radial kernel

@@ -178,6 +178,11 @@ __global__ void __launch_bounds__(kRedThreads) k_final_reduce(int B, const int* 
 // image shift floor((c + d) / nc): every (j, image) within the cutoff is
 // visited exactly once.
 constexpr float kCellMargin = 1e-3f;
+// margin (A) on the list cutoff when cells beyond it are skipped
+#ifndef NEP_PRUNE_MARGIN
+#define NEP_PRUNE_MARGIN 0.01f
+#endif
+constexpr float kPruneMargin = NEP_PRUNE_MARGIN;
 constexpr int kCellDiv = 2;
 // per-atom row starts of the angular prefix, for the reverse-slot search:
 // stencils of up to kMaxRows (x, y) rows, angular capacity below 256
@@ -391,18 +396,38 @@ __global__ void __launch_bounds__(128) k_build(const float4* __restrict__ pos4,
     const int rows = (2 * p.half[0] + 1) * (2 * p.half[1] + 1);
     const bool track = rows <= kMaxRows && cap_ang < 256;
     unsigned char* rs = row_start + (size_t)i * kRowStride;
+    // Cells that cannot hold a candidate are skipped: for each stencil row
+    // the z range shrinks to the cells that meet the sphere of the list
+    // cutoff (plus a margin far above the rounding of the binning) around
+    // atom i, given the row's distance from i in x and y.  Skipping only
+    // cells whose every point is beyond the cutoff leaves the list, its
+    // order and the row starts unchanged.
+    const float cs[3] = {L[0] / (float)p.nc[0], L[1] / (float)p.nc[1], L[2] / (float)p.nc[2]};
+    const float rl = sqrtf(rc2_rad) + kPruneMargin;
+    const float rl2 = rl * rl;
     int row = 0;
     for (int ox = -p.half[0]; ox <= p.half[0]; ++ox) {
         const int ux = cx + ox, sx = floor_div(ux, p.nc[0]), wx = ux - sx * p.nc[0];
+        const float gx = fmaxf(fmaxf((float)ux * cs[0] - pi.x, pi.x - (float)(ux + 1) * cs[0]), 0.0f);
         for (int oy = -p.half[1]; oy <= p.half[1]; ++oy, ++row) {
             const int uy = cy + oy, sy = floor_div(uy, p.nc[1]), wy = uy - sy * p.nc[1];
             if (track) rs[row] = (unsigned char)(n_ang < 255 ? n_ang : 255);
             const float fx = mul_rn((float)sx, L[0]);
             const float fy = mul_rn((float)sy, L[1]);
             const int rowcell = p.base + (wx * p.nc[1] + wy) * p.nc[2];
-            // z range [cz - half, cz + half], in pieces of one z image each
+            const float gy = fmaxf(fmaxf((float)uy * cs[1] - pi.y, pi.y - (float)(uy + 1) * cs[1]), 0.0f);
+            const float rem = rl2 - gx * gx - gy * gy;
+            // z range [cz - half, cz + half] cut to the cells that meet the
+            // sphere, in pieces of one z image each
             int lo = cz - p.half[2];
-            const int hi = cz + p.half[2];
+            int hi = cz + p.half[2];
+            if (rem <= 0.0f) {
+                hi = lo - 1;
+            } else {
+                const float hz = sqrtf(rem);
+                lo = max(lo, (int)floorf((pi.z - hz) / cs[2]));
+                hi = min(hi, (int)floorf((pi.z + hz) / cs[2]));
+            }
             while (lo <= hi) {
                 const int sz = floor_div(lo, p.nc[2]);
                 const int seg_hi = min(hi, (sz + 1) * p.nc[2] - 1);
