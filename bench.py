@@ -34,6 +34,10 @@ WORKLOAD = ("md900k: 900,000-atom rock-salt Ge-Sb-Te (50^3 cells, a=6 A, 20% cat
             "NEP n_R=8 n_A=6 K=8/8 l_max=4 +4-body (D=38), MLP 38-30-1 tanh, FP32, velocity Verlet "
             "dt=2 fs, 900 K, cell-list rebuild every 10 steps, skin 1 A")
 CAP, CAP_ANG, SKIN, DT, REBUILD = 160, 80, 1.0, 2.0, 10
+# neighbours per atom inside rc_rad and rc_ang of the rock-salt workload at
+# the start of a run (measured from its list; the single-GPU line measures
+# them live)
+NBAR_LATTICE = (49.12, 17.60)
 
 
 def parse():
@@ -57,6 +61,9 @@ def parse():
                     help="run the training leg alone and print its JSON object (for profiling it)")
     ap.add_argument("--ncell", type=int, default=50,
                     help="rock-salt cells per edge (50 = the 900k-atom workload; smaller for profiling)")
+    ap.add_argument("--md-mode", default="replicas", choices=["replicas", "slabs"],
+                    help="N > 1: independent replicas of the system per GPU (weak scaling, the default), or one "
+                         "system split into slabs with a point-to-point ghost halo (strong scaling)")
     return ap.parse_args()
 
 
@@ -863,6 +870,81 @@ def table2_leg(nb, torch, I) -> dict:
 
 
 # ------------------------------------------------------------------ our arm
+def slabs_main(args, nb, torch, dist, world: int, rank: int, local: int, I) -> None:
+    """One system over `world` GPUs: slabs along x with the point-to-point
+    ghost halo of halo.py (strong scaling).  Every rank times K eager steps
+    between barriers; the line reports the whole system's atom-steps per
+    second over the slowest rank, and rank 0's evaluation kernels."""
+    from paper_2607_06969_gb300 import halo as HL
+    if args.ncell == 50:
+        s, h = I.workload_md900k()
+    else:
+        s, h = I.rocksalt(args.ncell, vacancy=0.2, tag=1), I.HYPER_SMALL
+    N = s.n_atoms
+    model = nb.Model(h, I.init_params(h).astype(np.float32))
+    vel0 = I.maxwell_boltzmann(s.types, 900.0).astype(np.float32)
+    L = s.box[0]
+    slabs, halo = HL.plan(float(L[0]), world, h.rc_rad, SKIN)
+    lo, hi = slabs[rank]
+    k = HL.SlabRank(HL.LibOps(model), rank, world, L, lo, hi, halo, SKIN, I.MASSES, dt=DT, rebuild_every=REBUILD,
+                    cap=CAP, cap_ang=CAP_ANG, rc=h.rc_rad)
+    k.load(s.pos32(), s.types, vel0)
+    HL.run_dist(k.start(), dist, rank, world)
+    for _ in range(args.warmup):
+        HL.run_dist(k.step(), dist, rank, world)
+    k.check()
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    for trio in evs:
+        for e in trio:
+            e.record()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    start.record()
+    for j in range(K):
+        nb.set_timing_events(model, evs[j])
+        HL.run_dist(k.step(), dist, rank, world)
+    stop.record()
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = clocks.stop()
+    nb.set_timing_events(model, None)
+    k.check()
+    t = torch.tensor([start.elapsed_time(stop)], device="cuda", dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    e, v = HL.totals(k, dist)
+    t_kern = {"radial": statistics.mean(x[0].elapsed_time(x[1]) for x in evs),
+              "angular": statistics.mean(x[1].elapsed_time(x[2]) for x in evs),
+              "finish": statistics.mean(x[2].elapsed_time(x[3]) for x in evs)}
+    # the local system's kernels process its owned atoms and its ghosts;
+    # neighbour counts of the whole lattice (its atoms all see full shells)
+    nbar_rad, nbar_ang = NBAR_LATTICE
+    fl = algorithmic_flops(h, nbar_rad, nbar_ang)
+    props = torch.cuda.get_device_properties(local)
+    peak = props.multi_processor_count * 128 * 2 * 2070e6 / 1e12
+    dom = max(t_kern, key=t_kern.get)
+    achieved = fl[dom] * k.n_local / (t_kern[dom] * 1e-3) / 1e12
+    if rank == 0:
+        line = {"metric": METRIC, "value": N * K / (ms_max * 1e-3), "unit": "atom-steps/s", "n_gpus": world,
+                "steps": K, "warmup": args.warmup, "ms_per_step": ms_max / K, "higher_is_better": True,
+                "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n_atoms": N, "parallelism": f"slabs x{world}",
+                           "halo_A": halo, "l2": "inputs larger than L2", "graph": "eager steps"},
+                "roofline": {"bound": "alu", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak,
+                             "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                             "atoms_per_launch": k.n_local, "kernel_ms": t_kern,
+                             "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x 2070 MHz"},
+                "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clk,
+                "energy": {"e_tot_final": float(e.item())},
+                "halo": {"rank0_owned": k.n_own, "rank0_ghosts": k.n_gl + k.n_gr,
+                         "bytes_per_step_each_way": 12 * (k.n_gl + k.n_gr)}}
+        print(json.dumps(line), flush=True)
+
+
 def guarded(leg, *args, **kwargs) -> dict:
     """Run one secondary bench leg; an exception becomes {"error": ...} in
     its place, so that it cannot take the measured headline with it."""
@@ -895,6 +977,11 @@ def main():
             print(json.dumps({"train": train}), flush=True)
         if world > 1:
             dist.destroy_process_group()
+        return
+
+    if args.md_mode == "slabs" and world > 1:
+        slabs_main(args, nb, torch, dist, world, rank, local, I)
+        dist.destroy_process_group()
         return
 
     if args.ncell == 50:

@@ -273,6 +273,31 @@ nep_status nep_domain_gather(const float* pos, const int* type, int n_atoms, con
 nep_status nep_domain_scatter(const float* src, int n_local, int ncomp, const int* idx, int n_owned, float* dst,
                               int n_atoms, void* stream);
 
+/* Point-to-point halo of a slab decomposition (Section 3.5's one domain per
+ * device, with ghosts moved between neighbouring ranks only).  Each rank keeps
+ * just its own atoms; every step it sends the positions of its atoms within
+ * the halo of each slab face to the neighbouring rank across that face and
+ * receives that rank's ghosts; at a rebuild, atoms that left the slab move to
+ * the neighbour with their velocities.
+ * nep_domain_band: idx [cap] device output: the atoms with x in [x_lo, x_hi)
+ *   (either bound may be infinite), in atom order; counts [2] device: the
+ *   count, twice (entries beyond cap are not written).  pos [3][N] device;
+ *   work: nep_domain_workspace_bytes(N).  NEP_ERR_ARG unless x_lo < x_hi.
+ * nep_domain_take: dst [ncomp][n] = src [ncomp][n_src] at columns idx[0..n),
+ *   32-bit words copied bit for bit (positions, velocities, species, ids).
+ * nep_domain_place: dst[c * dst_stride + dst_offset + l] = src[c * n + l]
+ *   (src [ncomp][n], 32-bit words).  When box_x > 0, component 0 is an x
+ *   coordinate: it is moved by the multiple of box_x that brings it nearest
+ *   x_center (x - box_x rint((x - x_center)/box_x)) and taken relative to
+ *   x_origin; every other word, and every word when box_x <= 0, is copied bit
+ *   for bit.  NEP_ERR_ARG unless 0 <= dst_offset and dst_offset + n <=
+ *   dst_stride, or if box_x, x_center or x_origin is not finite. */
+nep_status nep_domain_band(const float* pos, int n_atoms, float x_lo, float x_hi, int* idx, int cap, int* counts,
+                           void* work, size_t work_bytes, void* stream);
+nep_status nep_domain_take(const void* src, int n_src, int ncomp, const int* idx, int n, void* dst, void* stream);
+nep_status nep_domain_place(const void* src, int n, int ncomp, float box_x, float x_center, float x_origin,
+                            void* dst, int dst_stride, int dst_offset, void* stream);
+
 /* nep_energy_forces_virial without a caller workspace.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate
  * device memory at all -- for example a force plugin inside a host MD code

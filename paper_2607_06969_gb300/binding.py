@@ -24,7 +24,7 @@ ENTRY_POINTS = (
     "nep_energy_forces_virial_noalloc", "nep_workspace_bytes_fp64", "nep_energy_forces_virial_fp64",
     "nep_train_workspace_bytes_fp64", "nep_param_grad_fp64", "nep_param_grad_adjoint_fp64",
     "nep_energy_forces_virial_owned", "nep_domain_workspace_bytes", "nep_domain_select", "nep_domain_gather",
-    "nep_domain_scatter", "nep_md_kick", "nep_md_wrap",
+    "nep_domain_scatter", "nep_domain_band", "nep_domain_take", "nep_domain_place", "nep_md_kick", "nep_md_wrap",
     "nep_param_grad",
     "nep_param_grad_adjoint", "nep_adam_step", "nep_md_step", "nep_autotune", "nep_set_variant",
     "nep_set_timing_events", "nep_fp32_peak", "nep_selftest_wait_timeout",
@@ -96,6 +96,9 @@ def lib() -> ctypes.CDLL:
     L.nep_domain_select.argtypes = [vp, i, vp, f, f, f, vp, vp, i, vp, vp, sz, vp]
     L.nep_domain_gather.argtypes = [vp, vp, i, vp, vp, i, vp, f, vp, vp, vp]
     L.nep_domain_scatter.argtypes = [vp, i, i, vp, i, vp, i, vp]
+    L.nep_domain_band.argtypes = [vp, i, f, f, vp, i, vp, vp, sz, vp]
+    L.nep_domain_take.argtypes = [vp, i, i, vp, i, vp, vp]
+    L.nep_domain_place.argtypes = [vp, i, i, f, f, f, vp, i, i, vp]
     L.nep_train_workspace_bytes_fp64.argtypes = [vp, i, i]
     L.nep_train_workspace_bytes_fp64.restype = sz
     L.nep_param_grad_fp64.argtypes = [vp, P(System), P(NList), vp, vp, vp, vp, vp, i, vp, vp, vp, sz, vp]
@@ -120,7 +123,8 @@ def lib() -> ctypes.CDLL:
                  "nep_energy_forces_virial", "nep_energy_forces_virial_noalloc",
                  "nep_energy_forces_virial_fp64", "nep_param_grad_fp64", "nep_param_grad_adjoint_fp64",
                  "nep_energy_forces_virial_owned", "nep_domain_select", "nep_domain_gather",
-                 "nep_domain_scatter", "nep_md_kick", "nep_md_wrap",
+                 "nep_domain_scatter", "nep_domain_band", "nep_domain_take", "nep_domain_place",
+                 "nep_md_kick", "nep_md_wrap",
                  "nep_param_grad", "nep_param_grad_adjoint",
                  "nep_md_step", "nep_check", "nep_set_timing_events"):
         getattr(L, name).restype = i

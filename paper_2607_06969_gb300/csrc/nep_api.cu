@@ -825,6 +825,41 @@ nep_status nep_domain_gather(const float* pos, const int* type, int n_atoms, con
     return NEP_OK;
 }
 
+nep_status nep_domain_band(const float* pos, int n_atoms, float x_lo, float x_hi, int* idx, int cap, int* counts,
+                           void* work, size_t work_bytes, void* stream) {
+    if (n_atoms < 0 || cap < 0) return fail(NEP_ERR_ARG, "n_atoms and cap must be >= 0");
+    if (!counts || (n_atoms > 0 && !pos) || (cap > 0 && !idx)) return fail(NEP_ERR_ARG, "a pointer argument is NULL");
+    if (!(x_lo < x_hi) || std::isnan(x_lo) || std::isnan(x_hi)) return fail(NEP_ERR_ARG, "need x_lo < x_hi");
+    if (work_bytes < nep::domain_scratch_bytes(n_atoms) || !work)
+        return fail(NEP_ERR_ARG, "workspace too small: %zu bytes given, %zu needed", work_bytes,
+                    nep::domain_scratch_bytes(n_atoms));
+    // the slab selection with no halo: every atom in [x_lo, x_hi) is "owned", none is a ghost
+    NEP_CUDA(nep::launch_domain_select(pos, n_atoms, 1.0f, x_lo, x_hi, 0.0f, idx, nullptr, cap, counts, work,
+                                       (cudaStream_t)stream),
+             "domain band");
+    return NEP_OK;
+}
+
+nep_status nep_domain_take(const void* src, int n_src, int ncomp, const int* idx, int n, void* dst, void* stream) {
+    if (n_src < 0 || n < 0 || ncomp < 1) return fail(NEP_ERR_ARG, "need n_src, n >= 0 and ncomp >= 1");
+    if (n > 0 && (!src || !idx || !dst)) return fail(NEP_ERR_ARG, "a pointer argument is NULL");
+    NEP_CUDA(nep::launch_domain_take(src, n_src, ncomp, idx, n, dst, (cudaStream_t)stream), "domain take");
+    return NEP_OK;
+}
+
+nep_status nep_domain_place(const void* src, int n, int ncomp, float box_x, float x_center, float x_origin,
+                            void* dst, int dst_stride, int dst_offset, void* stream) {
+    if (n < 0 || ncomp < 1 || dst_offset < 0 || (long long)dst_offset + n > dst_stride)
+        return fail(NEP_ERR_ARG, "need n >= 0, ncomp >= 1 and 0 <= dst_offset, dst_offset + n <= dst_stride");
+    if (!std::isfinite(box_x) || !std::isfinite(x_center) || !std::isfinite(x_origin))
+        return fail(NEP_ERR_ARG, "box_x, x_center and x_origin must be finite");
+    if (n > 0 && (!src || !dst)) return fail(NEP_ERR_ARG, "a pointer argument is NULL");
+    NEP_CUDA(nep::launch_domain_place(src, n, ncomp, box_x, x_center, x_origin, dst, dst_stride, dst_offset,
+                                      (cudaStream_t)stream),
+             "domain place");
+    return NEP_OK;
+}
+
 nep_status nep_domain_scatter(const float* src, int n_local, int ncomp, const int* idx, int n_owned, float* dst,
                               int n_atoms, void* stream) {
     if (n_local < 0 || n_owned < 0 || n_owned > n_local || ncomp < 1 || n_atoms < 0)

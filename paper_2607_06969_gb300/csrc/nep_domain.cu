@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(kDomBlock) k_dom_write(const float* __restrict
     const int at = c == 0 ? boff[2 * blockIdx.x] + r : counts[0] + boff[2 * blockIdx.x + 1] + r;
     if (at < cap) {
         idx[at] = i;
-        img_out[at] = img;
+        if (img_out) img_out[at] = img;
     }
 }
 
@@ -142,6 +142,33 @@ __global__ void k_dom_scatter(const float* __restrict__ src, int n_local, int nc
     if (l >= n_owned) return;
     const int i = idx[l];
     for (int c = 0; c < ncomp; ++c) dst[(size_t)c * N + i] = src[(size_t)c * n_local + l];
+}
+
+// dst[c][l] = src[c][idx[l]], 32-bit words
+__global__ void k_dom_take(const unsigned* __restrict__ src, int n_src, int ncomp, const int* __restrict__ idx,
+                           int n, unsigned* __restrict__ dst) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n) return;
+    const int i = idx[l];
+    for (int c = 0; c < ncomp; ++c) dst[(size_t)c * n + l] = src[(size_t)c * n_src + i];
+}
+
+// dst[c * stride + offset + l] = src[c][l]; component 0 (x) shifted by the
+// whole box lengths that bring it nearest x_center, then taken relative to
+// x_origin, when box_x > 0; every other word copied bit for bit
+__global__ void k_dom_place(const unsigned* __restrict__ src, int n, int ncomp, float box_x, float x_center,
+                            float x_origin, unsigned* __restrict__ dst, int stride, int offset) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n) return;
+    for (int c = 0; c < ncomp; ++c) {
+        unsigned v = src[(size_t)c * n + l];
+        if (c == 0 && box_x > 0.0f) {
+            const float x = __uint_as_float(v);
+            const float k = rintf(__fdiv_rn(__fsub_rn(x, x_center), box_x));
+            v = __float_as_uint(__fsub_rn(__fsub_rn(x, __fmul_rn(k, box_x)), x_origin));
+        }
+        dst[(size_t)c * stride + offset + l] = v;
+    }
 }
 
 inline int dom_blocks(int N) { return (N + kDomBlock - 1) / kDomBlock; }
@@ -168,6 +195,22 @@ cudaError_t launch_domain_gather(const float* pos, const int* type, int N, const
     if (n_local > 0)
         k_dom_gather<<<(n_local + 255) / 256, 256, 0, st>>>(pos, type, N, idx, img, n_local, Lx, x_origin,
                                                             pos_local, type_local);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_domain_take(const void* src, int n_src, int ncomp, const int* idx, int n, void* dst,
+                               cudaStream_t st) {
+    if (n > 0)
+        k_dom_take<<<(n + 255) / 256, 256, 0, st>>>(static_cast<const unsigned*>(src), n_src, ncomp, idx, n,
+                                                    static_cast<unsigned*>(dst));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_domain_place(const void* src, int n, int ncomp, float box_x, float x_center, float x_origin,
+                                void* dst, int stride, int offset, cudaStream_t st) {
+    if (n > 0)
+        k_dom_place<<<(n + 255) / 256, 256, 0, st>>>(static_cast<const unsigned*>(src), n, ncomp, box_x, x_center,
+                                                     x_origin, static_cast<unsigned*>(dst), stride, offset);
     return cudaGetLastError();
 }
 

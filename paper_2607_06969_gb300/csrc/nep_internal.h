@@ -216,6 +216,10 @@ cudaError_t launch_domain_gather(const float* pos, const int* type, int N, const
                                  cudaStream_t st);
 cudaError_t launch_domain_scatter(const float* src, int n_local, int ncomp, const int* idx, int n_owned,
                                   float* dst, int N, cudaStream_t st);
+cudaError_t launch_domain_take(const void* src, int n_src, int ncomp, const int* idx, int n, void* dst,
+                               cudaStream_t st);
+cudaError_t launch_domain_place(const void* src, int n, int ncomp, float box_x, float x_center, float x_origin,
+                                void* dst, int stride, int offset, cudaStream_t st);
 
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int n, float beta1, float beta2,
                         float eps, float c1, float c2, cudaStream_t st);

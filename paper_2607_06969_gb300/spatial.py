@@ -1,32 +1,23 @@
-"""Spatial decomposition of one large periodic system over GPUs (one process
-per GPU): slabs along x with a two-layer ghost halo, replicated positions
-and velocities, and one all-reduce per step.
+"""Slab decomposition of one periodic configuration along x, evaluated from
+a whole-system state that the caller holds: the building blocks of the
+multi-GPU MD in halo.py (its local system and list types), and a way to
+evaluate one slab of a system that is known in full.
 
-Each rank holds the whole system's positions, velocities and forces.  At a
-list rebuild (every few steps, after the positions are wrapped) it selects
-its owned atoms (x in its slab) and the ghosts within halo = 2 (rc + skin)
-of the slab (nep_domain_select).  It gathers them into a local system whose
-x runs over [0, slab + 2 halo + pad), with pad > rc + skin so that the local
-periodic image in x never comes within the list cutoff, and builds the local
-list there.  Every step it then:
-  * gathers the current positions of its local atoms (nep_domain_gather);
-  * evaluates them, summing energy and virial over the owned atoms only
-    (nep_energy_forces_virial_owned);
-  * scatters the owned rows of the forces into a zeroed whole-system array
-    (nep_domain_scatter).
-One all-reduce (sum) over the ranks combines the forces, the energy and the
-virial.  Every rank then integrates all atoms identically (nep_md_kick),
-which keeps the positions replicated without a position exchange.
+A slab's local system holds its owned atoms (x in the slab) and the ghost
+atoms within halo = 2 (rc + skin) of the slab (nep_domain_select), gathered
+into a frame whose x runs over [0, slab + 2 halo + pad), with pad > rc + skin
+so that the local periodic image in x never comes within the list cutoff
+(nep_domain_gather).  The owned atoms are evaluated with the energy and
+virial summed over them only (nep_energy_forces_virial_owned) and their
+force rows scattered back (nep_domain_scatter).
 
 With halo = 2 (rc + skin), each owned atom's neighbours (the first ghost
-layer) see their whole neighbourhood (the second layer).  So the owned atoms'
+layer) see their whole neighbourhood (the second layer), so the owned atoms'
 forces, energies and per-atom virials are those of the whole-system
-evaluation, up to the order of FP32 sums.  Ownership and the ghost set are
-fixed between rebuilds, as the Verlet list is.
-
-The exchange is an all-reduce of 3N floats and 10 doubles per step, which
-suits a few GPUs of one NVLink domain.  The slab plus two halos must fit in
-the box: slab + 2 halo <= L_x.
+evaluation, up to the order of FP32 sums.  The slab plus two halos must fit
+in the box: slab + 2 halo <= L_x.  MD over several GPUs keeps no
+whole-system state: halo.py moves only ghost positions between neighbouring
+ranks.
 """
 from __future__ import annotations
 
@@ -204,68 +195,3 @@ class SlabDomain:
                 nb._ptr(e_loc), self.n_local, 1, nb._ptr(self.idx), self.n_owned, nb._ptr(e_atom_global),
                 self.g.n_atoms, nb._stream(stream)), "nep_domain_scatter")
         return self.e_tot, self.vir
-
-
-def combine_owned(dist, force_global, e_tot, virial) -> None:
-    """In place over the process group: every rank's owned rows of the
-    forces (zeros elsewhere) and its owned energy and virial sums become the
-    whole system's (one all-reduce each)."""
-    dist.all_reduce(force_global)
-    dist.all_reduce(e_tot)
-    dist.all_reduce(virial)
-
-
-class SpatialMD:
-    """Velocity Verlet for one rank of a slab decomposition (dt in fs,
-    masses in u, rebuild every `rebuild_every` steps), with the whole
-    system's state replicated on every rank.  `reduce(force, e, v)` combines
-    the ranks' owned results in place (combine_owned with a process group,
-    or a sum over emulated ranks)."""
-
-    def __init__(self, model: nb.Model, gsys: nb.DeviceSystem, vel, masses, domains, reduce, dt: float = 2.0,
-                 skin: float = 1.0, rebuild_every: int = 10):
-        import torch
-        self.model, self.g, self.vel = model, gsys, vel
-        nb._dev(vel, torch.float32, 3 * gsys.n_atoms, "vel", "SpatialMD")
-        self.masses = np.ascontiguousarray(np.asarray(masses, np.float32))
-        if self.masses.size < model.hp.n_types:
-            raise ValueError(f"SpatialMD: {self.masses.size} masses for {model.hp.n_types} species")
-        self.domains, self.reduce = list(domains), reduce
-        self.dt, self.skin, self.every = dt, skin, rebuild_every
-        dev = gsys.pos.device
-        self.force = torch.zeros(3, gsys.n_atoms, dtype=torch.float32, device=dev)
-        self.e_tot = torch.zeros(1, dtype=torch.float64, device=dev)
-        self.vir = torch.zeros(1, 9, dtype=torch.float64, device=dev)
-        self.k = 0
-
-    def _forces(self) -> None:
-        self.force.zero_()
-        self.e_tot.zero_()
-        self.vir.zero_()
-        for d in self.domains:
-            e, v = d.evaluate(self.force)
-            self.e_tot += e
-            self.vir += v
-        self.reduce(self.force, self.e_tot, self.vir)
-
-    def start(self) -> None:
-        """Wrap, select, build the lists and evaluate the initial forces."""
-        nb.check(nb.lib().nep_md_wrap(self.model.handle, ctypes.byref(self.g.c), nb._stream()), "nep_md_wrap")
-        for d in self.domains:
-            d.rebuild()
-        self._forces()
-
-    def step(self) -> None:
-        lib, mp = nb.lib(), self.masses.ctypes.data_as(ctypes.c_void_p)
-        nb.check(lib.nep_md_kick(self.model.handle, ctypes.byref(self.g.c), nb._ptr(self.vel), nb._ptr(self.force),
-                                 mp, ctypes.c_float(0.5 * self.dt), ctypes.c_float(self.dt), nb._stream()),
-                 "nep_md_kick")
-        self.k += 1
-        if self.k % self.every == 0:
-            nb.check(lib.nep_md_wrap(self.model.handle, ctypes.byref(self.g.c), nb._stream()), "nep_md_wrap")
-            for d in self.domains:
-                d.rebuild()
-        self._forces()
-        nb.check(lib.nep_md_kick(self.model.handle, ctypes.byref(self.g.c), nb._ptr(self.vel), nb._ptr(self.force),
-                                 mp, ctypes.c_float(0.5 * self.dt), ctypes.c_float(0.0), nb._stream()),
-                 "nep_md_kick")

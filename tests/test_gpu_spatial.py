@@ -1,8 +1,7 @@
 """Spatial decomposition (slabs along x with a two-layer halo) against the
 whole-system evaluation, with the ranks emulated one after another on one
 GPU: the owned atoms' forces, the energy and the virial; the selection
-against a host recomputation; and a short decomposed MD run against
-nep_md_step.
+against a host recomputation; and three slabs against the FP64 oracle.
 
 The owned atoms see the same neighbours as in the whole system, in another
 list order.  FP32 sums in another order differ by a few ulp of the terms, so
@@ -94,39 +93,6 @@ def test_domain_select_against_host(nb):
         assert n_owned == own.size and n_local == own.size + len(gh)
         assert np.array_equal(d.idx[:n_local].cpu().numpy(), np.concatenate([own, gh]).astype(np.int32))
         assert np.array_equal(d.img[:n_local].cpu().numpy(), np.concatenate([np.zeros(own.size), im]).astype(np.int32))
-
-
-def test_spatial_md_tracks_whole_system_md(nb):
-    """Twelve velocity-Verlet steps (a rebuild at step 10) of two emulated
-    ranks against nep_md_step on the whole system."""
-    import torch
-    from paper_2607_06969_gb300 import spatial as SP
-    h = I.HYPER_SMALL
-    s = I.rocksalt(14, vacancy=0.2, tag=6)
-    model = nb.Model(h, I.init_params(h).astype(np.float32))
-    masses = I.MASSES.astype(np.float32)
-    v0 = np.ascontiguousarray(I.maxwell_boltzmann(s.types, 900.0).astype(np.float32).T)
-    # whole system
-    dsys, nl, ws, (_, force, et, vir) = whole(nb, model, s)
-    vel = torch.from_numpy(v0.copy()).cuda()
-    for k in range(1, 13):
-        nb.md_step(model, dsys, nl, vel, force, et, vir, masses, 2.0, SKIN, k % 10 == 0, ws)
-    # two slabs, state replicated in one set of arrays
-    gsys = nb.DeviceSystem.from_inputs(s)
-    vel2 = torch.from_numpy(v0.copy()).cuda()
-    slabs, halo = SP.plan_slabs(float(s.box[0, 0]), 2, h.rc_rad, SKIN)
-    doms = [SP.SlabDomain(model, gsys, lo, hi, halo, SKIN, 112, 56) for lo, hi in slabs]
-    md = SP.SpatialMD(model, gsys, vel2, masses, doms, reduce=lambda f, e, v: None, dt=2.0, skin=SKIN,
-                      rebuild_every=10)
-    md.start()
-    for _ in range(12):
-        md.step()
-    torch.cuda.synchronize()
-    for d in doms:
-        assert nb.check_list(d.nl) == nb.NEP_OK
-    assert (gsys.pos - dsys.pos).abs().max().item() <= 1e-4
-    assert (vel2 - vel).abs().max().item() <= 1e-5
-    assert abs(md.e_tot.item() - et.item()) <= 1e-5 * s.n_atoms
 
 
 def test_slab_evaluation_matches_oracle(nb):

@@ -1,10 +1,8 @@
-"""Host logic of the spatial decomposition: slab planning, the all-reduce
-that combines the ranks' owned rows (gloo, world size 2, CPU), and, with the
-FP64 oracle, the reason for the two-layer halo: a slab's local system of
+"""Host logic of the spatial decomposition: slab planning, a slab's local
+frame, and, with the FP64 oracle, the reason for the two-layer halo: a slab's local system of
 owned atoms and ghosts within 2 rc reproduces every owned atom's energy,
 force and per-atom virial (so the owned sums add up to the whole system's
 E and V), and one layer does not."""
-import os
 
 import numpy as np
 import pytest
@@ -21,41 +19,6 @@ def test_plan_slabs_cover_and_reject_overlapping_halos():
     with pytest.raises(ValueError):
         SP.plan_slabs(60.0, 2, 7.0, 1.0)          # 30 + 2 * 16 > 60
 
-
-def _worker(rank, world, port, out):
-    import torch
-    import torch.distributed as dist
-    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
-    dist.init_process_group("gloo", rank=rank, world_size=world)
-    N = 10
-    full = torch.arange(3 * N, dtype=torch.float32).reshape(3, N) + 0.5
-    owned = [np.arange(0, 4), np.arange(4, N)][rank]
-    f = torch.zeros(3, N)
-    f[:, owned] = full[:, owned]
-    e = torch.tensor([1.5 + rank], dtype=torch.float64)
-    v = torch.full((1, 9), 0.25 * (rank + 1), dtype=torch.float64)
-    SP.combine_owned(dist, f, e, v)
-    out.put((rank, torch.equal(f, full), e.item(), v[0, 0].item()))
-    dist.destroy_process_group()
-
-
-def test_combine_owned_gloo_world2():
-    import socket
-    import torch.multiprocessing as mp
-    with socket.socket() as sk:
-        sk.bind(("127.0.0.1", 0))
-        port = sk.getsockname()[1]
-    ctx = mp.get_context("spawn")
-    q = ctx.Queue()
-    ps = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
-    for p in ps:
-        p.start()
-    res = sorted(q.get(timeout=120) for _ in ps)
-    for p in ps:
-        p.join(timeout=60)
-        assert p.exitcode == 0
-    for rank, same, e, v in res:
-        assert same and e == 4.0 and v == 0.75
 
 
 def _slab_local(pos, L, lo, hi, halo):
@@ -121,69 +84,6 @@ def test_two_layer_halo_reproduces_owned_atoms_in_the_oracle():
             assert np.allclose(v_sum, whole["V"][0], rtol=0, atol=1e-9)
         else:
             assert worst > 1e-6            # ghosts' own neighbourhoods cut short
-
-
-def test_spatial_md_step_order(monkeypatch):
-    """SpatialMD's velocity-Verlet order with the library and the slab
-    domains replaced by recorders: kick + drift, a wrap and rebuild every
-    `rebuild_every` steps, the owned forces of every domain combined by one
-    reduce, then the closing half kick."""
-    import ctypes
-    from types import SimpleNamespace
-
-    import torch
-
-    from paper_2607_06969_gb300 import binding as nb
-    log = []
-
-    class Lib:
-        def nep_md_kick(self, m, sysc, vel, force, masses, half_dt, drift_dt, stream):
-            log.append(("kick", round(half_dt.value, 6), round(drift_dt.value, 6)))
-            return 0
-
-        def nep_md_wrap(self, m, sysc, stream):
-            log.append(("wrap",))
-            return 0
-
-    class Dom:
-        def __init__(self, k):
-            self.k = k
-
-        def rebuild(self):
-            log.append(("rebuild", self.k))
-
-        def evaluate(self, force):
-            log.append(("evaluate", self.k))
-            return torch.ones(1, dtype=torch.float64), torch.ones(1, 9, dtype=torch.float64)
-
-    class Vel:
-        is_cuda, dtype, shape = True, torch.float32, (3, 4)
-
-        def numel(self):
-            return 12
-
-        def is_contiguous(self):
-            return True
-
-        def data_ptr(self):
-            return 0
-
-    monkeypatch.setattr(nb, "lib", lambda: Lib())
-    monkeypatch.setattr(nb, "_stream", lambda stream=None: ctypes.c_void_p(0))
-    model = SimpleNamespace(handle=None, hp=SimpleNamespace(n_types=3))
-    gsys = SimpleNamespace(n_atoms=4, pos=torch.zeros(3, 4), c=nb.System())
-    md = SP.SpatialMD(model, gsys, Vel(), [72.6, 121.8, 127.6], [Dom(0), Dom(1)],
-                      reduce=lambda f, e, v: log.append(("reduce", float(e.item()))), dt=2.0, rebuild_every=3)
-    md.start()
-    assert log == [("wrap",), ("rebuild", 0), ("rebuild", 1), ("evaluate", 0), ("evaluate", 1), ("reduce", 2.0)]
-    for _ in range(3):
-        log.clear()
-        md.step()
-        body = [("evaluate", 0), ("evaluate", 1), ("reduce", 2.0), ("kick", 1.0, 0.0)]
-        if md.k % 3 == 0:
-            assert log == [("kick", 1.0, 2.0), ("wrap",), ("rebuild", 0), ("rebuild", 1)] + body
-        else:
-            assert log == [("kick", 1.0, 2.0)] + body
 
 
 def test_slab_domain_frame_and_capacity():
