@@ -802,7 +802,79 @@ def replicas_leg(nb, torch, I, K: int = 20, dist=None, world: int = 1, rank: int
             "ms_per_step": ms, "steps": K,
             "per_replica_loop": {"ms_per_step": ms_loop, "replica_steps_per_s": B_all / (ms_loop * 1e-3),
                                  "steps": KL},
-            "speedup_vs_loop": ms_loop / ms, "autotuned_angular_variant": chosen[0]}
+            "speedup_vs_loop": ms_loop / ms,
+            "autotuned": {"angular_variant": chosen[0], "radial_block": chosen[1], "finish_block": chosen[2]},
+            "bins": replica_bins(nb, torch, I, s, h, th, K) if world == 1 else None}
+
+
+def subset(I, s, idx):
+    """The configurations idx of batch s, in that order."""
+    idx = list(idx)
+    pos, typ, n = [], [], [0]
+    for b in idx:
+        a0, a1 = int(s.atom_off[b]), int(s.atom_off[b + 1])
+        pos.append(s.pos[a0:a1])
+        typ.append(s.types[a0:a1])
+        n.append(a1 - a0)
+    return I.System(pos=np.concatenate(pos), types=np.concatenate(typ), box=s.box[idx],
+                    atom_off=np.cumsum(n).astype(np.int64))
+
+
+def replica_bins(nb, torch, I, s, h, th, K: int) -> list:
+    """The replica batch split by size class (log2 of the atom count): per
+    class, its replicas as one batch at the default launch choices and at
+    the autotuned ones (radial and finish block sizes, angular variant),
+    against a loop that steps each replica with its own launches."""
+    masses = I.MASSES.astype(np.float32)
+    counts = np.diff(s.atom_off)
+    cls = np.floor(np.log2(counts)).astype(int)
+    rows = []
+    for c in sorted(set(cls.tolist())):
+        idx = np.nonzero(cls == c)[0]
+        sb = subset(I, s, idx)
+        model = nb.Model(h, th, precision=1)
+        ms_default = md_graph_ms(nb, torch, I, sb, model, K, shifts=True)
+        d = nb.DeviceSystem.from_inputs(sb)
+        nl = nb.NeighborList(sb.n_atoms, 160, 80, shifts=True)
+        ws = nb.Workspace(model, sb.n_atoms, sb.n_cfg, 160, 80)
+        nb.neighbors(model, d, nl, SKIN, ws)
+        chosen = nb.autotune(model, d, nl, ws)
+        ms_tuned = md_graph_ms(nb, torch, I, sb, model, K, shifts=True)
+        # one replica at a time, a sample of the class
+        loop = []
+        for b in idx[:32]:
+            one = subset(I, s, [b])
+            d1 = nb.DeviceSystem.from_inputs(one)
+            l1 = nb.NeighborList(one.n_atoms, 160, 80, shifts=True)
+            w1 = nb.Workspace(model, one.n_atoms, 1, 160, 80)
+            nb.neighbors(model, d1, l1, SKIN, w1)
+            out = nb.energy_forces_virial(model, d1, l1, w1)
+            v1 = torch.from_numpy(np.ascontiguousarray(
+                I.maxwell_boltzmann(one.types, 900.0).astype(np.float32).T)).cuda()
+            loop.append((d1, l1, w1, v1, out))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for k in range(3):
+            for d1, l1, w1, v1, (_, f1, et1, vr1) in loop:
+                nb.md_step(model, d1, l1, v1, f1, et1, vr1, masses, DT, SKIN, k == 0, w1)
+        e1.record()
+        torch.cuda.synchronize()
+        ms_loop_per_replica = e0.elapsed_time(e1) / 3 / len(loop)
+        B = len(idx)
+        rows.append({"atoms_per_replica": [int(2 ** c), int(2 ** (c + 1)) - 1], "replicas": B,
+                     "atoms": int(sb.n_atoms),
+                     "default": {"ms_per_step": ms_default, "replica_steps_per_s": B / (ms_default * 1e-3)},
+                     "tuned": {"ms_per_step": ms_tuned, "replica_steps_per_s": B / (ms_tuned * 1e-3),
+                               "atom_steps_per_s": sb.n_atoms / (ms_tuned * 1e-3),
+                               "angular_variant": chosen[0], "radial_block": chosen[1],
+                               "finish_block": chosen[2]},
+                     "loop": {"ms_per_replica_step": ms_loop_per_replica,
+                              "replica_steps_per_s": 1e3 / ms_loop_per_replica, "sampled_replicas": len(loop)},
+                     "speedup_vs_loop": (ms_loop_per_replica * B) / ms_tuned})
+        del model, loop
+        torch.cuda.empty_cache()
+    return rows
 
 
 def md_graph_ms(nb, torch, I, s, model, K: int, cap: int = 160, cap_ang: int = 80, shifts: bool = False) -> float:

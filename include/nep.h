@@ -390,14 +390,20 @@ nep_status nep_md_step(nep_model* m, const nep_system* sys, nep_nlist* nl, float
                        float dt, float skin, int rebuild, void* work, size_t work_bytes,
                        void* stream);
 
-/* Autotuner: times every compiled register-budget variant of the angular
- * kernel (the register-heavy one: 2, 3 or 4 resident blocks of 128 threads
- * per SM) on this system and list, `reps` timed launches each after one
- * untimed launch, and stores the fastest in the model for the system's size
- * class (log2 of the mean atom count per configuration).  Later hot calls on
- * systems of that class use it.  Not a hot call: it synchronises `stream`.
- * chosen[2] (may be NULL) receives the angular variant index (0, 1, 2 = 2,
- * 3, 4 blocks per SM) and 0 (reserved).  Untuned classes use variant 0. */
+/* Autotuner: on this system and list, times the launch choices of the three
+ * pair kernels, `reps` timed launches each after one untimed launch:
+ *   the radial kernel at 64, 128 and 256 threads per block;
+ *   every compiled register-budget variant of the angular kernel (the
+ *   register-heavy one: 2, 3 or 4 resident blocks of 128 threads per SM);
+ *   the finish kernel at 64, 128 and 256 threads per block.
+ * The fastest of each is stored in the model for the system's size class
+ * (log2 of the mean atom count per configuration); later hot calls on
+ * systems of that class use them.  Small systems gain from small blocks (more
+ * blocks cover more SMs); large ones do not care.  Not a hot call: it
+ * synchronises `stream` and overwrites the workspace's scratch.
+ * chosen[3] (may be NULL) receives the angular variant index (0, 1, 2 = 2, 3,
+ * 4 blocks per SM), the radial and the finish block size.  Untuned classes
+ * use variant 0, 256 (radial) and 128 (finish). */
 nep_status nep_autotune(nep_model* m, const nep_system* sys, const nep_nlist* nl, void* work,
                         size_t work_bytes, void* stream, int reps, int* chosen);
 
@@ -405,6 +411,12 @@ nep_status nep_autotune(nep_model* m, const nep_system* sys, const nep_nlist* nl
  * -1 = back to the default) for one size class (0..31, as in nep_autotune)
  * or for all of them (size_class = -1).  Host only, no device work. */
 nep_status nep_set_variant(nep_model* m, int size_class, int variant);
+
+/* Pin every launch choice of nep_autotune for one size class or all of them
+ * (size_class = -1): the angular variant (-1 = default) and the radial and
+ * finish block sizes (64, 128, 256, or 0 = default).  Host only.
+ * NEP_ERR_ARG for any other value. */
+nep_status nep_set_launch(nep_model* m, int size_class, int variant, int radial_block, int finish_block);
 
 /* Profiling hook: the next nep_energy_forces_virial / nep_md_step call of
  * this model records events[0] before the radial kernel (radial sums,

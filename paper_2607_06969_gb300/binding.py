@@ -26,7 +26,7 @@ ENTRY_POINTS = (
     "nep_energy_forces_virial_owned", "nep_domain_workspace_bytes", "nep_domain_select", "nep_domain_gather",
     "nep_domain_scatter", "nep_domain_band", "nep_domain_take", "nep_domain_place", "nep_md_kick", "nep_md_wrap",
     "nep_param_grad",
-    "nep_param_grad_adjoint", "nep_adam_step", "nep_md_step", "nep_autotune", "nep_set_variant",
+    "nep_param_grad_adjoint", "nep_adam_step", "nep_md_step", "nep_autotune", "nep_set_variant", "nep_set_launch",
     "nep_set_timing_events", "nep_fp32_peak", "nep_selftest_wait_timeout",
     "nep_check",
     "nep_last_error", "nep_version",
@@ -111,6 +111,8 @@ def lib() -> ctypes.CDLL:
     L.nep_autotune.argtypes = [vp, P(System), P(NList), vp, sz, vp, i, P(ctypes.c_int)]
     L.nep_autotune.restype = i
     L.nep_set_variant.argtypes = [vp, i, i]
+    L.nep_set_launch.argtypes = [vp, i, i, i, i]
+    L.nep_set_launch.restype = i
     L.nep_fp32_peak.argtypes = [vp, P(ctypes.c_double)]
     L.nep_fp32_peak.restype = i
     L.nep_selftest_wait_timeout.argtypes = [vp]
@@ -568,13 +570,22 @@ def set_timing_events(model: Model, events) -> None:
 
 def autotune(model: Model, dsys: DeviceSystem, nl: NeighborList, ws: Workspace, reps: int = 3,
              stream=None):
-    """nep_autotune: pick the angular kernel variant for this system's size
-    class; returns (chosen variant, 0)."""
+    """nep_autotune: pick the angular kernel variant and the radial and
+    finish block sizes for this system's size class; returns them as
+    (variant, radial block, finish block)."""
     _same_atoms(dsys, nl, "nep_autotune")
-    chosen = (ctypes.c_int * 2)()
+    chosen = (ctypes.c_int * 3)()
     check(lib().nep_autotune(model.handle, ctypes.byref(dsys.c), ctypes.byref(nl.c), ws.ptr, ws.bytes,
                              _stream(stream), int(reps), chosen), "nep_autotune")
-    return int(chosen[0]), int(chosen[1])
+    return int(chosen[0]), int(chosen[1]), int(chosen[2])
+
+
+def set_launch(model: Model, variant: int = -1, radial_block: int = 0, finish_block: int = 0,
+               size_class: int = -1) -> None:
+    """nep_set_launch: pin the launch choices (defaults: -1 / 0) for one size
+    class or all of them."""
+    check(lib().nep_set_launch(model.handle, int(size_class), int(variant), int(radial_block),
+                               int(finish_block)), "nep_set_launch")
 
 
 def set_variant(model: Model, variant: int, size_class: int = -1) -> None:

@@ -22,8 +22,10 @@ struct nep_model {
     int device;
     cudaEvent_t timing[4];
     int n_timing;
-    // autotuned kernel variants per size class (-1: default)
+    // autotuned launch choices per size class (-1 / 0: default)
     int tune_angular[nep::kSizeBins];   // angular kernel variant per size class, -1 = default
+    int tune_radial[nep::kSizeBins];    // radial kernel block size per size class, 0 = default
+    int tune_finish[nep::kSizeBins];    // finish kernel block size per size class, 0 = default
 };
 
 namespace {
@@ -218,6 +220,13 @@ int angular_variant(const nep_model* m, const nep_system* s) {
     const int b = size_bin(s);
     return m->tune_angular[b] >= 0 ? m->tune_angular[b] : nep::kDefaultAngularVariant;
 }
+int radial_block(const nep_model* m, const nep_system* s) { return m->tune_radial[size_bin(s)]; }
+int finish_block(const nep_model* m, const nep_system* s) { return m->tune_finish[size_bin(s)]; }
+bool block_choice(int b) {
+    for (int c : nep::kBlockChoices)
+        if (b == c) return true;
+    return false;
+}
 
 nep::EvalArgs make_args(const nep_model* m, const nep_system* s, const nep_nlist* nl, void* work,
                         const WsLayout& w) {
@@ -370,7 +379,7 @@ nep_status efv_impl(nep_model* m, const nep_system* s, const nep_nlist* nl, floa
         return nt ? cudaEventRecordWithFlags(m->timing[k], st, rec_flags) : cudaSuccess;
     };
     NEP_CUDA(mark(0), "timing event");
-    if (N > 0) NEP_CUDA(m->ks->radial(a, st), "radial kernel");
+    if (N > 0) NEP_CUDA(m->ks->radial(a, st, radial_block(m, s)), "radial kernel");
     NEP_CUDA(mark(1), "timing event");
     if (N > 0) NEP_CUDA(m->ks->angular(a, st, vd), "angular kernel");
     NEP_CUDA(mark(2), "timing event");
@@ -381,7 +390,7 @@ nep_status efv_impl(nep_model* m, const nep_system* s, const nep_nlist* nl, floa
     f.force = force;
     f.e_out = e_atom;
     f.n_owned = n_owned < 0 ? N : n_owned;
-    NEP_CUDA(m->ks->finish(a, f, w.max_chunks, st), "finish kernel");
+    NEP_CUDA(m->ks->finish(a, f, w.max_chunks, st, finish_block(m, s)), "finish kernel");
     NEP_CUDA(mark(3), "timing event");
     NEP_CUDA(nep::launch_final_reduce(B, at<int>(work, w.chunk_start), at<double>(work, w.partial), e_tot,
                                       virial, st),
@@ -408,7 +417,7 @@ nep_status train_impl(nep_model* m, const nep_system* s, const nep_nlist* nl, co
     a.p_out = at<float>(work, tl.p);
     a.fb_out = a.fb;
     const int vd = angular_variant(m, s);
-    if (N > 0) NEP_CUDA(m->ks->radial(a, st), "radial kernel");
+    if (N > 0) NEP_CUDA(m->ks->radial(a, st, 0), "radial kernel");
     if (N > 0) NEP_CUDA(m->ks->angular(a, st, vd), "angular kernel");
     if (e_lbl) {
         // forward forces, energies and virials, then the loss and its adjoints
@@ -419,7 +428,7 @@ nep_status train_impl(nep_model* m, const nep_system* s, const nep_nlist* nl, co
         f.force = at<float>(work, tl.force);
         f.e_out = nullptr;
         f.n_owned = N;
-        NEP_CUDA(m->ks->finish(a, f, w.max_chunks, st), "finish kernel");
+        NEP_CUDA(m->ks->finish(a, f, w.max_chunks, st, 0), "finish kernel");
         NEP_CUDA(nep::launch_final_reduce(B, at<int>(work, w.chunk_start), at<double>(work, w.partial),
                                           at<double>(work, tl.etot), at<double>(work, tl.vir), st),
                  "final reduce");
@@ -547,7 +556,11 @@ nep_status nep_create(const nep_hparams* hp, const float* params_host, size_t n_
                                hp->has_4body, hp->n_hidden);
     cudaGetDevice(&m->device);
     m->n_timing = 0;
-    for (int b = 0; b < nep::kSizeBins; ++b) m->tune_angular[b] = -1;
+    for (int b = 0; b < nep::kSizeBins; ++b) {
+        m->tune_angular[b] = -1;
+        m->tune_radial[b] = 0;
+        m->tune_finish[b] = 0;
+    }
     cudaError_t e = ks->init(hp->n_hidden);
     if (e == cudaSuccess) e = ks->train_init(hp->n_hidden);
     if (e != cudaSuccess) {
@@ -1067,6 +1080,23 @@ nep_status nep_set_variant(nep_model* m, int size_class, int variant) {
     return NEP_OK;
 }
 
+nep_status nep_set_launch(nep_model* m, int size_class, int variant, int radial_block, int finish_block) {
+    if (!m) return fail(NEP_ERR_ARG, "model is NULL");
+    if (size_class < -1 || size_class >= nep::kSizeBins)
+        return fail(NEP_ERR_ARG, "size_class must be -1 or 0..%d", nep::kSizeBins - 1);
+    if (variant < -1 || variant >= nep::kVariants)
+        return fail(NEP_ERR_ARG, "variant must be -1 or 0..%d", nep::kVariants - 1);
+    if ((radial_block && !block_choice(radial_block)) || (finish_block && !block_choice(finish_block)))
+        return fail(NEP_ERR_ARG, "block sizes must be 0 (default), 64, 128 or 256");
+    for (int b = 0; b < nep::kSizeBins; ++b)
+        if (size_class < 0 || b == size_class) {
+            m->tune_angular[b] = variant;
+            m->tune_radial[b] = radial_block;
+            m->tune_finish[b] = finish_block;
+        }
+    return NEP_OK;
+}
+
 nep_status nep_autotune(nep_model* m, const nep_system* sys, const nep_nlist* nl, void* work,
                         size_t work_bytes, void* stream, int reps, int* chosen) {
     nep_status s;
@@ -1082,39 +1112,67 @@ nep_status nep_autotune(nep_model* m, const nep_system* sys, const nep_nlist* nl
                               at<float4>(work, w.pos4), at<int>(work, w.cfg), nl->status, st),
              "pack");
     const nep::EvalArgs a = make_args(m, sys, nl, work, w);
+    NEP_CUDA(nep::launch_chunk_plan(sys->atom_off, sys->n_cfg, at<int>(work, w.chunk_start), st), "chunk plan");
     cudaEvent_t e0, e1;
     NEP_CUDA(cudaEventCreate(&e0), "event");
     NEP_CUDA(cudaEventCreate(&e1), "event");
-    float best_d = 1e30f;
-    int vd = nep::kDefaultAngularVariant;
-    // time the angular kernel variants (the one register-heavy kernel)
-    NEP_CUDA(m->ks->radial(a, st), "radial kernel");
-    for (int v = 0; v < nep::kVariants && N > 0; ++v) {
-        // one untimed launch, then the best of `reps` timed launches
-        float tmin = 1e30f;
+    // one untimed launch, then the best of `reps` timed launches of `launch`
+    auto best_of = [&](auto launch, float* tmin) -> cudaError_t {
+        *tmin = 1e30f;
         for (int r = 0; r <= reps; ++r) {
             cudaEventRecord(e0, st);
-            cudaError_t err = m->ks->angular(a, st, v);
+            cudaError_t err = launch();
             cudaEventRecord(e1, st);
             if (err == cudaSuccess) err = cudaEventSynchronize(e1);
-            if (err != cudaSuccess) {
-                cudaEventDestroy(e0);
-                cudaEventDestroy(e1);
-                return cuda_fail(err, "autotune launch");
-            }
+            if (err != cudaSuccess) return err;
             float ms = 0.0f;
             cudaEventElapsedTime(&ms, e0, e1);
-            if (r > 0 && ms < tmin) tmin = ms;
+            if (r > 0 && ms < *tmin) *tmin = ms;
         }
-        if (tmin < best_d) best_d = tmin, vd = v;
+        return cudaSuccess;
+    };
+    nep::FinishArgs f;
+    f.atom_off = sys->atom_off;
+    f.chunk_start = at<int>(work, w.chunk_start);
+    f.partial = at<double>(work, w.partial);
+    f.force = at<float>(work, w.fpart);   // scratch target: the tuner's forces are not kept
+    f.e_out = nullptr;
+    f.n_owned = N;
+    int vd = nep::kDefaultAngularVariant, rb = 0, fb = 0;
+    cudaError_t err = cudaSuccess;
+    if (N > 0) {
+        // the radial kernel's block size, then the angular variant (on the
+        // radial kernel's outputs), then the finish kernel's block size (on
+        // the angular kernel's outputs)
+        float best = 1e30f, t = 0.0f;
+        for (int c : nep::kBlockChoices) {
+            if ((err = best_of([&] { return m->ks->radial(a, st, c); }, &t))) break;
+            if (t < best) best = t, rb = c;
+        }
+        best = 1e30f;
+        for (int v = 0; v < nep::kVariants && !err; ++v) {
+            if ((err = best_of([&] { return m->ks->angular(a, st, v); }, &t))) break;
+            if (t < best) best = t, vd = v;
+        }
+        if (!err) err = m->ks->angular(a, st, vd);
+        best = 1e30f;
+        for (int c : nep::kBlockChoices) {
+            if (err) break;
+            if ((err = best_of([&] { return m->ks->finish(a, f, w.max_chunks, st, c); }, &t))) break;
+            if (t < best) best = t, fb = c;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (err != cudaSuccess) return cuda_fail(err, "autotune launch");
     const int b = size_bin(sys);
     m->tune_angular[b] = vd;
+    m->tune_radial[b] = rb;
+    m->tune_finish[b] = fb;
     if (chosen) {
         chosen[0] = vd;
-        chosen[1] = 0;   // reserved
+        chosen[1] = rb;
+        chosen[2] = fb;
     }
     return NEP_OK;
 }

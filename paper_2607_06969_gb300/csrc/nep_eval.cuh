@@ -175,7 +175,9 @@ struct NbrStream {
 // ---------------------------------------------------------------------------
 // radial descriptor sums and pair compaction, one atom
 // ---------------------------------------------------------------------------
-template <class C, bool MINIMG>
+// COMPR: the training variant, which also writes the compacted records of
+// the pairs inside rc_rad and the mask of the incoming angular slots
+template <class C, bool MINIMG, bool COMPR>
 NEP_HD void radial_atom(const EvalArgs& a, int i) {
     constexpr int KR = C::KR, T = C::T;
     const int N = a.N;
@@ -190,7 +192,7 @@ NEP_HD void radial_atom(const EvalArgs& a, int i) {
         for (int k = 0; k < KR; ++k) fb[t][k] = 0.0f;
     const int cnt = a.cnt[i], cnt_ang = a.cnt_ang[i];
     int nc = 0, ncr = 0, nr = 0;
-    unsigned long long amask = 0ull;
+    unsigned long long amask = 0ull;   // COMPR only
     NbrStream<MINIMG, NEP_RADIAL_DEPTH> ns(a, a.nbr, a.shift, i, cnt);
     for (int s = 0; s < cnt; ++s) {
         const int j = ns.j[0];
@@ -202,11 +204,11 @@ NEP_HD void radial_atom(const EvalArgs& a, int i) {
         const float d2 = dist2(dx, dy, dz);
         const int tj = f2i(pj.w);
         if (d2 < rcR2) {
-            if (a.compr) {
+            if (COMPR) {
                 a.compr[ncr * N + i] = make_float4(dx, dy, dz, i2f((int)(((unsigned)j << 2) | (unsigned)tj)));
                 ++ncr;
             }
-            if (s >= cnt_ang && a.rin) {
+            if (!COMPR && s >= cnt_ang && a.rin) {
                 a.rin[nr * N + i] = j;
                 if (!MINIMG) a.rin_sh[nr * N + i] = sh;
                 ++nr;
@@ -226,19 +228,22 @@ NEP_HD void radial_atom(const EvalArgs& a, int i) {
                 a.comp[nc * N + i] =
                     make_float4(dx, dy, dz, i2f((int)(((unsigned)addr << 2) | (unsigned)tj)));
                 ++nc;
-                if (s < 64) amask |= 1ull << s;
-            } else if (a.compr && (!a.amask || s >= 64)) {
+                if (COMPR && s < 64) amask |= 1ull << s;
+            } else if (COMPR && s >= 64) {
                 // the compacted-record force pass reads every angular slot
-                // not covered by the mask; the list walk of k_finish reads
-                // only the slots inside rc_A
+                // from 64 on and the masked ones below; the list walk of
+                // k_finish reads only the slots inside rc_A
                 a.fin[addr] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             }
         }
     }
     a.cnt_comp[i] = nc;
-    if (a.compr) a.cnt_compr[i] = ncr;
-    if (a.compr && a.amask) a.amask[i] = amask;
-    if (a.rin) a.cnt_rin[i] = nr;
+    if (COMPR) {
+        a.cnt_compr[i] = ncr;
+        a.amask[i] = amask;
+    } else if (a.rin) {
+        a.cnt_rin[i] = nr;
+    }
 #pragma unroll
     for (int t = 0; t < T; ++t)
 #pragma unroll
@@ -739,9 +744,8 @@ NEP_HD void radial_force_atom(const EvalArgs& a, int i, float& Fx, float& Fy, fl
         // mask, in batches of four independent loads, ascending) and every
         // slot from 64 on; without a mask every slot of the prefix
         const int na = a.cnt_ang[i];
-        int s0 = 0;
-        if (a.amask) {
-            s0 = na < 64 ? na : 64;
+        const int s0 = na < 64 ? na : 64;
+        {
             unsigned long long m = a.amask[i];
             while (m) {
                 int sl[4];
@@ -864,6 +868,9 @@ NEP_HD void finish_atom(const EvalArgs& a, int i, float* force, float* e_out, fl
 // (nep_autotune).  Variant 0 (255 registers) keeps S and dE/dS on chip
 // without spills and is the default.
 NEP_HD constexpr int variant_minb(int v) { return v + 2; }
+// Default block sizes of the radial and finish kernels; the autotuner may
+// pick another of kBlockChoices per size class.  Each size keeps the
+// kernel at 64 registers (1,024 / block resident blocks).
 constexpr int kRadialBlock = 256;
 constexpr int kFinishThreads = 128;
 
@@ -876,10 +883,10 @@ constexpr int kFinishThreads = 128;
 #ifndef NEP_FINISH_STAGE
 #define NEP_FINISH_STAGE 1
 #endif
-template <class C, bool MINIMG>
-__global__ void __launch_bounds__(kRadialBlock, NEP_RADIAL_MINB) k_radial(const EvalArgs a) {
+template <class C, bool MINIMG, bool COMPR, int BLOCK = kRadialBlock>
+__global__ void __launch_bounds__(BLOCK, NEP_RADIAL_MINB * kRadialBlock / BLOCK) k_radial(const EvalArgs a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < a.N) radial_atom<C, MINIMG>(a, i);
+    if (i < a.N) radial_atom<C, MINIMG, COMPR>(a, i);
 }
 
 // Persistent: one CTA per resident slot, the model image staged once, then a
@@ -970,13 +977,13 @@ inline int persistent_grid(int ntiles, int per_sm) {
     return ntiles < g ? ntiles : g;
 }
 
-template <class C, bool MINIMG>
-__global__ void __launch_bounds__(kFinishThreads, NEP_FINISH_MINB) k_finish(const EvalArgs a, float* force, float* e_out) {
+template <class C, bool MINIMG, int BLOCK = kFinishThreads>
+__global__ void __launch_bounds__(BLOCK, NEP_FINISH_MINB * kFinishThreads / BLOCK) k_finish(const EvalArgs a, float* force, float* e_out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
 #if NEP_FINISH_STAGE
     constexpr int kChunks = (C::KR % 4 == 0) ? C::T * C::KR / 4 : 1;
-    __shared__ float4 stage[kChunks * kFinishThreads];
-    if (i < a.N) finish_atom<C, MINIMG>(a, i, force, e_out, stage + threadIdx.x, kFinishThreads);
+    __shared__ float4 stage[kChunks * BLOCK];
+    if (i < a.N) finish_atom<C, MINIMG>(a, i, force, e_out, stage + threadIdx.x, BLOCK);
 #else
     if (i < a.N) finish_atom<C, MINIMG>(a, i, force, e_out);
 #endif
@@ -989,14 +996,33 @@ size_t angular_smem_bytes(int H, bool tmem_stage) {
     return sizeof(float) * ((size_t)smem_layout<C>(H).total + (tmem_stage ? 0 : (size_t)C::NA * kLM * kBlock));
 }
 
-template <class C>
-cudaError_t launch_radial_t(const EvalArgs& a, cudaStream_t st) {
-    const int grid = (a.N + kRadialBlock - 1) / kRadialBlock;
-    if (grid == 0) return cudaSuccess;
+template <class C, int BLOCK>
+void launch_radial_b(const EvalArgs& a, cudaStream_t st) {
+    const int grid = (a.N + BLOCK - 1) / BLOCK;
     if (a.min_image)
-        k_radial<C, true><<<grid, kRadialBlock, 0, st>>>(a);
+        k_radial<C, true, false, BLOCK><<<grid, BLOCK, 0, st>>>(a);
     else
-        k_radial<C, false><<<grid, kRadialBlock, 0, st>>>(a);
+        k_radial<C, false, false, BLOCK><<<grid, BLOCK, 0, st>>>(a);
+}
+
+// block: one of kBlockChoices, 0 for the default; the training variant
+// (compacted records) always runs at the default block
+template <class C>
+cudaError_t launch_radial_t(const EvalArgs& a, cudaStream_t st, int block) {
+    if (a.N == 0) return cudaSuccess;
+    if (a.compr) {
+        const int grid = (a.N + kRadialBlock - 1) / kRadialBlock;
+        if (a.min_image)
+            k_radial<C, true, true><<<grid, kRadialBlock, 0, st>>>(a);
+        else
+            k_radial<C, false, true><<<grid, kRadialBlock, 0, st>>>(a);
+    } else if (block == 64) {
+        launch_radial_b<C, 64>(a, st);
+    } else if (block == 128) {
+        launch_radial_b<C, 128>(a, st);
+    } else {
+        launch_radial_b<C, kRadialBlock>(a, st);
+    }
     return cudaGetLastError();
 }
 
@@ -1019,14 +1045,25 @@ cudaError_t launch_angular_t(const EvalArgs& a, cudaStream_t st, int v) {
     return cudaGetLastError();
 }
 
+template <class C, int BLOCK>
+void launch_finish_b(const EvalArgs& a, const FinishArgs& f, cudaStream_t st) {
+    const int grid = (a.N + BLOCK - 1) / BLOCK;
+    if (a.min_image)
+        k_finish<C, true, BLOCK><<<grid, BLOCK, 0, st>>>(a, f.force, f.e_out);
+    else
+        k_finish<C, false, BLOCK><<<grid, BLOCK, 0, st>>>(a, f.force, f.e_out);
+}
+
+// block: one of kBlockChoices, 0 for the default
 template <class C>
-cudaError_t launch_finish_t(const EvalArgs& a, const FinishArgs& f, int max_chunks, cudaStream_t st) {
-    const int grid = (a.N + kFinishThreads - 1) / kFinishThreads;
-    if (grid > 0) {
-        if (a.min_image)
-            k_finish<C, true><<<grid, kFinishThreads, 0, st>>>(a, f.force, f.e_out);
+cudaError_t launch_finish_t(const EvalArgs& a, const FinishArgs& f, int max_chunks, cudaStream_t st, int block) {
+    if (a.N > 0) {
+        if (block == 64)
+            launch_finish_b<C, 64>(a, f, st);
+        else if (block == 256)
+            launch_finish_b<C, 256>(a, f, st);
         else
-            k_finish<C, false><<<grid, kFinishThreads, 0, st>>>(a, f.force, f.e_out);
+            launch_finish_b<C, kFinishThreads>(a, f, st);
     }
     return launch_chunk_reduce(a, f, max_chunks, st);
 }

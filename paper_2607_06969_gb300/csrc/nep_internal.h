@@ -23,6 +23,7 @@ constexpr int kBlock = 128;      // threads per block of the per-atom kernels
 constexpr int kVariants = 3;              // angular kernel register budgets: 2, 3, 4 blocks per SM
 constexpr int kDefaultAngularVariant = 0; // 2 blocks per SM, S_nlm in tensor memory
 constexpr int kSizeBins = 32;             // tuning table: log2 of mean atoms per configuration
+constexpr int kBlockChoices[3] = {64, 128, 256};   // block sizes the tuner tries for radial / finish
 
 // Stencil/cell plan of one configuration for the neighbour build.
 struct CellPlan {
@@ -122,9 +123,11 @@ struct KernelSet {
     int n_rad, n_ang, k_rad, k_ang, has_4body, n_types;
     size_t (*smem_bytes)(int H);
     cudaError_t (*init)(int H);   // set kernel attributes (dynamic shared memory)
-    cudaError_t (*radial)(const EvalArgs&, cudaStream_t);
+    // block: threads per block of the radial / finish kernel, one of
+    // kBlockChoices, or 0 for the kernel's default
+    cudaError_t (*radial)(const EvalArgs&, cudaStream_t, int block);
     cudaError_t (*angular)(const EvalArgs&, cudaStream_t, int variant);   // FP32 or tensor-core network
-    cudaError_t (*finish)(const EvalArgs&, const FinishArgs&, int max_chunks, cudaStream_t);
+    cudaError_t (*finish)(const EvalArgs&, const FinishArgs&, int max_chunks, cudaStream_t, int block);
     cudaError_t (*train_init)(int H);
     cudaError_t (*train)(const TrainArgs&, cudaStream_t);   // tangent ... gradient
     int (*grad_chunks)(int N);

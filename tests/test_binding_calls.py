@@ -61,7 +61,7 @@ class StubLib:
             if name == "nep_fp32_peak":
                 args[1]._obj.value = 76.5
             if name == "nep_autotune":
-                args[7][0] = 2
+                args[7][0], args[7][1], args[7][2] = 2, 64, 128
             return nb.NEP_OK
         return call
 
@@ -199,10 +199,12 @@ def test_md_step_passes_masses_and_rebuild_flag(stub, parts):
 
 
 def test_tuning_and_helper_calls(stub, parts):
-    assert nb.autotune(parts.model, parts.dsys, parts.nl, parts.ws, reps=4, stream=STREAM) == (2, 0)
+    assert nb.autotune(parts.model, parts.dsys, parts.nl, parts.ws, reps=4, stream=STREAM) == (2, 64, 128)
     assert stub.last("nep_autotune")[6] == 4
     nb.set_variant(parts.model, 1, 3)
     assert stub.last("nep_set_variant")[1:] == (3, 1)
+    nb.set_launch(parts.model, 2, 128, 64, size_class=5)
+    assert stub.last("nep_set_launch")[1:] == (5, 2, 128, 64)
     assert nb.fp32_peak(stream=STREAM) == pytest.approx(76.5)
     assert nb.selftest_wait_timeout(stream=STREAM) == nb.NEP_OK
     assert nb.check_list(parts.nl, stream=STREAM) == nb.NEP_OK

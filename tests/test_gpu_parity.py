@@ -240,19 +240,32 @@ def test_every_angular_variant(nb, variant):
 
 
 def test_autotune_variants_agree(nb):
-    """Every compiled register-budget variant computes the same E, F, V; the
-    autotuner picks valid indices and later calls use them."""
+    """Every compiled register-budget variant and block size computes the
+    same E, F, V; the autotuner picks valid choices and later calls use them."""
     h = I.HYPER_SMALL
     s = I.packing_batch([57, 100, 250], tag=67)
     th = I.init_params(h).astype(np.float32)
     g = gpu_eval(nb, h, th, s, skin=1.0, cap=160, cap_ang=64)
     chosen = nb.autotune(g["model"], g["dsys"], g["nl"], g["ws"], reps=2)
-    assert all(0 <= c < 3 for c in chosen)
+    assert 0 <= chosen[0] < 3 and chosen[1] in (64, 128, 256) and chosen[2] in (64, 128, 256)
     e, f, et, v = nb.energy_forces_virial(g["model"], g["dsys"], g["nl"], g["ws"])
     assert np.abs(e.cpu().numpy() - g["E"]).max() <= 1e-6
     assert np.abs(f.cpu().numpy().T - g["F"]).max() <= 1e-5
     assert_parity(dict(E=e.cpu().numpy(), F=f.cpu().numpy().T, Etot=et.cpu().numpy(),
                        V=v.cpu().numpy().reshape(-1, 3, 3), status=0), oracle_eval(h, th, s), s)
+    # every block size of the radial and finish kernels gives the same bits
+    ref = None
+    for rb in (64, 128, 256):
+        for fb in (64, 128, 256):
+            nb.set_launch(g["model"], 0, rb, fb)
+            out = [t.cpu().numpy() for t in nb.energy_forces_virial(g["model"], g["dsys"], g["nl"], g["ws"])]
+            if ref is None:
+                ref = out
+            for x, y in zip(out, ref):
+                assert np.array_equal(x, y)
+    nb.set_launch(g["model"])
+    with pytest.raises(nb.NepError):
+        nb.set_launch(g["model"], 0, 96, 0)
 
 
 def test_graph_captured_md_matches_eager(nb):
