@@ -83,13 +83,22 @@ typedef struct nep_model nep_model;   /* opaque, library-owned */
 size_t nep_num_params(const nep_hparams* hp);
 
 /* Create a model from hyper-parameters and HOST parameters (P floats).
- * Allocates the model's device copy on the current device.  Returns
- * NEP_ERR_UNSUPPORTED when no kernel is compiled for hp (see
- * nep_supported). */
+ * Allocates the model's device copy on the current device.
+ * A shape with a compiled kernel set (nep_supported = 1) gets the fast path:
+ * FP32, FP16 or BF16 network, every call.  Any other FP32 shape with n_rad,
+ * n_ang <= 16 and k_rad, k_ang <= 16 (nep_supported = 2) gets the generic
+ * path: runtime-shaped FP32 kernels that evaluate each pair term from both of
+ * its atoms (about twice the fast path's pair work).  A generic model serves
+ * nep_neighbors, the FP32 evaluations (nep_energy_forces_virial, _owned,
+ * _noalloc), nep_md_step and the FP64 calls; nep_param_grad,
+ * nep_param_grad_adjoint and nep_autotune return NEP_ERR_UNSUPPORTED (its
+ * training gradient comes from nep_param_grad_fp64).  Other shapes, and
+ * FP16/BF16 for shapes without a kernel set, return NEP_ERR_UNSUPPORTED. */
 nep_status nep_create(const nep_hparams* hp, const float* params_host, size_t n_params,
                       nep_model** out);
 nep_status nep_destroy(nep_model* m);
-/* 1 if kernels for these hyper-parameters are compiled in, else 0. */
+/* 1 if a kernel set is compiled for these hyper-parameters (the fast path),
+ * 2 if only the generic FP32 path serves them, 0 if nep_create rejects them. */
 int nep_supported(const nep_hparams* hp);
 
 /* Replace the parameters from a DEVICE buffer of P floats, stream-ordered

@@ -16,7 +16,7 @@
 
 struct nep_model {
     nep_hparams hp;
-    const nep::KernelSet* ks;
+    const nep::KernelSet* ks;   // compiled fast path; null: the generic FP32 path (runtime shapes)
     nep::ParamLayout lay;
     float* params;   // device [P]
     int device;
@@ -68,6 +68,7 @@ struct WsLayout {
     size_t pos4, cfg, e_atom, fb, S, Pr, comp, cnt_comp, fin, fpart, wat, chunk_start, partial;
     size_t rin, rin_sh, cnt_rin;
     size_t amask;
+    size_t gen_p, gen_R, gen_w;   // generic FP32 path: dE/dq (radial), dE/dS, per-atom virial
     size_t plan, cell_of, rank, cell_cnt, cell_start, cell_atoms, scan_tmp, shell, row_start, slot_row;
     size_t total;
     int max_chunks, cmax;
@@ -97,6 +98,13 @@ WsLayout ws_layout(const nep_model* m, int N, int B, int cap, int cap_ang) {
     w.rin_sh = take(4 * n * cap);
     w.cnt_rin = take(4 * n);
     w.amask = take(8 * n);
+    if (!m->ks) {
+        w.gen_p = take(4 * n * m->hp.n_rad);
+        w.gen_R = take(4 * n * NA * nep::kLM);
+        w.gen_w = take(36 * n);
+    } else {
+        w.gen_p = w.gen_R = w.gen_w = 0;
+    }
     w.fpart = take(12 * n);
     w.wat = take(36 * n);
     w.chunk_start = take(4 * ((size_t)B + 1));
@@ -358,6 +366,55 @@ bool fp64_supported(const nep_hparams& hp) {
            hp.k_ang <= nep::kF64MaxK;
 }
 
+// The generic FP32 evaluation (a model with no compiled kernel set): the
+// FP64 path's two kernels in float, every pair term evaluated from both of
+// its atoms, then the same FP64 sums.
+nep_status efv_generic(nep_model* m, const nep_system* s, const nep_nlist* nl, float* e_atom, float* force,
+                       double* e_tot, double* virial, void* work, const WsLayout& w, cudaStream_t st,
+                       int n_owned) {
+    const int N = s->n_atoms;
+    nep::F32Args a{};
+    a.N = N;
+    a.B = s->n_cfg;
+    a.T = m->hp.n_types;
+    a.NR = m->hp.n_rad;
+    a.NA = m->hp.n_ang;
+    a.KR = m->hp.k_rad;
+    a.KA = m->hp.k_ang;
+    a.H = m->hp.n_hidden;
+    a.H4 = m->hp.has_4body;
+    a.D = m->lay.D;
+    a.L = m->lay;
+    a.rc_rad = m->hp.rc_rad;
+    a.rc_ang = m->hp.rc_ang;
+    a.pos = s->pos;
+    a.type = s->type;
+    a.cfg = at<int>(work, w.cfg);
+    a.box = s->box;
+    a.cnt = nl->cnt;
+    a.nbr = nl->nbr;
+    a.shift = nl->min_image ? nullptr : nl->shift;
+    a.prm = m->params;
+    a.e = e_atom ? e_atom : at<float>(work, w.e_atom);
+    a.p = at<float>(work, w.gen_p);
+    a.R = at<float>(work, w.gen_R);
+    a.w = at<float>(work, w.gen_w);
+    a.force = force;
+    a.atom_off = s->atom_off;
+    a.chunk_start = at<int>(work, w.chunk_start);
+    a.partial = at<double>(work, w.partial);
+    a.n_owned = n_owned < 0 ? N : n_owned;
+    const int nt = m->n_timing;
+    m->n_timing = 0;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (nt) NEP_CUDA(cudaStreamIsCapturing(st, &cap), "capture status");
+    const unsigned rec_flags = cap == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
+    if (nt) NEP_CUDA(cudaEventRecordWithFlags(m->timing[0], st, rec_flags), "timing event");
+    NEP_CUDA(nep::launch_efv_generic(a, w.max_chunks, e_tot, virial, st), "generic FP32 kernels");
+    for (int k = 1; k < 4 && nt; ++k) NEP_CUDA(cudaEventRecordWithFlags(m->timing[k], st, rec_flags), "timing event");
+    return NEP_OK;
+}
+
 nep_status efv_impl(nep_model* m, const nep_system* s, const nep_nlist* nl, float* e_atom,
                     float* force, double* e_tot, double* virial, void* work, const WsLayout& w,
                     cudaStream_t st, int n_owned = -1) {
@@ -366,6 +423,7 @@ nep_status efv_impl(nep_model* m, const nep_system* s, const nep_nlist* nl, floa
                               at<int>(work, w.cfg), nl->status, st),
              "pack");
     NEP_CUDA(nep::launch_chunk_plan(s->atom_off, B, at<int>(work, w.chunk_start), st), "chunk plan");
+    if (!m->ks) return efv_generic(m, s, nl, e_atom, force, e_tot, virial, work, w, st, n_owned);
     const nep::EvalArgs a = make_args(m, s, nl, work, w);
     const int vd = angular_variant(m, s);
     const int nt = m->n_timing;
@@ -527,8 +585,9 @@ size_t nep_num_params(const nep_hparams* hp) {
 int nep_supported(const nep_hparams* hp) {
     if (!hp_valid(hp)) return 0;
     if (hp->precision != 0 && hp->n_hidden > nep::kTcMaxHidden) return 0;
-    return nep::find_kernel_set(hp->n_rad, hp->n_ang, hp->k_rad, hp->k_ang, hp->has_4body,
-                                hp->n_types) != nullptr;
+    if (nep::find_kernel_set(hp->n_rad, hp->n_ang, hp->k_rad, hp->k_ang, hp->has_4body, hp->n_types))
+        return 1;
+    return hp->precision == 0 && fp64_supported(*hp) ? 2 : 0;
 }
 
 nep_status nep_create(const nep_hparams* hp, const float* params_host, size_t n_params,
@@ -538,10 +597,12 @@ nep_status nep_create(const nep_hparams* hp, const float* params_host, size_t n_
     if (!hp_valid(hp)) return fail(NEP_ERR_ARG, "invalid hyper-parameters (l_max must be 4, 1 <= n_types <= 4, rc_ang <= rc_rad)");
     const nep::KernelSet* ks = nep::find_kernel_set(hp->n_rad, hp->n_ang, hp->k_rad, hp->k_ang,
                                                     hp->has_4body, hp->n_types);
-    if (!ks)
+    if (!ks && (hp->precision != 0 || !fp64_supported(*hp)))
         return fail(NEP_ERR_UNSUPPORTED,
-                    "no kernel compiled for n_rad=%d n_ang=%d k_rad=%d k_ang=%d 4body=%d types=%d",
-                    hp->n_rad, hp->n_ang, hp->k_rad, hp->k_ang, hp->has_4body, hp->n_types);
+                    "no kernel compiled for n_rad=%d n_ang=%d k_rad=%d k_ang=%d 4body=%d types=%d, and the "
+                    "generic path takes FP32 only with n_rad, n_ang <= %d and k_rad, k_ang <= %d",
+                    hp->n_rad, hp->n_ang, hp->k_rad, hp->k_ang, hp->has_4body, hp->n_types, nep::kF64MaxN,
+                    nep::kF64MaxK);
     if (hp->precision != 0 && hp->n_hidden > nep::kTcMaxHidden)
         return fail(NEP_ERR_UNSUPPORTED, "the FP16/BF16 network supports n_hidden <= %d", nep::kTcMaxHidden);
     const size_t P = nep_num_params(hp);
@@ -561,8 +622,8 @@ nep_status nep_create(const nep_hparams* hp, const float* params_host, size_t n_
         m->tune_radial[b] = 0;
         m->tune_finish[b] = 0;
     }
-    cudaError_t e = ks->init(hp->n_hidden);
-    if (e == cudaSuccess) e = ks->train_init(hp->n_hidden);
+    cudaError_t e = ks ? ks->init(hp->n_hidden) : cudaSuccess;
+    if (e == cudaSuccess && ks) e = ks->train_init(hp->n_hidden);
     if (e != cudaSuccess) {
         delete m;
         return cuda_fail(e, "kernel attributes");
@@ -702,6 +763,7 @@ nep_status fp64_begin(nep_model* m, const nep_system* sys, const nep_nlist* nl, 
     a.atom_off = sys->atom_off;
     a.chunk_start = at<int>(work, w.chunk_start);
     a.partial = at<double>(work, w.partial);
+    a.n_owned = N;
     *out = a;
     return NEP_OK;
 }
@@ -998,6 +1060,8 @@ nep_status nep_energy_forces_virial_noalloc(nep_model* m, const nep_system* sys,
 
 size_t nep_train_workspace_bytes(const nep_model* m, int n_atoms, int n_cfg, int cap, int cap_ang) {
     if (!m || n_atoms < 0 || n_cfg < 1 || cap < 1 || cap_ang < 1) return 0;
+    // a generic model has no FP32 training operator: its evaluation scratch only
+    if (!m->ks) return ws_layout(m, n_atoms, n_cfg, cap, cap_ang).total;
     return train_layout(m, n_atoms, n_cfg, cap, cap_ang).total;
 }
 
@@ -1015,6 +1079,9 @@ nep_status nep_param_grad(nep_model* m, const nep_system* sys, const nep_nlist* 
     if (!nl->min_image && !nl->shift) return fail(NEP_ERR_STATE, "list was not built");
     if (m->hp.precision != 0)
         return fail(NEP_ERR_UNSUPPORTED, "the gradient is computed for FP32 models (precision 0)");
+    if (!m->ks)
+        return fail(NEP_ERR_UNSUPPORTED, "no FP32 training operator for this model's shape (generic path): "
+                                         "use nep_param_grad_fp64");
     TrainLayout tl;
     if ((s = check_train_work(m, sys, nl, work, work_bytes, &tl)) != NEP_OK) return s;
     return train_impl(m, sys, nl, e_lbl, f_lbl, v_lbl, w_host, loss_mode, nullptr, nullptr, nullptr, grad,
@@ -1032,6 +1099,9 @@ nep_status nep_param_grad_adjoint(nep_model* m, const nep_system* sys, const nep
     if (!nl->min_image && !nl->shift) return fail(NEP_ERR_STATE, "list was not built");
     if (m->hp.precision != 0)
         return fail(NEP_ERR_UNSUPPORTED, "the gradient is computed for FP32 models (precision 0)");
+    if (!m->ks)
+        return fail(NEP_ERR_UNSUPPORTED, "no FP32 training operator for this model's shape (generic path): "
+                                         "use nep_param_grad_adjoint_fp64");
     TrainLayout tl;
     if ((s = check_train_work(m, sys, nl, work, work_bytes, &tl)) != NEP_OK) return s;
     return train_impl(m, sys, nl, nullptr, nullptr, nullptr, nullptr, 0, a_e, lam, mu, grad, nullptr,
@@ -1101,6 +1171,7 @@ nep_status nep_autotune(nep_model* m, const nep_system* sys, const nep_nlist* nl
                         size_t work_bytes, void* stream, int reps, int* chosen) {
     nep_status s;
     if ((s = check_system(m, sys)) != NEP_OK) return s;
+    if (!m->ks) return fail(NEP_ERR_UNSUPPORTED, "the generic path has no launch choices to tune");
     if ((s = check_nlist(nl, sys->n_atoms)) != NEP_OK) return s;
     if (!nl->min_image && !nl->shift) return fail(NEP_ERR_STATE, "list was not built");
     if (reps < 1) reps = 1;

@@ -50,27 +50,53 @@ constexpr int kF64MaxD = kF64MaxN * 6;              // n_rad + 5 n_ang
 constexpr int kF64MaxTK = kMaxTypes * kF64MaxK;     // n_types * k_rad
 constexpr double kPi = 3.141592653589793;
 
+// The evaluation below is written once for two argument types: F64Args (every
+// intermediate in double) and F32Args (the generic FP32 evaluation, any
+// hyper-parameters within the same bounds).  R is the argument type's scalar.
+template <class A>
+struct ScalarOf;
+template <>
+struct ScalarOf<F64Args> {
+    using type = double;
+};
+template <>
+struct ScalarOf<F32Args> {
+    using type = float;
+};
+template <class A>
+using ScalarT = typename ScalarOf<A>::type;
+
+__device__ __forceinline__ void sincospi_r(double z, double* s, double* c) { sincospi(z, s, c); }
+__device__ __forceinline__ void sincospi_r(float z, float* s, float* c) { sincospif(z, s, c); }
+__device__ __forceinline__ double tanh_r(double x) { return tanh(x); }
+__device__ __forceinline__ float tanh_r(float x) { return tanhf(x); }
+__device__ __forceinline__ double sqrt_r(double x) { return sqrt(x); }
+__device__ __forceinline__ float sqrt_r(float x) { return sqrtf(x); }
+__device__ __forceinline__ double rint_r(double x) { return rint(x); }
+__device__ __forceinline__ float rint_r(float x) { return rintf(x); }
+
 // Q_k(r) and dQ_k/dr for k < K at r < rc: Q_k = (T_k(x) + 1)/2 f_c(r),
 // x = 2(r/rc - 1)^2 - 1, f_c = (1 + cos(pi r/rc))/2 (Eqs. 12-15)
-__device__ void basis64(double r, double rc, int K, double* f, double* fp) {
-    const double z = r / rc;
-    double sp, cp;
-    sincospi(z, &sp, &cp);
-    const double fc2 = 0.25 * (1.0 + cp);                 // f_c / 2
-    const double dfc2 = -0.25 * kPi / rc * sp;            // (d f_c/dr) / 2
-    const double t = z - 1.0, x = 2.0 * t * t - 1.0, dx = 4.0 * t / rc;
-    double Tm = 1.0, Tk = x, dTm = 0.0, dTk = 1.0;
-    f[0] = 2.0 * fc2;
-    fp[0] = 2.0 * dfc2;
+template <class R>
+__device__ void basis64(R r, R rc, int K, R* f, R* fp) {
+    const R z = r / rc;
+    R sp, cp;
+    sincospi_r(z, &sp, &cp);
+    const R fc2 = R(0.25) * (R(1.0) + cp);                 // f_c / 2
+    const R dfc2 = R(-0.25) * R(kPi) / rc * sp;            // (d f_c/dr) / 2
+    const R t = z - R(1.0), x = R(2.0) * t * t - R(1.0), dx = R(4.0) * t / rc;
+    R Tm = R(1.0), Tk = x, dTm = R(0.0), dTk = R(1.0);
+    f[0] = R(2.0) * fc2;
+    fp[0] = R(2.0) * dfc2;
     if (K > 1) {
-        f[1] = (x + 1.0) * fc2;
-        fp[1] = dx * fc2 + (x + 1.0) * dfc2;
+        f[1] = (x + R(1.0)) * fc2;
+        fp[1] = dx * fc2 + (x + R(1.0)) * dfc2;
     }
     for (int k = 2; k < K; ++k) {
-        const double Tn = 2.0 * x * Tk - Tm;
-        const double dTn = 2.0 * Tk + 2.0 * x * dTk - dTm;
-        f[k] = (Tn + 1.0) * fc2;
-        fp[k] = dTn * dx * fc2 + (Tn + 1.0) * dfc2;
+        const R Tn = R(2.0) * x * Tk - Tm;
+        const R dTn = R(2.0) * Tk + R(2.0) * x * dTk - dTm;
+        f[k] = (Tn + R(1.0)) * fc2;
+        fp[k] = dTn * dx * fc2 + (Tn + R(1.0)) * dfc2;
         Tm = Tk; Tk = Tn; dTm = dTk; dTk = dTn;
     }
 }
@@ -78,20 +104,23 @@ __device__ void basis64(double r, double rc, int K, double* f, double* fp) {
 // sum over the G aligned lanes of an atom; every lane receives the same bits.
 // The shuffles name only the group's lanes: a group whose atom index is past
 // N leaves as a whole, while the other groups of its warp go on.
-template <int G>
-__device__ __forceinline__ double group_sum(double v) {
+template <int G, class R>
+__device__ __forceinline__ R group_sum(R v) {
     const unsigned mask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
     return v;
 }
 
-struct Frame64 {
+template <class R>
+struct FrameT {
     int i, ti, b;
-    double L[3], x, y, z;
+    R L[3], x, y, z;
 };
-__device__ Frame64 frame64(const F64Args& a, int i) {
-    Frame64 fr;
+using Frame64 = FrameT<double>;
+template <class A>
+__device__ FrameT<ScalarT<A>> frame64(const A& a, int i) {
+    FrameT<ScalarT<A>> fr;
     fr.i = i;
     fr.ti = a.type[i];
     fr.b = a.cfg[i];
@@ -102,44 +131,46 @@ __device__ Frame64 frame64(const F64Args& a, int i) {
     return fr;
 }
 
-// list slot s of atom fr.i: r_ij = (r_j - r_i) + s L in double, with the
-// list's image or the minimum image; false when r >= rc_rad
-struct Pair64 {
+// list slot s of atom fr.i: r_ij = (r_j - r_i) + s L in R, with the list's
+// image or the minimum image; false when r >= rc_rad
+template <class R>
+struct PairT {
     int j, tj;
-    double d[3], r, u[3];
+    R d[3], r, u[3];
 };
-__device__ bool pair_at(const F64Args& a, const Frame64& fr, int s, Pair64& p) {
+using Pair64 = PairT<double>;
+template <class A, class R>
+__device__ bool pair_at(const A& a, const FrameT<R>& fr, int s, PairT<R>& p) {
     const int N = a.N;
     p.j = a.nbr[(size_t)s * N + fr.i];
-    const double ux = (double)a.pos[p.j] - fr.x, uy = (double)a.pos[N + p.j] - fr.y,
-                 uz = (double)a.pos[2 * N + p.j] - fr.z;
-    double sx, sy, sz;
+    const R ux = (R)a.pos[p.j] - fr.x, uy = (R)a.pos[N + p.j] - fr.y, uz = (R)a.pos[2 * N + p.j] - fr.z;
+    R sx, sy, sz;
     if (a.shift) {
         int ix, iy, iz;
         unpack_shift(a.shift[(size_t)s * N + fr.i], ix, iy, iz);
-        sx = ix; sy = iy; sz = iz;
+        sx = (R)ix; sy = (R)iy; sz = (R)iz;
     } else {
-        sx = -rint(ux / fr.L[0]);
-        sy = -rint(uy / fr.L[1]);
-        sz = -rint(uz / fr.L[2]);
+        sx = -rint_r(ux / fr.L[0]);
+        sy = -rint_r(uy / fr.L[1]);
+        sz = -rint_r(uz / fr.L[2]);
     }
     p.d[0] = ux + sx * fr.L[0];
     p.d[1] = uy + sy * fr.L[1];
     p.d[2] = uz + sz * fr.L[2];
-    p.r = sqrt(p.d[0] * p.d[0] + p.d[1] * p.d[1] + p.d[2] * p.d[2]);
+    p.r = sqrt_r(p.d[0] * p.d[0] + p.d[1] * p.d[1] + p.d[2] * p.d[2]);
     if (!(p.r < a.rc_rad)) return false;
     p.tj = a.type[p.j];
-    const double ir = 1.0 / p.r;
+    const R ir = R(1.0) / p.r;
     for (int c = 0; c < 3; ++c) p.u[c] = p.d[c] * ir;
     return true;
 }
 
 // g_n = sum_k cA[ti][tj][n][k] Q_k (and g'_n with Q'_k)
-__device__ void angular_g(const F64Args& a, int ti, int tj, const double* f, const double* fp, double* g,
-                          double* gp) {
-    const double* cA = a.prm + a.L.off_cA + (size_t)(ti * a.T + tj) * a.NA * a.KA;
+template <class A, class R>
+__device__ void angular_g(const A& a, int ti, int tj, const R* f, const R* fp, R* g, R* gp) {
+    const R* cA = a.prm + a.L.off_cA + (size_t)(ti * a.T + tj) * a.NA * a.KA;
     for (int n = 0; n < a.NA; ++n) {
-        double u = 0.0, v = 0.0;
+        R u = R(0.0), v = R(0.0);
         for (int k = 0; k < a.KA; ++k) {
             u += cA[n * a.KA + k] * f[k];
             v += cA[n * a.KA + k] * fp[k];
@@ -150,10 +181,11 @@ __device__ void angular_g(const F64Args& a, int ti, int tj, const double* f, con
 }
 
 // g_n only (the descriptors need no derivative)
-__device__ void angular_g_value(const F64Args& a, int ti, int tj, const double* f, double* g) {
-    const double* cA = a.prm + a.L.off_cA + (size_t)(ti * a.T + tj) * a.NA * a.KA;
+template <class A, class R>
+__device__ void angular_g_value(const A& a, int ti, int tj, const R* f, R* g) {
+    const R* cA = a.prm + a.L.off_cA + (size_t)(ti * a.T + tj) * a.NA * a.KA;
     for (int n = 0; n < a.NA; ++n) {
-        double u = 0.0;
+        R u = R(0.0);
         for (int k = 0; k < a.KA; ++k) u += cA[n * a.KA + k] * f[k];
         g[n] = u;
     }
@@ -161,24 +193,24 @@ __device__ void angular_g_value(const F64Args& a, int ti, int tj, const double* 
 
 // q [D], S [NA*24] and the species-resolved radial basis sums F [T*KR] of
 // atom fr.i (the same values in every lane of its group)
-template <int G>
-__device__ void descriptors64(const F64Args& a, const Frame64& fr, int lane, double* q, double* S, double* F) {
+template <int G, class A, class R>
+__device__ void descriptors64(const A& a, const FrameT<R>& fr, int lane, R* q, R* S, R* F) {
     const int T = a.T, NR = a.NR, NA = a.NA, KR = a.KR, KA = a.KA;
-    double f[kF64MaxK], fp[kF64MaxK], g[kF64MaxN];
-    for (int x = 0; x < T * KR; ++x) F[x] = 0.0;
-    for (int x = 0; x < NA * kLM; ++x) S[x] = 0.0;
+    R f[kF64MaxK], fp[kF64MaxK], g[kF64MaxN];
+    for (int x = 0; x < T * KR; ++x) F[x] = R(0.0);
+    for (int x = 0; x < NA * kLM; ++x) S[x] = R(0.0);
     const int nc = a.cnt[fr.i];
     for (int s = lane; s < nc; s += G) {
-        Pair64 p;
+        PairT<R> p;
         if (!pair_at(a, fr, s, p)) continue;
-        basis64(p.r, a.rc_rad, KR, f, fp);
+        basis64(p.r, (R)a.rc_rad, KR, f, fp);
         for (int k = 0; k < KR; ++k) F[p.tj * KR + k] += f[k];
         if (!(p.r < a.rc_ang)) continue;
-        basis64(p.r, a.rc_ang, KA, f, fp);
+        basis64(p.r, (R)a.rc_ang, KA, f, fp);
         angular_g_value(a, fr.ti, p.tj, f, g);
-        const HarmTermsT<double> ht = harm_terms(p.u[0], p.u[1], p.u[2]);
+        const HarmTermsT<R> ht = harm_terms(p.u[0], p.u[1], p.u[2]);
         for (int m = 0; m < kLM; ++m) {
-            double Y, gx, gy, gz;
+            R Y, gx, gy, gz;
             harm_m(m, ht, Y, gx, gy, gz);
             for (int n = 0; n < NA; ++n) S[n * kLM + m] += g[n] * Y;
         }
@@ -186,21 +218,21 @@ __device__ void descriptors64(const F64Args& a, const Frame64& fr, int lane, dou
     for (int x = 0; x < T * KR; ++x) F[x] = group_sum<G>(F[x]);
     for (int x = 0; x < NA * kLM; ++x) S[x] = group_sum<G>(S[x]);
     // q_n = sum_t sum_k cR[ti][t][n][k] F[t][k]
-    const double* cR = a.prm + a.L.off_cR + (size_t)fr.ti * T * NR * KR;
+    const R* cR = a.prm + a.L.off_cR + (size_t)fr.ti * T * NR * KR;
     for (int n = 0; n < NR; ++n) {
-        double v = 0.0;
+        R v = R(0.0);
         for (int t = 0; t < T; ++t)
             for (int k = 0; k < KR; ++k) v += cR[(t * NR + n) * KR + k] * F[t * KR + k];
         q[n] = v;
     }
     // q_nl = sum_m C_lm S_nlm^2 and q4_n = tr(A_n^3)
     for (int n = 0; n < NA; ++n) {
-        for (int l = 0; l < 4; ++l) q[NR + n * 4 + l] = 0.0;
+        for (int l = 0; l < 4; ++l) q[NR + n * 4 + l] = R(0.0);
         for (int m = 0; m < kLM; ++m) {
-            const double v = S[n * kLM + m];
-            q[NR + n * 4 + lm_l(m) - 1] += (double)clm(m) * v * v;
+            const R v = S[n * kLM + m];
+            q[NR + n * 4 + lm_l(m) - 1] += (R)clm(m) * v * v;
         }
-        if (a.H4) q[NR + NA * 4 + n] = fourbody<double>(S + n * kLM + 3, nullptr);
+        if (a.H4) q[NR + NA * 4 + n] = fourbody<R>(S + n * kLM + 3, nullptr);
     }
 }
 
@@ -212,29 +244,30 @@ __global__ void k_promote(const float* src, double* dst, int n) {
 // ------------------------------------------------------------ evaluation
 // A warp's groups all belong to one block row; G divides 32 and kF64Block,
 // so no group straddles a warp.
-template <int G>
-__global__ void __launch_bounds__(kF64Block) k64_atom(const F64Args a) {
+template <int G, class A>
+__global__ void __launch_bounds__(kF64Block) k64_atom(const A a) {
+    using R = ScalarT<A>;
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) / G;
     const int lane = threadIdx.x % G;
     if (i >= a.N) return;
     const int N = a.N, NR = a.NR, NA = a.NA, H = a.H, D = a.D;
-    const Frame64 fr = frame64(a, i);
-    double q[kF64MaxD], S[kF64MaxN * kLM], F[kF64MaxTK];
+    const FrameT<R> fr = frame64(a, i);
+    R q[kF64MaxD], S[kF64MaxN * kLM], F[kF64MaxTK];
     descriptors64<G>(a, fr, lane, q, S, F);
     // network: E_i = w1 . tanh(W0 q + b0) + b1, dE/dq = W0^T (w1 (1 - t^2));
     // lane takes hidden units h = lane, lane + G, ...
-    const double* W0 = a.prm + (size_t)fr.ti * a.L.mlp_stride;
-    const double* b0 = W0 + (size_t)H * D;
-    const double* w1 = b0 + H;
-    double E = 0.0, pq[kF64MaxD];
-    for (int d = 0; d < D; ++d) pq[d] = 0.0;
+    const R* W0 = a.prm + (size_t)fr.ti * a.L.mlp_stride;
+    const R* b0 = W0 + (size_t)H * D;
+    const R* w1 = b0 + H;
+    R E = R(0.0), pq[kF64MaxD];
+    for (int d = 0; d < D; ++d) pq[d] = R(0.0);
     for (int h = lane; h < H; h += G) {
-        const double* w = W0 + (size_t)h * D;
-        double z = b0[h];
+        const R* w = W0 + (size_t)h * D;
+        R z = b0[h];
         for (int d = 0; d < D; ++d) z += w[d] * q[d];
-        const double th = tanh(z);
+        const R th = tanh_r(z);
         E += w1[h] * th;
-        const double c = w1[h] * (1.0 - th * th);
+        const R c = w1[h] * (R(1.0) - th * th);
         for (int d = 0; d < D; ++d) pq[d] += c * w[d];
     }
     E = group_sum<G>(E) + w1[H];
@@ -244,10 +277,10 @@ __global__ void __launch_bounds__(kF64Block) k64_atom(const F64Args a) {
     // R_nlm = dE/dq_nl 2 C_lm S_nlm (+ dE/dq4_n dq4_n/dS_n2m), entries split over lanes
     for (int x = lane; x < NA * kLM; x += G) {
         const int n = x / kLM, m = x % kLM;
-        double v = 2.0 * (double)clm(m) * pq[NR + n * 4 + lm_l(m) - 1] * S[x];
+        R v = R(2.0) * (R)clm(m) * pq[NR + n * 4 + lm_l(m) - 1] * S[x];
         if (a.H4 && m >= 3 && m < 8) {
-            double J[5];
-            fourbody<double>(S + n * kLM + 3, J);
+            R J[5];
+            fourbody<R>(S + n * kLM + 3, J);
             v += pq[NR + NA * 4 + n] * J[m - 3];
         }
         a.R[(size_t)x * N + i] = v;
@@ -256,14 +289,15 @@ __global__ void __launch_bounds__(kF64Block) k64_atom(const F64Args a) {
 
 // dE_o/dr_oj for owner o of species to, neighbour species tn, distance r and
 // unit vector u = r_oj / r
-__device__ void pair_deriv(const F64Args& a, int o, int to, int tn, double r, const double* u, double* fo) {
+template <class A, class R>
+__device__ void pair_deriv(const A& a, int o, int to, int tn, R r, const R* u, R* fo) {
     const int N = a.N, T = a.T, NR = a.NR, NA = a.NA, KR = a.KR, KA = a.KA;
-    double f[kF64MaxK], fp[kF64MaxK], g[kF64MaxN], gp[kF64MaxN];
-    basis64(r, a.rc_rad, KR, f, fp);
-    const double* cR = a.prm + a.L.off_cR + (size_t)(to * T + tn) * NR * KR;
-    double gr = 0.0;
+    R f[kF64MaxK], fp[kF64MaxK], g[kF64MaxN], gp[kF64MaxN];
+    basis64(r, (R)a.rc_rad, KR, f, fp);
+    const R* cR = a.prm + a.L.off_cR + (size_t)(to * T + tn) * NR * KR;
+    R gr = R(0.0);
     for (int n = 0; n < NR; ++n) {
-        double dg = 0.0;
+        R dg = R(0.0);
         for (int k = 0; k < KR; ++k) dg += cR[n * KR + k] * fp[k];
         gr += a.p[(size_t)n * N + o] * dg;
     }
@@ -271,19 +305,19 @@ __device__ void pair_deriv(const F64Args& a, int o, int to, int tn, double r, co
     fo[1] = gr * u[1];
     fo[2] = gr * u[2];
     if (!(r < a.rc_ang)) return;
-    basis64(r, a.rc_ang, KA, f, fp);
+    basis64(r, (R)a.rc_ang, KA, f, fp);
     angular_g(a, to, tn, f, fp, g, gp);
-    const HarmTermsT<double> ht = harm_terms(u[0], u[1], u[2]);
-    double Y[kLM], Gr[kLM][3];
+    const HarmTermsT<R> ht = harm_terms(u[0], u[1], u[2]);
+    R Y[kLM], Gr[kLM][3];
     for (int m = 0; m < kLM; ++m) harm_m(m, ht, Y[m], Gr[m][0], Gr[m][1], Gr[m][2]);
-    const double ir = 1.0 / r;
+    const R ir = R(1.0) / r;
     for (int n = 0; n < NA; ++n) {
         // d S_nlm / d r_oj = g'_n Y_m u + g_n (grad P_m - l P_m u) / r
-        double sY = 0.0, slY = 0.0, sg[3] = {0.0, 0.0, 0.0};
+        R sY = R(0.0), slY = R(0.0), sg[3] = {R(0.0), R(0.0), R(0.0)};
         for (int m = 0; m < kLM; ++m) {
-            const double Rv = a.R[(size_t)(n * kLM + m) * N + o];
+            const R Rv = a.R[(size_t)(n * kLM + m) * N + o];
             sY += Rv * Y[m];
-            slY += Rv * lm_l(m) * Y[m];
+            slY += Rv * (R)lm_l(m) * Y[m];
             sg[0] += Rv * Gr[m][0];
             sg[1] += Rv * Gr[m][1];
             sg[2] += Rv * Gr[m][2];
@@ -292,21 +326,22 @@ __device__ void pair_deriv(const F64Args& a, int o, int to, int tn, double r, co
     }
 }
 
-template <int G>
-__global__ void __launch_bounds__(kF64Block) k64_force(const F64Args a) {
+template <int G, class A>
+__global__ void __launch_bounds__(kF64Block) k64_force(const A a) {
+    using R = ScalarT<A>;
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) / G;
     const int lane = threadIdx.x % G;
     if (i >= a.N) return;
     const int N = a.N;
-    const Frame64 fr = frame64(a, i);
-    double F[3] = {0.0, 0.0, 0.0}, W[9];
-    for (int c = 0; c < 9; ++c) W[c] = 0.0;
+    const FrameT<R> fr = frame64(a, i);
+    R F[3] = {R(0.0), R(0.0), R(0.0)}, W[9];
+    for (int c = 0; c < 9; ++c) W[c] = R(0.0);
     const int nc = a.cnt[i];
     for (int s = lane; s < nc; s += G) {
-        Pair64 p;
+        PairT<R> p;
         if (!pair_at(a, fr, s, p)) continue;
-        const double v[3] = {-p.u[0], -p.u[1], -p.u[2]};
-        double fij[3], fji[3];
+        const R v[3] = {-p.u[0], -p.u[1], -p.u[2]};
+        R fij[3], fji[3];
         pair_deriv(a, i, fr.ti, p.tj, p.r, p.u, fij);
         pair_deriv(a, p.j, p.tj, fr.ti, p.r, v, fji);
         for (int c = 0; c < 3; ++c) F[c] += fij[c] - fji[c];
@@ -329,7 +364,8 @@ __device__ int segment_of(const int* off, int B, int x) {
 }
 
 // FP64 sums of E_i and W_i per 1,024-atom chunk: strided per-thread sums,
-// then warp shuffles and the warp sums in order
+// then warp shuffles and the warp sums in order; atoms from n_owned on are
+// left out (the owned prefix of a spatial decomposition's local system)
 constexpr int kF64Red = 256;
 __device__ double block_sum(double v, double* red) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -342,17 +378,18 @@ __device__ double block_sum(double v, double* red) {
     return s;
 }
 
-__global__ void __launch_bounds__(kF64Red) k64_chunk_reduce(const F64Args a) {
+template <class A>
+__global__ void __launch_bounds__(kF64Red) k64_chunk_reduce(const A a) {
     const int k = blockIdx.x, B = a.B, N = a.N;
     if (k >= a.chunk_start[B]) return;
     const int b = segment_of(a.chunk_start, B, k);
     const int a0 = a.atom_off[b] + (k - a.chunk_start[b]) * kChunk;
-    const int a1 = min(a.atom_off[b + 1], a0 + kChunk);
+    const int a1 = min(min(a.atom_off[b + 1], a0 + kChunk), a.n_owned);
     double acc[10];
     for (int c = 0; c < 10; ++c) acc[c] = 0.0;
     for (int i = a0 + threadIdx.x; i < a1; i += kF64Red) {
-        acc[0] += a.e[i];
-        for (int c = 0; c < 9; ++c) acc[1 + c] += a.w[(size_t)c * N + i];
+        acc[0] += (double)a.e[i];
+        for (int c = 0; c < 9; ++c) acc[1 + c] += (double)a.w[(size_t)c * N + i];
     }
     __shared__ double red[kF64Red / 32];
     for (int c = 0; c < 10; ++c) {
@@ -689,26 +726,38 @@ cudaError_t launch_promote(const float* src, double* dst, int n, cudaStream_t st
     return cudaGetLastError();
 }
 
-cudaError_t launch_efv_fp64(const F64Args& a, int max_chunks, double* e_tot, double* virial,
-                            cudaStream_t st) {
+namespace {
+template <class A>
+cudaError_t launch_efv_t(const A& a, int max_chunks, double* e_tot, double* virial, cudaStream_t st) {
     if (a.N > 0) {
         const int G = fp64_lanes_per_atom(a.N);
         const int grid = (int)(((long long)a.N * G + kF64Block - 1) / kF64Block);
         if (G == 1) {
-            k64_atom<1><<<grid, kF64Block, 0, st>>>(a);
-            k64_force<1><<<grid, kF64Block, 0, st>>>(a);
+            k64_atom<1, A><<<grid, kF64Block, 0, st>>>(a);
+            k64_force<1, A><<<grid, kF64Block, 0, st>>>(a);
         } else if (G == 8) {
-            k64_atom<8><<<grid, kF64Block, 0, st>>>(a);
-            k64_force<8><<<grid, kF64Block, 0, st>>>(a);
+            k64_atom<8, A><<<grid, kF64Block, 0, st>>>(a);
+            k64_force<8, A><<<grid, kF64Block, 0, st>>>(a);
         } else {
-            k64_atom<32><<<grid, kF64Block, 0, st>>>(a);
-            k64_force<32><<<grid, kF64Block, 0, st>>>(a);
+            k64_atom<32, A><<<grid, kF64Block, 0, st>>>(a);
+            k64_force<32, A><<<grid, kF64Block, 0, st>>>(a);
         }
     }
-    if (max_chunks > 0) k64_chunk_reduce<<<max_chunks, kF64Red, 0, st>>>(a);
+    if (max_chunks > 0) k64_chunk_reduce<A><<<max_chunks, kF64Red, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return launch_final_reduce(a.B, a.chunk_start, a.partial, e_tot, virial, st);
+}
+}  // namespace
+
+cudaError_t launch_efv_fp64(const F64Args& a, int max_chunks, double* e_tot, double* virial,
+                            cudaStream_t st) {
+    return launch_efv_t(a, max_chunks, e_tot, virial, st);
+}
+
+cudaError_t launch_efv_generic(const F32Args& a, int max_chunks, double* e_tot, double* virial,
+                               cudaStream_t st) {
+    return launch_efv_t(a, max_chunks, e_tot, virial, st);
 }
 
 cudaError_t launch_loss_fp64(const F64Args& a, int max_chunks, const double* e_tot, const double* vir,

@@ -169,6 +169,34 @@ cudaError_t launch_neighbors(const float* pos, const float4* pos4, const int* at
 constexpr int kF64MaxN = 16;      // n_rad, n_ang
 constexpr int kF64MaxK = 16;      // k_rad, k_ang
 constexpr int kF64MaxBins = 256;  // n_types * n_ang * k_ang (training gradient)
+// The generic FP32 evaluation (any hyper-parameters within the FP64 path's
+// bounds): the evaluation fields of F64Args, in float.  The FP64 path's
+// evaluation kernels are templates over the two.
+struct F32Args {
+    int N, B, T, NR, NA, KR, KA, H, H4, D;
+    ParamLayout L;
+    float rc_rad, rc_ang;
+    const float* pos;              // [3][N]
+    const int* type;               // [N]
+    const int* cfg;                // [N]
+    const float* box;              // [B][3]
+    const int* cnt;                // [N]
+    const int* nbr;                // [cap][N]
+    const int* shift;              // [cap][N] packed images, or null (minimum image)
+    const float* prm;              // [P]
+    float* e;                      // [N]     E_i
+    float* p;                      // [NR][N] dE_i/dq_n, radial n
+    float* R;                      // [NA*24][N] dE_i/dS_nlm
+    float* w;                      // [9][N]  per-atom virial
+    float* force;                  // [3][N]
+    const int* atom_off;           // [B+1]
+    const int* chunk_start;        // [B+1]
+    double* partial;               // [chunks][10]
+    int n_owned;                   // atoms [0, n_owned) enter the E and virial sums
+};
+cudaError_t launch_efv_generic(const F32Args& a, int max_chunks, double* e_tot, double* virial,
+                               cudaStream_t st);
+
 struct F64Args {
     int N, B, T, NR, NA, KR, KA, H, H4, D;
     ParamLayout L;
@@ -189,6 +217,7 @@ struct F64Args {
     const int* atom_off;           // [B+1]
     const int* chunk_start;        // [B+1]
     double* partial;               // [chunks][10]
+    int n_owned;                   // atoms [0, n_owned) enter the E and virial sums
     // training gradient
     const double* lam;             // [3][N] dL/dF
     const double* aE;              // [B]    dL/dE

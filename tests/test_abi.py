@@ -51,7 +51,13 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu(L):
     out = ctypes.c_void_p()
     assert L.nep_create(ctypes.byref(bad), None, 0, ctypes.byref(out)) == nb.NEP_ERR_ARG
     assert "l_max" in nb.last_error()
-    uns = nb.hparams_of(I.Hyper(n_rad=5))
+    gen = nb.hparams_of(I.Hyper(n_rad=5))                  # no kernel set: the generic FP32 path
+    assert L.nep_supported(ctypes.byref(gen)) == 2
+    assert L.nep_create(ctypes.byref(gen), None, 0, ctypes.byref(out)) == nb.NEP_ERR_ARG   # parameter count
+    gen16 = nb.hparams_of(I.Hyper(n_rad=5), precision=1)   # FP16 needs a kernel set
+    assert L.nep_supported(ctypes.byref(gen16)) == 0
+    assert L.nep_create(ctypes.byref(gen16), None, 0, ctypes.byref(out)) == nb.NEP_ERR_UNSUPPORTED
+    uns = nb.hparams_of(I.Hyper(n_rad=17))                 # beyond the generic bounds
     assert L.nep_supported(ctypes.byref(uns)) == 0
     assert L.nep_create(ctypes.byref(uns), None, 0, ctypes.byref(out)) == nb.NEP_ERR_UNSUPPORTED
     ok = nb.hparams_of(I.HYPER_SMALL)
