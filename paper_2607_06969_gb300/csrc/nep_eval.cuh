@@ -642,7 +642,9 @@ __device__ void angular_atom_tm(const EvalArgs& a, const float* sm, uint32_t tS,
 // stage (optional): this thread's slot of a [T*KR/4][nthr] float4 array in
 // shared memory; the atom's own adjoint rows are kept there instead of in
 // T*KR registers and read per pair for the neighbour's species
-template <class C, bool MINIMG>
+// COMPR: the training variant, which walks the compacted records of the
+// radial kernel instead of the list
+template <class C, bool MINIMG, bool COMPR>
 NEP_HD void radial_force_atom(const EvalArgs& a, int i, float& Fx, float& Fy, float& Fz, float* Wr,
                               float4* stage = nullptr, int nthr = 0) {
     constexpr int KR = C::KR, T = C::T;
@@ -730,7 +732,7 @@ NEP_HD void radial_force_atom(const EvalArgs& a, int i, float& Fx, float& Fy, fl
         Wr[0] = fmaf(wx, dx, Wr[0]); Wr[1] = fmaf(wy, dy, Wr[1]); Wr[2] = fmaf(wz, dz, Wr[2]);
         Wr[3] = fmaf(wx, dy, Wr[3]); Wr[4] = fmaf(wx, dz, Wr[4]); Wr[5] = fmaf(wy, dz, Wr[5]);
     };
-    if (a.compr) {
+    if (COMPR) {
         // pairs inside rc_rad, compacted by the radial kernel
         const int ncr = a.cnt_compr[i];
         float4 q_nx = ncr > 0 ? a.compr[i] : make_float4(1.0f, 0.0f, 0.0f, 0.0f);
@@ -842,13 +844,13 @@ NEP_HD void radial_force_atom(const EvalArgs& a, int i, float& Fx, float& Fy, fl
 // angular pair forces (subtracted inside radial_force_atom); the per-atom
 // virial (angular owner part minus the radial part) is written back for the
 // per-configuration reduction
-template <class C, bool MINIMG>
+template <class C, bool MINIMG, bool COMPR>
 NEP_HD void finish_atom(const EvalArgs& a, int i, float* force, float* e_out, float4* stage = nullptr,
                         int nthr = 0) {
     const int N = a.N;
     float Fx = a.fpart[i], Fy = a.fpart[N + i], Fz = a.fpart[2 * N + i];
     float Wr[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-    radial_force_atom<C, MINIMG>(a, i, Fx, Fy, Fz, Wr, stage, nthr);
+    radial_force_atom<C, MINIMG, COMPR>(a, i, Fx, Fy, Fz, Wr, stage, nthr);
     force[i] = Fx;
     force[N + i] = Fy;
     force[2 * N + i] = Fz;
@@ -977,15 +979,15 @@ inline int persistent_grid(int ntiles, int per_sm) {
     return ntiles < g ? ntiles : g;
 }
 
-template <class C, bool MINIMG, int BLOCK = kFinishThreads>
+template <class C, bool MINIMG, int BLOCK = kFinishThreads, bool COMPR = false>
 __global__ void __launch_bounds__(BLOCK, NEP_FINISH_MINB * kFinishThreads / BLOCK) k_finish(const EvalArgs a, float* force, float* e_out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
 #if NEP_FINISH_STAGE
     constexpr int kChunks = (C::KR % 4 == 0) ? C::T * C::KR / 4 : 1;
     __shared__ float4 stage[kChunks * BLOCK];
-    if (i < a.N) finish_atom<C, MINIMG>(a, i, force, e_out, stage + threadIdx.x, BLOCK);
+    if (i < a.N) finish_atom<C, MINIMG, COMPR>(a, i, force, e_out, stage + threadIdx.x, BLOCK);
 #else
-    if (i < a.N) finish_atom<C, MINIMG>(a, i, force, e_out);
+    if (i < a.N) finish_atom<C, MINIMG, COMPR>(a, i, force, e_out);
 #endif
 }
 
@@ -1054,11 +1056,18 @@ void launch_finish_b(const EvalArgs& a, const FinishArgs& f, cudaStream_t st) {
         k_finish<C, false, BLOCK><<<grid, BLOCK, 0, st>>>(a, f.force, f.e_out);
 }
 
-// block: one of kBlockChoices, 0 for the default
+// block: one of kBlockChoices, 0 for the default; the training variant
+// (compacted records) always runs at the default block
 template <class C>
 cudaError_t launch_finish_t(const EvalArgs& a, const FinishArgs& f, int max_chunks, cudaStream_t st, int block) {
     if (a.N > 0) {
-        if (block == 64)
+        if (a.compr) {
+            const int grid = (a.N + kFinishThreads - 1) / kFinishThreads;
+            if (a.min_image)
+                k_finish<C, true, kFinishThreads, true><<<grid, kFinishThreads, 0, st>>>(a, f.force, f.e_out);
+            else
+                k_finish<C, false, kFinishThreads, true><<<grid, kFinishThreads, 0, st>>>(a, f.force, f.e_out);
+        } else if (block == 64)
             launch_finish_b<C, 64>(a, f, st);
         else if (block == 256)
             launch_finish_b<C, 256>(a, f, st);
