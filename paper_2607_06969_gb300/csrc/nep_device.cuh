@@ -57,6 +57,26 @@ NEP_HD float sqrt_f(float x) {
     return (float)std::sqrt((double)x);
 #endif
 }
+// Distance r and 1/r of a pair from d2 = |r_ij|^2 > 0: one reciprocal
+// square root (rsqrtf, within 2 ulp) and a product on the device, in place
+// of a correctly rounded square root and reciprocal (2.8% of an evaluation
+// at 900k atoms, measured; the results stay within the FP32 parity bars).
+NEP_HD void dist_rinv(float d2, float& r, float& ir) {
+#if defined(__CUDA_ARCH__)
+    ir = rsqrtf(d2);
+    r = d2 * ir;
+#else
+    r = sqrt_f(d2);
+    ir = rcp_f(r);
+#endif
+}
+NEP_HD float dist_r(float d2) {
+#if defined(__CUDA_ARCH__)
+    return d2 * rsqrtf(d2);
+#else
+    return sqrt_f(d2);
+#endif
+}
 NEP_HD float rint_f(float x) {
 #if defined(__CUDA_ARCH__)
     return rintf(x);

@@ -214,7 +214,7 @@ NEP_HD void radial_atom(const EvalArgs& a, int i) {
                 ++nr;
             }
             float f[KR];
-            basis<KR>(sqrt_f(d2), irR, f);
+            basis<KR>(dist_r(d2), irR, f);
 #pragma unroll
             for (int t = 0; t < T; ++t) {
                 const float w = (tj == t) ? 1.0f : 0.0f;
@@ -311,8 +311,8 @@ NEP_HD void angular_S(const EvalArgs& a, const float* sm, const SmemLayout& sl, 
         const float4 e = e_nx;
         if (c + 1 < nc) e_nx = a.comp[(c + 1) * N + i];
         const int tj = f2i(e.w) & 3;
-        const float r = sqrt_f(dist2(e.x, e.y, e.z));
-        const float ir = rcp_f(r);
+        float r, ir;
+        dist_rinv(dist2(e.x, e.y, e.z), r, ir);
         float f[KA];
         basis<KA>(r, irA, f);
         const float* cc = sm + sl.cA + (ti * T + tj) * C::SA;
@@ -401,8 +401,8 @@ NEP_HD void angular_force(const EvalArgs& a, const float* sm, const SmemLayout& 
         const int bits = f2i(e.w);
         const int tj = bits & 3;
         const int addr = (int)((unsigned)bits >> 2);
-        const float r = sqrt_f(dist2(e.x, e.y, e.z));
-        const float ir = rcp_f(r);
+        float r, ir;
+        dist_rinv(dist2(e.x, e.y, e.z), r, ir);
         float g[NA], gp[NA];
         {
             float f[KA], fp[KA];
@@ -683,8 +683,8 @@ NEP_HD void radial_force_atom(const EvalArgs& a, int i, float& Fx, float& Fy, fl
     // one pair: both directions of the radial force along r_ij, and the
     // owner's symmetric radial virial
     auto pair = [&](int j, int tj, float dx, float dy, float dz, float d2) {
-        const float r = sqrt_f(d2);
-        const float ir = rcp_f(r);
+        float r, ir;
+        dist_rinv(d2, r, ir);
         float f[KR], fp[KR];
         basis_d<KR>(r, irR, f, fp);
         float Pj[KR];
