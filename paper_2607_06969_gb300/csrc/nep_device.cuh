@@ -96,6 +96,18 @@ NEP_HD void load8_ro(const float* p, float* v) {
 #endif
 }
 
+// Two independent FP32 FMAs in one paired instruction on the device
+// (a.x * b.x + c.x, a.y * b.y + c.y, each rounded once as fmaf rounds it):
+// pairing two accumulation chains leaves every result bit unchanged and
+// halves the instructions the chains issue.
+NEP_HD float2 ffma2(float2 a, float2 b, float2 c) {
+#if defined(__CUDA_ARCH__)
+    return __ffma2_rn(a, b, c);
+#else
+    return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
+#endif
+}
+
 // index of the lowest set bit of a non-zero word
 NEP_HD int low_bit(unsigned long long m) {
 #if defined(__CUDA_ARCH__)

@@ -327,12 +327,22 @@ NEP_HD void angular_S(const EvalArgs& a, const float* sm, const SmemLayout& sl, 
             g[n] = acc;
         }
         const HarmTerms ht = harm_terms(e.x * ir, e.y * ir, e.z * ir);
+        // S[n][m] += g_n Y_m, two m at a time (paired FMAs)
+        float2 gb[NA];
 #pragma unroll
-        for (int m = 0; m < kLM; ++m) {
-            float Y, gx, gy, gz;
-            harm_m(m, ht, Y, gx, gy, gz);
+        for (int n = 0; n < NA; ++n) gb[n] = make_float2(g[n], g[n]);
 #pragma unroll
-            for (int n = 0; n < NA; ++n) S[n][m] = fmaf(g[n], Y, S[n][m]);
+        for (int m = 0; m < kLM; m += 2) {
+            float Y0, Y1, gx, gy, gz;
+            harm_m(m, ht, Y0, gx, gy, gz);
+            harm_m(m + 1, ht, Y1, gx, gy, gz);
+            const float2 y2 = make_float2(Y0, Y1);
+#pragma unroll
+            for (int n = 0; n < NA; ++n) {
+                const float2 s2 = ffma2(gb[n], y2, make_float2(S[n][m], S[n][m + 1]));
+                S[n][m] = s2.x;
+                S[n][m + 1] = s2.y;
+            }
         }
     }
 }
@@ -424,20 +434,33 @@ NEP_HD void angular_force(const EvalArgs& a, const float* sm, const SmemLayout& 
         }
         const HarmTerms ht = harm_terms(e.x * ir, e.y * ir, e.z * ir);
         float rad = 0.0f, Gx = 0.0f, Gy = 0.0f, Gz = 0.0f;
+        // a_m and b_m two m at a time (paired FMAs, each chain in n order)
+        float2 gb[NA], gpb[NA];
 #pragma unroll
-        for (int m = 0; m < kLM; ++m) {
-            float am = 0.0f, bm = 0.0f;
+        for (int n = 0; n < NA; ++n) {
+            gb[n] = make_float2(g[n], g[n]);
+            gpb[n] = make_float2(gp[n], gp[n]);
+        }
+#pragma unroll
+        for (int m0 = 0; m0 < kLM; m0 += 2) {
+            float2 am2 = make_float2(0.0f, 0.0f), bm2 = make_float2(0.0f, 0.0f);
 #pragma unroll
             for (int n = 0; n < NA; ++n) {
-                am = fmaf(Sb[n][m], g[n], am);
-                bm = fmaf(Sb[n][m], gp[n], bm);
+                const float2 s2 = make_float2(Sb[n][m0], Sb[n][m0 + 1]);
+                am2 = ffma2(s2, gb[n], am2);
+                bm2 = ffma2(s2, gpb[n], bm2);
             }
-            float Y, hx, hy, hz;
-            harm_m(m, ht, Y, hx, hy, hz);
-            rad = fmaf(fmaf(-(float)lm_l(m) * ir, am, bm), Y, rad);
-            Gx = fmaf(am, hx, Gx);
-            Gy = fmaf(am, hy, Gy);
-            Gz = fmaf(am, hz, Gz);
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int m = m0 + u;
+                const float am = u ? am2.y : am2.x, bm = u ? bm2.y : bm2.x;
+                float Y, hx, hy, hz;
+                harm_m(m, ht, Y, hx, hy, hz);
+                rad = fmaf(fmaf(-(float)lm_l(m) * ir, am, bm), Y, rad);
+                Gx = fmaf(am, hx, Gx);
+                Gy = fmaf(am, hy, Gy);
+                Gz = fmaf(am, hz, Gz);
+            }
         }
         const float fx = fmaf(ht.x, rad, Gx * ir);
         const float fy = fmaf(ht.y, rad, Gy * ir);
@@ -469,15 +492,24 @@ NEP_HD void network(const EvalArgs& a, const float* sm, const SmemLayout& sl, in
     for (int h = 0; h < a.H; ++h) {
         float w[DW];
         load_row<DW>(W0 + h * DW, w);
-        float z = b0[h];
+        // W0 q as two interleaved partial sums (even and odd d) in paired FMAs
+        float2 z2 = make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int d = 0; d < DW; ++d) z = fmaf(w[d], qv[d], z);
+        for (int d = 0; d < DW; d += 2)
+            z2 = ffma2(make_float2(w[d], w[d + 1]), make_float2(qv[d], qv[d + 1]), z2);
+        const float z = b0[h] + (z2.x + z2.y);
         const float t = tanh_f(z);
         const float wh = w1[h];
         E = fmaf(wh, t, E);
         const float sg = wh * (1.0f - t * t);
+        const float2 sg2 = make_float2(sg, sg);
+        static_assert(DW % 2 == 0, "W0 rows are padded to a multiple of 4");
 #pragma unroll
-        for (int d = 0; d < DW; ++d) pv[d] = fmaf(sg, w[d], pv[d]);
+        for (int d = 0; d < DW; d += 2) {
+            const float2 v = ffma2(sg2, make_float2(w[d], w[d + 1]), make_float2(pv[d], pv[d + 1]));
+            pv[d] = v.x;
+            pv[d + 1] = v.y;
+        }
     }
 #pragma unroll
     for (int d = 0; d < D; ++d) p[d] = pv[d];
