@@ -51,6 +51,7 @@ struct Cfg {
     static constexpr int D = NR + NA * 4 + (H4 ? NA : 0);
     static constexpr int NP = NA * (4 + (H4 ? 1 : 0));   // angular + 4-body descriptor count
     static constexpr int SA = stride4(NA * KA);          // per-species-pair stride
+    static_assert((NA + NA % 2) * KA <= SA, "the row-paired angular block fits the stride");
     static constexpr int SR = stride4(NR * KR);
     static constexpr int DW = round4(D);                  // row stride of W0 (zero padded)
 };
@@ -58,7 +59,7 @@ struct Cfg {
 // Shared-memory image of the model, padded so that the (up to 9) species
 // pairs or 3 species met by one warp fall in distinct banks.
 struct SmemLayout {
-    int cA, cR, W0, b0, w1, b1, total;
+    int cA, cA2, cR, W0, b0, w1, b1, total;
     int SW, HS;
 };
 
@@ -68,13 +69,48 @@ NEP_HD SmemLayout smem_layout(int H) {
     s.SW = stride4(H * C::DW);
     s.HS = (H % 2) ? H : H + 1;
     s.cA = 0;
-    s.cR = s.cA + C::T * C::T * C::SA;
+    s.cA2 = s.cA + C::T * C::T * C::SA;   // cA again, rows paired: (c[2p][k], c[2p+1][k])
+    s.cR = s.cA2 + C::T * C::T * C::SA;
     s.W0 = s.cR + C::T * C::T * C::SR;
     s.b0 = s.W0 + C::T * s.SW;
     s.w1 = s.b0 + C::T * s.HS;
     s.b1 = s.w1 + C::T * s.HS;
     s.total = s.b1 + C::T;
     return s;
+}
+
+// Position of c[n][k] in a row-paired coefficient block: rows 2p and 2p+1
+// interleaved, (c[2p][k], c[2p+1][k]) at 2 (p K + k); an odd last row pairs
+// with zeros.
+template <int K>
+NEP_HD int pair_index(int n, int k) { return 2 * ((n / 2) * K + k) + (n % 2); }
+
+// g[n] = sum_k c[n][k] f[k] for n < NA from a row-paired block c2, two rows
+// per paired FMA: each g[n] is the same chain, in the same k order, as a
+// scalar loop over its row
+template <int NA, int K>
+NEP_HD void contract_pairs(const float* c2, const float* f, float* g) {
+    float2 fb[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) fb[k] = make_float2(f[k], f[k]);
+#pragma unroll
+    for (int p = 0; p < (NA + 1) / 2; ++p) {
+        float2 acc = make_float2(0.0f, 0.0f);
+        const float* row = c2 + 2 * p * K;
+        if (K % 2 == 0) {
+#pragma unroll
+            for (int k = 0; k < K; k += 2) {
+                const float4 v = ld4(row + 2 * k);
+                acc = ffma2(make_float2(v.x, v.y), fb[k], acc);
+                acc = ffma2(make_float2(v.z, v.w), fb[k + 1], acc);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc = ffma2(*reinterpret_cast<const float2*>(row + 2 * k), fb[k], acc);
+        }
+        g[2 * p] = acc.x;
+        if (2 * p + 1 < NA) g[2 * p + 1] = acc.y;
+    }
 }
 
 // Fill the padded model image from the flat parameter vector; thread `tid`
@@ -87,7 +123,11 @@ NEP_HD void load_model(float* sm, const float* prm, int H, int tid, int nthr) {
     for (int x = tid; x < nA; x += nthr) {
         int pair = x / (C::NA * C::KA), r = x % (C::NA * C::KA);
         sm[s.cA + pair * C::SA + r] = prm[L.off_cA + x];
+        sm[s.cA2 + pair * C::SA + pair_index<C::KA>(r / C::KA, r % C::KA)] = prm[L.off_cA + x];
     }
+    if (C::NA % 2)   // the partner of an odd last row is zero
+        for (int x = tid; x < C::T * C::T * C::KA; x += nthr)
+            sm[s.cA2 + (x / C::KA) * C::SA + pair_index<C::KA>(C::NA, x % C::KA)] = 0.0f;
     const int nR = C::T * C::T * C::NR * C::KR;
     for (int x = tid; x < nR; x += nthr) {
         int pair = x / (C::NR * C::KR), r = x % (C::NR * C::KR);
@@ -315,17 +355,8 @@ NEP_HD void angular_S(const EvalArgs& a, const float* sm, const SmemLayout& sl, 
         dist_rinv(dist2(e.x, e.y, e.z), r, ir);
         float f[KA];
         basis<KA>(r, irA, f);
-        const float* cc = sm + sl.cA + (ti * T + tj) * C::SA;
         float g[NA];
-#pragma unroll
-        for (int n = 0; n < NA; ++n) {
-            float cv[KA];
-            load_row<KA>(cc + n * KA, cv);
-            float acc = 0.0f;
-#pragma unroll
-            for (int k = 0; k < KA; ++k) acc = fmaf(cv[k], f[k], acc);
-            g[n] = acc;
-        }
+        contract_pairs<NA, KA>(sm + sl.cA2 + (ti * T + tj) * C::SA, f, g);
         const HarmTerms ht = harm_terms(e.x * ir, e.y * ir, e.z * ir);
         // S[n][m] += g_n Y_m, two m at a time (paired FMAs)
         float2 gb[NA];
@@ -417,20 +448,9 @@ NEP_HD void angular_force(const EvalArgs& a, const float* sm, const SmemLayout& 
         {
             float f[KA], fp[KA];
             basis_d<KA>(r, irA, f, fp);
-            const float* cc = sm + sl.cA + (ti * T + tj) * C::SA;
-#pragma unroll
-            for (int n = 0; n < NA; ++n) {
-                float cv[KA];
-                load_row<KA>(cc + n * KA, cv);
-                float u = 0.0f, v = 0.0f;
-#pragma unroll
-                for (int k = 0; k < KA; ++k) {
-                    u = fmaf(cv[k], f[k], u);
-                    v = fmaf(cv[k], fp[k], v);
-                }
-                g[n] = u;
-                gp[n] = v;
-            }
+            const float* c2 = sm + sl.cA2 + (ti * T + tj) * C::SA;
+            contract_pairs<NA, KA>(c2, f, g);
+            contract_pairs<NA, KA>(c2, fp, gp);
         }
         const HarmTerms ht = harm_terms(e.x * ir, e.y * ir, e.z * ir);
         float rad = 0.0f, Gx = 0.0f, Gy = 0.0f, Gz = 0.0f;

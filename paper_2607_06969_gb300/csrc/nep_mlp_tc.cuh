@@ -143,6 +143,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_angular_tc(const EvalArgs a) {
         for (int x = tid; x < nA; x += kBlock) {
             const int pair = x / (NA * C::KA), r = x % (NA * C::KA);
             sm[sl.cA + pair * C::SA + r] = a.params[PL.off_cA + x];
+            sm[sl.cA2 + pair * C::SA + pair_index<C::KA>(r / C::KA, r % C::KA)] = a.params[PL.off_cA + x];
         }
         const int nR = T * T * NR * KR;
         for (int x = tid; x < nR; x += kBlock) {
