@@ -258,8 +258,14 @@ NEP_HD void radial_atom(const EvalArgs& a, int i) {
 #pragma unroll
             for (int t = 0; t < T; ++t) {
                 const float w = (tj == t) ? 1.0f : 0.0f;
+                const float2 w2 = make_float2(w, w);
 #pragma unroll
-                for (int k = 0; k < KR; ++k) fb[t][k] = fmaf(w, f[k], fb[t][k]);
+                for (int k = 0; k + 1 < KR; k += 2) {
+                    const float2 v = ffma2(w2, make_float2(f[k], f[k + 1]), make_float2(fb[t][k], fb[t][k + 1]));
+                    fb[t][k] = v.x;
+                    fb[t][k + 1] = v.y;
+                }
+                if (KR % 2) fb[t][KR - 1] = fmaf(w, f[KR - 1], fb[t][KR - 1]);
             }
         }
         if (s < cnt_ang) {
