@@ -103,6 +103,15 @@ __device__ __forceinline__ __half to_in<__half>(float x) { return __float2half_r
 template <>
 __device__ __forceinline__ __nv_bfloat16 to_in<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
 
+// tanh on the SFU (tanh.approx.f32, relative error about 2^-11): the
+// mixed-precision network's operands are 16-bit, whose rounding (2^-11 for
+// FP16, 2^-8 for BF16) already sets the scale of its error
+__device__ __forceinline__ float tanh_sfu(float x) {
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // polls of an mbarrier before the kernel gives up (flags status[3] bit 1)
 constexpr int kMbarPolls = 1 << 20;
 // largest hidden width of the mixed-precision network (g of one row in registers)
@@ -299,8 +308,8 @@ __global__ void __launch_bounds__(kBlock, MINB) k_angular_tc(const EvalArgs a) {
 #pragma unroll
                         for (int j = 0; j < 16; j += 2) {   // b0 and w1 are zero for h >= H
                             const int h = c + j;
-                            const float t0 = tanh_f(z[j] + b0s[s * Hp + h]);
-                            const float t1 = tanh_f(z[j + 1] + b0s[s * Hp + h + 1]);
+                            const float t0 = tanh_sfu(z[j] + b0s[s * Hp + h]);
+                            const float t1 = tanh_sfu(z[j + 1] + b0s[s * Hp + h + 1]);
                             const float w0 = w1s[s * Hp + h], w1v = w1s[s * Hp + h + 1];
                             E = fmaf(w0, t0, E);
                             E = fmaf(w1v, t1, E);
