@@ -434,7 +434,10 @@ NEP_HD void make_Sb(float (&Sb)[C::NA][kLM], GetS S, GetP pl) {
 
 // angular pair forces: f_ij = u sum_m (b_m - l a_m / r) Y_m + (1/r) sum_m a_m grad P_m(u),
 // a_m = sum_n Sb[n][m] g_n, b_m = sum_n Sb[n][m] g'_n; owner sums and reverse-slot scatter
-template <class C>
+// SPLIT: sum (b_m - l a_m / r) Y_m and a_m grad P_m as even and odd partial
+// sums over m, one paired FMA per pair of m (measured faster in the
+// tensor-core kernel, slower in the FP32 one)
+template <class C, bool SPLIT = false>
 NEP_HD void angular_force(const EvalArgs& a, const float* sm, const SmemLayout& sl, int ti, int i,
                           const float (&Sb)[C::NA][kLM], float& Fx, float& Fy, float& Fz, float* W) {
     constexpr int NA = C::NA, KA = C::KA, T = C::T;
@@ -460,6 +463,7 @@ NEP_HD void angular_force(const EvalArgs& a, const float* sm, const SmemLayout& 
         }
         const HarmTerms ht = harm_terms(e.x * ir, e.y * ir, e.z * ir);
         float rad = 0.0f, Gx = 0.0f, Gy = 0.0f, Gz = 0.0f;
+        float2 rad2 = make_float2(0.0f, 0.0f), gx2 = rad2, gy2 = rad2, gz2 = rad2;
         // a_m and b_m two m at a time (paired FMAs, each chain in n order)
         float2 gb[NA], gpb[NA];
 #pragma unroll
@@ -476,6 +480,17 @@ NEP_HD void angular_force(const EvalArgs& a, const float* sm, const SmemLayout& 
                 am2 = ffma2(s2, gb[n], am2);
                 bm2 = ffma2(s2, gpb[n], bm2);
             }
+            if (SPLIT) {
+                float Y0, hx0, hy0, hz0, Y1, hx1, hy1, hz1;
+                harm_m(m0, ht, Y0, hx0, hy0, hz0);
+                harm_m(m0 + 1, ht, Y1, hx1, hy1, hz1);
+                const float2 cl = make_float2(-(float)lm_l(m0) * ir, -(float)lm_l(m0 + 1) * ir);
+                rad2 = ffma2(ffma2(cl, am2, bm2), make_float2(Y0, Y1), rad2);
+                gx2 = ffma2(am2, make_float2(hx0, hx1), gx2);
+                gy2 = ffma2(am2, make_float2(hy0, hy1), gy2);
+                gz2 = ffma2(am2, make_float2(hz0, hz1), gz2);
+                continue;
+            }
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
                 const int m = m0 + u;
@@ -487,6 +502,12 @@ NEP_HD void angular_force(const EvalArgs& a, const float* sm, const SmemLayout& 
                 Gy = fmaf(am, hy, Gy);
                 Gz = fmaf(am, hz, Gz);
             }
+        }
+        if (SPLIT) {
+            rad = rad2.x + rad2.y;
+            Gx = gx2.x + gx2.y;
+            Gy = gy2.x + gy2.y;
+            Gz = gz2.x + gz2.y;
         }
         const float fx = fmaf(ht.x, rad, Gx * ir);
         const float fy = fmaf(ht.y, rad, Gy * ir);

@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_angular_tc(const EvalArgs a) {
             float W[9];
 #pragma unroll
             for (int k = 0; k < 9; ++k) W[k] = 0.0f;
-            angular_force<C>(a, sm, sl, ti, i, Sb, Fx, Fy, Fz, W);
+            angular_force<C, true>(a, sm, sl, ti, i, Sb, Fx, Fy, Fz, W);
             a.fpart[i] = Fx;
             a.fpart[N + i] = Fy;
             a.fpart[2 * N + i] = Fz;
