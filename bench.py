@@ -144,9 +144,9 @@ def algorithmic_flops(h, nbar_rad: float, nbar_ang: float) -> dict:
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the 460,800-atom
 # case of this workload (40^3 cells), divided by its atom count; traffic grows
 # in proportion to the atoms.  Valid only for the kernels as captured.
-TRAFFIC_PER_ATOM = {"radial": (243.147776e6 + 196.002304e6) / 460800,
-                    "angular": (287.553024e6 + 213.986560e6) / 460800,
-                    "finish": (387.718912e6 + 21.293568e6) / 460800}
+TRAFFIC_PER_ATOM = {"radial": (241.651456e6 + 197.628416e6) / 460800,
+                    "angular": (288.541184e6 + 214.722560e6) / 460800,
+                    "finish": (387.748608e6 + 19.879936e6) / 460800}
 
 
 def launches_per_step(rebuild: bool) -> int:
