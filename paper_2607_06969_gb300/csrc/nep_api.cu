@@ -69,7 +69,7 @@ struct WsLayout {
     size_t rin, rin_sh, cnt_rin;
     size_t amask;
     size_t gen_p, gen_R, gen_w;   // generic FP32 path: dE/dq (radial), dE/dS, per-atom virial
-    size_t plan, cell_of, rank, cell_cnt, cell_start, cell_atoms, scan_tmp, shell, row_start, slot_row;
+    size_t plan, cell_of, rank, cell_cnt, cell_start, cell_atoms, cell_pos, scan_tmp, shell, row_start, slot_row;
     size_t total;
     int max_chunks, cmax;
 };
@@ -117,6 +117,7 @@ WsLayout ws_layout(const nep_model* m, int N, int B, int cap, int cap_ang) {
     w.cell_cnt = take(4 * ((size_t)w.cmax + 1));
     w.cell_start = take(4 * ((size_t)w.cmax + 1));
     w.cell_atoms = take(4 * n);
+    w.cell_pos = take(16 * n);
     const size_t ntiles = ((size_t)w.cmax + 1 + 2047) / 2048;
     w.scan_tmp = take(4 * (ntiles + 1));
     w.shell = take(8 * n * (size_t)cap);
@@ -554,6 +555,7 @@ nep_status neighbors_impl(nep_model* m, const nep_system* s, float skin, nep_nli
     nw.cell_cnt = at<int>(work, w.cell_cnt);
     nw.cell_start = at<int>(work, w.cell_start);
     nw.cell_atoms = at<int>(work, w.cell_atoms);
+    nw.cell_pos = at<float4>(work, w.cell_pos);
     nw.scan_tmp = at<int>(work, w.scan_tmp);
     nw.shell = at<int2>(work, w.shell);
     nw.row_start = at<unsigned char>(work, w.row_start);

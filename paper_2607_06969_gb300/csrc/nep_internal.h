@@ -152,6 +152,7 @@ struct NbrWork {
     int* cell_cnt;         // [Cmax]
     int* cell_start;       // [Cmax+1]
     int* cell_atoms;       // [N]
+    float4* cell_pos;      // [N] positions in cell order, atom index bits in w
     int* scan_tmp;         // [ceil(Cmax/2048)+1]
     int2* shell;           // [cap][N] scratch for the list entries beyond rc_rad
     unsigned char* row_start;   // [N][32] where each stencil row's angular entries start

@@ -333,8 +333,11 @@ __global__ void k_fill(const int* __restrict__ cell_of, const int* __restrict__ 
 }
 
 // order each cell's atoms by index so that lists do not depend on the order
-// in which atomics handed out ranks
-__global__ void k_sort_cells(const int* __restrict__ cell_start, int ncell, int* cell_atoms) {
+// in which atomics handed out ranks, then write the positions in that order
+// (x, y, z, atom index as bits): the list build reads a row's candidates as
+// one contiguous range, with no dependent index load
+__global__ void k_sort_cells(const int* __restrict__ cell_start, int ncell, int* cell_atoms,
+                             const float4* __restrict__ pos4, float4* __restrict__ cell_pos) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
     const int s0 = cell_start[c], s1 = cell_start[c + 1];
@@ -346,6 +349,11 @@ __global__ void k_sort_cells(const int* __restrict__ cell_start, int ncell, int*
             --b;
         }
         cell_atoms[b + 1] = v;
+    }
+    for (int a = s0; a < s1; ++a) {
+        const int j = cell_atoms[a];
+        const float4 q = pos4[j];
+        cell_pos[a] = make_float4(q.x, q.y, q.z, i2f(j));
     }
 }
 
@@ -365,9 +373,9 @@ __device__ __forceinline__ int floor_div(int a, int b) {
 // cutoff for all of its lanes and skip the pair work together.
 //
 // The stencil is visited row by row: for each (ox, oy) the cells oz =
-// -half..half are consecutive cell ids (one range of the sorted atom array)
-// except where they wrap around the box, which splits the row in two ranges
-// with different z images.  The visit order is that of the cell triple loop.
+// -half..half are consecutive cell ids (one range of the cell-ordered
+// positions, which carry the atom index) except where they wrap around the
+// box, which splits the row in two ranges with different z images.  The visit order is that of the cell triple loop.
 // For the reverse-slot search the kernel also records, per atom, where each
 // row's angular entries start (row_start) and, per angular slot, its row.
 __global__ void __launch_bounds__(128) k_build(const float4* __restrict__ pos4,
@@ -376,7 +384,7 @@ __global__ void __launch_bounds__(128) k_build(const float4* __restrict__ pos4,
                                                const CellPlan* __restrict__ plan,
                                                const int* __restrict__ cell_of,
                                                const int* __restrict__ cell_start,
-                                               const int* __restrict__ cell_atoms, int N,
+                                               const float4* __restrict__ cell_pos, int N,
                                                float rc2_rad, float rc2_ang, float rc2_phys,
                                                int2* __restrict__ shell, unsigned char* __restrict__ row_start,
                                                unsigned char* __restrict__ slot_row, nep_nlist nl) {
@@ -437,38 +445,37 @@ __global__ void __launch_bounds__(128) k_build(const float4* __restrict__ pos4,
                 const bool zero_img = (sx == 0 && sy == 0 && sz == 0);
                 const int sh = pack_shift(sx, sy, sz);
                 const int q0 = cell_start[rowcell + wz0], q1 = cell_start[rowcell + wz1 + 1];
-                // candidates' indices two ahead, positions one ahead
-                int j_nx = q0 < q1 ? cell_atoms[q0] : 0;
-                int j_nx2 = q0 + 1 < q1 ? cell_atoms[q0 + 1] : 0;
-                float4 p_nx = pos4[j_nx];
+                // candidates one ahead
+                float4 c_nx = q0 < q1 ? cell_pos[q0] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                 for (int q = q0; q < q1; ++q) {
-                    const int j = j_nx;
-                    const float4 pj = p_nx;
-                    if (q + 1 < q1) {
-                        j_nx = j_nx2;
-                        p_nx = pos4[j_nx];
-                        if (q + 2 < q1) j_nx2 = cell_atoms[q + 2];
-                    }
+                    const float4 pj = c_nx;
+                    if (q + 1 < q1) c_nx = cell_pos[q + 1];
+                    const int j = f2i(pj.w);
                     if (j == i && zero_img) continue;
                     const float dx = add_rn(sub_rn(pj.x, pi.x), fx);
                     const float dy = add_rn(sub_rn(pj.y, pi.y), fy);
                     const float dz = add_rn(sub_rn(pj.z, pi.z), fz);
                     const float d2 = dist2(dx, dy, dz);
                     if (!(d2 < rc2_rad)) continue;
-                    if (d2 < rc2_ang) {
-                        const int slot = n_ang < cap_ang && n_ang + n_in < cap ? n_ang : -1;
-                        ++n_ang;
-                        if (slot < 0) continue;
-                        w_ang = n_ang;
-                        nl.nbr[(size_t)slot * N + i] = j;
-                        if (nl.shift) nl.shift[(size_t)slot * N + i] = sh;
-                        if (track) slot_row[(size_t)slot * N + i] = (unsigned char)row;
-                    } else if (d2 < rc2_phys) {
-                        const int slot = n_ang + n_in < cap ? cap - 1 - n_in : -1;
-                        ++n_in;
-                        if (slot < 0) continue;
-                        nl.nbr[(size_t)slot * N + i] = j;
-                        if (nl.shift) nl.shift[(size_t)slot * N + i] = sh;
+                    // the angular and the inside entries share one store
+                    // path (slots from the bottom and from the top)
+                    const bool ang = d2 < rc2_ang;
+                    if (ang || d2 < rc2_phys) {
+                        int slot;
+                        if (ang) {
+                            slot = n_ang < cap_ang && n_ang + n_in < cap ? n_ang : -1;
+                            ++n_ang;
+                            if (slot >= 0) w_ang = n_ang;
+                        } else {
+                            slot = n_ang + n_in < cap ? cap - 1 - n_in : -1;
+                            ++n_in;
+                        }
+                        if (slot >= 0) {
+                            const size_t at = (size_t)slot * N + i;
+                            nl.nbr[at] = j;
+                            if (nl.shift) nl.shift[at] = sh;
+                            if (ang && track) slot_row[at] = (unsigned char)row;
+                        }
                     } else {
                         if (n_out < cap) shell[(size_t)n_out * N + i] = make_int2(j, sh);
                         ++n_out;
@@ -490,26 +497,35 @@ __global__ void __launch_bounds__(128) k_build(const float4* __restrict__ pos4,
         nl.cnt_ang[i] = w_ang;
         return;
     }
-    // the inside block sits reversed at [cap - n_in, cap): reverse it in
-    // place, then copy it down behind the prefix (ascending copy, target
-    // never above source), then append the shell
+    // the inside block sits reversed at [cap - n_in, cap).  Where it does not
+    // overlap its target behind the prefix it is copied there in reverse
+    // order; otherwise it is reversed in place, then copied down (ascending
+    // copy, target never above source).  Then the shell is appended.
     const int base = cap - n_in;
-    for (int k = 0; k < n_in / 2; ++k) {
-        const size_t x = (size_t)(base + k) * N + i, y = (size_t)(cap - 1 - k) * N + i;
-        const int t = nl.nbr[x];
-        nl.nbr[x] = nl.nbr[y];
-        nl.nbr[y] = t;
-        if (nl.shift) {
-            const int u = nl.shift[x];
-            nl.shift[x] = nl.shift[y];
-            nl.shift[y] = u;
-        }
-    }
-    if (base != n_ang) {
+    if (base >= n_ang + n_in) {
         for (int k = 0; k < n_in; ++k) {
-            const size_t from = (size_t)(base + k) * N + i, to = (size_t)(n_ang + k) * N + i;
+            const size_t from = (size_t)(cap - 1 - k) * N + i, to = (size_t)(n_ang + k) * N + i;
             nl.nbr[to] = nl.nbr[from];
             if (nl.shift) nl.shift[to] = nl.shift[from];
+        }
+    } else {
+        for (int k = 0; k < n_in / 2; ++k) {
+            const size_t x = (size_t)(base + k) * N + i, y = (size_t)(cap - 1 - k) * N + i;
+            const int t = nl.nbr[x];
+            nl.nbr[x] = nl.nbr[y];
+            nl.nbr[y] = t;
+            if (nl.shift) {
+                const int u = nl.shift[x];
+                nl.shift[x] = nl.shift[y];
+                nl.shift[y] = u;
+            }
+        }
+        if (base != n_ang) {
+            for (int k = 0; k < n_in; ++k) {
+                const size_t from = (size_t)(base + k) * N + i, to = (size_t)(n_ang + k) * N + i;
+                nl.nbr[to] = nl.nbr[from];
+                if (nl.shift) nl.shift[to] = nl.shift[from];
+            }
         }
     }
     for (int k = 0; k < n_out; ++k) {
@@ -778,10 +794,10 @@ cudaError_t launch_neighbors(const float* pos, const float4* pos4, const int* at
     k_scan_sums<<<1, 1024, 0, st>>>(w.scan_tmp, ntiles, w.scan_tmp + ntiles);
     k_scan_add<<<blocks(n, 256), 256, 0, st>>>(w.cell_start, n, w.scan_tmp);
     k_fill<<<blocks(N, 256), 256, 0, st>>>(w.cell_of, w.rank, w.cell_start, N, w.cell_atoms);
-    k_sort_cells<<<blocks(cmax, 128), 128, 0, st>>>(w.cell_start, cmax, w.cell_atoms);
+    k_sort_cells<<<blocks(cmax, 128), 128, 0, st>>>(w.cell_start, cmax, w.cell_atoms, pos4, w.cell_pos);
     const float rr = rc_list * rc_list, ra = rc_list_ang * rc_list_ang, rp = rc_phys * rc_phys;
     k_build<<<blocks(N, 128), 128, 0, st>>>(pos4, cfg, box, w.plan, w.cell_of, w.cell_start,
-                                            w.cell_atoms, N, rr, ra, rp, w.shell, w.row_start, w.slot_row, *nl);
+                                            w.cell_pos, N, rr, ra, rp, w.shell, w.row_start, w.slot_row, *nl);
     k_rev<<<blocks(N, 128), 128, 0, st>>>(N, cfg, w.plan, w.row_start, w.slot_row, *nl);
     return cudaGetLastError();
 }
