@@ -121,7 +121,7 @@ WsLayout ws_layout(const nep_model* m, int N, int B, int cap, int cap_ang) {
     const size_t ntiles = ((size_t)w.cmax + 1 + 2047) / 2048;
     w.scan_tmp = take(4 * (ntiles + 1));
     w.shell = take(8 * n * (size_t)cap);
-    w.row_start = take(32 * n);
+    w.row_start = take((size_t)nep::kRowStride * n);
     w.slot_row = take(n * (size_t)cap_ang);
     w.total = o;
     return w;

@@ -24,6 +24,7 @@ constexpr int kVariants = 3;              // angular kernel register budgets: 2,
 constexpr int kDefaultAngularVariant = 0; // 2 blocks per SM, S_nlm in tensor memory
 constexpr int kSizeBins = 32;             // tuning table: log2 of mean atoms per configuration
 constexpr int kBlockChoices[3] = {64, 128, 256};   // block sizes the tuner tries for radial / finish
+constexpr int kRowStride = 64;            // list build: bytes of per-atom stencil row starts
 
 // Stencil/cell plan of one configuration for the neighbour build.
 struct CellPlan {
