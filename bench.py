@@ -144,9 +144,9 @@ def algorithmic_flops(h, nbar_rad: float, nbar_ang: float) -> dict:
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the 460,800-atom
 # case of this workload (40^3 cells), divided by its atom count; traffic grows
 # in proportion to the atoms.  Valid only for the kernels as captured.
-TRAFFIC_PER_ATOM = {"radial": (241.651456e6 + 197.628416e6) / 460800,
-                    "angular": (288.541184e6 + 214.722560e6) / 460800,
-                    "finish": (387.748608e6 + 19.879936e6) / 460800}
+TRAFFIC_PER_ATOM = {"radial": (239.36e6 + 195.71e6) / 460800,
+                    "angular": (279.96e6 + 208.61e6) / 460800,
+                    "finish": (384.11e6 + 19.88e6) / 460800}
 
 
 def launches_per_step(rebuild: bool) -> int:
