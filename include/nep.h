@@ -167,8 +167,10 @@ typedef struct {
 size_t nep_workspace_bytes(const nep_model* m, int n_atoms, int n_cfg, int cap, int cap_ang);
 
 /* Build the cell-list Verlet list (counting sort into cells of edge
- * >= rc + skin, 27-cell or wider image stencil, then a reverse index).
- * Deterministic: list order is fixed by cell order and atom index. */
+ * >= (rc + skin) / 3, a 7 x 7 x 7-cell or wider image stencil walked row by
+ * row, each row cut to the cells that can meet the cutoff sphere, then a
+ * reverse index).  Deterministic: list order is fixed by cell order and atom
+ * index. */
 nep_status nep_neighbors(nep_model* m, const nep_system* sys, float skin, nep_nlist* nl,
                          void* work, size_t work_bytes, void* stream);
 
