@@ -61,6 +61,8 @@ def parse():
                     help="run the training leg alone and print its JSON object (for profiling it)")
     ap.add_argument("--ncell", type=int, default=50,
                     help="rock-salt cells per edge (50 = the 900k-atom workload; smaller for profiling)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="MD leg: keep the default launch choices instead of running the library's tuner")
     ap.add_argument("--md-mode", default="replicas", choices=["replicas", "slabs"],
                     help="N > 1: independent replicas of the system per GPU (weak scaling, the default), or one "
                          "system split into slabs with a point-to-point ghost halo (strong scaling)")
@@ -460,6 +462,10 @@ def run_md(args, nb, torch, dist, world, local, s, h, model, theta, vel0, masses
     _raise_if_overflow(nb, nl)
     e_atom, force, e_tot, vir = nb.energy_forces_virial(model, dsys, nl, ws)
     torch.cuda.synchronize()
+    # the library's tuner picks the launch choices for this size class (it
+    # times the pair kernels on scratch outputs; the forces stay as computed)
+    tuned = None if args.no_autotune else nb.autotune(model, dsys, nl, ws)
+    torch.cuda.synchronize()
 
     # neighbour statistics inside the cutoffs (for the flop count), from the list
     def neighbour_stats():
@@ -545,7 +551,7 @@ def run_md(args, nb, torch, dist, world, local, s, h, model, theta, vel0, masses
         ms_max = float(t.item())
     del g
     return (ms_max, K, t_kern, (nbar_rad, nbar_start, nbar_end), nbar_ang, clk, dsys, nl, ws, e_atom,
-            force, e_tot, vir, stream, vel)
+            force, e_tot, vir, stream, vel, tuned)
 
 
 def train_leg(nb, torch, I, local, dist=None, world: int = 1, rank: int = 0) -> dict:
@@ -1078,7 +1084,7 @@ def main():
     else:
         raise RuntimeError("neighbour list did not fit")
     (ms_max, K, t_kern, (nbar_rad, nbar_start, nbar_end), nbar_ang, clk, dsys, nl, ws, e_atom, force,
-     e_tot, vir, stream, vel) = res
+     e_tot, vir, stream, vel, tuned) = res
     value = world * N * K / (ms_max * 1e-3)
 
     # roofline of the dominant kernel (FP32 CUDA-core bound)
@@ -1165,7 +1171,9 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": WORKLOAD, "n_atoms": N, "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2 (neighbour list 0.40 GB, pair scratch 1.4 GB)",
-                           "graph": "K steps captured in one CUDA graph"},
+                           "graph": "K steps captured in one CUDA graph",
+                           "launch": ({"autotuned": True, "angular_variant": tuned[0], "radial_block": tuned[1],
+                                       "finish_block": tuned[2]} if tuned else {"autotuned": False})},
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_val, "unit": "atom-steps/s", "steps": KE,
                         "h2d_bytes_per_step": 24 * N, "d2h_bytes_per_step": 36 * N + 8 + 72},
