@@ -61,6 +61,8 @@ def parse():
                     help="run the training leg alone and print its JSON object (for profiling it)")
     ap.add_argument("--ncell", type=int, default=50,
                     help="rock-salt cells per edge (50 = the 900k-atom workload; smaller for profiling)")
+    ap.add_argument("--mixed-ncell", type=int, default=80,
+                    help="cells per edge of the mixed-precision leg's system (80: the 3.7M-atom workload)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="MD leg: keep the default launch choices instead of running the library's tuner")
     ap.add_argument("--md-mode", default="replicas", choices=["replicas", "slabs"],
@@ -656,18 +658,23 @@ def train_leg(nb, torch, I, local, dist=None, world: int = 1, rank: int = 0) -> 
                     "loss_at": {str(k): losses[k] for k in (0, 10, 30, 100, 299)}}}
 
 
-def mixed_leg(nb, torch, I) -> dict:
+def mixed_leg(nb, torch, I, ncell: int = 80) -> dict:
     """Secondary leg: E+F+V of the 3,686,400-atom rock-salt system (80^3
     cells, 20% cation vacancies) with the larger NEP (n_R=12, n_A=8, 4-body,
     D=52, MLP 52-64-1), plain FP32 against the FP16 and BF16 tensor-core
     network; errors of the mixed forms are measured against the FP32 form,
-    which itself matches FP64 to 1e-6 eV/atom and 1e-4 eV/A."""
-    s, h = I.workload_mixed3m7()
+    which itself matches FP64 to 1e-6 eV/atom and 1e-4 eV/A.  ncell < 80
+    runs the same structure and model on ncell^3 cells (a small case for
+    profiling)."""
+    if ncell == 80:
+        s, h = I.workload_mixed3m7()
+    else:
+        s, h = I.rocksalt(ncell, vacancy=0.2, tag=3), I.HYPER_LARGE
     th = I.init_params(h).astype(np.float32)
     dsys = nb.DeviceSystem.from_inputs(s)
     cap, cap_ang = 80, 40
     nl = nb.NeighborList(s.n_atoms, cap, cap_ang, shifts=False)
-    out = {"workload": "mixed3m7: 3,686,400 atoms, 80^3 rock-salt cells, NEP n_R=12 n_A=8 +4-body "
+    out = {"workload": f"mixed3m7: {s.n_atoms:,} atoms, {ncell}^3 rock-salt cells, NEP n_R=12 n_A=8 +4-body "
                        "(D=52), MLP 52-64-1, one E+F+V per step", "n_atoms": s.n_atoms}
     ref = None
     for prec, name in ((0, "fp32"), (1, "fp16"), (2, "bf16")):
@@ -1142,7 +1149,7 @@ def main():
     # raises is recorded under its key as {"error": ...}; the line is printed
     # whatever the legs do.
     train = None if args.no_train else guarded(train_leg, nb, torch, I, local, dist, world, rank)
-    mixed = None if args.no_mixed else guarded(mixed_leg, nb, torch, I)
+    mixed = None if args.no_mixed else guarded(mixed_leg, nb, torch, I, args.mixed_ncell)
     replicas = None if args.no_replicas else guarded(replicas_leg, nb, torch, I, dist=dist, world=world,
                                                      rank=rank)
     table2 = None if args.no_table2 else guarded(table2_leg, nb, torch, I)
