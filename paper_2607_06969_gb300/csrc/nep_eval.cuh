@@ -480,7 +480,7 @@ NEP_HD void angular_force(const EvalArgs& a, const float* sm, const SmemLayout& 
                 am2 = ffma2(s2, gb[n], am2);
                 bm2 = ffma2(s2, gpb[n], bm2);
             }
-            if (SPLIT) {
+            if constexpr (SPLIT) {
                 float Y0, hx0, hy0, hz0, Y1, hx1, hy1, hz1;
                 harm_m(m0, ht, Y0, hx0, hy0, hz0);
                 harm_m(m0 + 1, ht, Y1, hx1, hy1, hz1);
@@ -489,21 +489,21 @@ NEP_HD void angular_force(const EvalArgs& a, const float* sm, const SmemLayout& 
                 gx2 = ffma2(am2, make_float2(hx0, hx1), gx2);
                 gy2 = ffma2(am2, make_float2(hy0, hy1), gy2);
                 gz2 = ffma2(am2, make_float2(hz0, hz1), gz2);
-                continue;
-            }
+            } else {
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int m = m0 + u;
-                const float am = u ? am2.y : am2.x, bm = u ? bm2.y : bm2.x;
-                float Y, hx, hy, hz;
-                harm_m(m, ht, Y, hx, hy, hz);
-                rad = fmaf(fmaf(-(float)lm_l(m) * ir, am, bm), Y, rad);
-                Gx = fmaf(am, hx, Gx);
-                Gy = fmaf(am, hy, Gy);
-                Gz = fmaf(am, hz, Gz);
+                for (int u = 0; u < 2; ++u) {
+                    const int m = m0 + u;
+                    const float am = u ? am2.y : am2.x, bm = u ? bm2.y : bm2.x;
+                    float Y, hx, hy, hz;
+                    harm_m(m, ht, Y, hx, hy, hz);
+                    rad = fmaf(fmaf(-(float)lm_l(m) * ir, am, bm), Y, rad);
+                    Gx = fmaf(am, hx, Gx);
+                    Gy = fmaf(am, hy, Gy);
+                    Gz = fmaf(am, hz, Gz);
+                }
             }
         }
-        if (SPLIT) {
+        if constexpr (SPLIT) {
             rad = rad2.x + rad2.y;
             Gx = gx2.x + gx2.y;
             Gy = gy2.x + gy2.y;
