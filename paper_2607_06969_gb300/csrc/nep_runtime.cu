@@ -378,9 +378,10 @@ __device__ __forceinline__ int floor_div(int a, int b) {
 // The stencil is visited row by row: for each (ox, oy) the cells oz =
 // -half..half are consecutive cell ids (one range of the cell-ordered
 // positions, which carry the atom index) except where they wrap around the
-// box, which splits the row in two ranges with different z images.  The visit order is that of the cell triple loop.
-// For the reverse-slot search the kernel also records, per atom, where each
-// row's angular entries start (row_start) and, per angular slot, its row.
+// box, which splits the row in two ranges with different z images.  The
+// visit order is that of the cell triple loop.  For the reverse-slot search
+// the kernel also records, per atom, where each row's angular entries start
+// (row_start) and, per angular slot, its row.
 __global__ void __launch_bounds__(128) k_build(const float4* __restrict__ pos4,
                                                const int* __restrict__ cfg,
                                                const float* __restrict__ box,
