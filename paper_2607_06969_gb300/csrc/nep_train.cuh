@@ -535,8 +535,9 @@ NEP_HD int grad_chunks_of(int N) {
 }
 
 // Work items of a tile: each sums, over the staged rows of its species,
-// four parameters of one block that read four consecutive columns:
-//   W0  (species, h, d0..d0+3):    alpha_h q_d + beta_h dq_d
+// four parameters of one block that read four consecutive columns, or for
+// W0 a 4 x 4 block of them (per atom four 16-byte loads for 32 FMAs):
+//   W0  (species, h0..h0+3, d0..d0+3):  alpha_h q_d + beta_h dq_d
 //   b0  (species, h0..h0+3):       alpha_h
 //   w1  (species, h0..h0+3):       gamma_h
 //   b1  (species):                 dPhi/dE of the atom's configuration
@@ -546,7 +547,7 @@ template <class C>
 struct GradItems {
     using G = GradStage<C>;
     static constexpr int T = C::T;
-    static NEP_HD int nW0(int H) { return T * H * (G::Dp / 4); }
+    static NEP_HD int nW0(int H) { return T * (G::Hp(H) / 4) * (G::Dp / 4); }
     static NEP_HD int nB(int H) { return T * (G::Hp(H) / 4); }
     static constexpr int nCR = T * T * C::NR * (G::KRp / 4);
     static constexpr int nCA = T * (G::NBp / 4);
@@ -563,21 +564,40 @@ NEP_HD void grad_item(const float* stage, const int* toff, int H, int it, float*
     float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
     int sp, pbase, cnt;
     if (it < I::nW0(H)) {
+        // each parameter's chain is the same as with one h per item: the
+        // same operations over the same atoms in the same order
         constexpr int NB = G::Dp / 4;
-        sp = it / (H * NB);
-        const int rem = it % (H * NB), h = rem / NB, d0 = 4 * (rem % NB);
+        const int HB = G::Hp(H) / 4;
+        sp = it / (HB * NB);
+        const int rem = it % (HB * NB), h0 = 4 * (rem / NB), d0 = 4 * (rem % NB);
+        float acc4[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc4[r][c] = 0.0f;
         for (int a = toff[sp]; a < toff[sp + 1]; ++a) {
             const float* row = stage + a * W;
-            const float al = row[G::o_al() + h], be = row[G::o_be(H) + h];
-            const float4 q = *reinterpret_cast<const float4*>(row + G::o_q() + d0);
-            const float4 dq = *reinterpret_cast<const float4*>(row + G::o_dq() + d0);
-            s0 = fmaf(be, dq.x, fmaf(al, q.x, s0));
-            s1 = fmaf(be, dq.y, fmaf(al, q.y, s1));
-            s2 = fmaf(be, dq.z, fmaf(al, q.z, s2));
-            s3 = fmaf(be, dq.w, fmaf(al, q.w, s3));
+            const float4 al4 = *reinterpret_cast<const float4*>(row + G::o_al() + h0);
+            const float4 be4 = *reinterpret_cast<const float4*>(row + G::o_be(H) + h0);
+            const float4 q4 = *reinterpret_cast<const float4*>(row + G::o_q() + d0);
+            const float4 dq4 = *reinterpret_cast<const float4*>(row + G::o_dq() + d0);
+            const float al[4] = {al4.x, al4.y, al4.z, al4.w}, be[4] = {be4.x, be4.y, be4.z, be4.w};
+            const float q[4] = {q4.x, q4.y, q4.z, q4.w}, dq[4] = {dq4.x, dq4.y, dq4.z, dq4.w};
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc4[r][c] = fmaf(be[r], dq[c], fmaf(al[r], q[c], acc4[r][c]));
         }
-        pbase = sp * L.mlp_stride + h * D + d0;
-        cnt = D - d0;
+        // rows h >= H and columns d >= D are padding: their sums are dropped
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            if (h0 + r >= H) break;
+            const int pb = sp * L.mlp_stride + (h0 + r) * D + d0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (d0 + c < D) acc[pb + c] += acc4[r][c];
+        }
+        return;
     } else if ((it -= I::nW0(H)) < 2 * I::nB(H)) {
         const int which = it / I::nB(H), r = it % I::nB(H), HB = G::Hp(H) / 4;
         sp = r / HB;
