@@ -7,6 +7,8 @@ NEP n_R=8, n_A=6, K=8/8, l_max=4 + 4-body (D=38), MLP 38-30-1 with random
 weights; velocity Verlet, dt = 2 fs, 900 K Maxwell-Boltzmann start, cell-list
 rebuild every 10 steps with a 1 A skin.  One bench step = one MD step
 (kick, drift, [rebuild], energy+forces+virial, kick), all in libnep kernels.
+Before timing, the library's tuner (nep_autotune) picks the launch choices
+for the system's size class (--no-autotune keeps the defaults).
 
 value: atom-steps/s over all ranks (device-timed, inputs resident in HBM).
 e2e:   the same metric through the C ABI with the MD state in pinned host
