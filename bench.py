@@ -1119,7 +1119,10 @@ def main():
     # end to end through the C ABI from pinned host buffers: the MD state
     # (positions, velocities) lives on the host and continues from the end of
     # the timed run; every step copies it in, runs nep_md_step, and copies
-    # positions, velocities, forces, energy and virial back out
+    # positions, velocities, forces, energy and virial back out.  The copies
+    # run on two streams of their own, one per direction, row by row: row r
+    # of the state goes back to the device for the next step as soon as it
+    # has reached the host, so the two directions overlap.
     KE = max(1, min(args.e2e_steps, K))
     torch.cuda.synchronize()
     pos_h = dsys.pos.cpu().pin_memory()
@@ -1127,21 +1130,42 @@ def main():
     f_h = torch.empty(3, N, dtype=torch.float32).pin_memory()
     e_h = torch.empty(1, dtype=torch.float64).pin_memory()
     v_h = torch.empty(1, 9, dtype=torch.float64).pin_memory()
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    rows_d = [dsys.pos[r] for r in range(3)] + [vel[r] for r in range(3)]
+    rows_h = [pos_h[r] for r in range(3)] + [vel_h[r] for r in range(3)]
+    row_out = [torch.cuda.Event() for _ in rows_d]
+    step_done, ins_done, outs_done = torch.cuda.Event(), torch.cuda.Event(), torch.cuda.Event()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(stream):
-        e0.record(stream)
-        for k in range(KE):
-            dsys.pos.copy_(pos_h, non_blocking=True)
-            vel.copy_(vel_h, non_blocking=True)
-            nb.md_step(model, dsys, nl, vel, force, e_tot, vir, masses, DT, SKIN, k % REBUILD == 0, ws,
-                       stream=stream)
-            pos_h.copy_(dsys.pos, non_blocking=True)
-            vel_h.copy_(vel, non_blocking=True)
+    e0.record(stream)
+    for k in range(KE):
+        # state in: each row once it is back on the host (all of it at k = 0)
+        if k == 0:
+            s_in.wait_event(e0)
+        with torch.cuda.stream(s_in):
+            for r, (d_, h_) in enumerate(zip(rows_d, rows_h)):
+                if k > 0:
+                    s_in.wait_event(row_out[r])
+                d_.copy_(h_, non_blocking=True)
+        ins_done.record(s_in)
+        stream.wait_event(ins_done)
+        if k > 0:
+            stream.wait_event(outs_done)      # forces, energy and virial of step k - 1 are out
+        nb.md_step(model, dsys, nl, vel, force, e_tot, vir, masses, DT, SKIN, k % REBUILD == 0, ws,
+                   stream=stream)
+        step_done.record(stream)
+        # results out: state rows first, then forces, energy and virial
+        s_out.wait_event(step_done)
+        with torch.cuda.stream(s_out):
+            for r, (d_, h_) in enumerate(zip(rows_d, rows_h)):
+                h_.copy_(d_, non_blocking=True)
+                row_out[r].record(s_out)
             f_h.copy_(force, non_blocking=True)
             e_h.copy_(e_tot, non_blocking=True)
             v_h.copy_(vir, non_blocking=True)
-        e1.record(stream)
+        outs_done.record(s_out)
+    stream.wait_event(outs_done)
+    e1.record(stream)
     torch.cuda.synchronize()
     _raise_if_overflow(nb, nl, stream)
     e2e_ms = e0.elapsed_time(e1)
