@@ -9,8 +9,8 @@
 // and sum_j dE_k/dr_kj . dr_kj = p_k . dq_k with p = dE/dq and dq the
 // tangent of the descriptors along dr.  Kernels, one thread per atom:
 //   tangent : dq (radial via species-resolved sums of Q'_k (rhat . dr),
-//             angular via dS_nlm), stored with dS.
-//   mlp2    : network second-order terms: alpha, beta, gamma (network
+//             angular via dS_nlm), stored with dS; then, for the same atom,
+//             the network second-order terms: alpha, beta, gamma (network
 //             gradient coefficients) and rho = aE p + d(p . dq)/dq.
 //   xzP/xzR : per angular pair X_n = sum_m P_nm Y_m + sum_m R_nm dY_m . dr and
 //             Z_n = (rhat . dr) sum_m R_nm Y_m, where P = dPhi/dS, R = dPhi/d(dS).
@@ -30,9 +30,6 @@ namespace nep {
 // (their register budget: 65,536 / (128 x blocks))
 #ifndef NEP_MINB_TANGENT
 #define NEP_MINB_TANGENT 2
-#endif
-#ifndef NEP_MINB_MLP2
-#define NEP_MINB_MLP2 2
 #endif
 #ifndef NEP_MINB_XZP
 #define NEP_MINB_XZP 2
@@ -653,21 +650,18 @@ NEP_HD void grad_item(const float* stage, const int* toff, int H, int it, float*
 }
 
 #if defined(__CUDACC__)
+// the tangent pass, then the network's second-order terms of the same atom
+// (they need only that atom's q, dq and p)
 template <class C>
 __global__ void __launch_bounds__(kBlock, NEP_MINB_TANGENT) k_tangent(const TrainArgs t) {
     extern __shared__ float sm[];
     load_model<C>(sm, t.e.params, t.e.H, threadIdx.x, blockDim.x);
     __syncthreads();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < t.e.N) tangent_atom<C>(t, sm, i);
-}
-template <class C>
-__global__ void __launch_bounds__(kBlock, NEP_MINB_MLP2) k_mlp2(const TrainArgs t) {
-    extern __shared__ float sm[];
-    load_model<C>(sm, t.e.params, t.e.H, threadIdx.x, blockDim.x);
-    __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < t.e.N) mlp2_atom<C>(t, sm, i);
+    if (i < t.e.N) {
+        tangent_atom<C>(t, sm, i);
+        mlp2_atom<C>(t, sm, i);
+    }
 }
 template <class C>
 __global__ void __launch_bounds__(kBlock, NEP_MINB_XZP) k_xzp(const TrainArgs t) {
@@ -816,7 +810,6 @@ cudaError_t train_init_t(int H) {
     cudaError_t e;
     if ((e = mlp_tc_init_t<C>(H))) return e;
     if ((e = cudaFuncSetAttribute(k_tangent<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
-    if ((e = cudaFuncSetAttribute(k_mlp2<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
     return cudaFuncSetAttribute(k_grad_partial<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)grad_stage_bytes<C>(H));
 }
@@ -831,7 +824,6 @@ cudaError_t train_t(const TrainArgs& t, cudaStream_t st) {
     if (N > 0) {
         const int grid = (N + kBlock - 1) / kBlock;
         k_tangent<C><<<grid, kBlock, smem, st>>>(t);
-        k_mlp2<C><<<grid, kBlock, smem, st>>>(t);
         k_xzp<C><<<grid, kBlock, 0, st>>>(t);
         k_xzr<C><<<grid, kBlock, 0, st>>>(t);
         k_cbins<C><<<grid, kBlock, 0, st>>>(t);
