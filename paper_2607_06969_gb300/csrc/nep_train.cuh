@@ -16,6 +16,8 @@
 //             Z_n = (rhat . dr) sum_m R_nm Y_m, where P = dPhi/dS, R = dPhi/d(dS).
 //   cbins   : per-atom angular c-gradient sum_j Q_k X_n + Q'_k Z_n by species
 //             (X_n = the sum of its P and R planes).
+// These four run one after another in one kernel (k_tangent), each thread on
+// its own atom; the gradient reduction follows in its own kernels.
 //   grad    : per-chunk sums over atoms of every parameter's contributions
 //             (tiles of atoms staged in shared memory in species order,
 //             accumulators in shared memory), then an FP64 sum over chunks
@@ -30,15 +32,6 @@ namespace nep {
 // (their register budget: 65,536 / (128 x blocks))
 #ifndef NEP_MINB_TANGENT
 #define NEP_MINB_TANGENT 2
-#endif
-#ifndef NEP_MINB_XZP
-#define NEP_MINB_XZP 2
-#endif
-#ifndef NEP_MINB_XZR
-#define NEP_MINB_XZR 2
-#endif
-#ifndef NEP_MINB_CBINS
-#define NEP_MINB_CBINS 2
 #endif
 
 constexpr int kGradChunk = 32;   // atoms per staged tile
@@ -650,8 +643,11 @@ NEP_HD void grad_item(const float* stage, const int* toff, int H, int it, float*
 }
 
 #if defined(__CUDACC__)
-// the tangent pass, then the network's second-order terms of the same atom
-// (they need only that atom's q, dq and p)
+// The per-atom backward of one atom in one thread: the tangent pass, the
+// network's second-order terms, the X and Z coefficients of its angular
+// pairs (P and R passes) and its angular c-gradient bins.  Each step needs
+// only this atom's own results of the steps before it (and inputs), so the
+// passes run back to back with no launch between them.
 template <class C>
 __global__ void __launch_bounds__(kBlock, NEP_MINB_TANGENT) k_tangent(const TrainArgs t) {
     extern __shared__ float sm[];
@@ -661,22 +657,10 @@ __global__ void __launch_bounds__(kBlock, NEP_MINB_TANGENT) k_tangent(const Trai
     if (i < t.e.N) {
         tangent_atom<C>(t, sm, i);
         mlp2_atom<C>(t, sm, i);
+        xzp_atom<C>(t, nullptr, i);
+        xzr_atom<C>(t, nullptr, i);
+        cbins_atom<C>(t, nullptr, i);
     }
-}
-template <class C>
-__global__ void __launch_bounds__(kBlock, NEP_MINB_XZP) k_xzp(const TrainArgs t) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < t.e.N) xzp_atom<C>(t, nullptr, i);
-}
-template <class C>
-__global__ void __launch_bounds__(kBlock, NEP_MINB_XZR) k_xzr(const TrainArgs t) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < t.e.N) xzr_atom<C>(t, nullptr, i);
-}
-template <class C>
-__global__ void __launch_bounds__(kBlock, NEP_MINB_CBINS) k_cbins(const TrainArgs t) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < t.e.N) cbins_atom<C>(t, nullptr, i);
 }
 constexpr int kGradThreads = 256;
 constexpr int kStageUnroll = 8;
@@ -824,9 +808,6 @@ cudaError_t train_t(const TrainArgs& t, cudaStream_t st) {
     if (N > 0) {
         const int grid = (N + kBlock - 1) / kBlock;
         k_tangent<C><<<grid, kBlock, smem, st>>>(t);
-        k_xzp<C><<<grid, kBlock, 0, st>>>(t);
-        k_xzr<C><<<grid, kBlock, 0, st>>>(t);
-        k_cbins<C><<<grid, kBlock, 0, st>>>(t);
         k_grad_partial<C><<<grad_chunks_t<C>(N), kGradThreads, grad_stage_bytes<C>(t.e.H), st>>>(t);
     }
     const ParamLayout L = param_layout(C::T, C::NR, C::NA, C::KR, C::KA, C::H4, t.e.H);
