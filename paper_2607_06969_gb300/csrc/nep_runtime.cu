@@ -714,17 +714,19 @@ __global__ void __launch_bounds__(kRedThreads) k_loss_cfg(
             const double dv = vir[9 * b + c] - v_lbl[9 * b + c];
             sV += dv * dv;
         }
+        // FP64 division is slow on this GPU: the virial adjoint's nine
+        // entries share one factor
         double Lb;
         if (mode == 0) {
             Lb = wE * (dE / n) * (dE / n) + wF * sF / (3.0 * n) + wV * sV / (9.0 * n * n);
             aE[b] = (float)(2.0 * wE * dE / (n * n) / B);
-            for (int c = 0; c < 9; ++c)
-                mu[9 * b + c] = (float)(2.0 * wV * (vir[9 * b + c] - v_lbl[9 * b + c]) / (9.0 * n * n) / B);
+            const double fv = 2.0 * wV / (9.0 * n * n) / B;
+            for (int c = 0; c < 9; ++c) mu[9 * b + c] = (float)(fv * (vir[9 * b + c] - v_lbl[9 * b + c]));
         } else {
             Lb = wE * dE * dE / n + wF * sF / (3.0 * n) + wV * sV / (9.0 * n);
             aE[b] = (float)(2.0 * wE * dE / n / B);
-            for (int c = 0; c < 9; ++c)
-                mu[9 * b + c] = (float)(2.0 * wV * (vir[9 * b + c] - v_lbl[9 * b + c]) / (9.0 * n) / B);
+            const double fv = 2.0 * wV / (9.0 * n) / B;
+            for (int c = 0; c < 9; ++c) mu[9 * b + c] = (float)(fv * (vir[9 * b + c] - v_lbl[9 * b + c]));
         }
         if (nb > 0.0) acc += Lb;
     }
