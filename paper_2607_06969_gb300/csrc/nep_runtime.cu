@@ -702,10 +702,14 @@ __global__ void __launch_bounds__(kRedThreads) k_loss_cfg(
     const double* __restrict__ vir, const double* __restrict__ e_lbl,
     const double* __restrict__ v_lbl, float wE, float wF, float wV, int mode, float* aE, float* mu,
     double* loss) {
+    // FP64 division is slow on this GPU: each configuration divides once,
+    // by its atom count, and the rest are products
+    const double iB = 1.0 / (double)B;
     double acc = 0.0;
     for (int b = threadIdx.x; b < B; b += kRedThreads) {
         const double nb = (double)(atom_off[b + 1] - atom_off[b]);
         const double n = nb > 0.0 ? nb : 1.0;
+        const double in = 1.0 / n;
         double sF = 0.0;
         for (int k = chunk_start[b]; k < chunk_start[b + 1]; ++k) sF += partial[k];
         const double dE = e_tot[b] - e_lbl[b];
@@ -714,18 +718,18 @@ __global__ void __launch_bounds__(kRedThreads) k_loss_cfg(
             const double dv = vir[9 * b + c] - v_lbl[9 * b + c];
             sV += dv * dv;
         }
-        // FP64 division is slow on this GPU: the virial adjoint's nine
-        // entries share one factor
+        constexpr double third = 1.0 / 3.0, ninth = 1.0 / 9.0;
         double Lb;
         if (mode == 0) {
-            Lb = wE * (dE / n) * (dE / n) + wF * sF / (3.0 * n) + wV * sV / (9.0 * n * n);
-            aE[b] = (float)(2.0 * wE * dE / (n * n) / B);
-            const double fv = 2.0 * wV / (9.0 * n * n) / B;
+            const double e = dE * in;
+            Lb = wE * e * e + wF * sF * (third * in) + wV * sV * (ninth * in * in);
+            aE[b] = (float)(2.0 * wE * dE * (in * in) * iB);
+            const double fv = 2.0 * wV * (ninth * in * in) * iB;
             for (int c = 0; c < 9; ++c) mu[9 * b + c] = (float)(fv * (vir[9 * b + c] - v_lbl[9 * b + c]));
         } else {
-            Lb = wE * dE * dE / n + wF * sF / (3.0 * n) + wV * sV / (9.0 * n);
-            aE[b] = (float)(2.0 * wE * dE / n / B);
-            const double fv = 2.0 * wV / (9.0 * n) / B;
+            Lb = wE * dE * dE * in + wF * sF * (third * in) + wV * sV * (ninth * in);
+            aE[b] = (float)(2.0 * wE * dE * in * iB);
+            const double fv = 2.0 * wV * (ninth * in) * iB;
             for (int c = 0; c < 9; ++c) mu[9 * b + c] = (float)(fv * (vir[9 * b + c] - v_lbl[9 * b + c]));
         }
         if (nb > 0.0) acc += Lb;
@@ -737,7 +741,7 @@ __global__ void __launch_bounds__(kRedThreads) k_loss_cfg(
         if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0 && loss) *loss = red[0] / B;
+    if (threadIdx.x == 0 && loss) *loss = red[0] * iB;
 }
 
 // External adjoints (vector-Jacobian product) into the kernels' layout.
